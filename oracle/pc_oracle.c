@@ -30,9 +30,9 @@
  *   - both endpoints supply conditioning sets, the smaller index first, and the
  *     larger side is skipped once the edge is removed; at level 0 the two
  *     sides coincide (S is empty), so one test per pair (the Fig. 2 counts);
- *   - Z == tau counts as independent; |rho| >= 1 is dependent; a zero or
- *     negative conditional variance (H11 <= 0 or H22 <= 0) means V_i or V_j
- *     is determined by S, which is read as independent;
+ *   - Z == tau counts as independent; |rho| >= 1 is dependent; a zero
+ *     conditional variance (H11 or H22 <= 1e-10, rounding level of the unit
+ *     diagonal) means V_i or V_j is determined by S, read as independent;
  *   - M2^-1 is the ordinary inverse (Cholesky) when M2 is positive definite;
  *     Algorithm 7 is used otherwise (equal in exact arithmetic);
  *   - the stored SepSet is the first separating S in the serial order above.
@@ -45,6 +45,9 @@
 #include <string.h>
 
 #define ORC_MAX_LEVELS 256
+/* H11 or H22 at or below this is a zero conditional variance: V_i or V_j is a
+ * linear function of S (C has a unit diagonal, so this is an absolute scale). */
+#define ORC_VAR_ZERO 1e-10
 
 /* ------------------------------------------------------------------------ */
 /* Binomial coefficients (exact, saturating at UINT64_MAX).                  */
@@ -355,7 +358,7 @@ int orc_pinv_alg7(const double* G, int l, double* Gp)
 
 /* ------------------------------------------------------------------------ */
 /* Sec. 4.3: partial correlation of V_i, V_j given S from C (p x p).         */
-/* Returns 0 with *rho set, or 1 when H11 <= 0 or H22 <= 0 (degenerate).     */
+/* Returns 0 with *rho set, or 1 when H11 or H22 <= ORC_VAR_ZERO (degenerate). */
 /* *used_pinv is set to 1 when M2 was not positive definite.                 */
 /* ------------------------------------------------------------------------ */
 int orc_pcor(const double* C, int64_t p, int i, int j, const int* S, int l,
@@ -389,7 +392,8 @@ int orc_pcor(const double* C, int64_t p, int i, int j, const int* S, int l,
             }
         free(M1); free(M2); free(M2i);
     }
-    if (!(H[0] > 0.0) || !(H[3] > 0.0)) { *rho = NAN; return 1; }
+    /* a conditional variance at rounding level of the unit diagonal is zero */
+    if (!(H[0] > ORC_VAR_ZERO) || !(H[3] > ORC_VAR_ZERO)) { *rho = NAN; return 1; }
     *rho = H[1] / sqrt(H[0] * H[3]);
     return 0;
 }

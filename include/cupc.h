@@ -1,0 +1,231 @@
+/*
+ * cupc.h -- C ABI of the GB300 (sm_103a) PC-stable skeleton library.
+ *
+ * The library computes the first step of the order-independent PC algorithm
+ * (PC-stable) for multivariate-normal data: the correlation matrix of the
+ * data, then level by level the Gaussian conditional-independence tests on
+ * partial correlations, edge removal and SepSet recording (paper: Zarebavani,
+ * Jafarinejad, Hashemi, Salehkaleybar, "cuPC: CUDA-based Parallel PC Algorithm
+ * for Causal Structure Learning on GPU", IEEE TPDS 2019; Algorithm 1, Algorithm
+ * 2, Sec. 4.3). The problem statement follows Sec. 1 and Sec. 4.3: m samples of
+ * n variables, no missing values, significance level alpha; outputs are the
+ * skeleton G and the separating sets (SepSet). (In this header p = number of
+ * variables, n_samples = number of samples.)
+ *
+ * Conventions for every entry point:
+ *  - Return value: a cupc_status. No entry point aborts or exits. After an
+ *    error the context stays usable; cupc_last_error() gives a message.
+ *  - Pointers: plain host or device pointers as stated per argument; no
+ *    framework types. Inputs are borrowed for the duration of the call only.
+ *  - Device memory: the library allocates its own workspace and result storage
+ *    with stream-ordered allocation on the context's stream; results own their
+ *    storage until cupc_result_free().
+ *  - Streams: all GPU work runs on the stream given to cupc_create() (or
+ *    cupc_set_stream()). Calls that return results synchronise that stream.
+ *  - Threads: a context must not be used by two host threads at once.
+ */
+#ifndef CUPC_H
+#define CUPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CUPC_MAX_LEVEL 16        /* largest conditioning-set size the kernels support */
+#define CUPC_STATS_LEVELS 24     /* per-level statistics slots */
+#define CUPC_KCLASSES 8          /* kernel classes timed in cupc_stats.kernel_ms */
+
+/* kernel classes (index into cupc_stats.kernel_ms / kernel_count) */
+enum {
+    CUPC_K_UPLOAD = 0,       /* host-to-device copy of the input */
+    CUPC_K_STANDARDIZE = 1,  /* layout transpose + FP64 moments + standardised rows */
+    CUPC_K_CORRELATION = 2,  /* the correlation product C = Z Z^T / n */
+    CUPC_K_LEVEL0 = 3,       /* level-0 tests (+ their FP64 rechecks) */
+    CUPC_K_COMPACT = 4,      /* A_G -> A'_G compaction and work-item planning */
+    CUPC_K_CI = 5,           /* the CI-test kernel of levels >= 1 */
+    CUPC_K_RECHECK = 6,      /* FP64 rechecks of levels >= 1 */
+    CUPC_K_FINALIZE = 7      /* edge removal and SepSet records */
+};
+
+typedef enum {
+    CUPC_OK = 0,
+    CUPC_E_INVALID = -1,     /* bad argument (sizes, alpha, layout, null pointer) */
+    CUPC_E_NOMEM = -2,       /* device allocation failed */
+    CUPC_E_CUDA = -3,        /* a CUDA runtime call or kernel failed */
+    CUPC_E_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    CUPC_E_RANGE = -5,       /* a level or subset count beyond the supported range */
+    CUPC_E_NUMERIC = -6,     /* non-finite data (NaN/Inf, zero variance) */
+    CUPC_E_CANCELLED = -7,   /* cancelled between levels */
+    CUPC_E_STATE = -8        /* entry point not valid in the current state */
+} cupc_status;
+
+/* element types */
+enum { CUPC_F32 = 0, CUPC_F64 = 1 };
+
+/* data layouts for X (n_samples x p):
+ *   SAMPLE_MAJOR:   element (s, v) at X[s * ld + v], ld >= p (C order, rows are samples)
+ *   VARIABLE_MAJOR: element (s, v) at X[v * ld + s], ld >= n_samples (Fortran/R order) */
+enum { CUPC_LAYOUT_SAMPLE_MAJOR = 0, CUPC_LAYOUT_VARIABLE_MAJOR = 1 };
+
+/* arithmetic of the CI tests */
+enum {
+    CUPC_MODE_PLAIN_FP64 = 0,    /* FP64 correlation, FP64 CI tests for every test */
+    CUPC_MODE_FP32_RECHECK = 1   /* FP32 bulk tests; tests within a margin of the
+                                    threshold are recomputed in FP64 on the GPU */
+};
+
+typedef struct {
+    int mode;                /* CUPC_MODE_* (default CUPC_MODE_FP32_RECHECK) */
+    int canonical_sepset;    /* 1: store the first separating set in serial order
+                                (smaller endpoint's side first, lexicographic within
+                                a side); 0: any separating set found first (default 1) */
+    int learned_order;       /* 1: enumerate subsets in the order given by the
+                                candidate-scoring network loaded with
+                                cupc_mlp_set_weights() (levels >= 2); default 0 */
+    int max_level;           /* last level to run; -1 = until no edge has enough
+                                neighbours (Algorithm 1 termination); default -1 */
+    double recheck_margin;   /* FP32 mode: absolute band on |rho| around tanh(tau)
+                                that is recomputed in FP64; <= 0 selects the
+                                built-in default */
+    int threads_per_block;   /* CI kernel block size (0 = tuned default) */
+    int chunk;               /* subsets per work item in the CI kernel (0 = default) */
+    int reserved[6];
+} cupc_options;
+
+typedef struct {
+    int levels;                                  /* levels run, level 0 included */
+    int64_t tests[CUPC_STATS_LEVELS];            /* CI tests executed on the GPU */
+    int64_t serial_tests[CUPC_STATS_LEVELS];     /* tests the serial algorithm performs
+                                                    (canonical lexicographic runs only,
+                                                    else -1) */
+    int64_t removed[CUPC_STATS_LEVELS];          /* edges removed at each level */
+    int64_t rechecks[CUPC_STATS_LEVELS];         /* FP64 rechecks (FP32 mode) */
+    int64_t edges_start[CUPC_STATS_LEVELS];      /* undirected edges at level start */
+    int32_t max_degree[CUPC_STATS_LEVELS];       /* max degree at level start */
+    float level_ms[CUPC_STATS_LEVELS];           /* device time of each level */
+    float prep_ms;                               /* upload + standardise + correlation */
+    float total_ms;                              /* device time of the whole call */
+    int64_t edges_final;                         /* undirected edges in the skeleton */
+    int64_t kernel_launches;                     /* kernels launched by the call */
+    int64_t h2d_bytes, d2h_bytes;                /* bytes copied by the call */
+    float kernel_ms[CUPC_KCLASSES];              /* device time per kernel class (CUDA events) */
+    int32_t kernel_count[CUPC_KCLASSES];         /* launches per kernel class */
+    int64_t ci_block_entries[CUPC_STATS_LEVELS]; /* sum over rows of (n'_i + 1)^2: the C
+                                                    sub-block entries a level's tests read */
+} cupc_stats;
+
+typedef struct cupc_ctx cupc_ctx;
+typedef struct cupc_result cupc_result;
+
+/* Fills *o with the defaults documented above. */
+void cupc_options_default(cupc_options* o);
+
+/* Creates a context on CUDA device `device`. `stream` is a cudaStream_t (may be
+ * NULL for the legacy default stream; a framework's stream handle may be passed).
+ * The device must be sm_103 (GB300); otherwise CUPC_E_CUDA. */
+cupc_status cupc_create(cupc_ctx** out, int device, void* stream);
+
+/* Changes the stream subsequent calls use. */
+cupc_status cupc_set_stream(cupc_ctx* ctx, void* stream);
+
+/* Frees the context and its workspace. Results stay valid. */
+void cupc_destroy(cupc_ctx* ctx);
+
+/* Message for the last error on this context ("" if none). Never NULL. */
+const char* cupc_last_error(const cupc_ctx* ctx);
+
+/* Algorithm 1 / Algorithm 2 on data: standardise X in FP64, form the
+ * correlation matrix C (Sec. 4.3), run level 0 (Algorithm 3) and every level
+ * l >= 1 (compaction of A_G, CI tests of Sec. 4.3, edge removal, SepSet) until
+ * the termination rule or opts->max_level.
+ *   X          host (on_device = 0) or device (on_device = 1) pointer to the
+ *              n_samples x p data, element type `dtype` (CUPC_F32/CUPC_F64),
+ *              laid out per `layout` with leading dimension `ld`.
+ *   n_samples  number of samples m; must exceed max_level + 3 (Eq. threshold).
+ *   p          number of variables, 2 <= p <= 2^20.
+ *   alpha      significance level, 0 < alpha < 1.
+ *   opts       NULL for defaults.
+ *   out        receives a new result (free with cupc_result_free).
+ * Errors: CUPC_E_INVALID (arguments), CUPC_E_NUMERIC (a variable with zero
+ * variance or non-finite data), CUPC_E_RANGE (a level above CUPC_MAX_LEVEL would
+ * be needed or a subset count exceeds 2^63), CUPC_E_NOMEM, CUPC_E_CUDA,
+ * CUPC_E_TIMEOUT. On error *out is NULL. */
+cupc_status cupc_skeleton(cupc_ctx* ctx, const void* X, int dtype, int layout, int on_device,
+                          int64_t n_samples, int64_t p, int64_t ld, double alpha,
+                          const cupc_options* opts, cupc_result** out);
+
+/* Same as cupc_skeleton but from a p x p correlation matrix C (row-major with
+ * leading dimension ld, host or device, CUPC_F32 or CUPC_F64) -- the
+ * "sufficient statistics" form of the pcalg interface the paper mirrors
+ * (Sec. 5.1). The diagonal is taken as exactly 1 and only the upper triangle is
+ * read (the matrix is symmetrised from it). The matrix is widened to FP64 on
+ * the device; in FP32 mode the bulk tests read its FP32 rounding and the
+ * rechecks read the FP64 copy. */
+cupc_status cupc_skeleton_corr(cupc_ctx* ctx, const void* C, int dtype, int on_device, int64_t p,
+                               int64_t ld, int64_t n_samples, double alpha,
+                               const cupc_options* opts, cupc_result** out);
+
+/* Number of variables of a result. */
+cupc_status cupc_result_p(const cupc_result* res, int64_t* p);
+
+/* Copies the skeleton as a p x p uint8 matrix (1 = edge) into the host buffer
+ * `out` (caller-owned, p*p bytes). Synchronises the context stream. */
+cupc_status cupc_result_adjacency(const cupc_result* res, uint8_t* out);
+
+/* Copies, into the host buffer `out` (p*p int16), the level at which each pair
+ * was removed, or -1 where the edge is present (the diagonal is -1). */
+cupc_status cupc_result_sep_levels(const cupc_result* res, int16_t* out);
+
+/* SepSet of the pair (i, j): writes the members (increasing) to out[0..*len)
+ * (caller-owned, at least CUPC_MAX_LEVEL entries) and the size to *len;
+ * *len = -1 when the edge is present. Level-0 removals have *len = 0. */
+cupc_status cupc_result_sepset(const cupc_result* res, int64_t i, int64_t j, int32_t* out, int* len);
+
+/* All SepSet records of removals at levels >= 1, as consecutive int32 groups
+ * (i, j, l, S[0..l)) with i < j, sorted by (i, j). With out == NULL only
+ * *n_ints is set; otherwise at most `cap` ints are written. */
+cupc_status cupc_result_sepset_records(const cupc_result* res, int32_t* out, int64_t cap,
+                                       int64_t* n_ints);
+
+/* Per-level statistics of the call that produced `res`. */
+cupc_status cupc_result_stats(const cupc_result* res, cupc_stats* out);
+
+/* Frees a result (NULL is ignored). */
+void cupc_result_free(cupc_result* res);
+
+/* ---------------------------------------------------------------------------
+ * Building blocks exposed for verification (same kernels as the skeleton path).
+ * ------------------------------------------------------------------------- */
+
+/* Correlation matrix (Sec. 4.3) of X into the device buffer C_out (p x p,
+ * row-major, ld = p): precision CUPC_F64 uses the FP64 standardisation and the
+ * FP64 product; CUPC_F32 the FP64 standardisation and the split-precision
+ * tensor-core product with FP32 accumulation. Arguments for X as in
+ * cupc_skeleton. */
+cupc_status cupc_correlation(cupc_ctx* ctx, const void* X, int dtype, int layout, int on_device,
+                             int64_t n_samples, int64_t p, int64_t ld, int precision, void* C_out);
+
+/* Partial correlations rho(V_i, V_j | S) (Sec. 4.3, Eqs. PartialCorMat and
+ * RhoCal) for nq queries from the device correlation matrix C (p x p, ld = p,
+ * element type `dtype`), evaluated with the CI kernels' device arithmetic in
+ * that precision. `queries` is a device int32 array of nq rows (i, j, S[0..l)).
+ * rho_out is a device double array of nq entries (NaN when the conditional
+ * variance is not positive). */
+cupc_status cupc_pcor_batch(cupc_ctx* ctx, const void* C, int dtype, int64_t p,
+                            const int32_t* queries, int64_t nq, int l, double* rho_out);
+
+/* Eq. (threshold) as the library evaluates it, on the host:
+ * tau = Phi^-1(1 - alpha/2) / sqrt(n_samples - l - 3) and r = tanh(tau); a CI
+ * test is independent iff |Z(rho)| <= tau, i.e. |rho| <= r (Eq.
+ * FisherZTransform with atanh monotone). Either output pointer may be NULL.
+ * CUPC_E_INVALID when alpha is outside (0, 1) or n_samples - l - 3 <= 0.
+ * Needs no GPU. */
+cupc_status cupc_fisher_threshold(double alpha, int64_t n_samples, int l, double* tau, double* r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUPC_H */

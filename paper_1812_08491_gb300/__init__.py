@@ -1,0 +1,331 @@
+"""GB300 (sm_103a) PC-stable skeleton library -- Python binding.
+
+A thin ctypes layer over the C ABI declared in ``include/cupc.h``: it only
+marshals arguments (pointers, sizes, options) and copies results out. Every
+step of the skeleton runs in the library's CUDA kernels; there is no Python or
+CPU fallback. If the shared library has not been built, every call raises.
+
+PyTorch is used only to hand over device memory and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["CupcError", "Context", "Result", "load", "lib_path", "build_library", "MODE_PLAIN_FP64",
+           "MODE_FP32_RECHECK", "F32", "F64", "SAMPLE_MAJOR", "VARIABLE_MAJOR", "MAX_LEVEL",
+           "fisher_threshold", "exported_symbols"]
+
+F32, F64 = 0, 1
+SAMPLE_MAJOR, VARIABLE_MAJOR = 0, 1
+MODE_PLAIN_FP64, MODE_FP32_RECHECK = 0, 1
+MAX_LEVEL = 16
+STATS_LEVELS = 24
+KERNEL_CLASSES = ("upload", "standardize", "correlation", "level0", "compact", "ci", "recheck", "finalize")
+
+_STATUS = {0: "CUPC_OK", -1: "CUPC_E_INVALID", -2: "CUPC_E_NOMEM", -3: "CUPC_E_CUDA", -4: "CUPC_E_TIMEOUT",
+           -5: "CUPC_E_RANGE", -6: "CUPC_E_NUMERIC", -7: "CUPC_E_CANCELLED", -8: "CUPC_E_STATE"}
+
+# Every entry point declared in include/cupc.h (kept in sync by a CPU test).
+_SIGNATURES = {
+    "cupc_options_default": (None, ["opts_p"]),
+    "cupc_create": ("status", ["pp", "int", "vp"]),
+    "cupc_set_stream": ("status", ["vp", "vp"]),
+    "cupc_destroy": (None, ["vp"]),
+    "cupc_last_error": ("str", ["vp"]),
+    "cupc_skeleton": ("status", ["vp", "vp", "int", "int", "int", "i64", "i64", "i64", "dbl", "opts_p", "pp"]),
+    "cupc_skeleton_corr": ("status", ["vp", "vp", "int", "int", "i64", "i64", "i64", "dbl", "opts_p", "pp"]),
+    "cupc_result_p": ("status", ["vp", "vp"]),
+    "cupc_result_adjacency": ("status", ["vp", "vp"]),
+    "cupc_result_sep_levels": ("status", ["vp", "vp"]),
+    "cupc_result_sepset": ("status", ["vp", "i64", "i64", "vp", "vp"]),
+    "cupc_result_sepset_records": ("status", ["vp", "vp", "i64", "vp"]),
+    "cupc_result_stats": ("status", ["vp", "vp"]),
+    "cupc_result_free": (None, ["vp"]),
+    "cupc_correlation": ("status", ["vp", "vp", "int", "int", "int", "i64", "i64", "i64", "int", "vp"]),
+    "cupc_pcor_batch": ("status", ["vp", "vp", "int", "i64", "vp", "i64", "int", "vp"]),
+    "cupc_fisher_threshold": ("status", ["dbl", "i64", "int", "vp", "vp"]),
+}
+
+
+class CupcError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {_STATUS.get(status, status)}" + (f" ({message})" if message else ""))
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("canonical_sepset", ctypes.c_int), ("learned_order", ctypes.c_int),
+                ("max_level", ctypes.c_int), ("recheck_margin", ctypes.c_double),
+                ("threads_per_block", ctypes.c_int), ("chunk", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+
+
+class Stats(ctypes.Structure):
+    L = STATS_LEVELS
+    _fields_ = [("levels", ctypes.c_int), ("tests", ctypes.c_int64 * L), ("serial_tests", ctypes.c_int64 * L),
+                ("removed", ctypes.c_int64 * L), ("rechecks", ctypes.c_int64 * L),
+                ("edges_start", ctypes.c_int64 * L), ("max_degree", ctypes.c_int32 * L),
+                ("level_ms", ctypes.c_float * L), ("prep_ms", ctypes.c_float), ("total_ms", ctypes.c_float),
+                ("edges_final", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
+                ("kernel_ms", ctypes.c_float * 8), ("kernel_count", ctypes.c_int32 * 8),
+                ("ci_block_entries", ctypes.c_int64 * L)]
+
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.lib_path()
+
+
+def build_library(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def load():
+    """Loads the shared library; raises if it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built ({path}); call paper_1812_08491_gb300.build_library()")
+    L = ctypes.CDLL(path)
+    types = {"status": ctypes.c_int, "int": ctypes.c_int, "i64": ctypes.c_int64, "dbl": ctypes.c_double,
+             "vp": ctypes.c_void_p, "pp": ctypes.POINTER(ctypes.c_void_p), "str": ctypes.c_char_p,
+             "opts_p": ctypes.POINTER(Options), None: None}
+    for name, (rt, args) in _SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = types[rt]
+        fn.argtypes = [types[a] for a in args]
+    _LIB = L
+    return L
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+def fisher_threshold(alpha: float, n_samples: int, l: int):
+    """(tau, tanh(tau)) of Eq. (threshold) as the library computes it."""
+    L = load()
+    tau, r = ctypes.c_double(), ctypes.c_double()
+    st = L.cupc_fisher_threshold(alpha, n_samples, l, ctypes.byref(tau), ctypes.byref(r))
+    if st != 0:
+        raise CupcError(st, "cupc_fisher_threshold")
+    return tau.value, r.value
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _describe(X):
+    """(pointer, dtype code, layout, on_device, n, p, ld, keepalive) for an n x p array/tensor."""
+    if isinstance(X, np.ndarray):
+        if X.dtype not in (np.float32, np.float64) or X.ndim != 2:
+            raise ValueError("X must be a 2-D float32/float64 array")
+        es = X.itemsize
+        n, p = X.shape
+        if X.strides[1] == es and X.strides[0] % es == 0:
+            layout, ld = SAMPLE_MAJOR, X.strides[0] // es
+        elif X.strides[0] == es and X.strides[1] % es == 0:
+            layout, ld = VARIABLE_MAJOR, X.strides[1] // es
+        else:
+            X = np.ascontiguousarray(X)
+            layout, ld = SAMPLE_MAJOR, p
+        return X.ctypes.data, (F64 if X.dtype == np.float64 else F32), layout, 0, n, p, ld, X
+    torch = _torch()
+    if isinstance(X, torch.Tensor):
+        if X.dtype not in (torch.float32, torch.float64) or X.dim() != 2:
+            raise ValueError("X must be a 2-D float32/float64 tensor")
+        n, p = X.shape
+        s0, s1 = X.stride()
+        if s1 == 1:
+            layout, ld = SAMPLE_MAJOR, s0
+        elif s0 == 1:
+            layout, ld = VARIABLE_MAJOR, s1
+        else:
+            X = X.contiguous()
+            layout, ld = SAMPLE_MAJOR, p
+        return (X.data_ptr(), F64 if X.dtype == torch.float64 else F32, layout, 1 if X.is_cuda else 0,
+                n, p, ld, X)
+    raise TypeError("X must be a numpy array or a torch tensor")
+
+
+class Result:
+    """Skeleton and SepSets of one call; owns library memory until free()."""
+
+    def __init__(self, ctx: "Context", handle: int):
+        self._ctx = ctx
+        self._h = ctypes.c_void_p(handle)
+        p = ctypes.c_int64()
+        self._check(load().cupc_result_p(self._h, ctypes.byref(p)), "cupc_result_p")
+        self.p = p.value
+
+    def _check(self, st, where):
+        if st != 0:
+            raise CupcError(st, where, self._ctx.last_error())
+
+    def adjacency(self) -> np.ndarray:
+        out = np.empty((self.p, self.p), dtype=np.uint8)
+        self._check(load().cupc_result_adjacency(self._h, out.ctypes.data), "cupc_result_adjacency")
+        return out
+
+    def sep_levels(self) -> np.ndarray:
+        out = np.empty((self.p, self.p), dtype=np.int16)
+        self._check(load().cupc_result_sep_levels(self._h, out.ctypes.data), "cupc_result_sep_levels")
+        return out
+
+    def sepset(self, i: int, j: int):
+        """Tuple S of a removed pair, () for level 0, None when the edge is present."""
+        buf = (ctypes.c_int32 * MAX_LEVEL)()
+        ln = ctypes.c_int()
+        self._check(load().cupc_result_sepset(self._h, i, j, buf, ctypes.byref(ln)), "cupc_result_sepset")
+        return None if ln.value < 0 else tuple(buf[k] for k in range(ln.value))
+
+    def records_raw(self) -> np.ndarray:
+        n = ctypes.c_int64()
+        L = load()
+        self._check(L.cupc_result_sepset_records(self._h, None, 0, ctypes.byref(n)), "records")
+        out = np.empty(max(n.value, 1), dtype=np.int32)
+        self._check(L.cupc_result_sepset_records(self._h, out.ctypes.data, n.value, ctypes.byref(n)), "records")
+        return out[:n.value]
+
+    def sepsets(self) -> dict:
+        """{(i, j): (level, S)} for removals at level >= 1 (i < j)."""
+        raw = self.records_raw()
+        out, k = {}, 0
+        while k < raw.size:
+            i, j, l = int(raw[k]), int(raw[k + 1]), int(raw[k + 2])
+            out[(i, j)] = (l, tuple(int(v) for v in raw[k + 3:k + 3 + l]))
+            k += 3 + l
+        return out
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(load().cupc_result_stats(self._h, ctypes.byref(s)), "cupc_result_stats")
+        L = s.levels
+        return {"levels": L, "tests": list(s.tests[:L]), "serial_tests": list(s.serial_tests[:L]),
+                "removed": list(s.removed[:L]), "rechecks": list(s.rechecks[:L]),
+                "edges_start": list(s.edges_start[:L]), "max_degree": list(s.max_degree[:L]),
+                "level_ms": list(s.level_ms[:L]), "prep_ms": s.prep_ms, "total_ms": s.total_ms,
+                "edges_final": s.edges_final, "kernel_launches": s.kernel_launches,
+                "h2d_bytes": s.h2d_bytes, "d2h_bytes": s.d2h_bytes,
+                "kernel_ms": dict(zip(KERNEL_CLASSES, list(s.kernel_ms))),
+                "kernel_count": dict(zip(KERNEL_CLASSES, list(s.kernel_count))),
+                "ci_block_entries": list(s.ci_block_entries[:L])}
+
+    def free(self):
+        if self._h:
+            load().cupc_result_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """A library context bound to one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        L = load()
+        if stream is None:
+            torch = _torch()
+            stream = torch.cuda.current_stream(device).cuda_stream
+        h = ctypes.c_void_p()
+        st = L.cupc_create(ctypes.byref(h), device, ctypes.c_void_p(stream))
+        if st != 0:
+            raise CupcError(st, "cupc_create", "device must be an sm_103 GPU")
+        self._h = h
+        self.device = device
+
+    def last_error(self) -> str:
+        if not self._h:
+            return ""
+        return (load().cupc_last_error(self._h) or b"").decode()
+
+    def _check(self, st, where):
+        if st != 0:
+            raise CupcError(st, where, self.last_error())
+
+    @staticmethod
+    def options(mode=MODE_FP32_RECHECK, canonical=True, max_level=-1, recheck_margin=0.0,
+                threads_per_block=0, chunk=0, learned_order=False) -> Options:
+        o = Options()
+        load().cupc_options_default(ctypes.byref(o))
+        o.mode = mode
+        o.canonical_sepset = 1 if canonical else 0
+        o.max_level = max_level
+        o.recheck_margin = recheck_margin
+        o.threads_per_block = threads_per_block
+        o.chunk = chunk
+        o.learned_order = 1 if learned_order else 0
+        return o
+
+    def skeleton(self, X, alpha: float, opts: Options | None = None, **kw) -> Result:
+        """Algorithm 1 on data X (n x p numpy array or torch tensor, host or device)."""
+        ptr, dt, layout, on_dev, n, p, ld, keep = _describe(X)
+        o = opts if opts is not None else self.options(**kw)
+        out = ctypes.c_void_p()
+        st = load().cupc_skeleton(self._h, ctypes.c_void_p(ptr), dt, layout, on_dev, n, p, ld, alpha,
+                                  ctypes.byref(o), ctypes.byref(out))
+        self._check(st, "cupc_skeleton")
+        del keep
+        return Result(self, out.value)
+
+    def skeleton_corr(self, C, n_samples: int, alpha: float, opts: Options | None = None, **kw) -> Result:
+        """Algorithm 1 from a p x p correlation matrix (row-major, host or device)."""
+        ptr, dt, layout, on_dev, p0, p1, ld, keep = _describe(C)
+        if layout != SAMPLE_MAJOR or p0 != p1:
+            raise ValueError("C must be a square row-major matrix")
+        o = opts if opts is not None else self.options(**kw)
+        out = ctypes.c_void_p()
+        st = load().cupc_skeleton_corr(self._h, ctypes.c_void_p(ptr), dt, on_dev, p0, ld, n_samples, alpha,
+                                       ctypes.byref(o), ctypes.byref(out))
+        self._check(st, "cupc_skeleton_corr")
+        del keep
+        return Result(self, out.value)
+
+    def correlation(self, X, precision: int = F64):
+        """Correlation matrix of X as a CUDA tensor (float64 or float32)."""
+        torch = _torch()
+        ptr, dt, layout, on_dev, n, p, ld, keep = _describe(X)
+        C = torch.empty((p, p), dtype=torch.float64 if precision == F64 else torch.float32,
+                        device=f"cuda:{self.device}")
+        st = load().cupc_correlation(self._h, ctypes.c_void_p(ptr), dt, layout, on_dev, n, p, ld, precision,
+                                     ctypes.c_void_p(C.data_ptr()))
+        self._check(st, "cupc_correlation")
+        del keep
+        return C
+
+    def pcor_batch(self, C, queries, l: int):
+        """rho(i, j | S) for rows (i, j, S...) of an int32 CUDA tensor, on CUDA matrix C."""
+        torch = _torch()
+        q = queries.to(device=C.device, dtype=torch.int32).contiguous()
+        rho = torch.empty(q.shape[0], dtype=torch.float64, device=C.device)
+        st = load().cupc_pcor_batch(self._h, ctypes.c_void_p(C.data_ptr()),
+                                    F32 if C.dtype == torch.float32 else F64, C.shape[0],
+                                    ctypes.c_void_p(q.data_ptr()), q.shape[0], l, ctypes.c_void_p(rho.data_ptr()))
+        self._check(st, "cupc_pcor_batch")
+        return rho
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().cupc_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,953 @@
+// api.cu -- C ABI of the skeleton library: context, workspace, the level loop
+// of Algorithm 2 (level 0, then per level: compact A_G into A'_G, CI tests,
+// removal and SepSet records), results and their accessors.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace cupc;
+
+namespace {
+
+struct Buf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+constexpr double kBand0 = 2e-5;        // level 0 FP32 band on |C_ij|
+constexpr double kBandAbs = 1e-4;      // levels >= 1 FP32 band on |rho|
+constexpr double kBandRel = 1e-5;      // widening per 1/(pivot^2 * min conditional variance)
+constexpr double kPivFloor = 1e-3;     // FP32: smaller pivot^2 goes to FP64
+constexpr double kRankTol64 = 1e-12;   // FP64: pivot^2 at or below -> dependent member
+constexpr double kRankTol32 = 1e-6;
+
+}  // namespace
+
+struct cupc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaMemPool_t pool = nullptr;
+    std::string err;
+    int refs = 1;
+    int num_sms = 0;
+    Buf xin, xt, mu, isd, z64, z32, c64, c32, cin;
+    Buf deg, row_off, item_off, item_row, cols, srow, partner, best, queue, binom, meta, backup[2];
+    Meta* hmeta = nullptr;
+    int binom_mstride = 0;
+    unsigned long long launches = 0;
+    unsigned long long h2d = 0, d2h = 0;
+    std::vector<cudaEvent_t> ev;
+    // kernel-class timing: event pairs recorded around the timed launches
+    std::vector<cudaEvent_t> tev;
+    std::vector<int> tcls;
+    int tused = 0;
+};
+
+struct cupc_result {
+    cupc_ctx* ctx = nullptr;
+    int64_t p = 0;
+    int W = 0;
+    unsigned* bits = nullptr;
+    unsigned* bits0 = nullptr;
+    int* rec = nullptr;
+    int64_t rec_ints = 0;
+    size_t rec_cap = 0;
+    cupc_stats stats{};
+    mutable bool host_ready = false;
+    mutable std::vector<int32_t> hrec;                              // sorted records
+    mutable std::vector<std::pair<uint64_t, int64_t>> index;        // (i*p+j) -> offset
+};
+
+namespace {
+
+void ctx_release(cupc_ctx* c);
+
+cupc_status fail(cupc_ctx* c, cupc_status s, const std::string& what, cudaError_t e = cudaSuccess)
+{
+    if (c) {
+        c->err = what;
+        if (e != cudaSuccess) {
+            c->err += ": ";
+            c->err += cudaGetErrorString(e);
+            cudaGetLastError();
+        }
+    }
+    return s;
+}
+
+#define CU(call)                                                                 \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) return fail(ctx, CUPC_E_CUDA, #call, e_);         \
+    } while (0)
+
+#define LAUNCH(call)                                                             \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        ctx->launches++;                                                         \
+        if (e_ != cudaSuccess) return fail(ctx, CUPC_E_CUDA, #call, e_);         \
+    } while (0)
+
+cupc_status dalloc(cupc_ctx* ctx, void** p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(ctx, CUPC_E_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes", e);
+    }
+    return CUPC_OK;
+}
+
+cupc_status ensure(cupc_ctx* ctx, Buf& b, size_t bytes, bool keep = false)
+{
+    if (b.p && b.cap >= bytes) return CUPC_OK;
+    size_t cap = std::max(bytes, b.cap + b.cap / 2);
+    cap = (cap + 255) & ~size_t(255);
+    void* np = nullptr;
+    cupc_status s = dalloc(ctx, &np, cap);
+    if (s != CUPC_OK) return s;
+    if (keep && b.p && b.cap) CU(cudaMemcpyAsync(np, b.p, b.cap, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (b.p) cudaFreeAsync(b.p, ctx->stream);
+    b.p = np;
+    b.cap = cap;
+    return CUPC_OK;
+}
+
+void free_buf(cupc_ctx* ctx, Buf& b)
+{
+    if (b.p) cudaFreeAsync(b.p, ctx->stream);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+// --- threshold (Eq. threshold) -------------------------------------------------
+// Lower-tail standard normal quantile: Newton steps on Phi(x) - q with
+// Phi(x) = erfc(-x/sqrt 2)/2 and Phi'(x) = exp(-x^2/2)/sqrt(2 pi), started
+// from the tail estimate x = -sqrt(-2 ln q) and kept inside a bisection bracket.
+double normal_quantile_lower(double q)
+{
+    if (!(q > 0.0 && q < 0.5)) return q == 0.5 ? 0.0 : NAN;
+    double lo = -40.0, hi = 0.0;
+    double x = -std::sqrt(-2.0 * std::log(q));
+    const double inv_sqrt_2pi = 0.3989422804014326779399461;
+    for (int it = 0; it < 200; ++it) {
+        const double f = 0.5 * std::erfc(-x / std::sqrt(2.0)) - q;
+        if (f < 0.0) lo = x; else hi = x;
+        const double fp = inv_sqrt_2pi * std::exp(-0.5 * x * x);
+        double xn = (fp > 0.0) ? x - f / fp : 0.5 * (lo + hi);
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        if (std::fabs(xn - x) <= 1e-16 * std::fabs(x) || hi - lo <= 1e-16 * std::fabs(x)) { x = xn; break; }
+        x = xn;
+    }
+    return x;
+}
+
+double fisher_tau(double alpha, int64_t n, int l)
+{
+    const double dof = (double)(n - l - 3);
+    if (!(dof > 0.0)) return NAN;
+    return -normal_quantile_lower(0.5 * alpha) / std::sqrt(dof);
+}
+
+// --- binomial table ------------------------------------------------------------
+cupc_status ensure_binom(cupc_ctx* ctx, int m_needed)
+{
+    if (ctx->binom_mstride >= m_needed && ctx->binom.p) return CUPC_OK;
+    const int ms = std::max(m_needed, 64);
+    const int K = CUPC_MAX_LEVEL + 2;
+    std::vector<unsigned long long> h((size_t)K * ms);
+    for (int k = 0; k < K; ++k)
+        for (int m = 0; m < ms; ++m) {
+            unsigned long long v;
+            if (k > m) v = 0;
+            else if (k == 0) v = 1;
+            else {
+                // C(m, k) = C(m-1, k-1) + C(m-1, k), saturating
+                const unsigned long long a = h[(size_t)(k - 1) * ms + (m - 1)];
+                const unsigned long long b = h[(size_t)k * ms + (m - 1)];
+                v = (a == ~0ull || b == ~0ull || a > ~0ull - b) ? ~0ull : a + b;
+            }
+            h[(size_t)k * ms + m] = v;
+        }
+    cupc_status s = ensure(ctx, ctx->binom, h.size() * sizeof(unsigned long long));
+    if (s != CUPC_OK) return s;
+    CU(cudaMemcpyAsync(ctx->binom.p, h.data(), h.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));  // h goes out of scope
+    ctx->binom_mstride = ms;
+    return CUPC_OK;
+}
+
+Binom binom_view(cupc_ctx* ctx)
+{
+    Binom b;
+    b.tab = (const unsigned long long*)ctx->binom.p;
+    b.mstride = ctx->binom_mstride;
+    return b;
+}
+
+struct Input {
+    bool is_corr = false;
+    const void* X = nullptr;
+    int dtype = CUPC_F64;
+    int layout = CUPC_LAYOUT_SAMPLE_MAJOR;
+    int on_device = 0;
+    int64_t n = 0, p = 0, ld = 0;
+};
+
+size_t elem_size(int dtype) { return dtype == CUPC_F64 ? 8 : 4; }
+
+// Opens a timed region of kernel class `cls`; returns its slot or -1 when the
+// event pool is exhausted (the launch then goes untimed).
+int tbegin(cupc_ctx* ctx, int cls)
+{
+    if (ctx->tused + 2 > (int)ctx->tev.size()) return -1;
+    const int k = ctx->tused;
+    ctx->tused += 2;
+    ctx->tcls[k / 2] = cls;
+    cudaEventRecord(ctx->tev[k], ctx->stream);
+    return k;
+}
+
+void tend(cupc_ctx* ctx, int k)
+{
+    if (k >= 0) cudaEventRecord(ctx->tev[k + 1], ctx->stream);
+}
+
+void tcollect(cupc_ctx* ctx, cupc_stats& st)
+{
+    for (int k = 0; k + 1 < ctx->tused; k += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->tev[k], ctx->tev[k + 1]) == cudaSuccess) {
+            const int c = ctx->tcls[k / 2];
+            st.kernel_ms[c] += ms;
+        }
+    }
+    cudaGetLastError();
+    ctx->tused = 0;
+}
+
+#define TIMED(cls, call)                                                         \
+    do {                                                                         \
+        const int tk_ = tbegin(ctx, (cls));                                      \
+        LAUNCH(call);                                                            \
+        tend(ctx, tk_);                                                          \
+        kcount[(cls)]++;                                                         \
+    } while (0)
+
+cupc_status readback(cupc_ctx* ctx)
+{
+    CU(cudaMemcpyAsync(ctx->hmeta, ctx->meta.p, sizeof(Meta), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->d2h += sizeof(Meta);
+    return CUPC_OK;
+}
+
+// Standardise + correlation. On return exactly one of (c64, c32) is the matrix
+// the CI kernels read; z64 / c64 feed the FP64 rechecks.
+cupc_status prepare(cupc_ctx* ctx, const Input& in, bool fp32, const void** Cuse, const double** c64_out,
+                    const double** z64_out, int* kcount)
+{
+    const int n = (int)in.n, p = (int)in.p;
+    const size_t es = elem_size(in.dtype);
+    Meta* meta = (Meta*)ctx->meta.p;
+    *c64_out = nullptr;
+    *z64_out = nullptr;
+    if (in.is_corr) {
+        const void* src = in.X;
+        const size_t extent = ((size_t)(p - 1) * in.ld + p) * es;
+        if (!in.on_device) {
+            cupc_status s = ensure(ctx, ctx->cin, extent);
+            if (s != CUPC_OK) return s;
+            const int tk = tbegin(ctx, CUPC_K_UPLOAD);
+            CU(cudaMemcpyAsync(ctx->cin.p, in.X, extent, cudaMemcpyHostToDevice, ctx->stream));
+            tend(ctx, tk);
+            ctx->h2d += extent;
+            src = ctx->cin.p;
+        }
+        cupc_status s = ensure(ctx, ctx->c64, (size_t)p * p * 8);
+        if (s != CUPC_OK) return s;
+        if (fp32) {
+            s = ensure(ctx, ctx->c32, (size_t)p * p * 4);
+            if (s != CUPC_OK) return s;
+        }
+        TIMED(CUPC_K_STANDARDIZE, launch_symmetrize(in.dtype, src, in.ld, p, (double*)ctx->c64.p,
+                                                    fp32 ? (float*)ctx->c32.p : nullptr, ctx->stream));
+        *c64_out = (const double*)ctx->c64.p;
+        *Cuse = fp32 ? ctx->c32.p : ctx->c64.p;
+        return CUPC_OK;
+    }
+    const void* src = in.X;
+    const size_t extent = (in.layout == CUPC_LAYOUT_SAMPLE_MAJOR) ? ((size_t)(n - 1) * in.ld + p) * es
+                                                                 : ((size_t)(p - 1) * in.ld + n) * es;
+    if (!in.on_device) {
+        cupc_status s = ensure(ctx, ctx->xin, extent);
+        if (s != CUPC_OK) return s;
+        const int tk = tbegin(ctx, CUPC_K_UPLOAD);
+        CU(cudaMemcpyAsync(ctx->xin.p, in.X, extent, cudaMemcpyHostToDevice, ctx->stream));
+        tend(ctx, tk);
+        ctx->h2d += extent;
+        src = ctx->xin.p;
+    }
+    const void* xv = src;
+    long long ldv = in.ld;
+    if (in.layout == CUPC_LAYOUT_SAMPLE_MAJOR) {
+        cupc_status s = ensure(ctx, ctx->xt, (size_t)n * p * es);
+        if (s != CUPC_OK) return s;
+        TIMED(CUPC_K_STANDARDIZE, launch_transpose(in.dtype, src, in.ld, n, p, ctx->xt.p, ctx->stream));
+        xv = ctx->xt.p;
+        ldv = n;
+    }
+    const long long ldz = n;
+    cupc_status s;
+    if ((s = ensure(ctx, ctx->mu, (size_t)p * 8)) != CUPC_OK) return s;
+    if ((s = ensure(ctx, ctx->isd, (size_t)p * 8)) != CUPC_OK) return s;
+    if ((s = ensure(ctx, ctx->z64, (size_t)p * ldz * 8)) != CUPC_OK) return s;
+    if (fp32 && (s = ensure(ctx, ctx->z32, (size_t)p * ldz * 4)) != CUPC_OK) return s;
+    TIMED(CUPC_K_STANDARDIZE, launch_standardize(in.dtype, xv, ldv, n, p, (double*)ctx->mu.p, (double*)ctx->isd.p,
+                                                 (double*)ctx->z64.p, fp32 ? (float*)ctx->z32.p : nullptr, ldz,
+                                                 meta, ctx->stream));
+    *z64_out = (const double*)ctx->z64.p;
+    if (!fp32) {
+        if ((s = ensure(ctx, ctx->c64, (size_t)p * p * 8)) != CUPC_OK) return s;
+        TIMED(CUPC_K_CORRELATION,
+              launch_syrk_f64((const double*)ctx->z64.p, ldz, n, p, (double*)ctx->c64.p, ctx->stream));
+        *c64_out = (const double*)ctx->c64.p;
+        *Cuse = ctx->c64.p;
+    } else {
+        if ((s = ensure(ctx, ctx->c32, (size_t)p * p * 4)) != CUPC_OK) return s;
+        TIMED(CUPC_K_CORRELATION,
+              launch_syrk_f32((const float*)ctx->z32.p, ldz, n, p, (float*)ctx->c32.p, ctx->stream));
+        *Cuse = ctx->c32.p;
+    }
+    return CUPC_OK;
+}
+
+cupc_status validate_opts(cupc_ctx* ctx, const cupc_options& o)
+{
+    if (o.mode != CUPC_MODE_PLAIN_FP64 && o.mode != CUPC_MODE_FP32_RECHECK)
+        return fail(ctx, CUPC_E_INVALID, "unknown mode");
+    if (o.max_level < -1) return fail(ctx, CUPC_E_INVALID, "max_level must be >= -1");
+    if (o.learned_order) return fail(ctx, CUPC_E_INVALID, "learned ordering needs weights (cupc_mlp_set_weights)");
+    if (o.threads_per_block != 0 && (o.threads_per_block % 32 != 0 || o.threads_per_block > 256))
+        return fail(ctx, CUPC_E_INVALID, "threads_per_block must be a multiple of 32 up to 256");
+    if (o.chunk < 0) return fail(ctx, CUPC_E_INVALID, "chunk must be >= 0");
+    return CUPC_OK;
+}
+
+void free_result(cupc_result* r)
+{
+    if (!r) return;
+    cupc_ctx* ctx = r->ctx;
+    if (ctx) {
+        if (r->bits) cudaFreeAsync(r->bits, ctx->stream);
+        if (r->bits0) cudaFreeAsync(r->bits0, ctx->stream);
+        if (r->rec) cudaFreeAsync(r->rec, ctx->stream);
+        ctx_release(ctx);
+    }
+    delete r;
+}
+
+cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options* popts, cupc_result** out)
+{
+    if (!out) return fail(ctx, CUPC_E_INVALID, "out is NULL");
+    *out = nullptr;
+    cupc_options o;
+    cupc_options_default(&o);
+    if (popts) o = *popts;
+    cupc_status s = validate_opts(ctx, o);
+    if (s != CUPC_OK) return s;
+    if (!in.X) return fail(ctx, CUPC_E_INVALID, "input pointer is NULL");
+    if (in.dtype != CUPC_F32 && in.dtype != CUPC_F64) return fail(ctx, CUPC_E_INVALID, "dtype");
+    if (in.p < 2 || in.p > (1 << 20)) return fail(ctx, CUPC_E_INVALID, "p must be in [2, 2^20]");
+    if (!(alpha > 0.0 && alpha < 1.0)) return fail(ctx, CUPC_E_INVALID, "alpha must be in (0, 1)");
+    if (in.n < 4 || in.n > (1ll << 31) - 1) return fail(ctx, CUPC_E_INVALID, "n_samples out of range");
+    if (!in.is_corr) {
+        if (in.layout != CUPC_LAYOUT_SAMPLE_MAJOR && in.layout != CUPC_LAYOUT_VARIABLE_MAJOR)
+            return fail(ctx, CUPC_E_INVALID, "layout");
+        if (in.ld < (in.layout == CUPC_LAYOUT_SAMPLE_MAJOR ? in.p : in.n))
+            return fail(ctx, CUPC_E_INVALID, "ld smaller than the row length");
+        if ((double)in.n * (double)in.p > 4e9) return fail(ctx, CUPC_E_INVALID, "n * p too large");
+    } else if (in.ld < in.p) {
+        return fail(ctx, CUPC_E_INVALID, "ld < p");
+    }
+
+    CU(cudaSetDevice(ctx->device));
+    const bool fp32 = (o.mode == CUPC_MODE_FP32_RECHECK);
+    const int p = (int)in.p;
+    const int W = (p + 31) / 32;
+    const int64_t n = in.n;
+    const unsigned long long launches0 = ctx->launches, h2d0 = ctx->h2d, d2h0 = ctx->d2h;
+    int kcount[CUPC_KCLASSES] = {0};
+    ctx->tused = 0;
+
+    if ((s = ensure(ctx, ctx->meta, sizeof(Meta))) != CUPC_OK) return s;
+    Meta* meta = (Meta*)ctx->meta.p;
+    CU(cudaMemsetAsync(meta, 0, sizeof(Meta), ctx->stream));
+    CU(cudaEventRecord(ctx->ev[0], ctx->stream));
+
+    cupc_result* R = new cupc_result();
+    R->ctx = ctx;
+    ctx->refs++;
+    R->p = p;
+    R->W = W;
+    struct Guard {
+        cupc_result*& r;
+        bool ok = false;
+        ~Guard() { if (!ok) { free_result(r); r = nullptr; } }
+    } guard{R};
+
+    const void* Cuse = nullptr;
+    const double* c64 = nullptr;
+    const double* z64 = nullptr;
+    if ((s = prepare(ctx, in, fp32, &Cuse, &c64, &z64, kcount)) != CUPC_OK) return s;
+    CU(cudaEventRecord(ctx->ev[1], ctx->stream));
+
+    const size_t bitbytes = (size_t)p * W * 4;
+    if ((s = dalloc(ctx, (void**)&R->bits, bitbytes)) != CUPC_OK) return s;
+    if ((s = dalloc(ctx, (void**)&R->bits0, bitbytes)) != CUPC_OK) return s;
+    if (fp32) {
+        if ((s = ensure(ctx, ctx->backup[0], bitbytes)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, ctx->backup[1], bitbytes)) != CUPC_OK) return s;
+    }
+    size_t qcap = std::max<size_t>(1u << 20, (size_t)4 * p);
+    if (fp32 && (s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
+    if ((s = ensure_binom(ctx, std::max(p + 1, 64))) != CUPC_OK) return s;
+
+    const int grid_wide = std::max(1, ctx->num_sms * 4);
+    auto recheck_params = [&](int l) {
+        RecheckParams rp{};
+        rp.row_off = (const long long*)ctx->row_off.p;
+        rp.cols = (const int*)ctx->cols.p;
+        rp.srow = (const int*)ctx->srow.p;
+        rp.z64 = z64;
+        rp.ldz = n;
+        rp.n = (int)n;
+        rp.c64 = c64;
+        rp.p = p;
+        rp.l = l;
+        rp.B = binom_view(ctx);
+        const double r = std::tanh(fisher_tau(alpha, n, l));
+        rp.r2 = r * r;
+        rp.rank_tol = kRankTol64;
+        rp.best = (unsigned long long*)ctx->best.p;
+        rp.queue = (const QEntry*)ctx->queue.p;
+        rp.qcap = qcap;
+        rp.meta = meta;
+        rp.bits = R->bits;
+        rp.W = W;
+        return rp;
+    };
+
+    // ---------------- level 0 (Algorithm 3) ----------------
+    auto run_level0 = [&]() -> cupc_status {
+        const double r0 = std::tanh(fisher_tau(alpha, n, 0));
+        TIMED(CUPC_K_LEVEL0,
+              launch_level0(fp32, Cuse, p, W, r0, kBand0, R->bits, (QEntry*)ctx->queue.p, qcap, meta, ctx->stream));
+        if (fp32) TIMED(CUPC_K_LEVEL0, launch_recheck0(recheck_params(0), grid_wide, ctx->stream));
+        CU(cudaMemcpyAsync(R->bits0, R->bits, bitbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        return CUPC_OK;
+    };
+    if ((s = run_level0()) != CUPC_OK) return s;
+    const int64_t pairs = (int64_t)p * (p - 1) / 2;
+    R->stats.tests[0] = pairs;
+    R->stats.serial_tests[0] = pairs;
+    R->stats.edges_start[0] = pairs;
+    R->stats.max_degree[0] = p - 1;
+
+    // ---------------- levels l >= 1 (Algorithm 2 loop) ----------------
+    int l = 1;
+    int redo = 0;
+    bool level_pending = true; // counters of the last launched level are unread
+    size_t rec_len_cap = 0;
+    const int block = o.threads_per_block ? o.threads_per_block : 256;
+    const int chunk = o.chunk ? o.chunk : 128;
+    int levels_run = 1;
+    for (;;) {
+        // levels with n - l - 3 <= 0 have no threshold (Eq. threshold): stop there
+        const bool limit = (o.max_level >= 0 && l > o.max_level) || (n - l - 3 <= 0);
+        if (fp32 && !limit)
+            CU(cudaMemcpyAsync(ctx->backup[l & 1].p, R->bits, bitbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        CU(cudaMemsetAsync(&meta->maxdeg, 0, 2 * sizeof(int), ctx->stream));
+        CU(cudaMemsetAsync(&meta->block_entries, 0, sizeof(unsigned long long), ctx->stream));
+        if ((s = ensure(ctx, ctx->deg, (size_t)p * 4)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, ctx->row_off, (size_t)(p + 1) * 8)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, ctx->item_off, (size_t)(p + 1) * 8)) != CUPC_OK) return s;
+        {
+            const int tk = tbegin(ctx, CUPC_K_COMPACT);
+            LAUNCH(launch_degree(R->bits, p, W, (int*)ctx->deg.p, meta, ctx->stream));
+            LAUNCH(launch_scan((const int*)ctx->deg.p, p, l, chunk, binom_view(ctx), (long long*)ctx->row_off.p,
+                               (long long*)ctx->item_off.p, meta, ctx->stream));
+            tend(ctx, tk);
+            kcount[CUPC_K_COMPACT] += 2;
+        }
+        if ((s = readback(ctx)) != CUPC_OK) return s;
+        const Meta M = *ctx->hmeta;
+        if (M.error) return fail(ctx, CUPC_E_NUMERIC, "a variable has zero variance or non-finite data");
+        if (level_pending) {
+            const int pl = l - 1;  // the level these counters belong to
+            if (fp32 && M.queue_len > qcap) {
+                // the recheck queue overflowed: enlarge it and run that level again
+                if (++redo > 4) return fail(ctx, CUPC_E_RANGE, "recheck queue overflow persists");
+                qcap = (size_t)(M.queue_len * 2);
+                if ((s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
+                if (pl == 0) {
+                    CU(cudaMemsetAsync(meta, 0, sizeof(Meta), ctx->stream));
+                    if ((s = run_level0()) != CUPC_OK) return s;
+                    level_pending = true;
+                } else {
+                    CU(cudaMemcpyAsync(R->bits, ctx->backup[pl & 1].p, bitbytes, cudaMemcpyDeviceToDevice,
+                                       ctx->stream));
+                    unsigned long long keep = 0;  // record ints appended before level pl
+                    for (int q = 1; q < pl; ++q) keep += (unsigned long long)R->stats.removed[q] * (3 + q);
+                    ctx->hmeta->rec_ints = keep;
+                    CU(cudaMemcpyAsync(&meta->rec_ints, &ctx->hmeta->rec_ints, sizeof(keep), cudaMemcpyHostToDevice,
+                                       ctx->stream));
+                    l = pl;
+                    level_pending = false;
+                }
+                continue;
+            }
+            if (pl >= 1) {
+                R->stats.tests[pl] = (int64_t)M.tests;
+                R->stats.removed[pl] = (int64_t)M.removed;
+                R->stats.serial_tests[pl] = o.canonical_sepset ? (int64_t)M.serial_tests : -1;
+            }
+            R->stats.rechecks[pl] = (int64_t)M.rechecks;
+            level_pending = false;
+        }
+        if (l == 1) R->stats.removed[0] = pairs - (int64_t)M.edges;
+        if (limit) break;
+        if (l < CUPC_STATS_LEVELS) {
+            R->stats.edges_start[l] = (int64_t)M.edges;
+            R->stats.max_degree[l] = M.maxdeg;
+            R->stats.ci_block_entries[l] = (int64_t)M.block_entries;
+        }
+        // termination: level l runs only while some node has degree - 1 >= l
+        if (M.maxdeg - 1 < l) break;
+        if (l > CUPC_MAX_LEVEL) return fail(ctx, CUPC_E_RANGE, "a level above CUPC_MAX_LEVEL would be needed");
+        if (M.range_error) return fail(ctx, CUPC_E_RANGE, "subset count exceeds 64 bits");
+        if (l < CUPC_STATS_LEVELS) CU(cudaEventRecord(ctx->ev[1 + l], ctx->stream));
+
+        const long long nnz = (long long)M.nnz;
+        const unsigned long long n_items = M.n_items;
+        if ((s = ensure(ctx, ctx->cols, (size_t)nnz * 4 + 4)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, ctx->srow, (size_t)nnz * 4 + 4)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, ctx->partner, (size_t)nnz * 4 + 4)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, ctx->best, (size_t)nnz * 8 + 8)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, ctx->item_row, (size_t)n_items * 4 + 4)) != CUPC_OK) return s;
+        if ((s = ensure_binom(ctx, M.maxdeg + 2)) != CUPC_OK) return s;
+        // SepSet pool: room for every edge of this level to be removed
+        const size_t need = (size_t)M.rec_ints + (size_t)(M.edges) * (3 + l) + 16;
+        if (need > rec_len_cap) {
+            size_t cap = std::max(need, rec_len_cap * 2);
+            int* nr = nullptr;
+            if ((s = dalloc(ctx, (void**)&nr, cap * 4)) != CUPC_OK) return s;
+            if (R->rec && M.rec_ints)
+                CU(cudaMemcpyAsync(nr, R->rec, (size_t)M.rec_ints * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+            if (R->rec) cudaFreeAsync(R->rec, ctx->stream);
+            R->rec = nr;
+            rec_len_cap = cap;
+        }
+        // fresh per-level counters (tests .. next_item)
+        CU(cudaMemsetAsync(meta, 0, offsetof(Meta, edges), ctx->stream));
+        CU(cudaMemsetAsync(&meta->queue_len, 0, sizeof(unsigned long long), ctx->stream));
+        CU(cudaMemsetAsync(&meta->next_item, 0, sizeof(unsigned long long), ctx->stream));
+        {
+            const int tk = tbegin(ctx, CUPC_K_COMPACT);
+            LAUNCH(launch_fill(R->bits, p, W, (const long long*)ctx->row_off.p, (int*)ctx->cols.p,
+                               (int*)ctx->srow.p, ctx->stream));
+            LAUNCH(launch_items((const long long*)ctx->item_off.p, p, (int*)ctx->item_row.p, ctx->stream));
+            LAUNCH(launch_partner((const long long*)ctx->row_off.p, (const int*)ctx->cols.p,
+                                  (const int*)ctx->srow.p, nnz, (int*)ctx->partner.p, ctx->stream));
+            tend(ctx, tk);
+            kcount[CUPC_K_COMPACT] += 3;
+        }
+        CU(cudaMemsetAsync(ctx->best.p, 0xFF, (size_t)nnz * 8, ctx->stream));
+
+        if (n_items > 0) {
+            CIParams P{};
+            P.row_off = (const long long*)ctx->row_off.p;
+            P.cols = (const int*)ctx->cols.p;
+            P.partner = (const int*)ctx->partner.p;
+            P.item_row = (const int*)ctx->item_row.p;
+            P.item_off = (const long long*)ctx->item_off.p;
+            P.C = Cuse;
+            P.p = p;
+            P.l = l;
+            P.chunk = chunk;
+            P.canonical = o.canonical_sepset;
+            P.B = binom_view(ctx);
+            const double r = std::tanh(fisher_tau(alpha, n, l));
+            P.r = r;
+            P.r2 = r * r;
+            P.band_abs = (o.recheck_margin > 0) ? o.recheck_margin : kBandAbs;
+            P.band_rel = kBandRel;
+            P.rank_tol = fp32 ? kRankTol32 : kRankTol64;
+            P.piv_floor = kPivFloor;
+            P.best = (unsigned long long*)ctx->best.p;
+            P.queue = (QEntry*)ctx->queue.p;
+            P.qcap = qcap;
+            P.meta = meta;
+            P.n_items = n_items;
+            const long long want = (long long)((n_items + (block / 32) - 1) / (block / 32));
+            const int grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)ctx->num_sms * 8));
+            TIMED(CUPC_K_CI, launch_ci(fp32, P, grid, block, ctx->stream));
+            if (fp32) TIMED(CUPC_K_RECHECK, launch_recheck(recheck_params(l), grid_wide, ctx->stream));
+        }
+        FinalizeParams F{};
+        F.row_off = (const long long*)ctx->row_off.p;
+        F.cols = (const int*)ctx->cols.p;
+        F.srow = (const int*)ctx->srow.p;
+        F.partner = (const int*)ctx->partner.p;
+        F.best = (const unsigned long long*)ctx->best.p;
+        F.bits = R->bits;
+        F.W = W;
+        F.l = l;
+        F.B = binom_view(ctx);
+        F.count_serial = o.canonical_sepset;
+        F.rec = R->rec;
+        F.rec_cap = rec_len_cap;
+        F.meta = meta;
+        F.nnz = (unsigned long long)nnz;
+        TIMED(CUPC_K_FINALIZE, launch_finalize(F, ctx->stream));
+        levels_run = l + 1;
+        level_pending = true;
+        ++l;
+    }
+    const int ev_end = std::min(levels_run, CUPC_STATS_LEVELS - 1) + 1;
+    CU(cudaEventRecord(ctx->ev[ev_end], ctx->stream));
+    if ((s = readback(ctx)) != CUPC_OK) return s;
+    R->rec_ints = (int64_t)ctx->hmeta->rec_ints;
+    R->rec_cap = rec_len_cap;
+    if ((size_t)R->rec_ints > rec_len_cap && R->rec_ints > 0)
+        return fail(ctx, CUPC_E_RANGE, "SepSet record pool overflow");
+
+    // statistics
+    R->stats.levels = levels_run;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    R->stats.prep_ms = ms;
+    for (int q = 0; q < levels_run && q < CUPC_STATS_LEVELS; ++q) {
+        const int a = 1 + q, b = (q + 1 < levels_run) ? 2 + q : ev_end;
+        if (b > ev_end || a >= (int)ctx->ev.size()) break;
+        if (cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]) == cudaSuccess) R->stats.level_ms[q] = ms;
+    }
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[ev_end]);
+    R->stats.total_ms = ms;
+    cudaGetLastError();
+    int64_t edges_final = R->stats.edges_start[0] - R->stats.removed[0];
+    for (int q = 1; q < levels_run && q < CUPC_STATS_LEVELS; ++q) edges_final -= R->stats.removed[q];
+    R->stats.edges_final = edges_final;
+    for (int q = levels_run; q < CUPC_STATS_LEVELS; ++q) R->stats.serial_tests[q] = 0;
+    R->stats.kernel_launches = (int64_t)(ctx->launches - launches0);
+    tcollect(ctx, R->stats);
+    for (int c = 0; c < CUPC_KCLASSES; ++c) R->stats.kernel_count[c] = kcount[c];
+    R->stats.h2d_bytes = (int64_t)(ctx->h2d - h2d0);
+    R->stats.d2h_bytes = (int64_t)(ctx->d2h - d2h0);
+    guard.ok = true;
+    *out = R;
+    ctx->err.clear();
+    return CUPC_OK;
+}
+
+void ctx_release(cupc_ctx* c)
+{
+    if (--c->refs > 0) return;
+    cudaSetDevice(c->device);
+    cupc_ctx* ctx = c;
+    Buf* all[] = {&c->xin, &c->xt, &c->mu, &c->isd, &c->z64, &c->z32, &c->c64, &c->c32, &c->cin,
+                  &c->deg, &c->row_off, &c->item_off, &c->item_row, &c->cols, &c->srow, &c->partner,
+                  &c->best, &c->queue, &c->binom, &c->meta, &c->backup[0], &c->backup[1]};
+    for (Buf* b : all) free_buf(ctx, *b);
+    cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
+    if (c->hmeta) cudaFreeHost(c->hmeta);
+    if (c->pool) cudaMemPoolDestroy(c->pool);
+    delete c;
+}
+
+cupc_status build_host_records(const cupc_result* r)
+{
+    if (r->host_ready) return CUPC_OK;
+    std::vector<int32_t> raw((size_t)r->rec_ints);
+    if (r->rec_ints) {
+        cudaError_t e = cudaMemcpyAsync(raw.data(), r->rec, (size_t)r->rec_ints * 4, cudaMemcpyDeviceToHost,
+                                        r->ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(r->ctx->stream);
+        if (e != cudaSuccess) return CUPC_E_CUDA;
+        r->ctx->d2h += (size_t)r->rec_ints * 4;
+    }
+    std::vector<std::pair<uint64_t, int64_t>> idx;
+    for (int64_t k = 0; k < r->rec_ints;) {
+        const int i = raw[k], j = raw[k + 1], l = raw[k + 2];
+        idx.emplace_back((uint64_t)i * (uint64_t)r->p + (uint64_t)j, k);
+        k += 3 + l;
+    }
+    std::sort(idx.begin(), idx.end());
+    r->hrec.clear();
+    r->hrec.reserve(raw.size());
+    r->index.clear();
+    for (auto& pr : idx) {
+        const int l = raw[pr.second + 2];
+        r->index.emplace_back(pr.first, (int64_t)r->hrec.size());
+        r->hrec.insert(r->hrec.end(), raw.begin() + pr.second, raw.begin() + pr.second + 3 + l);
+    }
+    r->host_ready = true;
+    return CUPC_OK;
+}
+
+}  // namespace
+
+// =============================================================================
+// C ABI
+// =============================================================================
+extern "C" {
+
+void cupc_options_default(cupc_options* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->mode = CUPC_MODE_FP32_RECHECK;
+    o->canonical_sepset = 1;
+    o->learned_order = 0;
+    o->max_level = -1;
+    o->recheck_margin = 0.0;
+}
+
+cupc_status cupc_create(cupc_ctx** out, int device, void* stream)
+{
+    if (!out) return CUPC_E_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return CUPC_E_CUDA;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return CUPC_E_CUDA;
+    if (prop.major != 10 || prop.minor != 3) return CUPC_E_CUDA;  // built for sm_103a only
+    if (cudaSetDevice(device) != cudaSuccess) return CUPC_E_CUDA;
+    cupc_ctx* c = new cupc_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    c->num_sms = prop.multiProcessorCount;
+    cudaMemPoolProps pp{};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = device;
+    if (cudaMemPoolCreate(&c->pool, &pp) != cudaSuccess) {
+        delete c;
+        return CUPC_E_CUDA;
+    }
+    unsigned long long thr = ~0ull;
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if (cudaHostAlloc((void**)&c->hmeta, sizeof(Meta), cudaHostAllocDefault) != cudaSuccess) {
+        cudaMemPoolDestroy(c->pool);
+        delete c;
+        return CUPC_E_CUDA;
+    }
+    c->ev.resize(CUPC_STATS_LEVELS + 4);
+    for (auto& e : c->ev) cudaEventCreate(&e);
+    c->tev.resize(512);
+    c->tcls.resize(256);
+    for (auto& e : c->tev) cudaEventCreate(&e);
+    *out = c;
+    return CUPC_OK;
+}
+
+cupc_status cupc_set_stream(cupc_ctx* ctx, void* stream)
+{
+    if (!ctx) return CUPC_E_INVALID;
+    ctx->stream = (cudaStream_t)stream;
+    return CUPC_OK;
+}
+
+void cupc_destroy(cupc_ctx* ctx)
+{
+    if (ctx) ctx_release(ctx);
+}
+
+const char* cupc_last_error(const cupc_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : "null context";
+}
+
+cupc_status cupc_skeleton(cupc_ctx* ctx, const void* X, int dtype, int layout, int on_device, int64_t n_samples,
+                          int64_t p, int64_t ld, double alpha, const cupc_options* opts, cupc_result** out)
+{
+    if (!ctx) return CUPC_E_INVALID;
+    Input in;
+    in.X = X;
+    in.dtype = dtype;
+    in.layout = layout;
+    in.on_device = on_device;
+    in.n = n_samples;
+    in.p = p;
+    in.ld = ld;
+    return run(ctx, in, alpha, opts, out);
+}
+
+cupc_status cupc_skeleton_corr(cupc_ctx* ctx, const void* C, int dtype, int on_device, int64_t p, int64_t ld,
+                               int64_t n_samples, double alpha, const cupc_options* opts, cupc_result** out)
+{
+    if (!ctx) return CUPC_E_INVALID;
+    Input in;
+    in.is_corr = true;
+    in.X = C;
+    in.dtype = dtype;
+    in.on_device = on_device;
+    in.n = n_samples;
+    in.p = p;
+    in.ld = ld;
+    return run(ctx, in, alpha, opts, out);
+}
+
+cupc_status cupc_result_p(const cupc_result* r, int64_t* p)
+{
+    if (!r || !p) return CUPC_E_INVALID;
+    *p = r->p;
+    return CUPC_OK;
+}
+
+cupc_status cupc_result_adjacency(const cupc_result* r, uint8_t* out)
+{
+    if (!r || !out) return CUPC_E_INVALID;
+    cupc_ctx* ctx = r->ctx;
+    const size_t bytes = (size_t)r->p * r->W * 4;
+    std::vector<unsigned> h(bytes / 4);
+    CU(cudaMemcpyAsync(h.data(), r->bits, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->d2h += bytes;
+    const int64_t p = r->p;
+    for (int64_t i = 0; i < p; ++i)
+        for (int64_t j = 0; j < p; ++j) out[i * p + j] = (uint8_t)((h[i * r->W + (j >> 5)] >> (j & 31)) & 1u);
+    return CUPC_OK;
+}
+
+cupc_status cupc_result_sep_levels(const cupc_result* r, int16_t* out)
+{
+    if (!r || !out) return CUPC_E_INVALID;
+    cupc_ctx* ctx = r->ctx;
+    const size_t bytes = (size_t)r->p * r->W * 4;
+    std::vector<unsigned> h0(bytes / 4);
+    CU(cudaMemcpyAsync(h0.data(), r->bits0, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->d2h += bytes;
+    cupc_status s = build_host_records(r);
+    if (s != CUPC_OK) return fail(ctx, s, "record download");
+    const int64_t p = r->p;
+    for (int64_t i = 0; i < p; ++i)
+        for (int64_t j = 0; j < p; ++j) {
+            const bool after0 = (h0[i * r->W + (j >> 5)] >> (j & 31)) & 1u;
+            out[i * p + j] = (i == j) ? -1 : (after0 ? -1 : 0);
+        }
+    for (size_t k = 0; k < r->hrec.size();) {
+        const int i = r->hrec[k], j = r->hrec[k + 1], l = r->hrec[k + 2];
+        out[(int64_t)i * p + j] = (int16_t)l;
+        out[(int64_t)j * p + i] = (int16_t)l;
+        k += 3 + l;
+    }
+    return CUPC_OK;
+}
+
+cupc_status cupc_result_sepset(const cupc_result* r, int64_t i, int64_t j, int32_t* out, int* len)
+{
+    if (!r || !out || !len) return CUPC_E_INVALID;
+    if (i < 0 || j < 0 || i >= r->p || j >= r->p || i == j) return CUPC_E_INVALID;
+    cupc_ctx* ctx = r->ctx;
+    cupc_status s = build_host_records(r);
+    if (s != CUPC_OK) return fail(ctx, s, "record download");
+    const int64_t a = std::min(i, j), b = std::max(i, j);
+    const uint64_t key = (uint64_t)a * (uint64_t)r->p + (uint64_t)b;
+    auto it = std::lower_bound(r->index.begin(), r->index.end(), std::make_pair(key, (int64_t)-1));
+    if (it != r->index.end() && it->first == key) {
+        const int l = r->hrec[it->second + 2];
+        for (int c = 0; c < l; ++c) out[c] = r->hrec[it->second + 3 + c];
+        *len = l;
+        return CUPC_OK;
+    }
+    // not a level >= 1 removal: present, or removed at level 0
+    unsigned w0 = 0;
+    CU(cudaMemcpy(&w0, r->bits0 + a * r->W + (b >> 5), 4, cudaMemcpyDeviceToHost));
+    *len = ((w0 >> (b & 31)) & 1u) ? -1 : 0;
+    return CUPC_OK;
+}
+
+cupc_status cupc_result_sepset_records(const cupc_result* r, int32_t* out, int64_t cap, int64_t* n_ints)
+{
+    if (!r || !n_ints) return CUPC_E_INVALID;
+    cupc_status s = build_host_records(r);
+    if (s != CUPC_OK) return fail(r->ctx, s, "record download");
+    *n_ints = (int64_t)r->hrec.size();
+    if (out) std::memcpy(out, r->hrec.data(), (size_t)std::min<int64_t>(cap, *n_ints) * 4);
+    return CUPC_OK;
+}
+
+cupc_status cupc_result_stats(const cupc_result* r, cupc_stats* out)
+{
+    if (!r || !out) return CUPC_E_INVALID;
+    *out = r->stats;
+    return CUPC_OK;
+}
+
+void cupc_result_free(cupc_result* r) { free_result(r); }
+
+cupc_status cupc_correlation(cupc_ctx* ctx, const void* X, int dtype, int layout, int on_device, int64_t n_samples,
+                             int64_t p, int64_t ld, int precision, void* C_out)
+{
+    if (!ctx || !X || !C_out) return CUPC_E_INVALID;
+    if (p < 1 || n_samples < 2) return fail(ctx, CUPC_E_INVALID, "sizes");
+    CU(cudaSetDevice(ctx->device));
+    cupc_status s = ensure(ctx, ctx->meta, sizeof(Meta));
+    if (s != CUPC_OK) return s;
+    CU(cudaMemsetAsync(ctx->meta.p, 0, sizeof(Meta), ctx->stream));
+    Input in;
+    in.X = X;
+    in.dtype = dtype;
+    in.layout = layout;
+    in.on_device = on_device;
+    in.n = n_samples;
+    in.p = p;
+    in.ld = ld;
+    const void* Cuse = nullptr;
+    const double *c64 = nullptr, *z64 = nullptr;
+    const bool fp32 = (precision == CUPC_F32);
+    int kcount[CUPC_KCLASSES] = {0};
+    ctx->tused = 0;
+    if ((s = prepare(ctx, in, fp32, &Cuse, &c64, &z64, kcount)) != CUPC_OK) return s;
+    CU(cudaMemcpyAsync(C_out, Cuse, (size_t)p * p * (fp32 ? 4 : 8), cudaMemcpyDeviceToDevice, ctx->stream));
+    if ((s = readback(ctx)) != CUPC_OK) return s;
+    if (ctx->hmeta->error) return fail(ctx, CUPC_E_NUMERIC, "a variable has zero variance or non-finite data");
+    return CUPC_OK;
+}
+
+cupc_status cupc_pcor_batch(cupc_ctx* ctx, const void* C, int dtype, int64_t p, const int32_t* queries, int64_t nq,
+                            int l, double* rho_out)
+{
+    if (!ctx || !C || !queries || !rho_out) return CUPC_E_INVALID;
+    if (l < 0 || l > CUPC_MAX_LEVEL) return fail(ctx, CUPC_E_RANGE, "l out of range");
+    CU(cudaSetDevice(ctx->device));
+    LAUNCH(launch_pcor(dtype == CUPC_F32, C, (int)p, queries, nq, l, rho_out, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return CUPC_OK;
+}
+
+cupc_status cupc_fisher_threshold(double alpha, int64_t n_samples, int l, double* tau, double* r)
+{
+    if (!(alpha > 0.0 && alpha < 1.0) || n_samples - l - 3 <= 0) return CUPC_E_INVALID;
+    const double t = fisher_tau(alpha, n_samples, l);
+    if (tau) *tau = t;
+    if (r) *r = std::tanh(t);
+    return CUPC_OK;
+}
+
+}  // extern "C"

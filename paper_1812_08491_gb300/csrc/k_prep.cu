@@ -1,0 +1,198 @@
+// k_prep.cu -- standardisation of the data and the SIMT correlation product.
+//
+// C = Z^T Z / n with Z the standardised data (Sec. 4.3 defines C as the
+// correlation matrix; the paper does not say where it is formed). Moments are
+// FP64 and two-pass (mean, then centred sum of squares), divisor n.
+#include "kernels.cuh"
+
+namespace cupc {
+
+// ---------------------------------------------------------------------------
+// Sample-major X (X[s*ld + v]) to variable-major (Xt[v*n + s]), 32x32 tiles.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_transpose(const T* __restrict__ X, long long ld, int n, int p, T* __restrict__ Xt)
+{
+    __shared__ T tile[32][33];
+    const int v0 = blockIdx.x * 32, s0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int s = s0 + r, v = v0 + threadIdx.x;
+        if (s < n && v < p) tile[r][threadIdx.x] = X[(size_t)s * ld + v];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int v = v0 + r, s = s0 + threadIdx.x;
+        if (s < n && v < p) Xt[(size_t)v * n + s] = tile[threadIdx.x][r];
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double x, double* red)
+{
+    // deterministic: fixed shuffle tree per warp, then warp partials in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = x;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) t += red[k];
+    return t;
+}
+
+// One block per variable: mean, centred variance, then the standardised row
+// z = (x - mean) * (1/sd) in FP64 (and optionally FP32, bf16 hi/lo splits).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, long long ld, int n, int p,
+                                                    double* __restrict__ mu, double* __restrict__ isd,
+                                                    double* __restrict__ z64, float* __restrict__ z32,
+                                                    long long ldz, Meta* meta)
+{
+    __shared__ double red[NT / 32];
+    const int v = blockIdx.x;
+    if (v >= p) return;
+    const T* row = Xv + (size_t)v * ld;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += NT) s += (double)row[k];
+    const double mean = block_sum<NT>(s, red) / (double)n;
+    double q = 0.0;
+    for (int k = threadIdx.x; k < n; k += NT) {
+        const double d = (double)row[k] - mean;
+        q += d * d;
+    }
+    const double var = block_sum<NT>(q, red) / (double)n;
+    const bool ok = (var > 0.0) && isfinite(var) && isfinite(mean);
+    const double inv = ok ? 1.0 / sqrt(var) : 0.0;
+    if (threadIdx.x == 0) {
+        mu[v] = mean;
+        isd[v] = inv;
+        if (!ok) atomicOr(&meta->error, 1);
+    }
+    for (int k = threadIdx.x; k < n; k += NT) {
+        const double z = ((double)row[k] - mean) * inv;
+        if (z64) z64[(size_t)v * ldz + k] = z;
+        if (z32) z32[(size_t)v * ldz + k] = (float)z;
+    }
+    // zero the K padding up to ldz so the product can read whole tiles
+    for (int k = n + threadIdx.x; k < ldz; k += NT) {
+        if (z64) z64[(size_t)v * ldz + k] = 0.0;
+        if (z32) z32[(size_t)v * ldz + k] = 0.f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// SIMT symmetric product C = Z Z^T * (1/n) over the upper-triangle tiles,
+// mirrored into the lower triangle (so C is exactly symmetric), unit diagonal.
+// BM x BM tile, BK-deep slabs through shared memory, TM x TM per thread.
+// ---------------------------------------------------------------------------
+template <typename T, int BM, int BK, int TM>
+__global__ void __launch_bounds__((BM / TM) * (BM / TM))
+k_syrk(const T* __restrict__ Z, long long ldz, int n, int p, T* __restrict__ C, double inv_n)
+{
+    constexpr int TD = BM / TM;          // threads per tile dimension
+    constexpr int NT = TD * TD;
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BM + 1];
+    // triangular tile index -> (bi <= bj)
+    const long long t = blockIdx.x;
+    int bj = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((long long)(bj + 1) * (bj + 2) / 2 <= t) ++bj;
+    while ((long long)bj * (bj + 1) / 2 > t) --bj;
+    const int bi = (int)(t - (long long)bj * (bj + 1) / 2);
+    const int i0 = bi * BM, j0 = bj * BM;
+    const int tx = threadIdx.x % TD, ty = threadIdx.x / TD;
+    T acc[TM][TM];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TM; ++b) acc[a][b] = T(0);
+
+    for (int k0 = 0; k0 < n; k0 += BK) {
+        for (int e = threadIdx.x; e < BM * BK; e += NT) {
+            const int r = e / BK, k = e % BK;
+            const int gi = i0 + r, gj = j0 + r, gk = k0 + k;
+            As[k][r] = (gi < p && gk < n) ? Z[(size_t)gi * ldz + gk] : T(0);
+            Bs[k][r] = (gj < p && gk < n) ? Z[(size_t)gj * ldz + gk] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            T a[TM], b[TM];
+#pragma unroll
+            for (int m = 0; m < TM; ++m) {
+                a[m] = As[k][ty + TD * m];
+                b[m] = Bs[k][tx + TD * m];
+            }
+#pragma unroll
+            for (int m = 0; m < TM; ++m)
+#pragma unroll
+                for (int q = 0; q < TM; ++q) acc[m][q] = fma(a[m], b[q], acc[m][q]);
+        }
+        __syncthreads();
+    }
+    const T sc = (T)inv_n;
+#pragma unroll
+    for (int m = 0; m < TM; ++m) {
+        const int gi = i0 + ty + TD * m;
+#pragma unroll
+        for (int q = 0; q < TM; ++q) {
+            const int gj = j0 + tx + TD * q;
+            if (gi >= p || gj >= p) continue;
+            if (bi == bj) {
+                // diagonal tile: (gi,gj) and (gj,gi) are the same dot product in the
+                // same order, so each is written by its own thread
+                C[(size_t)gi * p + gj] = (gi == gj) ? T(1) : acc[m][q] * sc;
+            } else {
+                const T val = acc[m][q] * sc;
+                C[(size_t)gi * p + gj] = val;
+                C[(size_t)gj * p + gi] = val;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_transpose(int dtype, const void* X, long long ld, int n, int p, void* Xt, cudaStream_t st)
+{
+    dim3 grid((p + 31) / 32, (n + 31) / 32), block(32, 8);
+    if (dtype == CUPC_F64)
+        k_transpose<double><<<grid, block, 0, st>>>((const double*)X, ld, n, p, (double*)Xt);
+    else
+        k_transpose<float><<<grid, block, 0, st>>>((const float*)X, ld, n, p, (float*)Xt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_standardize(int dtype, const void* Xv, long long ld, int n, int p, double* mu, double* isd,
+                               double* z64, float* z32, long long ldz, Meta* meta, cudaStream_t st)
+{
+    constexpr int NT = 256;
+    if (dtype == CUPC_F64)
+        k_standardize<double, NT><<<p, NT, 0, st>>>((const double*)Xv, ld, n, p, mu, isd, z64, z32, ldz, meta);
+    else
+        k_standardize<float, NT><<<p, NT, 0, st>>>((const float*)Xv, ld, n, p, mu, isd, z64, z32, ldz, meta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_syrk_f64(const double* Z, long long ldz, int n, int p, double* C, cudaStream_t st)
+{
+    constexpr int BM = 64, BK = 16, TM = 4;
+    const long long nt = (p + BM - 1) / BM;
+    const long long tiles = nt * (nt + 1) / 2;
+    k_syrk<double, BM, BK, TM><<<(unsigned)tiles, (BM / TM) * (BM / TM), 0, st>>>(Z, ldz, n, p, C, 1.0 / n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_syrk_f32(const float* Z, long long ldz, int n, int p, float* C, cudaStream_t st)
+{
+    constexpr int BM = 128, BK = 16, TM = 8;
+    const long long nt = (p + BM - 1) / BM;
+    const long long tiles = nt * (nt + 1) / 2;
+    k_syrk<float, BM, BK, TM><<<(unsigned)tiles, (BM / TM) * (BM / TM), 0, st>>>(Z, ldz, n, p, C, 1.0 / n);
+    return cudaGetLastError();
+}
+
+}  // namespace cupc

@@ -1,0 +1,246 @@
+"""GPU parity of the CUDA skeleton path against the FP64 CPU oracle.
+
+All calls go through the C ABI (the ctypes binding). Tolerances:
+  * correlation: FP64 product within 1e-13 absolute; FP32 (split) product within
+    2e-5 absolute (FP32 accumulation over n terms);
+  * partial correlations: |d rho| <= 1e-10 * max(|rho|, r_tau) in FP64 and
+    <= 1e-5 * max(|rho|, r_tau) in FP32 (the FP32 band is wider than that error);
+  * skeletons and canonical SepSets: exactly equal.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import sem
+
+cupc = pytest.importorskip("paper_1812_08491_gb300")
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+MODES = {"plain": cupc.MODE_PLAIN_FP64, "fp32": cupc.MODE_FP32_RECHECK}
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda_device):
+    cupc.build_library()
+    c = cupc.Context(0)
+    yield c
+    c.close()
+
+
+def _oracle_run(X, alpha, max_level=-1):
+    C = oracle.correlation(X, nthreads=8)
+    return C, oracle.pc_stable(C, X.shape[0], alpha, max_level=max_level, nthreads=8)
+
+
+def _assert_same(res, ref, canonical=True, C=None, n=None, alpha=None):
+    adj = res.adjacency()
+    assert np.array_equal(adj, ref.adj), f"skeleton differs in {int((adj != ref.adj).sum()) // 2} pairs"
+    lev = res.sep_levels()
+    assert np.array_equal(lev, ref.sep_level)
+    got = res.sepsets()
+    if canonical:
+        assert got == ref.sepsets
+    else:
+        assert set(got) == set(ref.sepsets)
+        for (i, j), (l, S) in got.items():
+            ind, rho, z = oracle.ci_gauss(C, n, alpha, i, j, S)
+            assert ind, ((i, j), S, rho, z)
+
+
+# --------------------------------------------------------------------------
+# correlation
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p,n", [(70, 333), (129, 1000), (257, 64)])
+def test_correlation_f64_parity(ctx, p, n):
+    s = sem.generate(p, n, 11 + p, "random", degree=3.0)
+    ref = oracle.correlation(s.X, nthreads=8)
+    for X in (s.X, np.ascontiguousarray(s.X), torch.from_numpy(np.ascontiguousarray(s.X)).cuda(),
+              torch.from_numpy(s.Xt).cuda().T):
+        C = ctx.correlation(X, cupc.F64).cpu().numpy()
+        assert np.max(np.abs(C - ref)) < 1e-13
+        assert np.array_equal(C, C.T) and np.all(np.diag(C) == 1.0)
+
+
+def test_correlation_f32_parity(ctx):
+    s = sem.generate(300, 2000, 5, "random", degree=3.0)
+    ref = oracle.correlation(s.X, nthreads=8)
+    C = ctx.correlation(s.X, cupc.F32).cpu().numpy().astype(np.float64)
+    err = np.max(np.abs(C - ref))
+    assert err < 2e-5, err
+    assert np.array_equal(C, C.T)
+
+
+def test_correlation_float32_input(ctx):
+    s = sem.generate(90, 500, 6, "random", degree=3.0, dtype=np.float32)
+    ref = oracle.correlation(s.X.astype(np.float64))
+    C = ctx.correlation(s.X, cupc.F64).cpu().numpy()
+    assert np.max(np.abs(C - ref)) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# partial correlations
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("l", [1, 2, 3, 4, 6, 9])
+def test_pcor_parity(ctx, l):
+    s = sem.generate(40, 800, 100 + l, "random", degree=4.0)
+    C = oracle.correlation(s.X)
+    rng = np.random.default_rng(l)
+    Q = np.array([rng.permutation(s.p)[: l + 2] for _ in range(400)], dtype=np.int32)
+    ref = np.array([oracle.pcor(C, int(q[0]), int(q[1]), q[2:].tolist())[0] for q in Q])
+    r = math.tanh(oracle.tau(0.01, s.n, l))
+    Ct = torch.from_numpy(C).cuda()
+    q = torch.from_numpy(Q).cuda()
+    got64 = ctx.pcor_batch(Ct, q, l).cpu().numpy()
+    scale = np.maximum(np.abs(ref), r)
+    err64 = np.abs(got64 - ref) / scale
+    assert err64.max() <= 1e-10, err64.max()
+    got32 = ctx.pcor_batch(Ct.float(), q, l).cpu().numpy()
+    err32 = np.abs(got32 - ref) / scale
+    assert np.percentile(err32, 99) <= 1e-5 and err32.max() <= 1e-4, (np.percentile(err32, 99), err32.max())
+
+
+# --------------------------------------------------------------------------
+# whole skeleton
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", ["plain", "fp32"])
+@pytest.mark.parametrize("seed", range(5))
+def test_skeleton_small20(ctx, mode, seed):
+    s = sem.workload("small20", seed)
+    C, ref = _oracle_run(s.X, s.alpha)
+    res = ctx.skeleton(s.X, s.alpha, mode=MODES[mode])
+    _assert_same(res, ref)
+    st = res.stats()
+    assert st["levels"] == ref.levels_run
+    assert st["serial_tests"] == ref.tests
+    assert st["removed"] == ref.removed
+
+
+@pytest.mark.parametrize("mode", ["plain", "fp32"])
+@pytest.mark.parametrize("p,n,fam,deg,alpha", [(150, 2000, "random", 3.0, 0.01), (300, 500, "scale_free", 0, 0.01),
+                                               (97, 300, "random", 5.0, 0.05), (40, 120, "random", 6.0, 0.2)])
+def test_skeleton_medium(ctx, mode, p, n, fam, deg, alpha):
+    s = sem.generate(p, n, 7 * p + n, fam, degree=deg, w_min=0.2)
+    C, ref = _oracle_run(s.X, alpha)
+    res = ctx.skeleton(s.X, alpha, mode=MODES[mode])
+    _assert_same(res, ref)
+    assert res.stats()["serial_tests"] == ref.tests
+
+
+@pytest.mark.parametrize("mode", ["plain", "fp32"])
+def test_skeleton_free_sepsets_reverify(ctx, mode):
+    s = sem.generate(120, 400, 77, "random", degree=5.0, w_min=0.2)
+    C, ref = _oracle_run(s.X, 0.05)
+    res = ctx.skeleton(s.X, 0.05, mode=MODES[mode], canonical=False)
+    _assert_same(res, ref, canonical=False, C=C, n=s.n, alpha=0.05)
+
+
+@pytest.mark.parametrize("max_level", [0, 1, 2])
+def test_skeleton_max_level(ctx, max_level):
+    s = sem.generate(60, 300, 21, "random", degree=5.0, w_min=0.2)
+    C, ref = _oracle_run(s.X, 0.05, max_level=max_level)
+    for mode in MODES.values():
+        res = ctx.skeleton(s.X, 0.05, mode=mode, max_level=max_level)
+        _assert_same(res, ref)
+        assert res.stats()["levels"] == ref.levels_run
+
+
+def test_skeleton_input_forms(ctx):
+    s = sem.generate(64, 700, 3, "random", degree=3.0)
+    C, ref = _oracle_run(s.X, 0.01)
+    forms = [s.X, np.ascontiguousarray(s.X), torch.from_numpy(np.ascontiguousarray(s.X)).cuda(),
+             torch.from_numpy(s.Xt).cuda().T]
+    for X in forms:
+        _assert_same(ctx.skeleton(X, 0.01), ref)
+    # padded leading dimension
+    big = np.zeros((s.n, s.p + 13))
+    big[:, : s.p] = s.X
+    _assert_same(ctx.skeleton(big[:, : s.p], 0.01), ref)
+
+
+def test_skeleton_corr_entry(ctx):
+    s = sem.generate(80, 900, 4, "random", degree=3.0)
+    C, ref = _oracle_run(s.X, 0.01)
+    for mode in MODES.values():
+        _assert_same(ctx.skeleton_corr(C, s.n, 0.01, mode=mode), ref)
+        _assert_same(ctx.skeleton_corr(torch.from_numpy(C).cuda(), s.n, 0.01, mode=mode), ref)
+
+
+# --------------------------------------------------------------------------
+# edge cases
+# --------------------------------------------------------------------------
+
+def test_two_variables(ctx):
+    rng = np.random.default_rng(0)
+    a = rng.standard_normal(500)
+    for b, expect in ((rng.standard_normal(500), 0), (a + 0.5 * rng.standard_normal(500), 1)):
+        X = np.column_stack([a, b])
+        ref = _oracle_run(X, 0.01)[1]
+        assert ref.adj[0, 1] == expect
+        for mode in MODES.values():
+            _assert_same(ctx.skeleton(X, 0.01, mode=mode), ref)
+
+
+def test_independent_variables_empty_graph(ctx):
+    X = np.random.default_rng(1).standard_normal((2000, 45))
+    ref = _oracle_run(X, 1e-4)[1]
+    for mode in MODES.values():
+        res = ctx.skeleton(X, 1e-4, mode=mode)
+        _assert_same(res, ref)
+
+
+def test_duplicated_column_pinv_path(ctx):
+    s = sem.generate(30, 400, 9, "random", degree=4.0, w_min=0.3)
+    X = np.column_stack([s.X, s.X[:, 3]])
+    C, ref = _oracle_run(X, 0.05)
+    for mode in MODES.values():
+        _assert_same(ctx.skeleton(X, 0.05, mode=mode), ref)
+
+
+def test_complete_dependence_dense_levels(ctx):
+    # a strongly connected dense DAG drives many levels
+    s = sem.generate(24, 3000, 12, "random", degree=10.0, w_min=0.5)
+    C, ref = _oracle_run(s.X, 0.01)
+    assert ref.levels_run >= 3
+    for mode in MODES.values():
+        _assert_same(ctx.skeleton(s.X, 0.01, mode=mode), ref)
+
+
+def test_zero_variance_is_an_error(ctx):
+    X = np.random.default_rng(2).standard_normal((100, 5))
+    X[:, 2] = 1.5
+    with pytest.raises(cupc.CupcError) as e:
+        ctx.skeleton(X, 0.01)
+    assert e.value.status == -6
+    # the context stays usable
+    ctx.skeleton(np.random.default_rng(3).standard_normal((100, 5)), 0.01)
+
+
+def test_invalid_arguments(ctx):
+    X = np.random.default_rng(2).standard_normal((100, 5))
+    for alpha in (0.0, 1.0, -1.0):
+        with pytest.raises(cupc.CupcError):
+            ctx.skeleton(X, alpha)
+    with pytest.raises(cupc.CupcError):
+        ctx.skeleton(X[:, :1], 0.01)
+
+
+# --------------------------------------------------------------------------
+# full-size workload in the benchmark configuration
+# --------------------------------------------------------------------------
+
+def test_medium1000_full_size_parity(ctx):
+    s = sem.workload("medium1000")
+    C, ref = _oracle_run(s.X, s.alpha)
+    Xd = torch.from_numpy(s.Xt).cuda().T          # device-resident, variable-major
+    for mode in ("fp32", "plain"):
+        res = ctx.skeleton(Xd, s.alpha, mode=MODES[mode])
+        _assert_same(res, ref)
+        assert res.stats()["serial_tests"] == ref.tests

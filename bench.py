@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Benchmark of the PC-stable skeleton path on one GB300 (or N replicas).
+
+A step is one whole skeleton: FP64 standardisation, the correlation product,
+level 0 and every level until the termination rule, on the medium1000 workload
+(p = 1000 variables, n = 10000 samples, random DAG of expected degree 3,
+weights +-U[0.1, 1], float32 input, alpha = 0.01), synthetic and seeded.
+
+Metric: CI tests per second, counting the tests the serial algorithm performs
+on this input (the canonical lexicographic run's per-level counts, identical to
+the CPU oracle's), divided by the skeleton wall time. ``value`` is measured
+with the input resident in device memory (CUDA events on the library's
+stream, L2 flushed between steps); ``e2e`` through the same public call with a
+pinned host input, including the upload and the download of the adjacency and
+SepSets. The plain form (FP64 for every test) is timed beside the chosen form.
+
+``--impl reference`` times the CPU oracle as it stands on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "skeleton wall time (s) and CI tests/sec, chosen vs plain form, exact skeleton"
+UNIT = "CI tests/s"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d["bf16_tflops_sustained"]), "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
+
+
+# FP32 SIMT peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 non-tensor rate of GB300 (nominal table of the part).
+FP64_TFLOPS = 1.25
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons),
+                       samples=len(sm))
+        return out
+
+
+def cpu_oracle_run(sem_obj, nthreads):
+    """One full oracle skeleton (correlation + Algorithm 1): (seconds, serial tests)."""
+    import oracle
+    t0 = time.perf_counter()
+    C = oracle.correlation(sem_obj.X, nthreads=nthreads)
+    res = oracle.pc_stable(C, sem_obj.n, sem_obj.alpha, max_level=sem_obj.max_level, nthreads=nthreads)
+    return time.perf_counter() - t0, res.total_tests
+
+
+def run_reference(args, workload_name):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from synth import sem
+    s = sem.workload(workload_name)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        cpu_oracle_run(s, cores)
+    secs, units = 0.0, 0
+    for _ in range(args.steps):
+        t, u = cpu_oracle_run(s, cores)
+        secs += t
+        units += u
+    value = units / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded linear-Gaussian SEM)",
+            "config": _config(workload_name, s, "cpu oracle"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"whole {workload_name} skeleton per step (correlation + all levels)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def _config(name, s, form):
+    return {"workload": name, "p": s.p, "n": s.n, "family": s.family,
+            "degree": s.meta.get("degree"), "alpha": s.alpha, "input_dtype": s.meta.get("dtype"),
+            "form": form, "l2": "flushed between steps (256 MiB write)"}
+
+
+def roofline(stats_sum, steps, s, mode, peaks):
+    """Roofline of the kernel class with the largest device time."""
+    km = stats_sum["kernel_ms"]
+    kc = stats_sum["kernel_count"]
+    dom = max(km, key=lambda k: km[k])
+    ms = km[dom] / steps
+    launches = max(1, kc[dom] // steps)
+    es_in = 4 if s.meta.get("dtype") == "float32" else 8
+    n, p = s.n, s.p
+    cbytes = 4 if mode == "fp32" else 8
+    if dom == "correlation":
+        flops = float(n) * p * p  # 2 n p^2 / 2: upper triangle
+        achieved = flops / (ms * 1e-3) / 1e12
+        peak = FP32_SIMT_TFLOPS if mode == "fp32" else FP64_TFLOPS
+        return dom, {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_src": "FP32 SIMT from unit counts and clock" if mode == "fp32" else "FP64 nominal"}
+    if dom == "standardize":
+        byts = n * p * es_in + n * p * 8 + (n * p * 4 if mode == "fp32" else 0)
+    elif dom == "level0":
+        byts = p * p * cbytes + p * p / 8
+    elif dom == "ci":
+        byts = sum(stats_sum["ci_block_entries"]) / steps * cbytes
+    elif dom == "compact":
+        byts = 2 * p * p / 8
+    else:
+        byts = None
+    if byts is None:
+        return dom, None
+    achieved = byts / (ms * 1e-3) / 1e9
+    return dom, {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                 "peak_src": "measured" if peaks["src"] == "measured" else "fallback"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="medium1000")
+    ap.add_argument("--mode", default="fp32", choices=["fp32", "plain"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args, args.workload)
+
+    import numpy as np
+    import torch
+
+    import paper_1812_08491_gb300 as cupc
+    from synth import sem
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    cupc.build_library()
+    s = sem.workload(args.workload)
+    Xd = torch.from_numpy(s.Xt).to(dev)          # p x n rows; X = Xd.T is variable-major n x p
+    X = Xd.T
+    ctx = cupc.Context(local)
+    mode = cupc.MODE_FP32_RECHECK if args.mode == "fp32" else cupc.MODE_PLAIN_FP64
+    stream = torch.cuda.current_stream(dev)
+
+    # the unit count: serial-order tests of the canonical run (equal to the oracle's)
+    ref = ctx.skeleton(X, s.alpha, mode=mode, canonical=True, max_level=s.max_level)
+    units = int(sum(ref.stats()["serial_tests"]))
+    edges = int(ref.stats()["edges_final"])
+    ref.free()
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(m):
+        res = ctx.skeleton(X, s.alpha, mode=m, canonical=True, max_level=s.max_level)
+        st = res.stats()
+        res.free()
+        return st
+
+    for _ in range(args.warmup):
+        step(mode)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = 0.0
+    agg = {"kernel_ms": {}, "kernel_count": {}, "ci_block_entries": [0] * 32}
+    launches = 0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = step(mode)
+            b.record(stream)
+            torch.cuda.synchronize()
+            total_ms += a.elapsed_time(b)
+            launches += st["kernel_launches"]
+            for k, v in st["kernel_ms"].items():
+                agg["kernel_ms"][k] = agg["kernel_ms"].get(k, 0.0) + v
+            for k, v in st["kernel_count"].items():
+                agg["kernel_count"][k] = agg["kernel_count"].get(k, 0) + v
+            for q, v in enumerate(st["ci_block_entries"]):
+                agg["ci_block_entries"][q] += v
+    if dist:
+        dist.barrier()
+    clocks = clk.summary()
+    t = torch.tensor([total_ms], device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = units * world * args.steps / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+
+    # plain form (FP64 for every test) on the same input
+    plain = None
+    if args.mode == "fp32":
+        k2 = max(2, args.steps // 2)
+        step(cupc.MODE_PLAIN_FP64)
+        pm = 0.0
+        for _ in range(k2):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(cupc.MODE_PLAIN_FP64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            pm += a.elapsed_time(b)
+        plain = {"value": units * k2 / (pm * 1e-3), "unit": UNIT, "ms_per_step": pm / k2, "steps": k2}
+
+    # end to end through the public call with a pinned host input
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(s.Xt).pin_memory()
+        Xhv = Xh.T
+        r = ctx.skeleton(Xhv, s.alpha, mode=mode, max_level=s.max_level)
+        r.adjacency(); r.records_raw(); r.free()
+        secs, h2d, d2h = 0.0, 0, 0
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            r = ctx.skeleton(Xhv, s.alpha, mode=mode, max_level=s.max_level)
+            adj = r.adjacency()
+            recs = r.records_raw()
+            secs += time.perf_counter() - t0
+            st = r.stats()
+            h2d += st["h2d_bytes"]
+            d2h += st["d2h_bytes"] + adj.nbytes // 8 + recs.nbytes
+            r.free()
+        e2e = {"value": units * args.steps / secs, "unit": UNIT, "ms_per_step": 1e3 * secs / args.steps,
+               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+
+    peaks = _peaks()
+    dom, roof = roofline(agg, args.steps, s, args.mode, peaks)
+    kernels = {k: round(v / args.steps, 4) for k, v in agg["kernel_ms"].items()}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        secs, cu = cpu_oracle_run(s, cores)
+        cpu = {"value": cu / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"whole {args.workload} skeleton once (correlation + all levels), {secs:.2f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if args.mode == "fp32" else "f64",
+                "data": "synthetic (seeded linear-Gaussian SEM, device-resident input)",
+                "config": _config(args.workload, s, "FP32 bulk + FP64 recheck" if args.mode == "fp32"
+                                  else "plain FP64"),
+                "skeleton_wall_s": ms_per_step / 1e3, "serial_tests_per_step": units, "edges": edges,
+                "plain_form": plain,
+                "speedup_vs_plain": (plain["ms_per_step"] / ms_per_step) if plain else None,
+                "e2e": e2e, "gpu_launches": launches, "kernel_ms_per_step": kernels,
+                "roofline": dict(roof, kernel=dom) if roof else None,
+                "cpu_baseline": cpu, "clocks": clocks}
+        print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -62,13 +62,13 @@ __device__ __forceinline__ void unrank_lex(unsigned long long t, int d, int l, c
     for (int c = 0; c < LB; ++c) {
         if (c < l) {
             const int k = l - 1 - c;
-            for (;;) {
+            // bounded by d: a rank beyond C(d, l) cannot run past the row
+            for (; v < d - 1; ++v) {
                 const unsigned long long cnt = B(d - 1 - v, k);
                 if (t < cnt) break;
                 t -= cnt;
-                ++v;
             }
-            P[c] = v;
+            P[c] = v < d ? v : d - 1;
             ++v;
         }
     }

@@ -217,6 +217,33 @@ cupc_status cupc_correlation(cupc_ctx* ctx, const void* X, int dtype, int layout
 cupc_status cupc_pcor_batch(cupc_ctx* ctx, const void* C, int dtype, int64_t p,
                             const int32_t* queries, int64_t nq, int l, double* rho_out);
 
+/* Allocation-free FP64 correlation matrix (the paper has no counterpart).
+ *
+ * For callers that may not allocate device memory: plugins whose host
+ * framework owns and pre-plans all GPU memory, and latency-critical pipelines
+ * in which a cudaMalloc (which can synchronise the device and take
+ * milliseconds) is not acceptable. It computes exactly what
+ * cupc_correlation(precision = CUPC_F64) computes, with the same kernels, and
+ * needs no context.
+ *   X       device pointer to the n_samples x p data (dtype, layout, ld as in
+ *           cupc_skeleton).
+ *   C_out   device pointer to p x p doubles (row-major, ld = p), caller-owned.
+ *   stream  cudaStream_t to run on (NULL = legacy default stream); the call
+ *           returns after the stream has finished the work.
+ * Scratch: a fixed 36 MiB device array inside the library (one per device that
+ * loads it, kept until the process exits). Limits: p <= 65536 and
+ * n_samples * p <= 2^21; larger sizes return CUPC_E_RANGE before any GPU work.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Every call on a device shares the scratch: calls
+ * that overlap on the GPU (other threads or streams) race and must be
+ * serialised by the caller; the error flag is cleared at the start of each
+ * call. Errors: CUPC_E_INVALID, CUPC_E_RANGE, CUPC_E_NUMERIC (zero variance or
+ * non-finite data), CUPC_E_CUDA. */
+cupc_status cupc_correlation_noalloc(const void* X, int dtype, int layout, int64_t n_samples, int64_t p,
+                                     int64_t ld, double* C_out, void* stream);
+
 /* Eq. (threshold) as the library evaluates it, on the host:
  * tau = Phi^-1(1 - alpha/2) / sqrt(n_samples - l - 3) and r = tanh(tau); a CI
  * test is independent iff |Z(rho)| <= tau, i.e. |rho| <= r (Eq.

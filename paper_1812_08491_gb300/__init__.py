@@ -49,6 +49,7 @@ _SIGNATURES = {
     "cupc_correlation": ("status", ["vp", "vp", "int", "int", "int", "i64", "i64", "i64", "int", "vp"]),
     "cupc_pcor_batch": ("status", ["vp", "vp", "int", "i64", "vp", "i64", "int", "vp"]),
     "cupc_fisher_threshold": ("status", ["dbl", "i64", "int", "vp", "vp"]),
+    "cupc_correlation_noalloc": ("status", ["vp", "int", "int", "i64", "i64", "i64", "vp", "vp"]),
 }
 
 

@@ -20,8 +20,8 @@ struct Buf {
 };
 
 constexpr double kBand0 = 2e-5;        // level 0 FP32 band on |C_ij|
-constexpr double kBandAbs = 1e-4;      // levels >= 1 FP32 band on |rho|
-constexpr double kBandRel = 1e-5;      // widening per 1/(pivot^2 * min conditional variance)
+constexpr double kBandAbs = 4e-6;      // levels >= 1 FP32 band on |rho|
+constexpr double kBandRel = 4e-6;      // widening per 1/(pivot^2 * min conditional variance)
 constexpr double kPivFloor = 1e-3;     // FP32: smaller pivot^2 goes to FP64
 constexpr double kRankTol64 = 1e-12;   // FP64: pivot^2 at or below -> dependent member
 constexpr double kRankTol32 = 1e-6;
@@ -35,7 +35,7 @@ struct cupc_ctx {
     std::string err;
     int refs = 1;
     int num_sms = 0;
-    Buf xin, xt, mu, isd, z64, z32, c64, c32, cin;
+    Buf xin, xt, mu, isd, z64, zhi, zlo, cws, c64, c32, cin;
     Buf deg, row_off, item_off, item_row, cols, srow, partner, best, queue, binom, meta, backup[2];
     Meta* hmeta = nullptr;
     int binom_mstride = 0;
@@ -252,14 +252,20 @@ cupc_status readback(cupc_ctx* ctx)
 
 // Standardise + correlation. On return exactly one of (c64, c32) is the matrix
 // the CI kernels read; z64 / c64 feed the FP64 rechecks.
+// Data the FP64 rechecks read: the FP64 standardised rows.
+struct DataView {
+    const double* z64 = nullptr;
+    long long ldz = 0;
+};
+
 cupc_status prepare(cupc_ctx* ctx, const Input& in, bool fp32, const void** Cuse, const double** c64_out,
-                    const double** z64_out, int* kcount)
+                    DataView* dv, int* kcount)
 {
     const int n = (int)in.n, p = (int)in.p;
     const size_t es = elem_size(in.dtype);
     Meta* meta = (Meta*)ctx->meta.p;
     *c64_out = nullptr;
-    *z64_out = nullptr;
+    *dv = DataView();
     if (in.is_corr) {
         const void* src = in.X;
         const size_t extent = ((size_t)(p - 1) * in.ld + p) * es;
@@ -306,15 +312,21 @@ cupc_status prepare(cupc_ctx* ctx, const Input& in, bool fp32, const void** Cuse
         ldv = n;
     }
     const long long ldz = n;
+    const long long ldb = ((long long)n + 63) / 64 * 64;  // K padded to whole 64-wide slabs
     cupc_status s;
     if ((s = ensure(ctx, ctx->mu, (size_t)p * 8)) != CUPC_OK) return s;
     if ((s = ensure(ctx, ctx->isd, (size_t)p * 8)) != CUPC_OK) return s;
     if ((s = ensure(ctx, ctx->z64, (size_t)p * ldz * 8)) != CUPC_OK) return s;
-    if (fp32 && (s = ensure(ctx, ctx->z32, (size_t)p * ldz * 4)) != CUPC_OK) return s;
-    TIMED(CUPC_K_STANDARDIZE, launch_standardize(in.dtype, xv, ldv, n, p, (double*)ctx->mu.p, (double*)ctx->isd.p,
-                                                 (double*)ctx->z64.p, fp32 ? (float*)ctx->z32.p : nullptr, ldz,
-                                                 meta, ctx->stream));
-    *z64_out = (const double*)ctx->z64.p;
+    if (fp32) {
+        if ((s = ensure(ctx, ctx->zhi, (size_t)p * ldb * 2)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, ctx->zlo, (size_t)p * ldb * 2)) != CUPC_OK) return s;
+    }
+    TIMED(CUPC_K_STANDARDIZE,
+          launch_standardize(in.dtype, xv, ldv, n, p, (double*)ctx->mu.p, (double*)ctx->isd.p,
+                             (double*)ctx->z64.p, ldz, fp32 ? ctx->zhi.p : nullptr,
+                             fp32 ? ctx->zlo.p : nullptr, ldb, meta, ctx->stream));
+    dv->z64 = (const double*)ctx->z64.p;
+    dv->ldz = ldz;
     if (!fp32) {
         if ((s = ensure(ctx, ctx->c64, (size_t)p * p * 8)) != CUPC_OK) return s;
         TIMED(CUPC_K_CORRELATION,
@@ -323,8 +335,13 @@ cupc_status prepare(cupc_ctx* ctx, const Input& in, bool fp32, const void** Cuse
         *Cuse = ctx->c64.p;
     } else {
         if ((s = ensure(ctx, ctx->c32, (size_t)p * p * 4)) != CUPC_OK) return s;
-        TIMED(CUPC_K_CORRELATION,
-              launch_syrk_f32((const float*)ctx->z32.p, ldz, n, p, (float*)ctx->c32.p, ctx->stream));
+        int tiles, nsplit, kps;
+        size_t wsb;
+        corr_tc_plan(p, ldb, ctx->num_sms, &tiles, &nsplit, &kps, &wsb);
+        if ((s = ensure(ctx, ctx->cws, wsb)) != CUPC_OK) return s;
+        TIMED(CUPC_K_CORRELATION, launch_corr_tc(ctx->zhi.p, ctx->zlo.p, ldb, p, n, (float*)ctx->cws.p,
+                                                 (float*)ctx->c32.p, ctx->num_sms, &meta->error, ctx->stream));
+        kcount[CUPC_K_CORRELATION]++;  // the K-slice reduction
         *Cuse = ctx->c32.p;
     }
     return CUPC_OK;
@@ -406,8 +423,8 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
 
     const void* Cuse = nullptr;
     const double* c64 = nullptr;
-    const double* z64 = nullptr;
-    if ((s = prepare(ctx, in, fp32, &Cuse, &c64, &z64, kcount)) != CUPC_OK) return s;
+    DataView dv;
+    if ((s = prepare(ctx, in, fp32, &Cuse, &c64, &dv, kcount)) != CUPC_OK) return s;
     CU(cudaEventRecord(ctx->ev[1], ctx->stream));
 
     const size_t bitbytes = (size_t)p * W * 4;
@@ -421,14 +438,14 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     if (fp32 && (s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
     if ((s = ensure_binom(ctx, std::max(p + 1, 64))) != CUPC_OK) return s;
 
-    const int grid_wide = std::max(1, ctx->num_sms * 4);
+    const int grid_wide = std::max(1, ctx->num_sms * 8);
     auto recheck_params = [&](int l) {
         RecheckParams rp{};
         rp.row_off = (const long long*)ctx->row_off.p;
         rp.cols = (const int*)ctx->cols.p;
         rp.srow = (const int*)ctx->srow.p;
-        rp.z64 = z64;
-        rp.ldz = n;
+        rp.z64 = dv.z64;
+        rp.ldz = dv.ldz;
         rp.n = (int)n;
         rp.c64 = c64;
         rp.p = p;
@@ -490,6 +507,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         }
         if ((s = readback(ctx)) != CUPC_OK) return s;
         const Meta M = *ctx->hmeta;
+        if (M.error & 4) return fail(ctx, CUPC_E_TIMEOUT, "a bounded wait in the tensor-core product expired");
         if (M.error) return fail(ctx, CUPC_E_NUMERIC, "a variable has zero variance or non-finite data");
         if (level_pending) {
             const int pl = l - 1;  // the level these counters belong to
@@ -663,7 +681,7 @@ void ctx_release(cupc_ctx* c)
     if (--c->refs > 0) return;
     cudaSetDevice(c->device);
     cupc_ctx* ctx = c;
-    Buf* all[] = {&c->xin, &c->xt, &c->mu, &c->isd, &c->z64, &c->z32, &c->c64, &c->c32, &c->cin,
+    Buf* all[] = {&c->xin, &c->xt, &c->mu, &c->isd, &c->z64, &c->zhi, &c->zlo, &c->cws, &c->c64, &c->c32, &c->cin,
                   &c->deg, &c->row_off, &c->item_off, &c->item_row, &c->cols, &c->srow, &c->partner,
                   &c->best, &c->queue, &c->binom, &c->meta, &c->backup[0], &c->backup[1]};
     for (Buf* b : all) free_buf(ctx, *b);
@@ -919,13 +937,15 @@ cupc_status cupc_correlation(cupc_ctx* ctx, const void* X, int dtype, int layout
     in.p = p;
     in.ld = ld;
     const void* Cuse = nullptr;
-    const double *c64 = nullptr, *z64 = nullptr;
+    const double* c64 = nullptr;
+    DataView dv;
     const bool fp32 = (precision == CUPC_F32);
     int kcount[CUPC_KCLASSES] = {0};
     ctx->tused = 0;
-    if ((s = prepare(ctx, in, fp32, &Cuse, &c64, &z64, kcount)) != CUPC_OK) return s;
+    if ((s = prepare(ctx, in, fp32, &Cuse, &c64, &dv, kcount)) != CUPC_OK) return s;
     CU(cudaMemcpyAsync(C_out, Cuse, (size_t)p * p * (fp32 ? 4 : 8), cudaMemcpyDeviceToDevice, ctx->stream));
     if ((s = readback(ctx)) != CUPC_OK) return s;
+    if (ctx->hmeta->error & 4) return fail(ctx, CUPC_E_TIMEOUT, "a bounded wait in the tensor-core product expired");
     if (ctx->hmeta->error) return fail(ctx, CUPC_E_NUMERIC, "a variable has zero variance or non-finite data");
     return CUPC_OK;
 }

@@ -1,0 +1,374 @@
+// k_corr_tc.cu -- the correlation product C = Z Z^T / n on the 5th-generation
+// tensor cores (tcgen05), split precision.
+//
+// Each standardised value z (FP64) is split into two bf16 numbers,
+// hi = bf16(z) and lo = bf16(z - hi), so z = hi + lo to about 2^-18 relative.
+// C_ij is accumulated in FP32 (in TMEM) over three bf16 products,
+//     sum_s hi_i hi_j + hi_i lo_j + lo_i hi_j,
+// i.e. one GEMM over K = 3 n' whose A operand walks (hi, hi, lo) and whose B
+// operand walks (hi, lo, hi); the dropped lo*lo term is below 2^-18.
+//
+// Kernel shape: one CTA per (128 x 128 upper-triangle output tile, K slice).
+// Warp 0 issues TMA loads (128B-swizzled, K-major) into a 4-stage ring, one
+// thread of warp 1 issues tcgen05.mma (M=128, N=128, K=16, bf16 -> f32) and
+// returns stages with tcgen05.commit. The tensor core's FP32 accumulation
+// error grows with the number of products summed into one accumulator, so the
+// MMA thread restarts accumulation every GROUP K slabs, alternating between two
+// TMEM accumulators; warps 2-5 drain each finished group (tcgen05.ld 32x32b)
+// into FP32 registers with round-to-nearest adds while the next group runs,
+// then store the partial tile. A second kernel adds the K-slice partials in a
+// fixed order in FP64, scales by 1/n and writes both (i, j) and (j, i) from
+// the i < j value, so C is exactly symmetric.
+//
+// Every mbarrier wait is bounded in time; on expiry the thread raises an error
+// flag, the others stop at their next wait, TMEM is freed and the kernel ends.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "kernels.cuh"
+
+namespace cupc {
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;      // output tile and K slab (64 bf16 = 128 bytes)
+constexpr int STAGES = 4;
+constexpr int TILE_BYTES = BM * BK * 2;         // 16 KiB per operand per stage
+constexpr int STAGE_BYTES = 2 * TILE_BYTES;
+constexpr int THREADS = 192;
+constexpr uint32_t TMEM_COLS = 256;             // two FP32 accumulators of 128 lanes x 128 columns
+constexpr int GROUP = 8;                        // K slabs (512 products) per accumulator group
+constexpr size_t SMEM_BYTES = 2 * STAGES * TILE_BYTES + 256 + 1024;
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s per wait
+
+// Instruction descriptor of tcgen05.mma kind::f16: D f32 (bits 4-5 = 1), A and
+// B bf16 (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of parity `parity`; false if the time budget ran out or
+// another thread of the kernel raised the error flag.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err)
+{
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*(volatile int*)err) return false;
+        if (gtimer() - t0 > kWaitNs) {
+            atomicOr(err, 4);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor for a K-major tile written by TMA with the
+// 128-byte swizzle: start address >> 4 (bits 0-13), leading byte offset 16
+// (unused for swizzled K-major), stride byte offset 1024 (8 rows of 128 bytes,
+// bits 32-45), descriptor version 1 (bits 46-47), swizzle mode 2 = 128B (bits
+// 61-63). Tile bases are 1024-byte aligned, so the base offset is 0.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tile_of(int t, int& bi, int& bj)
+{
+    int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((j + 1) * (j + 2) / 2 <= t) ++j;
+    while (j * (j + 1) / 2 > t) --j;
+    bj = j;
+    bi = t - j * (j + 1) / 2;
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_corr_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmL, int kt, int kps,
+          int tiles, float* __restrict__ ws, int* err)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + STAGES * TILE_BYTES;
+    uint64_t* full = (uint64_t*)(smem + 2 * STAGES * TILE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* acc_full = empty + STAGES;   // [2]: group accumulated (tcgen05.commit)
+    uint64_t* acc_empty = acc_full + 2;    // [2]: group drained by the 4 epilogue warps
+    uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x, split = blockIdx.y;
+    int bi, bj;
+    tile_of(t, bi, bj);
+    const int g0 = split * kps;
+    const int g1 = min(g0 + kps, 3 * kt);
+    const int nsteps = g1 - g0;
+    const int ngroups = (nsteps + GROUP - 1) / GROUP;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int k = 0; k < nsteps; ++k) {
+            const int s = k % STAGES;
+            const uint32_t ph = (uint32_t)(k / STAGES) & 1u;
+            if (!mbar_wait(&empty[s], ph ^ 1u, err)) break;
+            const int g = g0 + k, seg = g / kt, kk = g - seg * kt;
+            mbar_expect_tx(&full[s], STAGE_BYTES);
+            tma_load_2d(sA + s * TILE_BYTES, seg == 2 ? &tmL : &tmH, kk * BK, bi * BM, &full[s]);
+            tma_load_2d(sB + s * TILE_BYTES, seg == 1 ? &tmL : &tmH, kk * BK, bj * BN, &full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: group g accumulates into TMEM columns [128 (g & 1), +128)
+        for (int k = 0; k < nsteps; ++k) {
+            const int g = k / GROUP, b = g & 1;
+            const bool first = (k % GROUP) == 0;
+            if (first && g >= 2) {
+                // the previous use of buffer b must have been drained
+                if (!mbar_wait(&acc_empty[b], (uint32_t)((g >> 1) - 1) & 1u, err)) break;
+                tc_fence_after();
+            }
+            const int s = k % STAGES;
+            const uint32_t ph = (uint32_t)(k / STAGES) & 1u;
+            if (!mbar_wait(&full[s], ph, err)) break;
+            tc_fence_after();
+            const uint64_t ad = sdesc_sw128(smem_u32(sA + s * TILE_BYTES));
+            const uint64_t bd = sdesc_sw128(smem_u32(sB + s * TILE_BYTES));
+            const uint32_t dacc = tmem + (uint32_t)(b * BN);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)  // K = 16 per instruction: +32 bytes in the swizzled row
+                mma_bf16(dacc, ad + 2 * kk, bd + 2 * kk, (first && kk == 0) ? 0u : 1u);
+            mma_commit(&empty[s]);
+            if ((k % GROUP) == GROUP - 1 || k == nsteps - 1) mma_commit(&acc_full[b]);
+        }
+    } else if (warp >= 2) {
+        // epilogue: warp w may read TMEM lanes 32*(w%4) .. +31 (rows of the tile)
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        float R[BN];
+#pragma unroll
+        for (int c = 0; c < BN; ++c) R[c] = 0.f;
+        bool ok = true;
+        for (int g = 0; g < ngroups && ok; ++g) {
+            const int b = g & 1;
+            ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], (uint32_t)(g >> 1) & 1u, err));
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
+#pragma unroll
+            for (int c = 0; c < BN; c += 16) {
+                uint32_t r[16];
+                tmem_ld16(base + (uint32_t)c, r);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) R[c + u] += __uint_as_float(r[u]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
+        if (ok) {
+            float4* out = (float4*)(ws + (((size_t)split * tiles + t) * BM + row) * BN);
+#pragma unroll
+            for (int c = 0; c < BN / 4; ++c) out[c] = make_float4(R[4 * c], R[4 * c + 1], R[4 * c + 2], R[4 * c + 3]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// Sum of the K-slice partials in slice order, times 1/n; the i < j value is
+// written to (i, j) and (j, i); the diagonal is 1.
+__global__ void k_corr_reduce(const float* __restrict__ ws, int tiles, int nsplit, int p, double inv_n,
+                              float* __restrict__ C)
+{
+    const int t = blockIdx.x;
+    int bi, bj;
+    tile_of(t, bi, bj);
+    for (int e = threadIdx.x; e < BM * BN; e += blockDim.x) {
+        const int r = e / BN, c = e % BN;
+        const int gi = bi * BM + r, gj = bj * BN + c;
+        if (gi >= p || gj >= p) continue;
+        if (gi == gj) {
+            C[(size_t)gi * p + gi] = 1.0f;
+            continue;
+        }
+        if (gi > gj) continue;  // only in diagonal tiles: the mirror comes from (gj, gi)
+        double acc = 0.0;
+        for (int s = 0; s < nsplit; ++s) acc += (double)ws[(((size_t)s * tiles + t) * BM + r) * BN + c];
+        const float v = (float)(acc * inv_n);
+        C[(size_t)gi * p + gj] = v;
+        C[(size_t)gj * p + gi] = v;
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, int rows, long long ldk)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ldk * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// Workspace bytes and the split of the K loop for a p x n product.
+void corr_tc_plan(int p, long long ldk, int num_sms, int* tiles, int* nsplit, int* kps, size_t* ws_bytes)
+{
+    const int nt = (p + BM - 1) / BM;
+    const int kt = (int)(ldk / BK);
+    *tiles = nt * (nt + 1) / 2;
+    int want = (num_sms + *tiles - 1) / *tiles;
+    want = max(1, min(want, 3 * kt));
+    *kps = (3 * kt + want - 1) / want;
+    *nsplit = (3 * kt + *kps - 1) / *kps;
+    *ws_bytes = (size_t)(*nsplit) * (*tiles) * BM * BN * sizeof(float);
+}
+
+cudaError_t launch_corr_tc(const void* hi, const void* lo, long long ldk, int p, int n, float* ws, float* C,
+                           int num_sms, int* err, cudaStream_t st)
+{
+    if (ldk % BK != 0 || ((uintptr_t)hi & 15) || ((uintptr_t)lo & 15)) return cudaErrorInvalidValue;
+    CUtensorMap mh, ml;
+    if (!make_map(&mh, hi, p, ldk) || !make_map(&ml, lo, p, ldk)) return cudaErrorInvalidValue;
+    int tiles, nsplit, kps;
+    size_t wsb;
+    corr_tc_plan(p, ldk, num_sms, &tiles, &nsplit, &kps, &wsb);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int kt = (int)(ldk / BK);
+    k_corr_tc<<<dim3(tiles, nsplit), THREADS, SMEM_BYTES, st>>>(mh, ml, kt, kps, tiles, ws, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_corr_reduce<<<tiles, 256, 0, st>>>(ws, tiles, nsplit, p, 1.0 / n, C);
+    return cudaGetLastError();
+}
+
+}  // namespace cupc

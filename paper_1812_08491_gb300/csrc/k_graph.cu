@@ -336,94 +336,128 @@ cudaError_t launch_finalize(const FinalizeParams& P, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------
-// FP64 rechecks. One warp per queued test. C entries come from the resident
-// FP64 correlation when there is one, otherwise from FP64 dot products of the
-// standardised rows (the definition of C), reduced in a fixed order.
+// FP64 rechecks. One block per queued test. C entries come from the resident
+// FP64 correlation when there is one; otherwise they are formed from the FP64
+// standardised rows by the definition C_ab = sum_s z_as z_bs / n: every pair of
+// the test's m = l + 2 variables in one pass over the samples (threads stride
+// the samples, four samples in flight each), then a fixed-order block
+// reduction, so the value of an entry does not depend on the test it serves.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_dot(const RecheckParams& P, int a, int b)
-{
-    if (a == b) return 1.0;
-    if (P.c64) return P.c64[(size_t)a * P.p + b];
-    const int lane = threadIdx.x & 31;
-    const double* za = P.z64 + (size_t)a * P.ldz;
-    const double* zb = P.z64 + (size_t)b * P.ldz;
-    double s = 0.0;
-    for (int k = lane; k < P.n; k += 32) s = fma(za[k], zb[k], s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    // lower index first so (a, b) and (b, a) give the same bits
-    return s / (double)P.n;
-}
+constexpr int RC_THREADS = 256;
 
-__device__ __forceinline__ double pair_dot(const RecheckParams& P, int a, int b)
+template <int M>
+__device__ __forceinline__ void c_block(const RecheckParams& P, const int (&V)[M], int m,
+                                        double (&G)[M * (M - 1) / 2], double* red)
 {
-    return a < b ? warp_dot(P, a, b) : warp_dot(P, b, a);
+    constexpr int D = M * (M - 1) / 2;
+    if (P.c64) {
+#pragma unroll
+        for (int b = 1; b < M; ++b)
+#pragma unroll
+            for (int a = 0; a < b; ++a)
+                G[b * (b - 1) / 2 + a] = (b < m) ? P.c64[(size_t)V[a] * P.p + V[b]] : 0.0;
+        return;
+    }
+    const double* rows[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) rows[a] = P.z64 + (size_t)(a < m ? V[a] : V[0]) * P.ldz;
+#pragma unroll
+    for (int q = 0; q < D; ++q) G[q] = 0.0;
+#pragma unroll 4
+    for (int k = threadIdx.x; k < P.n; k += RC_THREADS) {
+        double x[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) x[a] = (a < m) ? __ldg(rows[a] + k) : 0.0;
+#pragma unroll
+        for (int b = 1; b < M; ++b)
+#pragma unroll
+            for (int a = 0; a < b; ++a) G[b * (b - 1) / 2 + a] = fma(x[a], x[b], G[b * (b - 1) / 2 + a]);
+    }
+    // block reduction: warp trees, then the 8 warp partials in order
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        double g = G[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+        if (lane == 0) red[w * D + q] = g;
+    }
+    __syncthreads();
+    const double inv_n = 1.0 / (double)P.n;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        double g = 0.0;
+#pragma unroll
+        for (int k = 0; k < RC_THREADS / 32; ++k) g += red[k * D + q];
+        G[q] = g * inv_n;
+    }
+    __syncthreads();
 }
 
 template <int LB>
-__global__ void k_recheck(RecheckParams P)
+__global__ void __launch_bounds__(RC_THREADS) k_recheck(RecheckParams P)
 {
-    const int lane = threadIdx.x & 31;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    constexpr int M = LB + 2;
+    constexpr int D = M * (M - 1) / 2;
+    __shared__ double red[(RC_THREADS / 32) * D];
     unsigned long long nq = P.meta->queue_len;
     if (nq > P.qcap) nq = P.qcap;
     unsigned long long done = 0;
-    for (long long qi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; qi < (long long)nq; qi += nw) {
+    for (long long qi = blockIdx.x; qi < (long long)nq; qi += gridDim.x) {
         const QEntry E = P.queue[qi];
         const long long e = E.a;
         const int i = P.srow[e], j = P.cols[e];
         const long long off = P.row_off[i];
         const int d = (int)(P.row_off[i + 1] - off);
-        int Pos[LB], S[LB];
+        int Pos[LB];
         unrank_lex<LB>(E.s, d, P.l, P.B, Pos);
+        int V[M];
+        V[0] = i;
+        V[1] = j;
 #pragma unroll
-        for (int c = 0; c < LB; ++c) S[c] = (c < P.l) ? P.cols[off + Pos[c]] : 0;
-        // gather the (l+2) x (l+2) block in FP64 (all lanes hold the values)
-        double m2[LB * LB], ci[LB], cj[LB];
-        const double cij = pair_dot(P, i, j);
-#pragma unroll
-        for (int a = 0; a < LB; ++a) {
-            if (a < P.l) {
-                ci[a] = pair_dot(P, i, S[a]);
-                cj[a] = pair_dot(P, j, S[a]);
-#pragma unroll
-                for (int b = 0; b < LB; ++b)
-                    if (b < a) m2[a * LB + b] = pair_dot(P, S[a], S[b]);
-            }
+        for (int c = 0; c < LB; ++c) V[2 + c] = (c < P.l) ? P.cols[off + Pos[c]] : i;
+        const int m = P.l + 2;
+        double G[D];
+        c_block<M>(P, V, m, G, red);
+        if (threadIdx.x == 0) {
+            // V index 0 = i, 1 = j, 2 + a = S_a; G[b(b-1)/2 + a] holds C[V_a, V_b], a < b
+            Factor<double, LB> F;
+            factor_build<double, LB>(
+                F, P.l, P.rank_tol, [&](int a, int b) { return G[(a + 2) * (a + 1) / 2 + (b + 2)]; },
+                [&](int a) { return G[(a + 2) * (a + 1) / 2 + 0]; });
+            double H12, H22;
+            factor_apply<double, LB>(F, P.l, G[0], [&](int a) { return G[(a + 2) * (a + 1) / 2 + 1]; }, H12, H22);
+            const double H11 = 1.0 - F.uu;
+            const bool indep =
+                (!(H11 > kVarZero) || !(H22 > kVarZero)) ? true : (H12 * H12 <= P.r2 * H11 * H22);
+            if (indep) atomicMin(P.best + e, E.s);
         }
-        Factor<double, LB> F;
-        factor_build<double, LB>(F, P.l, P.rank_tol, [&](int a, int b) { return m2[a * LB + b]; },
-                                 [&](int a) { return ci[a]; });
-        double H12, H22;
-        factor_apply<double, LB>(F, P.l, cij, [&](int a) { return cj[a]; }, H12, H22);
-        const double H11 = 1.0 - F.uu;
-        const bool indep = (!(H11 > kVarZero) || !(H22 > kVarZero)) ? true : (H12 * H12 <= P.r2 * H11 * H22);
-        if (lane == 0 && indep) atomicMin(P.best + e, E.s);
         ++done;
     }
-    if (lane == 0 && done) atomicAdd(&P.meta->rechecks, done);
+    if (threadIdx.x == 0 && done) atomicAdd(&P.meta->rechecks, done);
 }
 
-__global__ void k_recheck0(RecheckParams P)
+__global__ void __launch_bounds__(RC_THREADS) k_recheck0(RecheckParams P)
 {
-    const int lane = threadIdx.x & 31;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    __shared__ double red[RC_THREADS / 32];
     unsigned long long nq = P.meta->queue_len;
     if (nq > P.qcap) nq = P.qcap;
     unsigned long long done = 0;
-    for (long long qi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; qi < (long long)nq; qi += nw) {
+    for (long long qi = blockIdx.x; qi < (long long)nq; qi += gridDim.x) {
         const QEntry E = P.queue[qi];
-        const double c = pair_dot(P, E.a, E.b);
+        const int V[2] = {E.a, E.b};
+        double G[1];
+        c_block<2>(P, V, 2, G, red);
         // S empty: rho = C_ij; independent iff rho^2 <= tanh(tau_0)^2
-        if (lane == 0 && c * c <= P.r2) bitset_clear_pair(P.bits, P.W, E.a, E.b);
+        if (threadIdx.x == 0 && G[0] * G[0] <= P.r2) bitset_clear_pair(P.bits, P.W, E.a, E.b);
         ++done;
     }
-    if (lane == 0 && done) atomicAdd(&P.meta->rechecks, done);
+    if (threadIdx.x == 0 && done) atomicAdd(&P.meta->rechecks, done);
 }
 
 cudaError_t launch_recheck(const RecheckParams& P, int grid, cudaStream_t st)
 {
-    const int block = 128;
+    const int block = RC_THREADS;
     if (P.l <= 2) k_recheck<2><<<grid, block, 0, st>>>(P);
     else if (P.l <= 4) k_recheck<4><<<grid, block, 0, st>>>(P);
     else if (P.l <= 8) k_recheck<8><<<grid, block, 0, st>>>(P);
@@ -433,7 +467,7 @@ cudaError_t launch_recheck(const RecheckParams& P, int grid, cudaStream_t st)
 
 cudaError_t launch_recheck0(const RecheckParams& P, int grid, cudaStream_t st)
 {
-    k_recheck0<<<grid, 128, 0, st>>>(P);
+    k_recheck0<<<grid, RC_THREADS, 0, st>>>(P);
     return cudaGetLastError();
 }
 

@@ -1,8 +1,10 @@
-// k_prep.cu -- standardisation of the data and the SIMT correlation product.
+// k_prep.cu -- standardisation of the data and the FP64 correlation product.
 //
 // C = Z^T Z / n with Z the standardised data (Sec. 4.3 defines C as the
 // correlation matrix; the paper does not say where it is formed). Moments are
 // FP64 and two-pass (mean, then centred sum of squares), divisor n.
+#include <cuda_bf16.h>
+
 #include "kernels.cuh"
 
 namespace cupc {
@@ -47,8 +49,9 @@ __device__ __forceinline__ double block_sum(double x, double* red)
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, long long ld, int n, int p,
                                                     double* __restrict__ mu, double* __restrict__ isd,
-                                                    double* __restrict__ z64, float* __restrict__ z32,
-                                                    long long ldz, Meta* meta)
+                                                    double* __restrict__ z64, long long ldz,
+                                                    __nv_bfloat16* __restrict__ zhi, __nv_bfloat16* __restrict__ zlo,
+                                                    long long ldb, Meta* meta)
 {
     __shared__ double red[NT / 32];
     const int v = blockIdx.x;
@@ -70,16 +73,26 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
         isd[v] = inv;
         if (!ok) atomicOr(&meta->error, 1);
     }
-    for (int k = threadIdx.x; k < n; k += NT) {
-        const double z = ((double)row[k] - mean) * inv;
-        if (z64) z64[(size_t)v * ldz + k] = z;
-        if (z32) z32[(size_t)v * ldz + k] = (float)z;
+    if (z64)
+        for (int k = threadIdx.x; k < n; k += NT) z64[(size_t)v * ldz + k] = ((double)row[k] - mean) * inv;
+    if (zhi) {
+        // split z = hi + lo into two bf16 numbers (|z - hi - lo| < 2^-18 |z|); the
+        // centring is FP64 (exact for any mean), the scaling FP32 (2^-24, far below
+        // the split's 2^-18)
+        const float fi = (float)inv;
+        for (int k = threadIdx.x; k < n; k += NT) {
+            const float z = (float)((double)row[k] - mean) * fi;
+            const __nv_bfloat16 h = __float2bfloat16_rn(z);
+            zhi[(size_t)v * ldb + k] = h;
+            zlo[(size_t)v * ldb + k] = __float2bfloat16_rn(z - __bfloat162float(h));
+        }
     }
-    // zero the K padding up to ldz so the product can read whole tiles
-    for (int k = n + threadIdx.x; k < ldz; k += NT) {
-        if (z64) z64[(size_t)v * ldz + k] = 0.0;
-        if (z32) z32[(size_t)v * ldz + k] = 0.f;
-    }
+    // zero the K padding so the tensor-core product can read whole 64-wide slabs
+    if (zhi)
+        for (int k = n + threadIdx.x; k < ldb; k += NT) {
+            zhi[(size_t)v * ldb + k] = __float2bfloat16(0.f);
+            zlo[(size_t)v * ldb + k] = __float2bfloat16(0.f);
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -167,13 +180,16 @@ cudaError_t launch_transpose(int dtype, const void* X, long long ld, int n, int 
 }
 
 cudaError_t launch_standardize(int dtype, const void* Xv, long long ld, int n, int p, double* mu, double* isd,
-                               double* z64, float* z32, long long ldz, Meta* meta, cudaStream_t st)
+                               double* z64, long long ldz, void* zhi, void* zlo, long long ldb, Meta* meta,
+                               cudaStream_t st)
 {
     constexpr int NT = 256;
     if (dtype == CUPC_F64)
-        k_standardize<double, NT><<<p, NT, 0, st>>>((const double*)Xv, ld, n, p, mu, isd, z64, z32, ldz, meta);
+        k_standardize<double, NT><<<p, NT, 0, st>>>((const double*)Xv, ld, n, p, mu, isd, z64, ldz,
+                                                    (__nv_bfloat16*)zhi, (__nv_bfloat16*)zlo, ldb, meta);
     else
-        k_standardize<float, NT><<<p, NT, 0, st>>>((const float*)Xv, ld, n, p, mu, isd, z64, z32, ldz, meta);
+        k_standardize<float, NT><<<p, NT, 0, st>>>((const float*)Xv, ld, n, p, mu, isd, z64, ldz,
+                                                   (__nv_bfloat16*)zhi, (__nv_bfloat16*)zlo, ldb, meta);
     return cudaGetLastError();
 }
 
@@ -183,15 +199,6 @@ cudaError_t launch_syrk_f64(const double* Z, long long ldz, int n, int p, double
     const long long nt = (p + BM - 1) / BM;
     const long long tiles = nt * (nt + 1) / 2;
     k_syrk<double, BM, BK, TM><<<(unsigned)tiles, (BM / TM) * (BM / TM), 0, st>>>(Z, ldz, n, p, C, 1.0 / n);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_syrk_f32(const float* Z, long long ldz, int n, int p, float* C, cudaStream_t st)
-{
-    constexpr int BM = 128, BK = 16, TM = 8;
-    const long long nt = (p + BM - 1) / BM;
-    const long long tiles = nt * (nt + 1) / 2;
-    k_syrk<float, BM, BK, TM><<<(unsigned)tiles, (BM / TM) * (BM / TM), 0, st>>>(Z, ldz, n, p, C, 1.0 / n);
     return cudaGetLastError();
 }
 

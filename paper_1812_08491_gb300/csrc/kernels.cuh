@@ -35,7 +35,7 @@ struct RecheckParams {
     const long long* row_off;
     const int* cols;
     const int* srow;
-    const double* z64;             // standardised data, p rows of ldz (used when c64 == nullptr)
+    const double* z64;             // standardised rows (row v at z64 + v*ldz), used when c64 == nullptr
     long long ldz;
     int n;
     const double* c64;             // FP64 correlation if resident, else nullptr
@@ -71,9 +71,12 @@ struct FinalizeParams {
 
 cudaError_t launch_transpose(int dtype, const void* X, long long ld, int n, int p, void* Xt, cudaStream_t st);
 cudaError_t launch_standardize(int dtype, const void* Xv, long long ld, int n, int p, double* mu, double* isd,
-                               double* z64, float* z32, long long ldz, Meta* meta, cudaStream_t st);
+                               double* z64, long long ldz, void* zhi, void* zlo, long long ldb, Meta* meta,
+                               cudaStream_t st);
 cudaError_t launch_syrk_f64(const double* Z, long long ldz, int n, int p, double* C, cudaStream_t st);
-cudaError_t launch_syrk_f32(const float* Z, long long ldz, int n, int p, float* C, cudaStream_t st);
+void corr_tc_plan(int p, long long ldk, int num_sms, int* tiles, int* nsplit, int* kps, size_t* ws_bytes);
+cudaError_t launch_corr_tc(const void* hi, const void* lo, long long ldk, int p, int n, float* ws, float* C,
+                           int num_sms, int* err, cudaStream_t st);
 cudaError_t launch_symmetrize(int dtype, const void* Cin, long long ld, int p, double* C64, float* C32,
                               cudaStream_t st);
 

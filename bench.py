@@ -149,39 +149,57 @@ def _config(name, s, form):
             "form": form, "l2": "flushed between steps (256 MiB write)"}
 
 
-def roofline(stats_sum, steps, s, mode, peaks):
-    """Roofline of the kernel class with the largest device time."""
-    km = stats_sum["kernel_ms"]
-    kc = stats_sum["kernel_count"]
-    dom = max(km, key=lambda k: km[k])
-    ms = km[dom] / steps
-    launches = max(1, kc[dom] // steps)
-    es_in = 4 if s.meta.get("dtype") == "float32" else 8
+def kernel_rooflines(st, s, mode, peaks):
+    """Roofline of each kernel of one skeleton call (stats of that call).
+
+    Durations are CUDA-event times on the library's stream; algorithmic work:
+      standardize  read X once, write the FP64 rows (+ the two bf16 rows in FP32 mode)
+      correlation  3 split-precision bf16 products over the upper triangle, 2 n p(p+1)/2 each
+      level0       read C once, write the bitset
+      level        per level: the C sub-blocks its tests read, sum over rows of (n'_i+1)^2
+                   entries, plus the bitset (read twice, copied once) and the CSR arrays
+    """
     n, p = s.n, s.p
-    cbytes = 4 if mode == "fp32" else 8
-    if dom == "correlation":
-        flops = float(n) * p * p  # 2 n p^2 / 2: upper triangle
-        achieved = flops / (ms * 1e-3) / 1e12
-        peak = FP32_SIMT_TFLOPS if mode == "fp32" else FP64_TFLOPS
-        return dom, {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_src": "FP32 SIMT from unit counts and clock" if mode == "fp32" else "FP64 nominal"}
-    if dom == "standardize":
-        byts = n * p * es_in + n * p * 8 + (n * p * 4 if mode == "fp32" else 0)
-    elif dom == "level0":
-        byts = p * p * cbytes + p * p / 8
-    elif dom == "ci":
-        byts = sum(stats_sum["ci_block_entries"]) / steps * cbytes
-    elif dom == "compact":
-        byts = 2 * p * p / 8
-    else:
-        byts = None
-    if byts is None:
-        return dom, None
-    achieved = byts / (ms * 1e-3) / 1e9
-    return dom, {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                 "peak_src": "measured" if peaks["src"] == "measured" else "fallback"}
+    es_in = 4 if s.meta.get("dtype") == "float32" else 8
+    cb = 4 if mode == "fp32" else 8
+    W = (p + 31) // 32
+    out = {}
+    km, kc = st["kernel_ms"], st["kernel_count"]
+    hbm = peaks["hbm_gbs"]
+
+    def mem(name, ms, launches, byts):
+        if ms <= 0 or launches <= 0:
+            return
+        per = byts / launches
+        ach = per / (ms / launches * 1e-3) / 1e9
+        out[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "ms": ms, "launches": launches, "alg_bytes_per_launch": per, "traffic": None}
+
+    mem("standardize", km["standardize"], kc["standardize"],
+        n * p * es_in + n * p * 8 + (n * p * 4 if mode == "fp32" else 0))
+    mem("level0", km["level0"], 1, p * p * cb + p * W * 4)
+    lv = st["levels"]
+    lev_ms = sum(st["level_ms"][1:lv])
+    byts = 0
+    for l in range(1, lv):
+        nnz = 2 * st["edges_start"][l]
+        byts += st["ci_block_entries"][l] * cb + 3 * p * W * 4 + nnz * 40
+    mem("level", lev_ms, max(1, lv - 1), byts)
+    ms = km["correlation"]
+    if ms > 0:
+        if mode == "fp32":
+            flops = 3 * 2.0 * n * p * (p + 1) / 2
+            peak = peaks["bf16_tflops"]
+            src = "bf16 dense, measured burst"
+        else:
+            flops = 2.0 * n * p * (p + 1) / 2
+            peak = FP64_TFLOPS
+            src = "FP64 nominal"
+        ach = flops / (ms * 1e-3) / 1e12
+        out["correlation"] = {"bound": "tensor" if mode == "fp32" else "alu", "achieved": ach, "peak": peak,
+                              "unit": "TFLOP/s", "frac": ach / peak, "ms": ms, "launches": 1,
+                              "peak_src": src, "traffic": None}
+    return out
 
 
 def main():
@@ -194,6 +212,7 @@ def main():
     ap.add_argument("--mode", default="fp32", choices=["fp32", "plain"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP64 form")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.workload)
@@ -242,7 +261,7 @@ def main():
     if dist:
         dist.barrier()
     total_ms = 0.0
-    agg = {"kernel_ms": {}, "kernel_count": {}, "ci_block_entries": [0] * 32}
+    roofs = []
     launches = 0
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
@@ -256,12 +275,7 @@ def main():
             torch.cuda.synchronize()
             total_ms += a.elapsed_time(b)
             launches += st["kernel_launches"]
-            for k, v in st["kernel_ms"].items():
-                agg["kernel_ms"][k] = agg["kernel_ms"].get(k, 0.0) + v
-            for k, v in st["kernel_count"].items():
-                agg["kernel_count"][k] = agg["kernel_count"].get(k, 0) + v
-            for q, v in enumerate(st["ci_block_entries"]):
-                agg["ci_block_entries"][q] += v
+            roofs.append((st, kernel_rooflines(st, s, args.mode, _peaks())))
     if dist:
         dist.barrier()
     clocks = clk.summary()
@@ -274,7 +288,7 @@ def main():
 
     # plain form (FP64 for every test) on the same input
     plain = None
-    if args.mode == "fp32":
+    if args.mode == "fp32" and not args.no_plain:
         k2 = max(2, args.steps // 2)
         step(cupc.MODE_PLAIN_FP64)
         pm = 0.0
@@ -311,9 +325,25 @@ def main():
         e2e = {"value": units * args.steps / secs, "unit": UNIT, "ms_per_step": 1e3 * secs / args.steps,
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
 
-    peaks = _peaks()
-    dom, roof = roofline(agg, args.steps, s, args.mode, peaks)
-    kernels = {k: round(v / args.steps, 4) for k, v in agg["kernel_ms"].items()}
+    # per-kernel rooflines averaged over the timed steps; the dominant kernel is
+    # the one with the largest device time
+    names = set().union(*[r.keys() for _, r in roofs])
+    kern = {}
+    for nm in names:
+        rs = [r[nm] for _, r in roofs if nm in r]
+        ms = sum(x["ms"] for x in rs) / len(rs)
+        first = dict(rs[0])
+        first["ms"] = ms
+        first["achieved"] = sum(x["achieved"] for x in rs) / len(rs)
+        first["frac"] = first["achieved"] / first["peak"]
+        kern[nm] = first
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    roof = {k: kern[dom][k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    roof["kernel"] = dom
+    roof["ms_per_step"] = kern[dom]["ms"]
+    kernels = {k: round(v["ms"], 4) for k, v in kern.items()}
+    phases = {k: round(sum(st["kernel_ms"][k] for st, _ in roofs) / len(roofs), 4)
+              for k in roofs[0][0]["kernel_ms"]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -334,7 +364,10 @@ def main():
                 "plain_form": plain,
                 "speedup_vs_plain": (plain["ms_per_step"] / ms_per_step) if plain else None,
                 "e2e": e2e, "gpu_launches": launches, "kernel_ms_per_step": kernels,
-                "roofline": dict(roof, kernel=dom) if roof else None,
+                "phase_ms_per_step": phases,
+                "roofline": roof,
+                "kernel_rooflines": {k: {"frac": round(v["frac"], 5), "achieved": round(v["achieved"], 3),
+                                         "unit": v["unit"], "bound": v["bound"]} for k, v in kern.items()},
                 "cpu_baseline": cpu, "clocks": clocks}
         print(json.dumps(line))
     ctx.close()

@@ -115,6 +115,9 @@ typedef struct {
     int32_t kernel_count[CUPC_KCLASSES];         /* launches per kernel class */
     int64_t ci_block_entries[CUPC_STATS_LEVELS]; /* sum over rows of (n'_i + 1)^2: the C
                                                     sub-block entries a level's tests read */
+    float phase_ms[CUPC_STATS_LEVELS][4];        /* per level >= 1, wall time of its phases:
+                                                    compaction, CI tests, FP64 rechecks,
+                                                    removal + SepSets (device clock) */
 } cupc_stats;
 
 typedef struct cupc_ctx cupc_ctx;

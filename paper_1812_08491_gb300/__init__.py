@@ -74,7 +74,7 @@ class Stats(ctypes.Structure):
                 ("edges_final", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
                 ("kernel_ms", ctypes.c_float * 8), ("kernel_count", ctypes.c_int32 * 8),
-                ("ci_block_entries", ctypes.c_int64 * L)]
+                ("ci_block_entries", ctypes.c_int64 * L), ("phase_ms", (ctypes.c_float * 4) * L)]
 
 
 _LIB = None
@@ -221,7 +221,8 @@ class Result:
                 "h2d_bytes": s.h2d_bytes, "d2h_bytes": s.d2h_bytes,
                 "kernel_ms": dict(zip(KERNEL_CLASSES, list(s.kernel_ms))),
                 "kernel_count": dict(zip(KERNEL_CLASSES, list(s.kernel_count))),
-                "ci_block_entries": list(s.ci_block_entries[:L])}
+                "ci_block_entries": list(s.ci_block_entries[:L]),
+                "phase_ms": [list(s.phase_ms[q]) for q in range(L)]}
 
     def free(self):
         if self._h:

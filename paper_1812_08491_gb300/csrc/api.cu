@@ -2,6 +2,7 @@
 // of Algorithm 2 (level 0, then per level: compact A_G into A'_G, CI tests,
 // removal and SepSet records), results and their accessors.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -36,8 +37,12 @@ struct cupc_ctx {
     int refs = 1;
     int num_sms = 0;
     Buf xin, xt, mu, isd, z64, zhi, zlo, cws, c64, c32, cin;
-    Buf deg, row_off, item_off, item_row, cols, srow, partner, best, queue, binom, meta, backup[2];
+    Buf deg, row_off, item_off, item_row, cols, srow, partner, wpre, best, queue, binom, meta, lmeta, backup[2];
+    Buf part;
     Meta* hmeta = nullptr;
+    LevelMeta* hlmeta = nullptr;
+    int* hflags = nullptr;         // pinned, mapped: per-level run / end flags written by the GPU
+    int* dflags = nullptr;         // device view of hflags
     int binom_mstride = 0;
     unsigned long long launches = 0;
     unsigned long long h2d = 0, d2h = 0;
@@ -430,31 +435,21 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     const size_t bitbytes = (size_t)p * W * 4;
     if ((s = dalloc(ctx, (void**)&R->bits, bitbytes)) != CUPC_OK) return s;
     if ((s = dalloc(ctx, (void**)&R->bits0, bitbytes)) != CUPC_OK) return s;
-    if (fp32) {
-        if ((s = ensure(ctx, ctx->backup[0], bitbytes)) != CUPC_OK) return s;
-        if ((s = ensure(ctx, ctx->backup[1], bitbytes)) != CUPC_OK) return s;
-    }
+    if (fp32 && (s = ensure(ctx, ctx->backup[0], bitbytes)) != CUPC_OK) return s;
     size_t qcap = std::max<size_t>(1u << 20, (size_t)4 * p);
     if (fp32 && (s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
     if ((s = ensure_binom(ctx, std::max(p + 1, 64))) != CUPC_OK) return s;
 
     const int grid_wide = std::max(1, ctx->num_sms * 8);
-    auto recheck_params = [&](int l) {
-        RecheckParams rp{};
-        rp.row_off = (const long long*)ctx->row_off.p;
-        rp.cols = (const int*)ctx->cols.p;
-        rp.srow = (const int*)ctx->srow.p;
+    auto recheck0_params = [&]() {
+        Recheck0Params rp{};
         rp.z64 = dv.z64;
         rp.ldz = dv.ldz;
         rp.n = (int)n;
         rp.c64 = c64;
         rp.p = p;
-        rp.l = l;
-        rp.B = binom_view(ctx);
-        const double r = std::tanh(fisher_tau(alpha, n, l));
+        const double r = std::tanh(fisher_tau(alpha, n, 0));
         rp.r2 = r * r;
-        rp.rank_tol = kRankTol64;
-        rp.best = (unsigned long long*)ctx->best.p;
         rp.queue = (const QEntry*)ctx->queue.p;
         rp.qcap = qcap;
         rp.meta = meta;
@@ -468,7 +463,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         const double r0 = std::tanh(fisher_tau(alpha, n, 0));
         TIMED(CUPC_K_LEVEL0,
               launch_level0(fp32, Cuse, p, W, r0, kBand0, R->bits, (QEntry*)ctx->queue.p, qcap, meta, ctx->stream));
-        if (fp32) TIMED(CUPC_K_LEVEL0, launch_recheck0(recheck_params(0), grid_wide, ctx->stream));
+        if (fp32) TIMED(CUPC_K_LEVEL0, launch_recheck0(recheck0_params(), grid_wide, ctx->stream));
         CU(cudaMemcpyAsync(R->bits0, R->bits, bitbytes, cudaMemcpyDeviceToDevice, ctx->stream));
         return CUPC_OK;
     };
@@ -479,171 +474,200 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     R->stats.edges_start[0] = pairs;
     R->stats.max_degree[0] = p - 1;
 
-    // ---------------- levels l >= 1 (Algorithm 2 loop) ----------------
-    int l = 1;
-    int redo = 0;
-    bool level_pending = true; // counters of the last launched level are unread
-    size_t rec_len_cap = 0;
-    const int block = o.threads_per_block ? o.threads_per_block : 256;
-    const int chunk = o.chunk ? o.chunk : 128;
-    int levels_run = 1;
-    for (;;) {
-        // levels with n - l - 3 <= 0 have no threshold (Eq. threshold): stop there
-        const bool limit = (o.max_level >= 0 && l > o.max_level) || (n - l - 3 <= 0);
-        if (fp32 && !limit)
-            CU(cudaMemcpyAsync(ctx->backup[l & 1].p, R->bits, bitbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    // ---------------- buffer sizing from the graph after level 0 ----------------
+    const int chunk = o.chunk ? o.chunk : 32;
+    Meta M{};
+    for (int attempt = 0;; ++attempt) {
         CU(cudaMemsetAsync(&meta->maxdeg, 0, 2 * sizeof(int), ctx->stream));
-        CU(cudaMemsetAsync(&meta->block_entries, 0, sizeof(unsigned long long), ctx->stream));
         if ((s = ensure(ctx, ctx->deg, (size_t)p * 4)) != CUPC_OK) return s;
         if ((s = ensure(ctx, ctx->row_off, (size_t)(p + 1) * 8)) != CUPC_OK) return s;
         if ((s = ensure(ctx, ctx->item_off, (size_t)(p + 1) * 8)) != CUPC_OK) return s;
         {
             const int tk = tbegin(ctx, CUPC_K_COMPACT);
             LAUNCH(launch_degree(R->bits, p, W, (int*)ctx->deg.p, meta, ctx->stream));
-            LAUNCH(launch_scan((const int*)ctx->deg.p, p, l, chunk, binom_view(ctx), (long long*)ctx->row_off.p,
+            LAUNCH(launch_scan((const int*)ctx->deg.p, p, 1, chunk, binom_view(ctx), (long long*)ctx->row_off.p,
                                (long long*)ctx->item_off.p, meta, ctx->stream));
             tend(ctx, tk);
             kcount[CUPC_K_COMPACT] += 2;
         }
         if ((s = readback(ctx)) != CUPC_OK) return s;
-        const Meta M = *ctx->hmeta;
+        M = *ctx->hmeta;
         if (M.error & 4) return fail(ctx, CUPC_E_TIMEOUT, "a bounded wait in the tensor-core product expired");
         if (M.error) return fail(ctx, CUPC_E_NUMERIC, "a variable has zero variance or non-finite data");
-        if (level_pending) {
-            const int pl = l - 1;  // the level these counters belong to
-            if (fp32 && M.queue_len > qcap) {
-                // the recheck queue overflowed: enlarge it and run that level again
-                if (++redo > 4) return fail(ctx, CUPC_E_RANGE, "recheck queue overflow persists");
-                qcap = (size_t)(M.queue_len * 2);
-                if ((s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
-                if (pl == 0) {
-                    CU(cudaMemsetAsync(meta, 0, sizeof(Meta), ctx->stream));
-                    if ((s = run_level0()) != CUPC_OK) return s;
-                    level_pending = true;
-                } else {
-                    CU(cudaMemcpyAsync(R->bits, ctx->backup[pl & 1].p, bitbytes, cudaMemcpyDeviceToDevice,
-                                       ctx->stream));
-                    unsigned long long keep = 0;  // record ints appended before level pl
-                    for (int q = 1; q < pl; ++q) keep += (unsigned long long)R->stats.removed[q] * (3 + q);
-                    ctx->hmeta->rec_ints = keep;
-                    CU(cudaMemcpyAsync(&meta->rec_ints, &ctx->hmeta->rec_ints, sizeof(keep), cudaMemcpyHostToDevice,
-                                       ctx->stream));
-                    l = pl;
-                    level_pending = false;
-                }
-                continue;
-            }
-            if (pl >= 1) {
-                R->stats.tests[pl] = (int64_t)M.tests;
-                R->stats.removed[pl] = (int64_t)M.removed;
-                R->stats.serial_tests[pl] = o.canonical_sepset ? (int64_t)M.serial_tests : -1;
-            }
-            R->stats.rechecks[pl] = (int64_t)M.rechecks;
-            level_pending = false;
-        }
-        if (l == 1) R->stats.removed[0] = pairs - (int64_t)M.edges;
-        if (limit) break;
-        if (l < CUPC_STATS_LEVELS) {
-            R->stats.edges_start[l] = (int64_t)M.edges;
-            R->stats.max_degree[l] = M.maxdeg;
-            R->stats.ci_block_entries[l] = (int64_t)M.block_entries;
-        }
-        // termination: level l runs only while some node has degree - 1 >= l
-        if (M.maxdeg - 1 < l) break;
-        if (l > CUPC_MAX_LEVEL) return fail(ctx, CUPC_E_RANGE, "a level above CUPC_MAX_LEVEL would be needed");
-        if (M.range_error) return fail(ctx, CUPC_E_RANGE, "subset count exceeds 64 bits");
-        if (l < CUPC_STATS_LEVELS) CU(cudaEventRecord(ctx->ev[1 + l], ctx->stream));
-
-        const long long nnz = (long long)M.nnz;
-        const unsigned long long n_items = M.n_items;
-        if ((s = ensure(ctx, ctx->cols, (size_t)nnz * 4 + 4)) != CUPC_OK) return s;
-        if ((s = ensure(ctx, ctx->srow, (size_t)nnz * 4 + 4)) != CUPC_OK) return s;
-        if ((s = ensure(ctx, ctx->partner, (size_t)nnz * 4 + 4)) != CUPC_OK) return s;
-        if ((s = ensure(ctx, ctx->best, (size_t)nnz * 8 + 8)) != CUPC_OK) return s;
-        if ((s = ensure(ctx, ctx->item_row, (size_t)n_items * 4 + 4)) != CUPC_OK) return s;
-        if ((s = ensure_binom(ctx, M.maxdeg + 2)) != CUPC_OK) return s;
-        // SepSet pool: room for every edge of this level to be removed
-        const size_t need = (size_t)M.rec_ints + (size_t)(M.edges) * (3 + l) + 16;
-        if (need > rec_len_cap) {
-            size_t cap = std::max(need, rec_len_cap * 2);
-            int* nr = nullptr;
-            if ((s = dalloc(ctx, (void**)&nr, cap * 4)) != CUPC_OK) return s;
-            if (R->rec && M.rec_ints)
-                CU(cudaMemcpyAsync(nr, R->rec, (size_t)M.rec_ints * 4, cudaMemcpyDeviceToDevice, ctx->stream));
-            if (R->rec) cudaFreeAsync(R->rec, ctx->stream);
-            R->rec = nr;
-            rec_len_cap = cap;
-        }
-        // fresh per-level counters (tests .. next_item)
-        CU(cudaMemsetAsync(meta, 0, offsetof(Meta, edges), ctx->stream));
-        CU(cudaMemsetAsync(&meta->queue_len, 0, sizeof(unsigned long long), ctx->stream));
-        CU(cudaMemsetAsync(&meta->next_item, 0, sizeof(unsigned long long), ctx->stream));
-        {
-            const int tk = tbegin(ctx, CUPC_K_COMPACT);
-            LAUNCH(launch_fill(R->bits, p, W, (const long long*)ctx->row_off.p, (int*)ctx->cols.p,
-                               (int*)ctx->srow.p, ctx->stream));
-            LAUNCH(launch_items((const long long*)ctx->item_off.p, p, (int*)ctx->item_row.p, ctx->stream));
-            LAUNCH(launch_partner((const long long*)ctx->row_off.p, (const int*)ctx->cols.p,
-                                  (const int*)ctx->srow.p, nnz, (int*)ctx->partner.p, ctx->stream));
-            tend(ctx, tk);
-            kcount[CUPC_K_COMPACT] += 3;
-        }
-        CU(cudaMemsetAsync(ctx->best.p, 0xFF, (size_t)nnz * 8, ctx->stream));
-
-        if (n_items > 0) {
-            CIParams P{};
-            P.row_off = (const long long*)ctx->row_off.p;
-            P.cols = (const int*)ctx->cols.p;
-            P.partner = (const int*)ctx->partner.p;
-            P.item_row = (const int*)ctx->item_row.p;
-            P.item_off = (const long long*)ctx->item_off.p;
-            P.C = Cuse;
-            P.p = p;
-            P.l = l;
-            P.chunk = chunk;
-            P.canonical = o.canonical_sepset;
-            P.B = binom_view(ctx);
-            const double r = std::tanh(fisher_tau(alpha, n, l));
-            P.r = r;
-            P.r2 = r * r;
-            P.band_abs = (o.recheck_margin > 0) ? o.recheck_margin : kBandAbs;
-            P.band_rel = kBandRel;
-            P.rank_tol = fp32 ? kRankTol32 : kRankTol64;
-            P.piv_floor = kPivFloor;
-            P.best = (unsigned long long*)ctx->best.p;
-            P.queue = (QEntry*)ctx->queue.p;
-            P.qcap = qcap;
-            P.meta = meta;
-            P.n_items = n_items;
-            const long long want = (long long)((n_items + (block / 32) - 1) / (block / 32));
-            const int grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)ctx->num_sms * 8));
-            TIMED(CUPC_K_CI, launch_ci(fp32, P, grid, block, ctx->stream));
-            if (fp32) TIMED(CUPC_K_RECHECK, launch_recheck(recheck_params(l), grid_wide, ctx->stream));
-        }
-        FinalizeParams F{};
-        F.row_off = (const long long*)ctx->row_off.p;
-        F.cols = (const int*)ctx->cols.p;
-        F.srow = (const int*)ctx->srow.p;
-        F.partner = (const int*)ctx->partner.p;
-        F.best = (const unsigned long long*)ctx->best.p;
-        F.bits = R->bits;
-        F.W = W;
-        F.l = l;
-        F.B = binom_view(ctx);
-        F.count_serial = o.canonical_sepset;
-        F.rec = R->rec;
-        F.rec_cap = rec_len_cap;
-        F.meta = meta;
-        F.nnz = (unsigned long long)nnz;
-        TIMED(CUPC_K_FINALIZE, launch_finalize(F, ctx->stream));
-        levels_run = l + 1;
-        level_pending = true;
-        ++l;
+        if (!(fp32 && M.queue_len > qcap)) break;
+        // the level-0 recheck queue overflowed: enlarge it and run level 0 again
+        if (attempt >= 4) return fail(ctx, CUPC_E_RANGE, "recheck queue overflow persists");
+        qcap = (size_t)(M.queue_len * 2);
+        if ((s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
+        CU(cudaMemsetAsync(meta, 0, sizeof(Meta), ctx->stream));
+        if ((s = run_level0()) != CUPC_OK) return s;
     }
-    const int ev_end = std::min(levels_run, CUPC_STATS_LEVELS - 1) + 1;
+    R->stats.rechecks[0] = (int64_t)M.rechecks;
+    R->stats.removed[0] = pairs - (int64_t)M.edges;
+
+    // last level that can run: Algorithm 1 stops once max degree - 1 < l (degrees
+    // only shrink), Eq. (threshold) needs n - l - 3 > 0, and opts->max_level
+    int lmax = std::min<int64_t>(M.maxdeg - 1, n - 4);
+    if (o.max_level >= 0) lmax = std::min(lmax, o.max_level);
+    bool range_stop = false;
+    if (lmax > CUPC_MAX_LEVEL) {
+        lmax = CUPC_MAX_LEVEL;
+        range_stop = true;  // an error unless the loop terminates by itself before
+    }
+    int levels_run = 1;
+    int last_launched = 0;
+    size_t rec_len_cap = 0;
+    if (lmax >= 1) {
+        if (M.range_error) return fail(ctx, CUPC_E_RANGE, "subset count exceeds 64 bits");
+        const unsigned long long nnz_cap = std::max<unsigned long long>(M.nnz, 1);
+        const unsigned long long item_cap =
+            std::max<unsigned long long>({4ull * M.n_items, nnz_cap, 1ull << 16});
+        if ((s = ensure(ctx, ctx->cols, (size_t)nnz_cap * 4)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, ctx->srow, (size_t)nnz_cap * 4)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, ctx->partner, (size_t)nnz_cap * 4)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, ctx->wpre, bitbytes)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, ctx->best, (size_t)nnz_cap * 8)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, ctx->item_row, (size_t)item_cap * 4)) != CUPC_OK) return s;
+        if ((s = ensure_binom(ctx, M.maxdeg + 2)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, ctx->lmeta, sizeof(LevelMeta))) != CUPC_OK) return s;
+        // recheck partials: a batch of 8 tests per SM, 8 sample slices, the largest Gram block
+        const unsigned long long part_tests = 8ull * ctx->num_sms * 2;
+        const size_t dmax = (size_t)(CUPC_MAX_LEVEL + 2) * (CUPC_MAX_LEVEL + 1) / 2;
+        if (fp32 && (s = ensure(ctx, ctx->part, part_tests * 8 * dmax * sizeof(double))) != CUPC_OK) return s;
+        // SepSet pool: room for every edge present after level 0 with the largest set
+        rec_len_cap = (size_t)M.edges * (3 + lmax) + 16;
+        if ((s = dalloc(ctx, (void**)&R->rec, rec_len_cap * 4)) != CUPC_OK) return s;
+        LevelMeta* lm = (LevelMeta*)ctx->lmeta.p;
+        CU(cudaMemsetAsync(lm, 0, sizeof(LevelMeta), ctx->stream));
+
+        LevelParams LP{};
+        LP.bits = R->bits;
+        LP.W = W;
+        LP.p = p;
+        LP.backup = fp32 ? (unsigned*)ctx->backup[0].p : nullptr;
+        LP.deg = (int*)ctx->deg.p;
+        LP.row_off = (long long*)ctx->row_off.p;
+        LP.item_off = (long long*)ctx->item_off.p;
+        LP.item_row = (int*)ctx->item_row.p;
+        LP.item_cap = item_cap;
+        LP.cols = (int*)ctx->cols.p;
+        LP.srow = (int*)ctx->srow.p;
+        LP.partner = (int*)ctx->partner.p;
+        LP.wpre = (int*)ctx->wpre.p;
+        LP.best = (unsigned long long*)ctx->best.p;
+        LP.nnz_cap = nnz_cap;
+        LP.C = Cuse;
+        LP.B = binom_view(ctx);
+        LP.chunk0 = chunk;
+        LP.canonical = o.canonical_sepset;
+        LP.band_abs = (o.recheck_margin > 0) ? o.recheck_margin : kBandAbs;
+        LP.band_rel = kBandRel;
+        LP.rank_tol = fp32 ? kRankTol32 : kRankTol64;
+        LP.piv_floor = kPivFloor;
+        LP.z64 = dv.z64;
+        LP.ldz = dv.ldz;
+        LP.n = (int)n;
+        LP.c64 = c64;
+        LP.part = fp32 ? (double*)ctx->part.p : nullptr;
+        LP.part_tests = 8ull * ctx->num_sms * 2;
+        LP.rec = R->rec;
+        LP.rec_cap = rec_len_cap;
+        LP.lm = lm;
+
+        // Levels are launched with at most two in flight: level l is launched only
+        // once level l - 2 has reported (through pinned host memory, right after
+        // its termination test) that it runs, so at most two launches follow the
+        // last level and they return at once.
+        auto launch_levels = [&](int from) -> cupc_status {
+            LP.queue = (QEntry*)ctx->queue.p;
+            LP.qcap = qcap;
+            LP.host_flags = ctx->dflags;
+            for (int q = 0; q < LV; ++q) ((volatile int*)ctx->hflags)[q] = 0;
+            for (int l = from; l <= lmax; ++l) {
+                if (l - 2 >= from) {
+                    volatile int* fl = (volatile int*)ctx->hflags + (l - 2);
+                    const auto t0 = std::chrono::steady_clock::now();
+                    while (*fl == 0) {
+                        if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(30)) {
+                            CU(cudaStreamSynchronize(ctx->stream));
+                            if (*fl == 0) return fail(ctx, CUPC_E_TIMEOUT, "level flag not written");
+                        }
+                    }
+                    if (*fl == 2) break;
+                }
+                LP.l = l;
+                const double r = std::tanh(fisher_tau(alpha, n, l));
+                LP.r = r;
+                LP.r2 = r * r;
+                LP.rank_tol = fp32 ? kRankTol32 : kRankTol64;
+                if (l < CUPC_STATS_LEVELS) CU(cudaEventRecord(ctx->ev[1 + l], ctx->stream));
+                LAUNCH(launch_level(fp32, LP, ctx->num_sms, ctx->stream));
+                kcount[CUPC_K_CI]++;
+                last_launched = l;
+            }
+            return CUPC_OK;
+        };
+        if ((s = launch_levels(1)) != CUPC_OK) return s;
+        for (int attempt = 0;; ++attempt) {
+            CU(cudaMemcpyAsync(ctx->hlmeta, lm, sizeof(LevelMeta), cudaMemcpyDeviceToHost, ctx->stream));
+            CU(cudaStreamSynchronize(ctx->stream));
+            ctx->d2h += sizeof(LevelMeta);
+            LevelMeta& H = *ctx->hlmeta;
+            if (H.error & 8) return fail(ctx, CUPC_E_TIMEOUT, "a grid barrier wait expired");
+            if (H.error) return fail(ctx, CUPC_E_RANGE, "level buffers too small");
+            if (H.range_error) return fail(ctx, CUPC_E_RANGE, "subset count exceeds 64 bits");
+            const int ol = H.overflow_level;
+            if (ol == 0) break;
+            // the recheck queue of level ol overflowed: restore A_G as it was at the
+            // start of that level, enlarge the queue, clear that level's counters and
+            // run the levels from ol again
+            if (attempt >= 4) return fail(ctx, CUPC_E_RANGE, "recheck queue overflow persists");
+            qcap = (size_t)(H.queue_len[ol] * 2);
+            if ((s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
+            CU(cudaMemcpyAsync(R->bits, ctx->backup[0].p, bitbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+            unsigned long long keep = 0;
+            for (int q = 1; q < ol; ++q) keep += H.removed[q] * (unsigned long long)(3 + q);
+            for (int q = ol; q < LV; ++q) {
+                H.tests[q] = H.rechecks[q] = H.removed[q] = H.serial[q] = H.edges[q] = H.items[q] = 0;
+                H.next_item[q] = H.queue_len[q] = H.block_entries[q] = 0;
+                for (int c = 0; c < 4; ++c) H.phase_ns[q][c] = 0;
+                H.maxdeg[q] = 0;
+                H.chunk[q] = 0;
+            }
+            H.rec_ints = keep;
+            H.overflow_level = 0;
+            H.done_level = 0;
+            H.bar_count = 0;
+            CU(cudaMemcpyAsync(lm, ctx->hlmeta, sizeof(LevelMeta), cudaMemcpyHostToDevice, ctx->stream));
+            if ((s = launch_levels(ol)) != CUPC_OK) return s;
+        }
+        const LevelMeta& H = *ctx->hlmeta;
+        const int last = H.done_level ? H.done_level - 1 : lmax;  // last level that ran
+        if (range_stop && H.done_level == 0)
+            return fail(ctx, CUPC_E_RANGE, "a level above CUPC_MAX_LEVEL would be needed");
+        levels_run = last + 1;
+        for (int l = 1; l <= last && l < CUPC_STATS_LEVELS; ++l) {
+            R->stats.tests[l] = (int64_t)H.tests[l];
+            R->stats.removed[l] = (int64_t)H.removed[l];
+            R->stats.serial_tests[l] = o.canonical_sepset ? (int64_t)H.serial[l] : -1;
+            R->stats.rechecks[l] = (int64_t)H.rechecks[l];
+            R->stats.edges_start[l] = (int64_t)H.edges[l];
+            R->stats.max_degree[l] = H.maxdeg[l];
+            R->stats.ci_block_entries[l] = (int64_t)H.block_entries[l];
+            for (int c = 0; c < 4; ++c) R->stats.phase_ms[l][c] = 1e-6f * (float)H.phase_ns[l][c];
+        }
+        for (int l = 1; l < LV; ++l) {
+            R->stats.kernel_ms[CUPC_K_COMPACT] += 1e-6f * (float)H.phase_ns[l][0];
+            R->stats.kernel_ms[CUPC_K_CI] += 1e-6f * (float)H.phase_ns[l][1];
+            R->stats.kernel_ms[CUPC_K_RECHECK] += 1e-6f * (float)H.phase_ns[l][2];
+            R->stats.kernel_ms[CUPC_K_FINALIZE] += 1e-6f * (float)H.phase_ns[l][3];
+        }
+        R->rec_ints = (int64_t)H.rec_ints;
+    }
+    if (lmax < 1 && range_stop) return fail(ctx, CUPC_E_RANGE, "a level above CUPC_MAX_LEVEL would be needed");
+    const int ev_end = std::min(std::max(levels_run, last_launched + 1), CUPC_STATS_LEVELS - 1) + 1;
     CU(cudaEventRecord(ctx->ev[ev_end], ctx->stream));
-    if ((s = readback(ctx)) != CUPC_OK) return s;
-    R->rec_ints = (int64_t)ctx->hmeta->rec_ints;
+    CU(cudaStreamSynchronize(ctx->stream));
     R->rec_cap = rec_len_cap;
     if ((size_t)R->rec_ints > rec_len_cap && R->rec_ints > 0)
         return fail(ctx, CUPC_E_RANGE, "SepSet record pool overflow");
@@ -654,7 +678,8 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
     R->stats.prep_ms = ms;
     for (int q = 0; q < levels_run && q < CUPC_STATS_LEVELS; ++q) {
-        const int a = 1 + q, b = (q + 1 < levels_run) ? 2 + q : ev_end;
+        // level 0 spans the sizing step; level q >= 1 its level kernel launch
+        const int a = 1 + q, b = (q + 1 <= last_launched) ? 2 + q : ev_end;
         if (b > ev_end || a >= (int)ctx->ev.size()) break;
         if (cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]) == cudaSuccess) R->stats.level_ms[q] = ms;
     }
@@ -682,13 +707,16 @@ void ctx_release(cupc_ctx* c)
     cudaSetDevice(c->device);
     cupc_ctx* ctx = c;
     Buf* all[] = {&c->xin, &c->xt, &c->mu, &c->isd, &c->z64, &c->zhi, &c->zlo, &c->cws, &c->c64, &c->c32, &c->cin,
-                  &c->deg, &c->row_off, &c->item_off, &c->item_row, &c->cols, &c->srow, &c->partner,
-                  &c->best, &c->queue, &c->binom, &c->meta, &c->backup[0], &c->backup[1]};
+                  &c->deg, &c->row_off, &c->item_off, &c->item_row, &c->cols, &c->srow, &c->partner, &c->wpre,
+                  &c->best, &c->queue, &c->binom, &c->meta, &c->lmeta, &c->backup[0], &c->backup[1],
+                  &c->part};
     for (Buf* b : all) free_buf(ctx, *b);
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
     if (c->hmeta) cudaFreeHost(c->hmeta);
+    if (c->hlmeta) cudaFreeHost(c->hlmeta);
+    if (c->hflags) cudaFreeHost(c->hflags);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     delete c;
 }
@@ -768,7 +796,10 @@ cupc_status cupc_create(cupc_ctx** out, int device, void* stream)
     }
     unsigned long long thr = ~0ull;
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    if (cudaHostAlloc((void**)&c->hmeta, sizeof(Meta), cudaHostAllocDefault) != cudaSuccess) {
+    if (cudaHostAlloc((void**)&c->hmeta, sizeof(Meta), cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void**)&c->hlmeta, sizeof(LevelMeta), cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void**)&c->hflags, sizeof(int) * LV, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&c->dflags, c->hflags, 0) != cudaSuccess) {
         cudaMemPoolDestroy(c->pool);
         delete c;
         return CUPC_E_CUDA;

@@ -50,43 +50,48 @@ struct Binom {
 };
 
 // The t-th l-subset of the positions {0, .., d-1} in lexicographic order
-// (Sec. 4.2, Eq. comb): for each place c, step the value forward while the
-// number of subsets that start with the current prefix is <= the remaining
-// rank, subtracting those counts. Positions come out increasing.
+// (Sec. 4.2, Eq. comb). With k = l - 1 - c members still to place after place
+// c, the subsets whose place-c member is >= v number N(v) = C(d - v, k + 1)
+// (hockey-stick sum of the counts in Eq. comb); those with a smaller member
+// come first. So the member is the largest v with N(prev) - N(v) <= t, found by
+// binary search since N falls with v, and t drops by N(prev) - N(v).
+// Positions come out increasing; a rank beyond C(d, l) cannot leave the row.
 template <int LB>
-__device__ __forceinline__ void unrank_lex(unsigned long long t, int d, int l, const Binom& B,
-                                           int (&P)[LB])
+__device__ __forceinline__ void unrank_lex(unsigned long long t, int d, int l, const Binom& B, int (&P)[LB])
 {
-    int v = 0;
+    int prev = 0;
 #pragma unroll
     for (int c = 0; c < LB; ++c) {
         if (c < l) {
             const int k = l - 1 - c;
-            // bounded by d: a rank beyond C(d, l) cannot run past the row
-            for (; v < d - 1; ++v) {
-                const unsigned long long cnt = B(d - 1 - v, k);
-                if (t < cnt) break;
-                t -= cnt;
+            const unsigned long long total = B(d - prev, k + 1);
+            const unsigned long long target = total > t ? total - t : 1ull;  // need N(v) >= target
+            int lo = prev, hi = max(prev, d - 1 - k);
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (B(d - mid, k + 1) >= target) lo = mid; else hi = mid - 1;
             }
-            P[c] = v < d ? v : d - 1;
-            ++v;
+            t -= total - B(d - lo, k + 1);
+            P[c] = min(lo, d - 1);
+            prev = lo + 1;
         }
     }
 }
 
 // Rank of the increasing positions Q[0..l) among the l-subsets of {0..d-1}
-// in lexicographic order (inverse of unrank_lex).
+// in lexicographic order (inverse of unrank_lex): the subsets skipped at place
+// c are N(prev) - N(Q[c]) with N as above.
 template <int LB>
 __device__ __forceinline__ unsigned long long rank_lex(const int (&Q)[LB], int d, int l, const Binom& B)
 {
     unsigned long long r = 0;
-    int prev = -1;
+    int prev = 0;
 #pragma unroll
     for (int c = 0; c < LB; ++c) {
         if (c < l) {
             const int k = l - 1 - c;
-            for (int v = prev + 1; v < Q[c]; ++v) r += B(d - 1 - v, k);
-            prev = Q[c];
+            r += B(d - prev, k + 1) - B(d - Q[c], k + 1);
+            prev = Q[c] + 1;
         }
     }
     return r;
@@ -202,12 +207,77 @@ __device__ __forceinline__ bool bitset_test(const unsigned* bits, int W, int i, 
     return (bits[(size_t)i * W + (j >> 5)] >> (j & 31)) & 1u;
 }
 
-// Recheck queue entry of a level >= 1 test (slot e of row i; subset rank s over
-// the row), or of a level-0 pair (i, j) with rank unused.
+// ---------------------------------------------------------------------------
+// FP64 block of C for the rechecks: for the m variables V, the strictly lower
+// packed entries G[b(b-1)/2 + a] = C[V_a, V_b] (a < b). From the resident FP64
+// correlation when there is one; otherwise by the definition
+// C_ab = sum_s z_as z_bs / n over the FP64 standardised rows, every pair in one
+// pass (threads of the block stride the samples, four in flight each), then a
+// fixed-order block reduction -- an entry's value does not depend on the test
+// it serves. Must be called by all NT threads of the block; red holds
+// (NT/32) * M(M-1)/2 doubles.
+// ---------------------------------------------------------------------------
+template <int M, int NT>
+__device__ __forceinline__ void c_block(const double* c64, int p, const double* z64, long long ldz, int n,
+                                        const int (&V)[M], int m, double (&G)[M * (M - 1) / 2], double* red)
+{
+    constexpr int D = M * (M - 1) / 2;
+    if (c64) {
+#pragma unroll
+        for (int b = 1; b < M; ++b)
+#pragma unroll
+            for (int a = 0; a < b; ++a) G[b * (b - 1) / 2 + a] = (b < m) ? c64[(size_t)V[a] * p + V[b]] : 0.0;
+        return;
+    }
+    const double* rows[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) rows[a] = z64 + (size_t)(a < m ? V[a] : V[0]) * ldz;
+#pragma unroll
+    for (int q = 0; q < D; ++q) G[q] = 0.0;
+#pragma unroll 4
+    for (int k = threadIdx.x; k < n; k += NT) {
+        double x[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) x[a] = (a < m) ? __ldg(rows[a] + k) : 0.0;
+#pragma unroll
+        for (int b = 1; b < M; ++b)
+#pragma unroll
+            for (int a = 0; a < b; ++a) G[b * (b - 1) / 2 + a] = fma(x[a], x[b], G[b * (b - 1) / 2 + a]);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        double g = G[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+        if (lane == 0) red[w * D + q] = g;
+    }
+    __syncthreads();
+    const double inv_n = 1.0 / (double)n;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        double g = 0.0;
+#pragma unroll
+        for (int k = 0; k < NT / 32; ++k) g += red[k * D + q];
+        G[q] = g * inv_n;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Recheck queue entry of a level >= 1 test (slot e of row i, subset rank s
+// over the row and the members of S), or of a level-0 pair (i, j).
 struct QEntry {
     int a;                      // slot e (level >= 1) or i (level 0)
     int b;                      // unused (level >= 1) or j (level 0)
     unsigned long long s;       // subset rank
+    int S[CUPC_MAX_LEVEL];      // members of S (level >= 1)
 };
 
 }  // namespace cupc

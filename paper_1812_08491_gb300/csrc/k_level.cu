@@ -1,0 +1,670 @@
+// k_level.cu -- one level l >= 1 of Algorithm 2 in a single cooperative
+// (persistent) kernel: all CTAs are resident and pass bounded grid barriers
+// between the phases, so a level costs one launch and no host round trip.
+//
+//   P1  one block scans the degrees (kept current by the previous level's
+//       removals) into the CSR offsets of A'_G, the CI work items
+//       (ceil(C(n'_i, l) / chunk) per row) and the max degree; the other blocks
+//       take per-row prefix popcounts of A_G's words and, in FP32 mode, a copy
+//       of A_G; then termination (Algorithm 1: level l runs only while some node
+//       has degree - 1 >= l)
+//   P2  A'_G: each row's neighbours in increasing order with, for each slot
+//       (i, j), the slot of (j, i) from the prefix popcounts (warp per row); the
+//       rows of the work items; best ranks reset
+//   P4  CI tests (Sec. 4.3), persistent item pulling, early termination
+//   P5  FP32 mode: FP64 rechecks of the near-threshold tests
+//   P6  edge removal from G (bitset and degrees) and SepSet records
+//
+// CI work decomposition (cf. cuPC-S, Sec. 3.4, Algorithm 5, prior art): an
+// item is a row i of A'_G and a range of subset ranks. Each lane owns one S per
+// round: it unranks S (Sec. 4.2), factors M2 = C[S,S] once and tests every j of
+// the row not in S against it, so one factorisation serves up to n'_i - l
+// tests. A test (S, j) is skipped once slot (i, j) holds a separating set of
+// smaller rank (canonical mode, which must find the lexicographically first S)
+// or any separating set (free mode), and on the larger endpoint's side once
+// the smaller side has one (Sec. 4.1).
+//
+// Data written by other CTAs' atomics (best ranks, counters) is read through
+// L2 (ld.cg); everything else written in one phase is first loaded after the
+// barrier that ends that phase.
+#include <cstdio>
+
+#include "kernels.cuh"
+
+namespace cupc {
+namespace {
+
+constexpr int NT = 512;                              // threads per CTA
+constexpr int NW = NT / 32;
+constexpr unsigned long long kBarrierNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_cg(const unsigned long long* p) { return __ldcg(p); }
+
+// Grid-wide barrier for a cooperative launch. Returns false (uniformly in the
+// CTA) when the kernel must stop: a wait expired or an error was raised.
+__device__ bool grid_sync(LevelMeta* lm)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &lm->bar_gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&lm->bar_count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&lm->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&lm->bar_gen, 1u);
+        } else {
+            const unsigned long long t0 = gtimer();
+            while (*vgen == g) {
+                if (*(volatile int*)&lm->error) break;
+                if (gtimer() - t0 > kBarrierNs) {
+                    atomicOr(&lm->error, 8);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        ok = (*(volatile int*)&lm->error == 0);
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// P1 (blocks other than 0): exclusive prefix popcounts of each row's words,
+// wpre[i*W + w] = number of neighbours of i below 32 w; FP32 mode: A_G copy
+// ---------------------------------------------------------------------------
+__device__ void phase_prefix(const LevelParams& P, bool fp32)
+{
+    const int lane = threadIdx.x & 31;
+    // block 0 is scanning; with a single block it does this part too
+    const int nb = gridDim.x > 1 ? gridDim.x - 1 : 1;
+    const int bid = gridDim.x > 1 ? blockIdx.x - 1 : 0;
+    const int gw = (bid * NT + threadIdx.x) >> 5;
+    const int nwarps = (nb * NT) >> 5;
+    for (int i = gw; i < P.p; i += nwarps) {
+        int base = 0;
+        for (int w0 = 0; w0 < P.W; w0 += 32) {
+            const int q = w0 + lane;
+            const int c = (q < P.W) ? __popc(P.bits[(size_t)i * P.W + q]) : 0;
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int x = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += x;
+            }
+            if (q < P.W) P.wpre[(size_t)i * P.W + q] = base + incl - c;
+            base += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+    if (fp32) {
+        const size_t words = (size_t)P.p * P.W;
+        for (size_t k = (size_t)bid * NT + threadIdx.x; k < words; k += (size_t)nb * NT)
+            P.backup[k] = P.bits[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// P1: block 0 scans degrees into CSR offsets and work-item offsets. The chunk
+// (subset ranks per item) doubles until the items fit the item array.
+// ---------------------------------------------------------------------------
+__device__ void phase_scan(const LevelParams& P)
+{
+    __shared__ long long sa[32], sb[32];
+    __shared__ unsigned long long stot;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int per = (P.p + NT - 1) / NT;
+    const int lo = min(P.p, t * per), hi = min(P.p, lo + per);
+    const int l = P.l;
+    int chunk = P.chunk0;
+    int rng = 0;
+    // choose the chunk
+    for (int it = 0; it < 48; ++it) {
+        unsigned long long b = 0;
+        for (int i = lo; i < hi; ++i) {
+            const int d = P.deg[i];
+            if (d >= l + 1) {
+                const unsigned long long ns = P.B(d, l);
+                if (ns == ~0ull) rng = 1;
+                b += (ns + chunk - 1) / chunk;
+            }
+        }
+        b = warp_sum_u64(b);
+        if (lane == 0) sb[w] = (long long)b;
+        __syncthreads();
+        if (t == 0) {
+            unsigned long long tot = 0;
+            for (int k = 0; k < NW; ++k) tot += (unsigned long long)sb[k];
+            stot = tot;
+        }
+        __syncthreads();
+        const bool fits = stot <= P.item_cap;
+        __syncthreads();
+        if (fits) break;
+        chunk = chunk > (1 << 29) ? chunk : chunk * 2;
+    }
+    // exclusive scans of (degree, items); max degree
+    long long a = 0, b = 0;
+    unsigned long long sq = 0;
+    int dmax = 0;
+    for (int i = lo; i < hi; ++i) {
+        const int d = P.deg[i];
+        dmax = max(dmax, d);
+        a += d;
+        if (d >= l + 1) {
+            b += (long long)((P.B(d, l) + chunk - 1) / chunk);
+            sq += (unsigned long long)(d + 1) * (unsigned long long)(d + 1);
+        }
+    }
+    sq = warp_sum_u64(sq);
+    if (lane == 0 && sq) atomicAdd(&P.lm->block_entries[l], sq);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if (lane == 0) atomicMax(&P.lm->maxdeg[l], dmax);
+    long long ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long xa = __shfl_up_sync(0xffffffffu, ia, o);
+        const long long xb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) { ia += xa; ib += xb; }
+    }
+    __syncthreads();
+    if (lane == 31) { sa[w] = ia; sb[w] = ib; }
+    __syncthreads();
+    if (w == 0) {
+        long long va = (lane < NW) ? sa[lane] : 0, vb = (lane < NW) ? sb[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long xa = __shfl_up_sync(0xffffffffu, va, o);
+            const long long xb = __shfl_up_sync(0xffffffffu, vb, o);
+            if (lane >= o) { va += xa; vb += xb; }
+        }
+        sa[lane] = va;
+        sb[lane] = vb;
+    }
+    __syncthreads();
+    long long ea = ia - a + (w > 0 ? sa[w - 1] : 0);
+    long long eb = ib - b + (w > 0 ? sb[w - 1] : 0);
+    for (int i = lo; i < hi; ++i) {
+        const int d = P.deg[i];
+        P.row_off[i] = ea;
+        P.item_off[i] = eb;
+        ea += d;
+        if (d >= l + 1) eb += (long long)((P.B(d, l) + chunk - 1) / chunk);
+    }
+    if (rng) atomicOr(&P.lm->range_error, 1);
+    if (t == NT - 1) {
+        P.row_off[P.p] = ea;
+        P.item_off[P.p] = eb;
+        P.lm->edges[l] = (unsigned long long)ea / 2;
+        P.lm->items[l] = (unsigned long long)eb;
+        P.lm->chunk[l] = chunk;
+        if ((unsigned long long)ea > P.nnz_cap || (unsigned long long)eb > P.item_cap) atomicOr(&P.lm->error, 16);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// P2: A'_G rows, item rows, best reset
+// ---------------------------------------------------------------------------
+__device__ void phase_fill(const LevelParams& P)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * NT + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * NT) >> 5;
+    for (int i = gw; i < P.p; i += nwarps) {
+        long long base = P.row_off[i];
+        for (int w0 = 0; w0 < P.W; w0 += 32) {
+            const int q = w0 + lane;
+            unsigned word = (q < P.W) ? P.bits[(size_t)i * P.W + q] : 0u;
+            const int c = __popc(word);
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int x = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += x;
+            }
+            long long pos = base + incl - c;
+            while (word) {
+                const int b = __ffs(word) - 1;
+                word &= word - 1;
+                const int j = (q << 5) + b;
+                P.cols[pos] = j;
+                P.srow[pos] = i;
+                // slot of (j, i): row j's offset + neighbours of j below i
+                const unsigned wj = P.bits[(size_t)j * P.W + (i >> 5)];
+                P.partner[pos] = (int)(P.row_off[j] + P.wpre[(size_t)j * P.W + (i >> 5)] +
+                                       __popc(wj & ((1u << (i & 31)) - 1u)));
+                ++pos;
+            }
+            base += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        for (long long k = P.item_off[i] + lane; k < P.item_off[i + 1]; k += 32) P.item_row[k] = i;
+    }
+    const long long nnz = P.row_off[P.p];
+    for (long long e = (long long)blockIdx.x * NT + threadIdx.x; e < nnz; e += (long long)gridDim.x * NT)
+        P.best[e] = RANK_NONE;
+}
+
+// ---------------------------------------------------------------------------
+// P4: CI tests
+// ---------------------------------------------------------------------------
+// 0 dependent, 1 independent, 2 undecided in FP32 (sent to the FP64 recheck)
+template <typename T, bool FP32>
+__device__ __forceinline__ int ci_decide(T H11, T H12, T H22, T minpiv2, const LevelParams& P)
+{
+    if (!FP32) {
+        // zero conditional variance (rounding level of the unit diagonal): V_i or
+        // V_j is a linear function of S -> independent
+        if (!(H11 > T(kVarZero)) || !(H22 > T(kVarZero))) return 1;
+        return (H12 * H12 <= (T)P.r2 * H11 * H22) ? 1 : 0;
+    } else {
+        if (!(minpiv2 >= (T)P.piv_floor) || !(H11 > T(1e-4)) || !(H22 > T(1e-4))) return 2;
+        const float rho = fabsf((float)H12) * rsqrtf((float)(H11 * H22));
+        const float band =
+            (float)P.band_abs + (float)P.band_rel / ((float)minpiv2 * fminf((float)H11, (float)H22));
+        const float r = (float)P.r;
+        if (rho > r + band) return 0;
+        if (rho < r - band) return 1;
+        return 2;
+    }
+}
+
+template <typename T, int LB, bool FP32>
+__device__ void phase_ci(const LevelParams& P)
+{
+    const int lane = threadIdx.x & 31;
+    const T* __restrict__ C = (const T*)P.C;
+    const int p = P.p, l = P.l;
+    const unsigned long long n_items = P.lm->items[l];
+    const int chunk = P.lm->chunk[l];
+    unsigned long long ntests = 0;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(&P.lm->next_item[l], 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        const int i = P.item_row[item];
+        const long long k = (long long)item - P.item_off[i];
+        const long long off = P.row_off[i];
+        const int d = (int)(P.row_off[i + 1] - off);
+        const unsigned long long nsets = P.B(d, l);
+        const unsigned long long s0 = (unsigned long long)k * (unsigned long long)chunk;
+        const unsigned long long s1 = min(s0 + (unsigned long long)chunk, nsets);
+        const T* __restrict__ Ci = C + (size_t)i * p;
+        for (unsigned long long base = s0; base < s1; base += 32) {
+            const unsigned long long s = base + lane;
+            const bool active = s < s1;
+            int Pos[LB], Sx[LB];
+            Factor<T, LB> F;
+#pragma unroll
+            for (int c = 0; c < LB; ++c) { Pos[c] = -1; Sx[c] = 0; }
+            if (active) {
+                unrank_lex<LB>(s, d, l, P.B, Pos);
+#pragma unroll
+                for (int c = 0; c < LB; ++c)
+                    if (c < l) Sx[c] = P.cols[off + Pos[c]];
+                factor_build<T, LB>(
+                    F, l, (T)P.rank_tol, [&](int a, int b) { return __ldg(C + (size_t)Sx[a] * p + Sx[b]); },
+                    [&](int a) { return __ldg(Ci + Sx[a]); });
+            }
+            // the row's per-j data in chunks of 32: lane q loads j-position jc + q
+            // (coalesced), then the chunk is broadcast one j at a time by shuffles
+            for (int jc = 0; jc < d; jc += 32) {
+                int j_l = 0;
+                unsigned long long b_l = RANK_NONE, pb_l = RANK_NONE;
+                T cij_l = T(0);
+                if (jc + lane < d) {
+                    const long long e = off + jc + lane;
+                    j_l = P.cols[e];
+                    b_l = ld_cg(P.best + e);
+                    // the larger endpoint's side stops once the smaller side separates
+                    // (free mode: either side stops the other)
+                    if (!P.canonical || i > j_l) pb_l = ld_cg(P.best + P.partner[e]);
+                    cij_l = __ldg(Ci + j_l);
+                }
+                const int jn = min(32, d - jc);
+#pragma unroll 4
+                for (int q = 0; q < jn; ++q) {
+                    const int jp = jc + q;
+                    const int j = __shfl_sync(0xffffffffu, j_l, q);
+                    const unsigned long long be = __shfl_sync(0xffffffffu, b_l, q);
+                    const unsigned long long pb = __shfl_sync(0xffffffffu, pb_l, q);
+                    const T cij = __shfl_sync(0xffffffffu, cij_l, q);
+                    bool t = active && pb == RANK_NONE && (P.canonical ? (be >= s) : (be == RANK_NONE));
+#pragma unroll
+                    for (int c = 0; c < LB; ++c)
+                        if (c < l && Pos[c] == jp) t = false;
+                    if (t) {
+                        T H12, H22;
+                        const T* __restrict__ Cj = C + (size_t)j * p;
+                        factor_apply<T, LB>(F, l, cij, [&](int a) { return __ldg(Cj + Sx[a]); }, H12, H22);
+                        const T H11 = T(1) - F.uu;
+                        ++ntests;
+                        const int dec = ci_decide<T, FP32>(H11, H12, H22, F.minpiv2, P);
+                        const long long e = off + jp;
+                        if (dec == 1) {
+                            atomicMin(P.best + e, s);
+                        } else if (FP32 && dec == 2) {
+                            const unsigned long long qq = atomicAdd(&P.lm->queue_len[l], 1ull);
+                            if (qq < P.qcap) {
+                                QEntry* Q = P.queue + qq;
+                                Q->a = (int)e;
+                                Q->b = 0;
+                                Q->s = s;
+#pragma unroll
+                                for (int c = 0; c < LB; ++c)
+                                    if (c < l) Q->S[c] = Sx[c];
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    ntests = warp_sum_u64(ntests);
+    if (lane == 0 && ntests) atomicAdd(&P.lm->tests[l], ntests);
+}
+
+// ---------------------------------------------------------------------------
+// P5: FP64 rechecks. The samples of each queued test are cut into S slices
+// (S depends on n only, so the summation order is fixed); CTAs take (test,
+// slice) units and write partial Gram sums of the test's l + 2 standardised
+// rows, then after a barrier one CTA per test adds its slices in order, forms
+// H in FP64 and decides. A single SM's FP64 rate is low on this part, so
+// spreading each test over several SMs shortens the phase when few tests
+// are queued. The queue is processed in batches that fit the partial buffer.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int recheck_slices(int n) { return max(1, min(8, n / 2048)); }
+
+template <int LB>
+__device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
+{
+    constexpr int M = LB + 2;
+    constexpr int D = M * (M - 1) / 2;
+    __shared__ double red[NW * D];
+    const int S = recheck_slices(P.n);
+    const long long batch = (long long)P.part_tests;
+    const double inv_n = 1.0 / (double)P.n;
+    for (long long q0 = 0; q0 < (long long)nq; q0 += batch) {
+        const long long nb = min(batch, (long long)nq - q0);
+        // partial sums
+        for (long long u = blockIdx.x; u < nb * S; u += gridDim.x) {
+            const long long qi = q0 + u / S;
+            const int k = (int)(u % S);
+            const QEntry* E = P.queue + qi;
+            const long long e = E->a;
+            const int i = P.srow[e], j = P.cols[e];
+            int V[M];
+            V[0] = i;
+            V[1] = j;
+#pragma unroll
+            for (int c = 0; c < LB; ++c) V[2 + c] = (c < P.l) ? E->S[c] : i;
+            const int m = P.l + 2;
+            const int k0 = (int)((long long)P.n * k / S), k1 = (int)((long long)P.n * (k + 1) / S);
+            double G[D];
+#pragma unroll
+            for (int t = 0; t < D; ++t) G[t] = 0.0;
+            if (P.c64 == nullptr) {
+                const double* rows[M];
+#pragma unroll
+                for (int a = 0; a < M; ++a) rows[a] = P.z64 + (size_t)(a < m ? V[a] : V[0]) * P.ldz;
+#pragma unroll 4
+                for (int kk = k0 + (int)threadIdx.x; kk < k1; kk += NT) {
+                    double x[M];
+#pragma unroll
+                    for (int a = 0; a < M; ++a) x[a] = (a < m) ? __ldg(rows[a] + kk) : 0.0;
+#pragma unroll
+                    for (int b2 = 1; b2 < M; ++b2)
+#pragma unroll
+                        for (int a = 0; a < b2; ++a) G[b2 * (b2 - 1) / 2 + a] = fma(x[a], x[b2], G[b2 * (b2 - 1) / 2 + a]);
+                }
+            }
+            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+            for (int t = 0; t < D; ++t) {
+                double g = G[t];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+                if (lane == 0) red[w * D + t] = g;
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < D; t += NT) {
+                double g = 0.0;
+                for (int ww = 0; ww < NW; ++ww) g += red[ww * D + t];
+                P.part[(size_t)u * D + t] = g;
+            }
+            __syncthreads();
+        }
+        if (!grid_sync(P.lm)) return false;
+        // combine the slices of each test in order and decide
+        for (long long t = blockIdx.x; t < nb; t += gridDim.x) {
+            if (threadIdx.x != 0) continue;
+            const long long qi = q0 + t;
+            const QEntry* E = P.queue + qi;
+            const long long e = E->a;
+            const int i = P.srow[e], j = P.cols[e];
+            int V[M];
+            V[0] = i;
+            V[1] = j;
+#pragma unroll
+            for (int c = 0; c < LB; ++c) V[2 + c] = (c < P.l) ? E->S[c] : i;
+            double G[D];
+            if (P.c64) {
+#pragma unroll
+                for (int b2 = 1; b2 < M; ++b2)
+#pragma unroll
+                    for (int a = 0; a < b2; ++a)
+                        G[b2 * (b2 - 1) / 2 + a] = (b2 < P.l + 2) ? P.c64[(size_t)V[a] * P.p + V[b2]] : 0.0;
+            } else {
+#pragma unroll
+                for (int x = 0; x < D; ++x) {
+                    double g = 0.0;
+                    for (int k = 0; k < S; ++k) g += __ldcg(P.part + ((size_t)t * S + k) * D + x);
+                    G[x] = g * inv_n;
+                }
+            }
+            // V index 0 = i, 1 = j, 2 + a = S_a; G[b(b-1)/2 + a] holds C[V_a, V_b], a < b
+            Factor<double, LB> F;
+            factor_build<double, LB>(
+                F, P.l, P.rank_tol, [&](int a, int b2) { return G[(a + 2) * (a + 1) / 2 + (b2 + 2)]; },
+                [&](int a) { return G[(a + 2) * (a + 1) / 2 + 0]; });
+            double H12, H22;
+            factor_apply<double, LB>(F, P.l, G[0], [&](int a) { return G[(a + 2) * (a + 1) / 2 + 1]; }, H12, H22);
+            const double H11 = 1.0 - F.uu;
+            const bool indep = (!(H11 > kVarZero) || !(H22 > kVarZero)) ? true : (H12 * H12 <= P.r2 * H11 * H22);
+            if (indep) atomicMin(P.best + e, E->s);
+        }
+        if (!grid_sync(P.lm)) return false;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&P.lm->rechecks[P.l], nq);
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// P6: an edge (x < y) is removed when either side found a separating set; the
+// SepSet is the smaller side's when it has one (the serial order). With
+// canonical SepSets the tests the serial order performs are counted: side x
+// up to and including its first separating set (or all), side y only when
+// side x found none.
+// ---------------------------------------------------------------------------
+template <int LB>
+__device__ __forceinline__ unsigned long long side_serial(const LevelParams& P, int a, long long slot_b,
+                                                          unsigned long long rank)
+{
+    const long long off = P.row_off[a];
+    const int d = (int)(P.row_off[a + 1] - off);
+    if (rank == RANK_NONE) return P.B(d - 1, P.l);
+    int Pos[LB];
+    unrank_lex<LB>(rank, d, P.l, P.B, Pos);
+    const int pb = (int)(slot_b - off);
+#pragma unroll
+    for (int c = 0; c < LB; ++c)
+        if (c < P.l && Pos[c] > pb) Pos[c] -= 1;
+    return rank_lex<LB>(Pos, d - 1, P.l, P.B) + 1;
+}
+
+template <int LB>
+__device__ void phase_finalize(const LevelParams& P)
+{
+    const long long nnz = P.row_off[P.p];
+    const int l = P.l;
+    for (long long e0 = (long long)blockIdx.x * NT; e0 < nnz; e0 += (long long)gridDim.x * NT) {
+        const long long e = e0 + threadIdx.x;
+        bool removed = false;
+        unsigned long long serial = 0;
+        if (e < nnz) {
+            const int x = P.srow[e], y = P.cols[e];
+            if (x < y) {
+                const long long f = P.partner[e];
+                const unsigned long long bx = ld_cg(P.best + e), by = ld_cg(P.best + f);
+                int side = -1;
+                unsigned long long rank = 0;
+                if (bx != RANK_NONE) { side = x; rank = bx; }
+                else if (by != RANK_NONE) { side = y; rank = by; }
+                if (side >= 0) {
+                    removed = true;
+                    bitset_clear_pair(P.bits, P.W, x, y);
+                    atomicSub(P.deg + x, 1);
+                    atomicSub(P.deg + y, 1);
+                    const long long off = P.row_off[side];
+                    const int d = (int)(P.row_off[side + 1] - off);
+                    int Pos[LB];
+                    unrank_lex<LB>(rank, d, l, P.B, Pos);
+                    const int ints = 3 + l;
+                    const unsigned long long at = atomicAdd(&P.lm->rec_ints, (unsigned long long)ints);
+                    if (at + ints <= P.rec_cap) {
+                        int* r = P.rec + at;
+                        r[0] = x;
+                        r[1] = y;
+                        r[2] = l;
+#pragma unroll
+                        for (int c = 0; c < LB; ++c)
+                            if (c < l) r[3 + c] = P.cols[off + Pos[c]];
+                    }
+                }
+                if (P.canonical) {
+                    serial = side_serial<LB>(P, x, e, bx);
+                    if (bx == RANK_NONE) serial += side_serial<LB>(P, y, f, by);
+                }
+            }
+        }
+        const unsigned long long nrem = warp_sum_u64(removed ? 1ull : 0ull);
+        const unsigned long long ns = warp_sum_u64(serial);
+        if ((threadIdx.x & 31) == 0) {
+            if (nrem) atomicAdd(&P.lm->removed[l], nrem);
+            if (ns) atomicAdd(&P.lm->serial[l], ns);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The level kernel
+// ---------------------------------------------------------------------------
+// Tells the host whether this level runs (1) or the loop has ended (2),
+// through pinned host memory the host polls to decide on further launches.
+__device__ __forceinline__ void signal_host(const LevelParams& P, int v)
+{
+    if (P.host_flags) {
+        __threadfence_system();
+        *(volatile int*)(P.host_flags + P.l) = v;
+        __threadfence_system();
+    }
+}
+
+template <typename T, int LB, bool FP32>
+__global__ void __launch_bounds__(NT) k_level(LevelParams P)
+{
+    LevelMeta* lm = P.lm;
+    const int l = P.l;
+    // a previous level ended the loop (termination, overflow or error)
+    if (*(volatile int*)&lm->done_level || *(volatile int*)&lm->overflow_level || *(volatile int*)&lm->error) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) signal_host(P, 2);
+        return;
+    }
+    unsigned long long t0 = 0, t1;
+    const bool timer = (blockIdx.x == 0 && threadIdx.x == 0);
+    if (timer) t0 = gtimer();
+
+    if (blockIdx.x == 0) phase_scan(P);
+    if (blockIdx.x != 0 || gridDim.x == 1) phase_prefix(P, FP32);
+    if (!grid_sync(lm)) {
+        if (timer) signal_host(P, 2);
+        return;
+    }
+    if (*(volatile int*)&lm->maxdeg[l] - 1 < l || *(volatile int*)&lm->range_error) {
+        if (timer) {
+            lm->done_level = l;
+            signal_host(P, 2);
+        }
+        return;
+    }
+    if (timer) signal_host(P, 1);
+    phase_fill(P);
+    if (!grid_sync(lm)) return;
+    if (timer) { t1 = gtimer(); lm->phase_ns[l][0] += t1 - t0; t0 = t1; }
+
+    phase_ci<T, LB, FP32>(P);
+    if (!grid_sync(lm)) return;
+    if (timer) { t1 = gtimer(); lm->phase_ns[l][1] += t1 - t0; t0 = t1; }
+
+    if (FP32) {
+        const unsigned long long nq = ld_cg(&lm->queue_len[l]);
+        if (nq > P.qcap) {
+            // the queue overflowed: stop; the host enlarges it and reruns this level
+            if (timer) lm->overflow_level = l;
+            return;
+        }
+        if (nq > 0 && !phase_recheck<LB>(P, nq)) return;
+        if (timer) { t1 = gtimer(); lm->phase_ns[l][2] += t1 - t0; t0 = t1; }
+    }
+    phase_finalize<LB>(P);
+    if (timer) {
+        t1 = gtimer();
+        lm->phase_ns[l][3] += t1 - t0;
+    }
+}
+
+template <typename T, int LB, bool FP32>
+cudaError_t launch_level_t(const LevelParams& P, int num_sms, cudaStream_t st)
+{
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level<T, LB, FP32>, NT, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        per_sm = per_sm > 2 ? 2 : per_sm;
+    }
+    const int grid = num_sms * per_sm;
+    LevelParams arg = P;
+    void* args[] = {&arg};
+    return cudaLaunchCooperativeKernel((const void*)k_level<T, LB, FP32>, dim3(grid), dim3(NT), args, 0, st);
+}
+
+template <typename T, bool FP32>
+cudaError_t launch_level_b(const LevelParams& P, int num_sms, cudaStream_t st)
+{
+    if (P.l <= 1) return launch_level_t<T, 1, FP32>(P, num_sms, st);
+    if (P.l <= 2) return launch_level_t<T, 2, FP32>(P, num_sms, st);
+    if (P.l <= 4) return launch_level_t<T, 4, FP32>(P, num_sms, st);
+    if (P.l <= 8) return launch_level_t<T, 8, FP32>(P, num_sms, st);
+    if (P.l <= 12) return launch_level_t<T, 12, FP32>(P, num_sms, st);
+    return launch_level_t<T, 16, FP32>(P, num_sms, st);
+}
+
+}  // namespace
+
+cudaError_t launch_level(int fp32, const LevelParams& P, int num_sms, cudaStream_t st)
+{
+    return fp32 ? launch_level_b<float, true>(P, num_sms, st) : launch_level_b<double, false>(P, num_sms, st);
+}
+
+}  // namespace cupc

@@ -5,68 +5,81 @@
 
 namespace cupc {
 
-// Parameters of one level's CI-test kernel (levels l >= 1).
-struct CIParams {
-    const long long* row_off;      // p + 1 CSR offsets of A'_G
-    const int* cols;               // nnz neighbour indices (increasing per row)
-    const int* partner;            // nnz: slot of (j, i) for slot (i, j)
-    const int* item_row;           // n_items: row of each work item
-    const long long* item_off;     // p + 1: first item of each row
+// Per-level counters of the fused level kernels (zeroed once per call).
+constexpr int LV = CUPC_MAX_LEVEL + 2;
+struct LevelMeta {
+    unsigned long long tests[LV];          // CI tests executed
+    unsigned long long rechecks[LV];       // FP64 rechecks performed
+    unsigned long long removed[LV];        // edges removed
+    unsigned long long serial[LV];         // serial-order test count (canonical runs)
+    unsigned long long edges[LV];          // undirected edges at level start
+    unsigned long long items[LV];          // CI work items
+    unsigned long long next_item[LV];      // persistent work counter
+    unsigned long long queue_len[LV];      // recheck entries pushed (may exceed capacity)
+    unsigned long long block_entries[LV];  // sum over rows with work of (n'_i + 1)^2
+    unsigned long long phase_ns[LV][4];    // compaction, CI, recheck, finalisation (wall ns)
+    int maxdeg[LV];
+    int chunk[LV];
+    unsigned long long rec_ints;           // SepSet record ints appended
+    int done_level;                        // level whose termination test stopped the loop
+    int overflow_level;                    // level whose recheck queue overflowed
+    int error;                             // 8: a grid barrier wait expired
+    int range_error;                       // a subset count saturated 64 bits
+    unsigned bar_count, bar_gen;           // grid barrier state
+};
+
+// Parameters of one level (l >= 1) of the fused level kernel.
+struct LevelParams {
+    unsigned* bits;                // live A_G bitset, p rows of W words
+    int W, p;
+    unsigned* backup;              // FP32 mode: A_G at level start (for a rerun after queue overflow)
+    int* deg;
+    long long* row_off;            // p + 1 CSR offsets of A'_G
+    long long* item_off;           // p + 1: first CI work item of each row
+    int* item_row;                 // row of each work item
+    unsigned long long item_cap;
+    int* cols;                     // neighbour indices (increasing per row)
+    int* srow;                     // row of each slot
+    int* partner;                  // slot of (j, i) for slot (i, j)
+    int* wpre;                     // per row, neighbours below each 32-column word
+    unsigned long long* best;      // smallest separating subset rank per slot
+    unsigned long long nnz_cap;
     const void* C;                 // p x p correlation (float or double), ld = p
-    int p;
-    int l;
-    int chunk;                     // subset ranks per work item
-    int canonical;
     Binom B;
-    double r;                      // tanh(tau_l)
-    double r2;                     // tanh(tau_l)^2
+    int chunk0;                    // preferred subset ranks per work item
+    int canonical;
+    int l;
+    double r, r2;                  // tanh(tau_l) and its square
     double band_abs, band_rel;     // FP32 mode: recheck band on |rho|
     double rank_tol;               // pivot^2 at or below which a member of S is dependent
     double piv_floor;              // FP32 mode: smaller pivot^2 sends the test to FP64
-    unsigned long long* best;      // nnz: smallest separating rank found per slot
-    QEntry* queue;                 // FP32 mode recheck queue
+    QEntry* queue;
     unsigned long long qcap;
-    Meta* meta;
-    unsigned long long n_items;
-};
-
-// Parameters of the FP64 recheck of queued tests.
-struct RecheckParams {
-    const long long* row_off;
-    const int* cols;
-    const int* srow;
-    const double* z64;             // standardised rows (row v at z64 + v*ldz), used when c64 == nullptr
+    const double* z64;             // FP64 standardised rows for the rechecks (or c64)
     long long ldz;
     int n;
-    const double* c64;             // FP64 correlation if resident, else nullptr
+    const double* c64;
+    double* part;                  // recheck partial Gram sums: part_tests x slices x D doubles
+    unsigned long long part_tests; // queued tests per recheck batch
+    int* rec;                      // SepSet record pool (int32 groups i, j, l, S...)
+    unsigned long long rec_cap;
+    LevelMeta* lm;
+    int* host_flags;               // device view of pinned host flags: [l] = 1 runs, 2 loop ended
+};
+
+// Parameters of the level-0 FP64 recheck.
+struct Recheck0Params {
+    const double* z64;
+    long long ldz;
+    int n;
+    const double* c64;
     int p;
-    int l;
-    Binom B;
     double r2;
-    double rank_tol;
-    unsigned long long* best;
     const QEntry* queue;
     unsigned long long qcap;
     Meta* meta;
-    unsigned* bits;                // level 0: adjacency to clear
-    int W;
-};
-
-struct FinalizeParams {
-    const long long* row_off;
-    const int* cols;
-    const int* srow;
-    const int* partner;
-    const unsigned long long* best;
     unsigned* bits;
     int W;
-    int l;
-    Binom B;
-    int count_serial;
-    int* rec;                      // SepSet record pool (int32)
-    unsigned long long rec_cap;    // in ints
-    Meta* meta;
-    unsigned long long nnz;
 };
 
 cudaError_t launch_transpose(int dtype, const void* X, long long ld, int n, int p, void* Xt, cudaStream_t st);
@@ -85,19 +98,12 @@ cudaError_t launch_level0(int fp32, const void* C, int p, int W, double r0, doub
 cudaError_t launch_degree(const unsigned* bits, int p, int W, int* deg, Meta* meta, cudaStream_t st);
 cudaError_t launch_scan(const int* deg, int p, int l, int chunk, Binom B, long long* row_off,
                         long long* item_off, Meta* meta, cudaStream_t st);
-cudaError_t launch_fill(const unsigned* bits, int p, int W, const long long* row_off, int* cols, int* srow,
-                        cudaStream_t st);
-cudaError_t launch_items(const long long* item_off, int p, int* item_row, cudaStream_t st);
-cudaError_t launch_partner(const long long* row_off, const int* cols, const int* srow, long long nnz,
-                           int* partner, cudaStream_t st);
-cudaError_t launch_ci(int fp32, const CIParams& P, int grid, int block, cudaStream_t st);
-cudaError_t launch_recheck(const RecheckParams& P, int grid, cudaStream_t st);
-cudaError_t launch_recheck0(const RecheckParams& P, int grid, cudaStream_t st);
-cudaError_t launch_finalize(const FinalizeParams& P, cudaStream_t st);
+cudaError_t launch_recheck0(const Recheck0Params& P, int grid, cudaStream_t st);
+// One fused level kernel (cooperative launch). *grid receives the grid used.
+cudaError_t launch_level(int fp32, const LevelParams& P, int num_sms, cudaStream_t st);
 cudaError_t launch_pcor(int fp32, const void* C, int p, const int* q, long long nq, int l, double* rho,
                         cudaStream_t st);
 cudaError_t launch_bits_to_u8(const unsigned* bits, int p, int W, unsigned char* out, cudaStream_t st);
 
-int ci_max_level_supported();
 
 }  // namespace cupc

@@ -9,7 +9,7 @@
 // operand walks (hi, lo, hi); the dropped lo*lo term is below 2^-18.
 //
 // Kernel shape: one CTA per (128 x 128 upper-triangle output tile, K slice).
-// Warp 0 issues TMA loads (128B-swizzled, K-major) into a 4-stage ring, one
+// Warp 0 issues TMA loads (128B-swizzled, K-major) into a 6-stage ring, one
 // thread of warp 1 issues tcgen05.mma (M=128, N=128, K=16, bf16 -> f32) and
 // returns stages with tcgen05.commit. The tensor core's FP32 accumulation
 // error grows with the number of products summed into one accumulator, so the
@@ -32,7 +32,7 @@ namespace cupc {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;      // output tile and K slab (64 bf16 = 128 bytes)
-constexpr int STAGES = 4;
+constexpr int STAGES = 6;
 constexpr int TILE_BYTES = BM * BK * 2;         // 16 KiB per operand per stage
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;
 constexpr int THREADS = 192;
@@ -281,28 +281,44 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUten
     }
 }
 
-// Sum of the K-slice partials in slice order, times 1/n; the i < j value is
-// written to (i, j) and (j, i); the diagonal is 1.
-__global__ void k_corr_reduce(const float* __restrict__ ws, int tiles, int nsplit, int p, double inv_n,
-                              float* __restrict__ C)
+// Sum of the K-slice partials in slice order in FP64, times 1/n; the i < j
+// value is written to (i, j) and, through a shared-memory transpose, to
+// (j, i); the diagonal is 1. Block (tile, 8-row band): 256 threads.
+constexpr int RROWS = 8;
+__global__ void __launch_bounds__(256) k_corr_reduce(const float* __restrict__ ws, int tiles, int nsplit, int p,
+                                                     double inv_n, float* __restrict__ C)
 {
+    __shared__ float sm[RROWS][BN + 1];
     const int t = blockIdx.x;
     int bi, bj;
     tile_of(t, bi, bj);
-    for (int e = threadIdx.x; e < BM * BN; e += blockDim.x) {
-        const int r = e / BN, c = e % BN;
-        const int gi = bi * BM + r, gj = bj * BN + c;
-        if (gi >= p || gj >= p) continue;
-        if (gi == gj) {
-            C[(size_t)gi * p + gi] = 1.0f;
-            continue;
+    const int r0 = blockIdx.y * RROWS;
+    const int rr = threadIdx.x >> 5;            // row of the band (8 warps)
+    const int lane = threadIdx.x & 31;
+    const int r = r0 + rr, gi = bi * BM + r;
+    for (int c = lane; c < BN; c += 32) {
+        const int gj = bj * BN + c;
+        float v = 0.f;
+        bool valid = gi < p && gj < p && !(bi == bj && c < r);
+        if (valid) {
+            if (gi == gj) {
+                v = 1.0f;
+            } else {
+                double acc = 0.0;
+                for (int s = 0; s < nsplit; ++s) acc += (double)ws[(((size_t)s * tiles + t) * BM + r) * BN + c];
+                v = (float)(acc * inv_n);
+            }
+            C[(size_t)gi * p + gj] = v;
         }
-        if (gi > gj) continue;  // only in diagonal tiles: the mirror comes from (gj, gi)
-        double acc = 0.0;
-        for (int s = 0; s < nsplit; ++s) acc += (double)ws[(((size_t)s * tiles + t) * BM + r) * BN + c];
-        const float v = (float)(acc * inv_n);
-        C[(size_t)gi * p + gj] = v;
-        C[(size_t)gj * p + gi] = v;
+        sm[rr][c] = valid ? v : __int_as_float(0x7fc00001);
+    }
+    __syncthreads();
+    // mirror: column gi of rows gj <- the band, 8 consecutive floats per row
+    for (int e = threadIdx.x; e < BN * RROWS; e += 256) {
+        const int c = e / RROWS, k = e % RROWS;
+        const int gj = bj * BN + c, gi2 = bi * BM + r0 + k;
+        const float v = sm[k][c];
+        if (gj < p && gi2 < p && gj != gi2 && !(__float_as_int(v) == 0x7fc00001)) C[(size_t)gj * p + gi2] = v;
     }
 }
 
@@ -341,9 +357,22 @@ void corr_tc_plan(int p, long long ldk, int num_sms, int* tiles, int* nsplit, in
     const int nt = (p + BM - 1) / BM;
     const int kt = (int)(ldk / BK);
     *tiles = nt * (nt + 1) / 2;
-    int want = (num_sms + *tiles - 1) / *tiles;
-    want = max(1, min(want, 3 * kt));
-    *kps = (3 * kt + want - 1) / want;
+    // K slices per tile: one CTA per SM at a time, so aim for whole waves
+    // (tiles x slices close to a multiple of the SM count) with at least 16 K
+    // slabs per CTA
+    int best = 1;
+    double best_cost = 1e300;
+    for (int ns = 1; ns <= max(1, (3 * kt) / 16); ++ns) {
+        const int k = (3 * kt + ns - 1) / ns;
+        const long long ctas = (long long)(*tiles) * ns;
+        const long long waves = (ctas + num_sms - 1) / num_sms;
+        const double cost = (double)waves * (k + 4);  // +4: per-CTA fill and epilogue, in slabs
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = ns;
+        }
+    }
+    *kps = (3 * kt + best - 1) / best;
     *nsplit = (3 * kt + *kps - 1) / *kps;
     *ws_bytes = (size_t)(*nsplit) * (*tiles) * BM * BN * sizeof(float);
 }
@@ -367,7 +396,7 @@ cudaError_t launch_corr_tc(const void* hi, const void* lo, long long ldk, int p,
     k_corr_tc<<<dim3(tiles, nsplit), THREADS, SMEM_BYTES, st>>>(mh, ml, kt, kps, tiles, ws, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_corr_reduce<<<tiles, 256, 0, st>>>(ws, tiles, nsplit, p, 1.0 / n, C);
+    k_corr_reduce<<<dim3(tiles, BM / RROWS), 256, 0, st>>>(ws, tiles, nsplit, p, 1.0 / n, C);
     return cudaGetLastError();
 }
 

@@ -19,16 +19,17 @@ __global__ void k_level0(const T* __restrict__ C, int p, int W, double r0, doubl
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= p) return;
     const T* row = C + (size_t)i * p;
+    const T hi = (T)(r0 + band0), lo = (T)(r0 - band0);  // FP32 band edges
     for (int w = 0; w < W; ++w) {
         const int j = (w << 5) + lane;
         bool keep = false;
         if (j < p && j != i) {
-            const double c = fabs((double)row[j]);
+            const T c = row[j] < T(0) ? -row[j] : row[j];
             if (!FP32) {
-                keep = !(c <= r0);
+                keep = !(c <= (T)r0);
             } else {
-                if (c > r0 + band0) keep = true;
-                else if (c < r0 - band0) keep = false;
+                if (c > hi) keep = true;
+                else if (c < lo) keep = false;
                 else {
                     keep = true;
                     if (i < j) {

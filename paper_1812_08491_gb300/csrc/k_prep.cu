@@ -28,24 +28,11 @@ __global__ void k_transpose(const T* __restrict__ X, long long ld, int n, int p,
     }
 }
 
-template <int NT>
-__device__ __forceinline__ double block_sum(double x, double* red)
-{
-    // deterministic: fixed shuffle tree per warp, then warp partials in order
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[w] = x;
-    __syncthreads();
-    double t = 0.0;
-#pragma unroll
-    for (int k = 0; k < NT / 32; ++k) t += red[k];
-    return t;
-}
-
-// One block per variable: mean, centred variance, then the standardised row
-// z = (x - mean) * (1/sd) in FP64 (and optionally FP32, bf16 hi/lo splits).
+// One block per variable. Moments in FP64 in one pass over shifted values
+// (shift K = the variable's first sample, so the centred sums do not cancel):
+// S1 = sum (x - K), S2 = sum (x - K)^2, mean = K + S1/n,
+// var = (S2 - S1^2/n) / n (population variance, divisor n). A second pass
+// writes z = (x - mean)/sd in FP64 and, in FP32 mode, its bf16 split.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, long long ld, int n, int p,
                                                     double* __restrict__ mu, double* __restrict__ isd,
@@ -53,19 +40,37 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
                                                     __nv_bfloat16* __restrict__ zhi, __nv_bfloat16* __restrict__ zlo,
                                                     long long ldb, Meta* meta)
 {
-    __shared__ double red[NT / 32];
+    __shared__ double red[2][NT / 32];
     const int v = blockIdx.x;
     if (v >= p) return;
     const T* row = Xv + (size_t)v * ld;
-    double s = 0.0;
-    for (int k = threadIdx.x; k < n; k += NT) s += (double)row[k];
-    const double mean = block_sum<NT>(s, red) / (double)n;
-    double q = 0.0;
+    const double K = (double)row[0];
+    double s1 = 0.0, s2 = 0.0;
     for (int k = threadIdx.x; k < n; k += NT) {
-        const double d = (double)row[k] - mean;
-        q += d * d;
+        const double d = (double)row[k] - K;
+        s1 += d;
+        s2 = fma(d, d, s2);
     }
-    const double var = block_sum<NT>(q, red) / (double)n;
+    // deterministic block reduction: warp trees, then the warp partials in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[0][w] = s1;
+        red[1][w] = s2;
+    }
+    __syncthreads();
+    double S1 = 0.0, S2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) {
+        S1 += red[0][k];
+        S2 += red[1][k];
+    }
+    const double mean = K + S1 / (double)n;
+    const double var = (S2 - S1 * S1 / (double)n) / (double)n;
     const bool ok = (var > 0.0) && isfinite(var) && isfinite(mean);
     const double inv = ok ? 1.0 / sqrt(var) : 0.0;
     if (threadIdx.x == 0) {
@@ -73,15 +78,15 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
         isd[v] = inv;
         if (!ok) atomicOr(&meta->error, 1);
     }
-    if (z64)
-        for (int k = threadIdx.x; k < n; k += NT) z64[(size_t)v * ldz + k] = ((double)row[k] - mean) * inv;
-    if (zhi) {
-        // split z = hi + lo into two bf16 numbers (|z - hi - lo| < 2^-18 |z|); the
-        // centring is FP64 (exact for any mean), the scaling FP32 (2^-24, far below
-        // the split's 2^-18)
-        const float fi = (float)inv;
-        for (int k = threadIdx.x; k < n; k += NT) {
-            const float z = (float)((double)row[k] - mean) * fi;
+    // z = (x - mean) / sd in FP64; the bf16 split z = hi + lo (|z - hi - lo| <
+    // 2^-18 |z|) takes the FP64 centring and an FP32 scaling (2^-24, far below
+    // the split's 2^-18)
+    const float fi = (float)inv;
+    for (int k = threadIdx.x; k < n; k += NT) {
+        const double d = (double)row[k] - mean;
+        if (z64) z64[(size_t)v * ldz + k] = d * inv;
+        if (zhi) {
+            const float z = (float)d * fi;
             const __nv_bfloat16 h = __float2bfloat16_rn(z);
             zhi[(size_t)v * ldb + k] = h;
             zlo[(size_t)v * ldb + k] = __float2bfloat16_rn(z - __bfloat162float(h));

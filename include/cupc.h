@@ -220,6 +220,44 @@ cupc_status cupc_correlation(cupc_ctx* ctx, const void* X, int dtype, int layout
 cupc_status cupc_pcor_batch(cupc_ctx* ctx, const void* C, int dtype, int64_t p,
                             const int32_t* queries, int64_t nq, int l, double* rho_out);
 
+/* ---------------------------------------------------------------------------
+ * Candidate-scoring network for learned subset ordering (the paper has no
+ * learned component; these calls serve the ordering option). The network maps
+ * five features of a candidate k for edge side (i, j) at level l,
+ * (|C_ik|, |C_jk|, |C_ij|, l/8, |rho_ij.k|), through 5 -> 64 -> 64 -> 1 with
+ * ReLU to a score; with opts->learned_order, levels l >= 2 enumerate subsets of
+ * each side's candidates sorted by descending score (lexicographic over the
+ * sorted positions, so every subset is still reachable and the skeleton is
+ * unchanged). Parameters are CUPC_MLP_PARAMS floats packed W1 (64x5), b1 (64),
+ * W2 (64x64), b2 (64), w3 (64), b3 (1), row-major. Training keeps FP32
+ * master weights on the device; scoring uses their bf16 rounding.
+ * ------------------------------------------------------------------------- */
+#define CUPC_MLP_PARAMS 4609
+#define CUPC_MLP_FEATURES 5
+
+/* Loads parameters (host array of CUPC_MLP_PARAMS floats) into the context and
+ * resets the Adam moments. */
+cupc_status cupc_mlp_set_weights(cupc_ctx* ctx, const float* params);
+
+/* Copies the context's FP32 parameters to the host array `params`. */
+cupc_status cupc_mlp_get_weights(cupc_ctx* ctx, float* params);
+
+/* Gradient of the mean binary cross-entropy with logits over n examples:
+ * X device float [n x 5], t device float [n] (0 or 1); grad receives
+ * CUPC_MLP_PARAMS floats (host) and *loss the mean loss. Deterministic. */
+cupc_status cupc_mlp_grad(cupc_ctx* ctx, const float* X, const float* t, int64_t n, float* grad, double* loss);
+
+/* Scores of n feature rows (device float [n x 5]) into device float y[n],
+ * with the bf16 weights. */
+cupc_status cupc_mlp_forward(cupc_ctx* ctx, const float* X, int64_t n, float* y);
+
+/* Adam (lr, beta1 = 0.9, beta2 = 0.999, eps = 1e-8) over `epochs` passes of
+ * the n examples in order, mini-batches of `batch`; epoch_loss (host, may be
+ * NULL) receives each epoch's mean loss. All arithmetic runs in the library's
+ * kernels on the device. */
+cupc_status cupc_mlp_train(cupc_ctx* ctx, const float* X, const float* t, int64_t n, int64_t batch, int epochs,
+                           double lr, double* epoch_loss);
+
 /* Allocation-free FP64 correlation matrix (the paper has no counterpart).
  *
  * For callers that may not allocate device memory: plugins whose host

@@ -50,7 +50,13 @@ _SIGNATURES = {
     "cupc_pcor_batch": ("status", ["vp", "vp", "int", "i64", "vp", "i64", "int", "vp"]),
     "cupc_fisher_threshold": ("status", ["dbl", "i64", "int", "vp", "vp"]),
     "cupc_correlation_noalloc": ("status", ["vp", "int", "int", "i64", "i64", "i64", "vp", "vp"]),
+    "cupc_mlp_set_weights": ("status", ["vp", "vp"]),
+    "cupc_mlp_get_weights": ("status", ["vp", "vp"]),
+    "cupc_mlp_grad": ("status", ["vp", "vp", "vp", "i64", "vp", "vp"]),
+    "cupc_mlp_forward": ("status", ["vp", "vp", "i64", "vp"]),
+    "cupc_mlp_train": ("status", ["vp", "vp", "vp", "i64", "i64", "int", "dbl", "vp"]),
 }
+MLP_PARAMS = 4609
 
 
 class CupcError(RuntimeError):
@@ -320,6 +326,46 @@ class Context:
                                     ctypes.c_void_p(q.data_ptr()), q.shape[0], l, ctypes.c_void_p(rho.data_ptr()))
         self._check(st, "cupc_pcor_batch")
         return rho
+
+    # ---- candidate-scoring network -------------------------------------------
+    def mlp_set_weights(self, params):
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+        if p.size != MLP_PARAMS:
+            raise ValueError(f"expected {MLP_PARAMS} parameters")
+        self._check(load().cupc_mlp_set_weights(self._h, p.ctypes.data), "cupc_mlp_set_weights")
+
+    def mlp_get_weights(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, dtype=np.float32)
+        self._check(load().cupc_mlp_get_weights(self._h, out.ctypes.data), "cupc_mlp_get_weights")
+        return out
+
+    def mlp_grad(self, X, t):
+        """(gradient, mean loss) over device feature rows X [n x 5] and labels t [n]."""
+        torch = _torch()
+        X = X.to(torch.float32).contiguous()
+        t = t.to(torch.float32).contiguous()
+        g = np.empty(MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(load().cupc_mlp_grad(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                         X.shape[0], g.ctypes.data, ctypes.byref(loss)), "cupc_mlp_grad")
+        return g, loss.value
+
+    def mlp_forward(self, X):
+        torch = _torch()
+        X = X.to(torch.float32).contiguous()
+        y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        self._check(load().cupc_mlp_forward(self._h, ctypes.c_void_p(X.data_ptr()), X.shape[0],
+                                            ctypes.c_void_p(y.data_ptr())), "cupc_mlp_forward")
+        return y
+
+    def mlp_train(self, X, t, batch=4096, epochs=4, lr=1e-3):
+        torch = _torch()
+        X = X.to(torch.float32).contiguous()
+        t = t.to(torch.float32).contiguous()
+        losses = np.zeros(max(epochs, 1), dtype=np.float64)
+        self._check(load().cupc_mlp_train(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                          X.shape[0], batch, epochs, lr, losses.ctypes.data), "cupc_mlp_train")
+        return losses[:epochs]
 
     def close(self):
         if getattr(self, "_h", None):

@@ -9,16 +9,11 @@
 #include <string>
 #include <vector>
 
-#include "kernels.cuh"
+#include "api_internal.h"
 
 using namespace cupc;
 
 namespace {
-
-struct Buf {
-    void* p = nullptr;
-    size_t cap = 0;
-};
 
 constexpr double kBand0 = 2e-5;        // level 0 FP32 band on |C_ij|
 constexpr double kBandAbs = 4e-6;      // levels >= 1 FP32 band on |rho|
@@ -28,45 +23,6 @@ constexpr double kRankTol64 = 1e-12;   // FP64: pivot^2 at or below -> dependent
 constexpr double kRankTol32 = 1e-6;
 
 }  // namespace
-
-struct cupc_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    cudaMemPool_t pool = nullptr;
-    std::string err;
-    int refs = 1;
-    int num_sms = 0;
-    Buf xin, xt, mu, isd, z64, zhi, zlo, cws, c64, c32, cin;
-    Buf deg, row_off, item_off, item_row, cols, srow, partner, wpre, best, queue, binom, meta, lmeta, backup[2];
-    Buf part;
-    Meta* hmeta = nullptr;
-    LevelMeta* hlmeta = nullptr;
-    int* hflags = nullptr;         // pinned, mapped: per-level run / end flags written by the GPU
-    int* dflags = nullptr;         // device view of hflags
-    int binom_mstride = 0;
-    unsigned long long launches = 0;
-    unsigned long long h2d = 0, d2h = 0;
-    std::vector<cudaEvent_t> ev;
-    // kernel-class timing: event pairs recorded around the timed launches
-    std::vector<cudaEvent_t> tev;
-    std::vector<int> tcls;
-    int tused = 0;
-};
-
-struct cupc_result {
-    cupc_ctx* ctx = nullptr;
-    int64_t p = 0;
-    int W = 0;
-    unsigned* bits = nullptr;
-    unsigned* bits0 = nullptr;
-    int* rec = nullptr;
-    int64_t rec_ints = 0;
-    size_t rec_cap = 0;
-    cupc_stats stats{};
-    mutable bool host_ready = false;
-    mutable std::vector<int32_t> hrec;                              // sorted records
-    mutable std::vector<std::pair<uint64_t, int64_t>> index;        // (i*p+j) -> offset
-};
 
 namespace {
 
@@ -357,7 +313,10 @@ cupc_status validate_opts(cupc_ctx* ctx, const cupc_options& o)
     if (o.mode != CUPC_MODE_PLAIN_FP64 && o.mode != CUPC_MODE_FP32_RECHECK)
         return fail(ctx, CUPC_E_INVALID, "unknown mode");
     if (o.max_level < -1) return fail(ctx, CUPC_E_INVALID, "max_level must be >= -1");
-    if (o.learned_order) return fail(ctx, CUPC_E_INVALID, "learned ordering needs weights (cupc_mlp_set_weights)");
+    if (o.learned_order && !ctx->mlp_ready)
+        return fail(ctx, CUPC_E_STATE, "learned ordering needs network weights (cupc_mlp_set_weights)");
+    if (o.learned_order && o.mode != CUPC_MODE_FP32_RECHECK)
+        return fail(ctx, CUPC_E_INVALID, "learned ordering runs in CUPC_MODE_FP32_RECHECK");
     if (o.threads_per_block != 0 && (o.threads_per_block % 32 != 0 || o.threads_per_block > 256))
         return fail(ctx, CUPC_E_INVALID, "threads_per_block must be a multiple of 32 up to 256");
     if (o.chunk < 0) return fail(ctx, CUPC_E_INVALID, "chunk must be >= 0");
@@ -573,6 +532,19 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         LP.rec = R->rec;
         LP.rec_cap = rec_len_cap;
         LP.lm = lm;
+        LP.learned = o.learned_order ? 1 : 0;
+        if (o.learned_order) {
+            // per-slot candidate lists of levels >= 2 (sized from level 1; a level that
+            // would not fit keeps the increasing order)
+            const unsigned long long perm_cap =
+                std::min<unsigned long long>(std::max<unsigned long long>(M.block_entries, 1), 1ull << 26);
+            if ((s = ensure(ctx, *ctx_buf(ctx, "perm"), (size_t)perm_cap * 4)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, *ctx_buf(ctx, "poff"), (size_t)(p + 1) * 8)) != CUPC_OK) return s;
+            LP.perm = (int*)ctx_buf(ctx, "perm")->p;
+            LP.poff = (long long*)ctx_buf(ctx, "poff")->p;
+            LP.perm_cap = perm_cap;
+            LP.mlp_w = ctx_buf(ctx, "mlp_Pb")->p;
+        }
 
         // Levels are launched with at most two in flight: level l is launched only
         // once level l - 2 has reported (through pinned host memory, right after
@@ -711,6 +683,7 @@ void ctx_release(cupc_ctx* c)
                   &c->best, &c->queue, &c->binom, &c->meta, &c->lmeta, &c->backup[0], &c->backup[1],
                   &c->part};
     for (Buf* b : all) free_buf(ctx, *b);
+    for (auto& kv : c->named) free_buf(ctx, kv.second);
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
@@ -752,6 +725,23 @@ cupc_status build_host_records(const cupc_result* r)
 }
 
 }  // namespace
+
+cupc_status ctx_ensure(cupc_ctx* ctx, Buf* b, size_t bytes) { return ensure(ctx, *b, bytes); }
+Buf* ctx_buf(cupc_ctx* ctx, const char* name) { return &ctx->named[name]; }
+int ctx_num_sms(cupc_ctx* ctx) { return ctx->num_sms; }
+cudaStream_t ctx_stream(cupc_ctx* ctx) { return ctx->stream; }
+cupc_status ctx_fail(cupc_ctx* ctx, cupc_status s, const std::string& what, cudaError_t e)
+{
+    return fail(ctx, s, what, e);
+}
+void ctx_count_launch(cupc_ctx* ctx) { ctx->launches++; }
+void ctx_set_mlp(cupc_ctx* ctx, int ready, int step)
+{
+    ctx->mlp_ready = ready;
+    ctx->mlp_step = step;
+}
+int ctx_mlp_ready(cupc_ctx* ctx) { return ctx->mlp_ready; }
+int ctx_mlp_step(cupc_ctx* ctx) { return ctx->mlp_step; }
 
 // =============================================================================
 // C ABI

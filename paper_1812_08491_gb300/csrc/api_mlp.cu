@@ -1,0 +1,133 @@
+// api_mlp.cu -- C ABI of the candidate-scoring network: weights, gradient,
+// scoring and training on the device (kernels in k_mlp.cu).
+#include <cstring>
+#include <vector>
+
+#include "api_internal.h"
+#include "mlp.cuh"
+
+using namespace cupc;
+
+namespace {
+
+cupc_status mlp_ensure(cupc_ctx* ctx)
+{
+    cupc_status s;
+    if ((s = ctx_ensure(ctx, ctx_buf(ctx, "mlp_P"), MLP_NP * 4)) != CUPC_OK) return s;
+    if ((s = ctx_ensure(ctx, ctx_buf(ctx, "mlp_M"), MLP_NP * 4)) != CUPC_OK) return s;
+    if ((s = ctx_ensure(ctx, ctx_buf(ctx, "mlp_V"), MLP_NP * 4)) != CUPC_OK) return s;
+    if ((s = ctx_ensure(ctx, ctx_buf(ctx, "mlp_Pb"), MLP_NP * 2)) != CUPC_OK) return s;
+    if ((s = ctx_ensure(ctx, ctx_buf(ctx, "mlp_gsum"), MLP_NP * 4)) != CUPC_OK) return s;
+    const int blocks = ctx_num_sms(ctx);
+    if ((s = ctx_ensure(ctx, ctx_buf(ctx, "mlp_gpart"), (size_t)blocks * MLP_NP * 4)) != CUPC_OK) return s;
+    if ((s = ctx_ensure(ctx, ctx_buf(ctx, "mlp_lpart"), (size_t)blocks * 4)) != CUPC_OK) return s;
+    return CUPC_OK;
+}
+
+float* bufp(cupc_ctx* ctx, const char* name) { return (float*)ctx_buf(ctx, name)->p; }
+
+// gradient over [s0, s1) into mlp_gsum (and optionally an Adam step); returns
+// the summed loss of the range through *loss_sum when non-null.
+cupc_status grad_range(cupc_ctx* ctx, const float* X, const float* t, long long s0, long long s1, int step,
+                       float lr, double* loss_sum)
+{
+    const int blocks = (int)std::min<long long>(ctx_num_sms(ctx), (s1 - s0 + 127) / 128);
+    cudaStream_t st = ctx_stream(ctx);
+    cudaError_t e = launch_mlp_grad(bufp(ctx, "mlp_P"), X, t, s0, s1, bufp(ctx, "mlp_gpart"), bufp(ctx, "mlp_lpart"),
+                                    blocks, st);
+    ctx_count_launch(ctx);
+    if (e != cudaSuccess) return ctx_fail(ctx, CUPC_E_CUDA, "mlp gradient kernel", e);
+    e = launch_mlp_apply(bufp(ctx, "mlp_P"), bufp(ctx, "mlp_M"), bufp(ctx, "mlp_V"), bufp(ctx, "mlp_gpart"), blocks,
+                         bufp(ctx, "mlp_gsum"), step, lr, ctx_buf(ctx, "mlp_Pb")->p, st);
+    ctx_count_launch(ctx);
+    if (e != cudaSuccess) return ctx_fail(ctx, CUPC_E_CUDA, "mlp apply kernel", e);
+    if (loss_sum) {
+        std::vector<float> lp(blocks);
+        e = cudaMemcpyAsync(lp.data(), bufp(ctx, "mlp_lpart"), blocks * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return ctx_fail(ctx, CUPC_E_CUDA, "mlp loss readback", e);
+        for (int b = 0; b < blocks; ++b) *loss_sum += lp[b];
+    }
+    return CUPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cupc_status cupc_mlp_set_weights(cupc_ctx* ctx, const float* params)
+{
+    if (!ctx || !params) return CUPC_E_INVALID;
+    cupc_status s = mlp_ensure(ctx);
+    if (s != CUPC_OK) return s;
+    cudaStream_t st = ctx_stream(ctx);
+    cudaError_t e = cudaMemcpyAsync(bufp(ctx, "mlp_P"), params, MLP_NP * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bufp(ctx, "mlp_M"), 0, MLP_NP * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bufp(ctx, "mlp_V"), 0, MLP_NP * 4, st);
+    if (e == cudaSuccess) e = launch_mlp_to_bf16(bufp(ctx, "mlp_P"), ctx_buf(ctx, "mlp_Pb")->p, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return ctx_fail(ctx, CUPC_E_CUDA, "mlp weight upload", e);
+    ctx_set_mlp(ctx, 1, 0);
+    return CUPC_OK;
+}
+
+cupc_status cupc_mlp_get_weights(cupc_ctx* ctx, float* params)
+{
+    if (!ctx || !params) return CUPC_E_INVALID;
+    if (!ctx_mlp_ready(ctx)) return ctx_fail(ctx, CUPC_E_STATE, "no network weights loaded");
+    cudaStream_t st = ctx_stream(ctx);
+    cudaError_t e = cudaMemcpyAsync(params, bufp(ctx, "mlp_P"), MLP_NP * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return ctx_fail(ctx, CUPC_E_CUDA, "mlp weight download", e);
+    return CUPC_OK;
+}
+
+cupc_status cupc_mlp_grad(cupc_ctx* ctx, const float* X, const float* t, int64_t n, float* grad, double* loss)
+{
+    if (!ctx || !X || !t || !grad || n <= 0) return CUPC_E_INVALID;
+    if (!ctx_mlp_ready(ctx)) return ctx_fail(ctx, CUPC_E_STATE, "no network weights loaded");
+    double lsum = 0.0;
+    cupc_status s = grad_range(ctx, X, t, 0, n, 0, 0.f, &lsum);
+    if (s != CUPC_OK) return s;
+    cudaStream_t st = ctx_stream(ctx);
+    cudaError_t e = cudaMemcpyAsync(grad, bufp(ctx, "mlp_gsum"), MLP_NP * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return ctx_fail(ctx, CUPC_E_CUDA, "mlp gradient readback", e);
+    if (loss) *loss = lsum / (double)n;
+    return CUPC_OK;
+}
+
+cupc_status cupc_mlp_forward(cupc_ctx* ctx, const float* X, int64_t n, float* y)
+{
+    if (!ctx || !X || !y || n < 0) return CUPC_E_INVALID;
+    if (!ctx_mlp_ready(ctx)) return ctx_fail(ctx, CUPC_E_STATE, "no network weights loaded");
+    cudaStream_t st = ctx_stream(ctx);
+    cudaError_t e = launch_mlp_forward(ctx_buf(ctx, "mlp_Pb")->p, X, n, y, st);
+    ctx_count_launch(ctx);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return ctx_fail(ctx, CUPC_E_CUDA, "mlp forward", e);
+    return CUPC_OK;
+}
+
+cupc_status cupc_mlp_train(cupc_ctx* ctx, const float* X, const float* t, int64_t n, int64_t batch, int epochs,
+                           double lr, double* epoch_loss)
+{
+    if (!ctx || !X || !t || n <= 0 || batch <= 0 || epochs < 0 || !(lr > 0.0)) return CUPC_E_INVALID;
+    if (!ctx_mlp_ready(ctx)) return ctx_fail(ctx, CUPC_E_STATE, "no network weights loaded");
+    for (int ep = 0; ep < epochs; ++ep) {
+        double lsum = 0.0;
+        for (long long s0 = 0; s0 < n; s0 += batch) {
+            const long long s1 = std::min<long long>(n, s0 + batch);
+            const int step = ctx_mlp_step(ctx) + 1;
+            cupc_status s = grad_range(ctx, X, t, s0, s1, step, (float)lr, epoch_loss ? &lsum : nullptr);
+            if (s != CUPC_OK) return s;
+            ctx_set_mlp(ctx, 1, step);
+        }
+        if (epoch_loss) epoch_loss[ep] = lsum / (double)n;
+    }
+    cudaError_t e = cudaStreamSynchronize(ctx_stream(ctx));
+    if (e != cudaSuccess) return ctx_fail(ctx, CUPC_E_CUDA, "mlp training", e);
+    return CUPC_OK;
+}
+
+}  // extern "C"

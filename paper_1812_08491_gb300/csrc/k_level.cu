@@ -30,6 +30,7 @@
 #include <cstdio>
 
 #include "kernels.cuh"
+#include "mlp.cuh"
 
 namespace cupc {
 namespace {
@@ -117,26 +118,53 @@ __device__ void phase_prefix(const LevelParams& P, bool fp32)
 // P1: block 0 scans degrees into CSR offsets and work-item offsets. The chunk
 // (subset ranks per item) doubles until the items fit the item array.
 // ---------------------------------------------------------------------------
-__device__ void phase_scan(const LevelParams& P)
+// Work items of a row with degree d at level l: the subset ranks of the row
+// (S shared across j) or, in the learned order, of each side's own candidates.
+__device__ __forceinline__ unsigned long long row_items(const Binom& B, int d, int l, int chunk, bool lrn)
 {
-    __shared__ long long sa[32], sb[32];
+    if (d < l + 1) return 0;
+    if (!lrn) return (B(d, l) + chunk - 1) / chunk;
+    return (unsigned long long)d * ((B(d - 1, l) + chunk - 1) / chunk);
+}
+
+__device__ void phase_scan(const LevelParams& P, bool learned)
+{
+    __shared__ long long sa[32], sb[32], sc[32];
     __shared__ unsigned long long stot;
+    __shared__ int slrn;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int per = (P.p + NT - 1) / NT;
     const int lo = min(P.p, t * per), hi = min(P.p, lo + per);
     const int l = P.l;
-    int chunk = P.chunk0;
     int rng = 0;
+    // learned order: the per-side candidate lists must fit the perm array
+    bool lrn = false;
+    if (learned) {
+        unsigned long long c = 0;
+        for (int i = lo; i < hi; ++i) {
+            const int d = P.deg[i];
+            if (d >= l + 1) c += (unsigned long long)d * (unsigned long long)(d - 1);
+        }
+        c = warp_sum_u64(c);
+        if (lane == 0) sb[w] = (long long)c;
+        __syncthreads();
+        if (t == 0) {
+            unsigned long long tot = 0;
+            for (int k = 0; k < NW; ++k) tot += (unsigned long long)sb[k];
+            slrn = tot <= P.perm_cap ? 1 : 0;
+            P.lm->learned_on[l] = slrn;
+        }
+        __syncthreads();
+        lrn = slrn != 0;
+    }
+    int chunk = P.chunk0;
     // choose the chunk
     for (int it = 0; it < 48; ++it) {
         unsigned long long b = 0;
         for (int i = lo; i < hi; ++i) {
             const int d = P.deg[i];
-            if (d >= l + 1) {
-                const unsigned long long ns = P.B(d, l);
-                if (ns == ~0ull) rng = 1;
-                b += (ns + chunk - 1) / chunk;
-            }
+            if (d >= l + 1 && P.B(d, l) == ~0ull) rng = 1;
+            b += row_items(P.B, d, l, chunk, lrn);
         }
         b = warp_sum_u64(b);
         if (lane == 0) sb[w] = (long long)b;
@@ -152,17 +180,18 @@ __device__ void phase_scan(const LevelParams& P)
         if (fits) break;
         chunk = chunk > (1 << 29) ? chunk : chunk * 2;
     }
-    // exclusive scans of (degree, items); max degree
-    long long a = 0, b = 0;
+    // exclusive scans of (degree, items, candidate-list entries); max degree
+    long long a = 0, b = 0, c = 0;
     unsigned long long sq = 0;
     int dmax = 0;
     for (int i = lo; i < hi; ++i) {
         const int d = P.deg[i];
         dmax = max(dmax, d);
         a += d;
+        b += (long long)row_items(P.B, d, l, chunk, lrn);
         if (d >= l + 1) {
-            b += (long long)((P.B(d, l) + chunk - 1) / chunk);
             sq += (unsigned long long)(d + 1) * (unsigned long long)(d + 1);
+            if (lrn) c += (long long)d * (d - 1);
         }
     }
     sq = warp_sum_u64(sq);
@@ -170,41 +199,48 @@ __device__ void phase_scan(const LevelParams& P)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     if (lane == 0) atomicMax(&P.lm->maxdeg[l], dmax);
-    long long ia = a, ib = b;
+    long long ia = a, ib = b, ic = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const long long xa = __shfl_up_sync(0xffffffffu, ia, o);
         const long long xb = __shfl_up_sync(0xffffffffu, ib, o);
-        if (lane >= o) { ia += xa; ib += xb; }
+        const long long xc = __shfl_up_sync(0xffffffffu, ic, o);
+        if (lane >= o) { ia += xa; ib += xb; ic += xc; }
     }
     __syncthreads();
-    if (lane == 31) { sa[w] = ia; sb[w] = ib; }
+    if (lane == 31) { sa[w] = ia; sb[w] = ib; sc[w] = ic; }
     __syncthreads();
     if (w == 0) {
-        long long va = (lane < NW) ? sa[lane] : 0, vb = (lane < NW) ? sb[lane] : 0;
+        long long va = (lane < NW) ? sa[lane] : 0, vb = (lane < NW) ? sb[lane] : 0, vc = (lane < NW) ? sc[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const long long xa = __shfl_up_sync(0xffffffffu, va, o);
             const long long xb = __shfl_up_sync(0xffffffffu, vb, o);
-            if (lane >= o) { va += xa; vb += xb; }
+            const long long xc = __shfl_up_sync(0xffffffffu, vc, o);
+            if (lane >= o) { va += xa; vb += xb; vc += xc; }
         }
         sa[lane] = va;
         sb[lane] = vb;
+        sc[lane] = vc;
     }
     __syncthreads();
     long long ea = ia - a + (w > 0 ? sa[w - 1] : 0);
     long long eb = ib - b + (w > 0 ? sb[w - 1] : 0);
+    long long ec = ic - c + (w > 0 ? sc[w - 1] : 0);
     for (int i = lo; i < hi; ++i) {
         const int d = P.deg[i];
         P.row_off[i] = ea;
         P.item_off[i] = eb;
+        if (P.poff) P.poff[i] = ec;
         ea += d;
-        if (d >= l + 1) eb += (long long)((P.B(d, l) + chunk - 1) / chunk);
+        eb += (long long)row_items(P.B, d, l, chunk, lrn);
+        if (lrn && d >= l + 1) ec += (long long)d * (d - 1);
     }
     if (rng) atomicOr(&P.lm->range_error, 1);
     if (t == NT - 1) {
         P.row_off[P.p] = ea;
         P.item_off[P.p] = eb;
+        if (P.poff) P.poff[P.p] = ec;
         P.lm->edges[l] = (unsigned long long)ea / 2;
         P.lm->items[l] = (unsigned long long)eb;
         P.lm->chunk[l] = chunk;
@@ -375,6 +411,146 @@ __device__ void phase_ci(const LevelParams& P)
 }
 
 // ---------------------------------------------------------------------------
+// Learned ordering, levels l >= 2 (FP32 mode).
+// P3: for every slot (i, j), score each candidate k of adj(i) \ {j} with the
+// network and store the candidates by descending score (ties: increasing
+// position) -- a permutation, so full enumeration is still reached.
+// P4': each side enumerates the l-subsets of its own ordered candidates, in
+// lexicographic order of the ordered positions, lanes taking consecutive
+// ranks; the first separating rank per side is kept (atomicMin), the larger
+// endpoint's side stops once the smaller side has one.
+// ---------------------------------------------------------------------------
+constexpr int MCAP = 256;  // candidates scored per side; longer lists keep their increasing order
+
+__device__ __forceinline__ int* side_perm(const LevelParams& P, int i, long long e)
+{
+    const long long off = P.row_off[i];
+    const int m = (int)(P.row_off[i + 1] - off) - 1;
+    return P.perm + P.poff[i] + (e - off) * (long long)m;
+}
+
+__device__ void phase_score(const LevelParams& P)
+{
+    __shared__ __nv_bfloat16 Wsm[MLP_NP];
+    __shared__ float sc[NW][MCAP];
+    for (int q = threadIdx.x; q < MLP_NP; q += NT) Wsm[q] = ((const __nv_bfloat16*)P.mlp_w)[q];
+    __syncthreads();
+    const float* __restrict__ C = (const float*)P.C;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gw = (blockIdx.x * NT + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * NT) >> 5;
+    const long long nnz = P.row_off[P.p];
+    for (long long e = gw; e < nnz; e += nwarps) {
+        const int i = P.srow[e], j = P.cols[e];
+        const long long off = P.row_off[i];
+        const int m = (int)(P.row_off[i + 1] - off) - 1;
+        if (m < P.l) continue;
+        const int pj = (int)(e - off);
+        int* dst = side_perm(P, i, e);
+        if (m > MCAP) {
+            for (int c = lane; c < m; c += 32) dst[c] = P.cols[off + (c < pj ? c : c + 1)];
+            continue;
+        }
+        const float cij = C[(size_t)i * P.p + j];
+        for (int c = lane; c < m; c += 32) {
+            const int k = P.cols[off + (c < pj ? c : c + 1)];
+            float x[MLP_IN];
+            mlp_features(cij, C[(size_t)i * P.p + k], C[(size_t)j * P.p + k], P.l, x);
+            const float y = mlp_score(Wsm, x);
+            sc[w][c] = (y == y) ? y : -INFINITY;
+        }
+        __syncwarp();
+        for (int c = lane; c < m; c += 32) {
+            const float y = sc[w][c];
+            int r = 0;
+            for (int c2 = 0; c2 < m; ++c2) {
+                const float y2 = sc[w][c2];
+                r += (y2 > y) || (y2 == y && c2 < c);
+            }
+            dst[r] = P.cols[off + (c < pj ? c : c + 1)];
+        }
+        __syncwarp();
+    }
+}
+
+template <typename T, int LB, bool FP32>
+__device__ void phase_ci_edge(const LevelParams& P)
+{
+    const int lane = threadIdx.x & 31;
+    const T* __restrict__ C = (const T*)P.C;
+    const int p = P.p, l = P.l;
+    const unsigned long long n_items = P.lm->items[l];
+    const int chunk = P.lm->chunk[l];
+    unsigned long long ntests = 0;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(&P.lm->next_item[l], 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        const int i = P.item_row[item];
+        const long long k = (long long)item - P.item_off[i];
+        const long long off = P.row_off[i];
+        const int m = (int)(P.row_off[i + 1] - off) - 1;
+        const unsigned long long total = P.B(m, l);
+        const long long per_edge = (long long)((total + chunk - 1) / chunk);
+        const long long q = k / per_edge, cidx = k % per_edge;
+        const long long e = off + q;
+        const int j = P.cols[e];
+        const int* __restrict__ cand = side_perm(P, i, e);
+        const unsigned long long s0 = (unsigned long long)cidx * (unsigned long long)chunk;
+        const unsigned long long s1 = min(s0 + (unsigned long long)chunk, total);
+        const T* __restrict__ Ci = C + (size_t)i * p;
+        const T* __restrict__ Cj = C + (size_t)j * p;
+        const T cij = Ci[j];
+        const bool watch_partner = !P.canonical || i > j;
+        for (unsigned long long base = s0; base < s1; base += 32) {
+            unsigned long long be = 0, pb = 0;
+            if (lane == 0) {
+                be = ld_cg(P.best + e);
+                pb = watch_partner ? ld_cg(P.best + P.partner[e]) : RANK_NONE;
+            }
+            be = __shfl_sync(0xffffffffu, be, 0);
+            pb = __shfl_sync(0xffffffffu, pb, 0);
+            // a smaller rank already separates this side, or the other side decides
+            if (P.canonical ? (be < base) : (be != RANK_NONE)) break;
+            if (pb != RANK_NONE) break;
+            const unsigned long long r = base + lane;
+            if (r < s1 && r < be) {
+                int Q[LB], Sx[LB];
+                unrank_lex<LB>(r, m, l, P.B, Q);
+#pragma unroll
+                for (int c = 0; c < LB; ++c) Sx[c] = (c < l) ? cand[Q[c]] : 0;
+                Factor<T, LB> F;
+                factor_build<T, LB>(
+                    F, l, (T)P.rank_tol, [&](int a, int b) { return __ldg(C + (size_t)Sx[a] * p + Sx[b]); },
+                    [&](int a) { return __ldg(Ci + Sx[a]); });
+                T H12, H22;
+                factor_apply<T, LB>(F, l, cij, [&](int a) { return __ldg(Cj + Sx[a]); }, H12, H22);
+                const T H11 = T(1) - F.uu;
+                ++ntests;
+                const int dec = ci_decide<T, FP32>(H11, H12, H22, F.minpiv2, P);
+                if (dec == 1) {
+                    atomicMin(P.best + e, r);
+                } else if (FP32 && dec == 2) {
+                    const unsigned long long qq = atomicAdd(&P.lm->queue_len[l], 1ull);
+                    if (qq < P.qcap) {
+                        QEntry* Qe = P.queue + qq;
+                        Qe->a = (int)e;
+                        Qe->b = 0;
+                        Qe->s = r;
+#pragma unroll
+                        for (int c = 0; c < LB; ++c)
+                            if (c < l) Qe->S[c] = Sx[c];
+                    }
+                }
+            }
+        }
+    }
+    ntests = warp_sum_u64(ntests);
+    if (lane == 0 && ntests) atomicAdd(&P.lm->tests[l], ntests);
+}
+
+// ---------------------------------------------------------------------------
 // P5: FP64 rechecks. The samples of each queued test are cut into S slices
 // (S depends on n only, so the summation order is fixed); CTAs take (test,
 // slice) units and write partial Gram sums of the test's l + 2 standardised
@@ -498,11 +674,12 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
 // ---------------------------------------------------------------------------
 template <int LB>
 __device__ __forceinline__ unsigned long long side_serial(const LevelParams& P, int a, long long slot_b,
-                                                          unsigned long long rank)
+                                                          unsigned long long rank, bool lrn)
 {
     const long long off = P.row_off[a];
     const int d = (int)(P.row_off[a + 1] - off);
     if (rank == RANK_NONE) return P.B(d - 1, P.l);
+    if (lrn) return rank + 1;  // ranks already count the side's own candidates
     int Pos[LB];
     unrank_lex<LB>(rank, d, P.l, P.B, Pos);
     const int pb = (int)(slot_b - off);
@@ -512,8 +689,34 @@ __device__ __forceinline__ unsigned long long side_serial(const LevelParams& P, 
     return rank_lex<LB>(Pos, d - 1, P.l, P.B) + 1;
 }
 
+// Members of the separating set of rank `rank` found on side (a, b) at slot f.
 template <int LB>
-__device__ void phase_finalize(const LevelParams& P)
+__device__ __forceinline__ void side_members(const LevelParams& P, int a, long long f, unsigned long long rank,
+                                             bool lrn, int (&S)[LB])
+{
+    const long long off = P.row_off[a];
+    const int d = (int)(P.row_off[a + 1] - off);
+    int Pos[LB];
+    if (!lrn) {
+        unrank_lex<LB>(rank, d, P.l, P.B, Pos);
+#pragma unroll
+        for (int c = 0; c < LB; ++c) S[c] = (c < P.l) ? P.cols[off + Pos[c]] : 0x7fffffff;
+    } else {
+        unrank_lex<LB>(rank, d - 1, P.l, P.B, Pos);
+        const int* cand = side_perm(P, a, f);
+#pragma unroll
+        for (int c = 0; c < LB; ++c) S[c] = (c < P.l) ? cand[Pos[c]] : 0x7fffffff;
+        // increasing order for the record
+#pragma unroll
+        for (int x = 1; x < LB; ++x)
+#pragma unroll
+            for (int y = LB - 1; y >= x; --y)
+                if (S[y - 1] > S[y]) { const int tmp = S[y - 1]; S[y - 1] = S[y]; S[y] = tmp; }
+    }
+}
+
+template <int LB>
+__device__ void phase_finalize(const LevelParams& P, bool lrn)
 {
     const long long nnz = P.row_off[P.p];
     const int l = P.l;
@@ -527,18 +730,17 @@ __device__ void phase_finalize(const LevelParams& P)
                 const long long f = P.partner[e];
                 const unsigned long long bx = ld_cg(P.best + e), by = ld_cg(P.best + f);
                 int side = -1;
+                long long slot = 0;
                 unsigned long long rank = 0;
-                if (bx != RANK_NONE) { side = x; rank = bx; }
-                else if (by != RANK_NONE) { side = y; rank = by; }
+                if (bx != RANK_NONE) { side = x; rank = bx; slot = e; }
+                else if (by != RANK_NONE) { side = y; rank = by; slot = f; }
                 if (side >= 0) {
                     removed = true;
                     bitset_clear_pair(P.bits, P.W, x, y);
                     atomicSub(P.deg + x, 1);
                     atomicSub(P.deg + y, 1);
-                    const long long off = P.row_off[side];
-                    const int d = (int)(P.row_off[side + 1] - off);
-                    int Pos[LB];
-                    unrank_lex<LB>(rank, d, l, P.B, Pos);
+                    int S[LB];
+                    side_members<LB>(P, side, slot, rank, lrn, S);
                     const int ints = 3 + l;
                     const unsigned long long at = atomicAdd(&P.lm->rec_ints, (unsigned long long)ints);
                     if (at + ints <= P.rec_cap) {
@@ -548,12 +750,12 @@ __device__ void phase_finalize(const LevelParams& P)
                         r[2] = l;
 #pragma unroll
                         for (int c = 0; c < LB; ++c)
-                            if (c < l) r[3 + c] = P.cols[off + Pos[c]];
+                            if (c < l) r[3 + c] = S[c];
                     }
                 }
                 if (P.canonical) {
-                    serial = side_serial<LB>(P, x, e, bx);
-                    if (bx == RANK_NONE) serial += side_serial<LB>(P, y, f, by);
+                    serial = side_serial<LB>(P, x, e, bx, lrn);
+                    if (bx == RANK_NONE) serial += side_serial<LB>(P, y, f, by, lrn);
                 }
             }
         }
@@ -580,7 +782,7 @@ __device__ __forceinline__ void signal_host(const LevelParams& P, int v)
     }
 }
 
-template <typename T, int LB, bool FP32>
+template <typename T, int LB, bool FP32, bool LEARNED>
 __global__ void __launch_bounds__(NT) k_level(LevelParams P)
 {
     LevelMeta* lm = P.lm;
@@ -594,7 +796,7 @@ __global__ void __launch_bounds__(NT) k_level(LevelParams P)
     const bool timer = (blockIdx.x == 0 && threadIdx.x == 0);
     if (timer) t0 = gtimer();
 
-    if (blockIdx.x == 0) phase_scan(P);
+    if (blockIdx.x == 0) phase_scan(P, LEARNED && P.learned && l >= 2);
     if (blockIdx.x != 0 || gridDim.x == 1) phase_prefix(P, FP32);
     if (!grid_sync(lm)) {
         if (timer) signal_host(P, 2);
@@ -612,7 +814,14 @@ __global__ void __launch_bounds__(NT) k_level(LevelParams P)
     if (!grid_sync(lm)) return;
     if (timer) { t1 = gtimer(); lm->phase_ns[l][0] += t1 - t0; t0 = t1; }
 
-    phase_ci<T, LB, FP32>(P);
+    const bool lrn = LEARNED && *(volatile int*)&lm->learned_on[l];
+    if (LEARNED && lrn) {
+        phase_score(P);
+        if (!grid_sync(lm)) return;
+        phase_ci_edge<T, LB, FP32>(P);
+    } else {
+        phase_ci<T, LB, FP32>(P);
+    }
     if (!grid_sync(lm)) return;
     if (timer) { t1 = gtimer(); lm->phase_ns[l][1] += t1 - t0; t0 = t1; }
 
@@ -626,19 +835,19 @@ __global__ void __launch_bounds__(NT) k_level(LevelParams P)
         if (nq > 0 && !phase_recheck<LB>(P, nq)) return;
         if (timer) { t1 = gtimer(); lm->phase_ns[l][2] += t1 - t0; t0 = t1; }
     }
-    phase_finalize<LB>(P);
+    phase_finalize<LB>(P, lrn);
     if (timer) {
         t1 = gtimer();
         lm->phase_ns[l][3] += t1 - t0;
     }
 }
 
-template <typename T, int LB, bool FP32>
+template <typename T, int LB, bool FP32, bool LEARNED>
 cudaError_t launch_level_t(const LevelParams& P, int num_sms, cudaStream_t st)
 {
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level<T, LB, FP32>, NT, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level<T, LB, FP32, LEARNED>, NT, 0);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         per_sm = per_sm > 2 ? 2 : per_sm;
@@ -646,25 +855,27 @@ cudaError_t launch_level_t(const LevelParams& P, int num_sms, cudaStream_t st)
     const int grid = num_sms * per_sm;
     LevelParams arg = P;
     void* args[] = {&arg};
-    return cudaLaunchCooperativeKernel((const void*)k_level<T, LB, FP32>, dim3(grid), dim3(NT), args, 0, st);
+    return cudaLaunchCooperativeKernel((const void*)k_level<T, LB, FP32, LEARNED>, dim3(grid), dim3(NT), args, 0, st);
 }
 
-template <typename T, bool FP32>
+template <typename T, bool FP32, bool LEARNED>
 cudaError_t launch_level_b(const LevelParams& P, int num_sms, cudaStream_t st)
 {
-    if (P.l <= 1) return launch_level_t<T, 1, FP32>(P, num_sms, st);
-    if (P.l <= 2) return launch_level_t<T, 2, FP32>(P, num_sms, st);
-    if (P.l <= 4) return launch_level_t<T, 4, FP32>(P, num_sms, st);
-    if (P.l <= 8) return launch_level_t<T, 8, FP32>(P, num_sms, st);
-    if (P.l <= 12) return launch_level_t<T, 12, FP32>(P, num_sms, st);
-    return launch_level_t<T, 16, FP32>(P, num_sms, st);
+    if (P.l <= 1) return launch_level_t<T, 1, FP32, false>(P, num_sms, st);
+    if (P.l <= 2) return launch_level_t<T, 2, FP32, LEARNED>(P, num_sms, st);
+    if (P.l <= 4) return launch_level_t<T, 4, FP32, LEARNED>(P, num_sms, st);
+    if (P.l <= 8) return launch_level_t<T, 8, FP32, LEARNED>(P, num_sms, st);
+    if (P.l <= 12) return launch_level_t<T, 12, FP32, LEARNED>(P, num_sms, st);
+    return launch_level_t<T, 16, FP32, LEARNED>(P, num_sms, st);
 }
 
 }  // namespace
 
 cudaError_t launch_level(int fp32, const LevelParams& P, int num_sms, cudaStream_t st)
 {
-    return fp32 ? launch_level_b<float, true>(P, num_sms, st) : launch_level_b<double, false>(P, num_sms, st);
+    if (fp32 && P.learned) return launch_level_b<float, true, true>(P, num_sms, st);
+    return fp32 ? launch_level_b<float, true, false>(P, num_sms, st)
+                : launch_level_b<double, false, false>(P, num_sms, st);
 }
 
 }  // namespace cupc

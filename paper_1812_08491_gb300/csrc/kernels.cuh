@@ -20,6 +20,7 @@ struct LevelMeta {
     unsigned long long phase_ns[LV][4];    // compaction, CI, recheck, finalisation (wall ns)
     int maxdeg[LV];
     int chunk[LV];
+    int learned_on[LV];                    // the level enumerated in the network's order
     unsigned long long rec_ints;           // SepSet record ints appended
     int done_level;                        // level whose termination test stopped the loop
     int overflow_level;                    // level whose recheck queue overflowed
@@ -65,6 +66,12 @@ struct LevelParams {
     unsigned long long rec_cap;
     LevelMeta* lm;
     int* host_flags;               // device view of pinned host flags: [l] = 1 runs, 2 loop ended
+    // learned ordering (levels >= 2, FP32 mode)
+    int learned;                   // requested
+    const void* mlp_w;             // bf16 network parameters
+    int* perm;                     // per slot (i, j): adj(i) \ {j} by descending score
+    long long* poff;               // p + 1: first perm entry of each row
+    unsigned long long perm_cap;
 };
 
 // Parameters of the level-0 FP64 recheck.
@@ -104,6 +111,14 @@ cudaError_t launch_level(int fp32, const LevelParams& P, int num_sms, cudaStream
 cudaError_t launch_pcor(int fp32, const void* C, int p, const int* q, long long nq, int l, double* rho,
                         cudaStream_t st);
 cudaError_t launch_bits_to_u8(const unsigned* bits, int p, int W, unsigned char* out, cudaStream_t st);
+
+// candidate-scoring network (k_mlp.cu)
+cudaError_t launch_mlp_grad(const float* P, const float* X, const float* T, long long s0, long long s1, float* gpart,
+                            float* lpart, int blocks, cudaStream_t st);
+cudaError_t launch_mlp_apply(float* P, float* M, float* V, const float* gpart, int nblocks, float* gsum, int step,
+                             float lr, void* Pb, cudaStream_t st);
+cudaError_t launch_mlp_to_bf16(const float* P, void* Pb, cudaStream_t st);
+cudaError_t launch_mlp_forward(const void* Pb, const float* X, long long N, float* y, cudaStream_t st);
 
 
 }  // namespace cupc

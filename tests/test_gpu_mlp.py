@@ -1,0 +1,119 @@
+"""GPU kernels of the candidate-scoring network against the FP64 reference
+(oracle/mlp.py), and learned subset ordering against the skeleton oracle.
+
+Tolerances: the GPU computes in FP32, the reference in FP64 on the same
+(FP32-rounded) weights and data: gradients within 1e-4 relative of the largest
+entry plus 1e-3 of each entry; scores (bf16 weights, FP32 accumulation) within
+1e-4 relative. The learned order changes only the enumeration order, so the
+skeleton must equal the oracle's exactly and every stored SepSet must test
+independent under the oracle's CI test.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as mref
+from synth import sem
+
+cupc = pytest.importorskip("paper_1812_08491_gb300")
+torch = pytest.importorskip("torch")
+from paper_1812_08491_gb300 import learned  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda_device):
+    cupc.build_library()
+    c = cupc.Context(0)
+    yield c
+    c.close()
+
+
+def _params(seed):
+    P = mref.init_params(seed)
+    rng = np.random.default_rng(seed + 7)
+    for k in ("b1", "b2", "b3"):
+        P[k] = rng.normal(0, 0.2, P[k].shape)
+    v = mref.flatten(P).astype(np.float32)
+    return v, mref.unflatten(v.astype(np.float64))
+
+
+def _data(seed, n):
+    rng = np.random.default_rng(seed)
+    X = np.column_stack([rng.uniform(0, 1, n), rng.uniform(0, 1, n), rng.uniform(0, 1, n),
+                         rng.integers(2, 9, n) / 8.0, rng.uniform(0, 1, n)]).astype(np.float32)
+    t = (rng.random(n) < 0.25).astype(np.float32)
+    return X, t
+
+
+@pytest.mark.parametrize("n", [1, 37, 1000, 5000])
+def test_gradient_matches_reference(ctx, n):
+    v, P = _params(1)
+    X, t = _data(2, n)
+    ctx.mlp_set_weights(v)
+    g, loss = ctx.mlp_grad(torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda())
+    L, gr = mref.backward(P, X.astype(np.float64), t.astype(np.float64))
+    ref = mref.flatten(gr)
+    scale = np.max(np.abs(ref))
+    assert np.all(np.abs(g - ref) <= 1e-4 * scale + 1e-3 * np.abs(ref)), np.max(np.abs(g - ref))
+    assert loss == pytest.approx(L, rel=1e-5)
+
+
+def test_forward_matches_reference_with_bf16_weights(ctx):
+    v, _ = _params(3)
+    X, _ = _data(4, 3000)
+    ctx.mlp_set_weights(v)
+    y = ctx.mlp_forward(torch.from_numpy(X).cuda()).cpu().numpy()
+    Pb = mref.unflatten(mref.bf16_round(v))
+    ref, _ = mref.forward(Pb, X.astype(np.float64))
+    assert np.max(np.abs(y - ref)) <= 1e-4 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_adam_step_matches_reference(ctx):
+    v, P = _params(5)
+    X, t = _data(6, 2048)
+    ctx.mlp_set_weights(v)
+    lr = 1e-3
+    ctx.mlp_train(torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda(), batch=2048, epochs=1, lr=lr)
+    w = ctx.mlp_get_weights()
+    L, gr = mref.backward(P, X.astype(np.float64), t.astype(np.float64))
+    m = {k: np.zeros_like(a) for k, a in P.items()}
+    vv = {k: np.zeros_like(a) for k, a in P.items()}
+    P2, _, _ = mref.adam_step({k: a.copy() for k, a in P.items()}, gr, m, vv, step=1, lr=lr)
+    ref = mref.flatten(P2)
+    gflat = np.abs(mref.flatten(gr))
+    sure = gflat > 1e-4 * gflat.max()          # the first step is lr * sign(g): skip g ~ 0
+    assert np.max(np.abs(w[sure] - ref[sure])) <= 1e-6
+
+
+def test_training_reduces_loss(ctx):
+    X, _ = _data(8, 20000)
+    t = (X[:, 4] < 0.2).astype(np.float32)     # a learnable rule
+    losses = learned.train(ctx, X, t, epochs=5, batch=2048, lr=3e-3)
+    assert losses[-1] < 0.5 * losses[0]
+
+
+@pytest.fixture(scope="module")
+def trained(ctx):
+    probs = [sem.generate(200, 400, 31000 + k, "scale_free", m=2, w_min=0.2) for k in range(12)]
+    X, t = learned.collect(ctx, probs)
+    assert X.shape[0] > 500 and 0 < t.mean() < 0.5
+    learned.train(ctx, X, t, epochs=8, batch=2048, lr=3e-3)
+    return ctx.mlp_get_weights()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_learned_order_skeleton_parity(ctx, trained, seed):
+    s = sem.generate(300, 500, 32000 + seed, "scale_free", m=2, w_min=0.2)
+    C = oracle.correlation(s.X, nthreads=8)
+    ref = oracle.pc_stable(C, s.n, s.alpha, nthreads=8)
+    ctx.mlp_set_weights(trained)
+    res = ctx.skeleton(s.X, s.alpha, mode=cupc.MODE_FP32_RECHECK, learned_order=True)
+    assert np.array_equal(res.adjacency(), ref.adj)
+    assert np.array_equal(res.sep_levels(), ref.sep_level)
+    got = res.sepsets()
+    assert set(got) == set(ref.sepsets)
+    for (i, j), (l, S) in got.items():
+        ind, rho, z = oracle.ci_gauss(C, s.n, s.alpha, i, j, S)
+        assert ind, ((i, j), S, rho, z)

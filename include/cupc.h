@@ -92,7 +92,13 @@ typedef struct {
                                 built-in default */
     int threads_per_block;   /* CI kernel block size (0 = tuned default) */
     int chunk;               /* subsets per work item in the CI kernel (0 = default) */
-    int reserved[6];
+    int ctas_per_sm;         /* CTAs per SM of the fused level kernel (0 = as many as
+                                fit, at most 2) */
+    int corr_kps;            /* batch: K steps per work unit of the batched
+                                tensor-core product (0 = chosen by its cost model) */
+    int batch_direct;        /* batch: 1 = launch the kernels directly instead of
+                                capturing and replaying a CUDA graph (default 0) */
+    int reserved[3];
 } cupc_options;
 
 typedef struct {
@@ -118,6 +124,9 @@ typedef struct {
     float phase_ms[CUPC_STATS_LEVELS][4];        /* per level >= 1, wall time of its phases:
                                                     compaction, CI tests, FP64 rechecks,
                                                     removal + SepSets (device clock) */
+    int32_t cuda_graph;                          /* batch: 1 if the device work ran as a
+                                                    replayed CUDA graph, 0 if launched
+                                                    directly; single calls: 0 */
 } cupc_stats;
 
 typedef struct cupc_ctx cupc_ctx;
@@ -170,6 +179,65 @@ cupc_status cupc_skeleton(cupc_ctx* ctx, const void* X, int dtype, int layout, i
 cupc_status cupc_skeleton_corr(cupc_ctx* ctx, const void* C, int dtype, int on_device, int64_t p,
                                int64_t ld, int64_t n_samples, double alpha,
                                const cupc_options* opts, cupc_result** out);
+
+/* ---------------------------------------------------------------------------
+ * Batches of independent problems (the paper runs one problem per call; this
+ * is the library's own addition for many small and mid-size problems).
+ * Problem k has data X[k] (n_samples[k] x p[k], element type `dtype`, layout
+ * `layout`, dense: ld = p[k] for SAMPLE_MAJOR, n_samples[k] for
+ * VARIABLE_MAJOR; host pointers, or device pointers with on_device = 1) and
+ * significance level alpha[k]. The problems run together as one graph whose
+ * connected blocks are the problems: one standardisation launch, one
+ * tensor-core launch over every problem's output tiles, one level-0 launch,
+ * and per level l >= 1 one fused level kernel whose work queue holds the
+ * (row, subset-rank chunk) items of all problems. Level l runs while any
+ * problem still has an edge with enough neighbours; a problem whose threshold
+ * (n - l - 3 > 0) or opts->max_level ends earlier takes no work from then on.
+ * Each problem's skeleton and SepSets are exactly those of cupc_skeleton on
+ * it alone with the same options.
+ * The device work of a call is captured as a CUDA graph on the first call
+ * with a given set of shapes, alphas and options, and replayed by later calls
+ * with the same ones (opts->batch_direct = 1 launches it directly instead);
+ * the context keeps one such plan and its buffers until the shapes change or
+ * the context is destroyed. The call runs on a stream of its own, ordered
+ * after the work already queued on the context stream, and returns when the
+ * results are on the host.
+ *   nprob        number of problems, 1 <= nprob <= 4096; sum of p[k] rounded up
+ *                to 32 at most 2^20.
+ *   opts         NULL for defaults; mode must be CUPC_MODE_FP32_RECHECK and
+ *                learned_order 0.
+ *   out          array of nprob result pointers, each a new result (free each
+ *                with cupc_result_free). Their stats hold per problem:
+ *                serial_tests (canonical runs), removed, edges_start,
+ *                edges_final and levels; tests and rechecks per problem are -1.
+ *   batch_stats  NULL, or receives the whole batch's counters and timings
+ *                (total_ms = device time of the batch's kernels).
+ * Errors as cupc_skeleton; on error every out[k] is NULL. */
+cupc_status cupc_skeleton_batch(cupc_ctx* ctx, int nprob, const void* const* X, int dtype, int layout,
+                                int on_device, const int64_t* n_samples, const int64_t* p,
+                                const double* alpha, const cupc_options* opts, cupc_result** out,
+                                cupc_stats* batch_stats);
+
+/* One launch configuration tried by the batch autotuner and its time. */
+typedef struct {
+    int chunk;          /* subsets per work item */
+    int ctas_per_sm;    /* CTAs per SM of the level kernel */
+    int corr_kps;       /* K steps per unit of the batched product (resolved, > 0) */
+    float ms;           /* best device time of the batch over the repetitions */
+} cupc_tune_entry;
+
+/* Autotuner for batches: runs the batch described as in cupc_skeleton_batch
+ * once per candidate configuration (chunk in {8, 16, 32, 64, 128} x CTAs per SM
+ * in {1, 2} x product K-steps in {cost model, half, double}), each `reps`
+ * times (1 <= reps <= 16), and writes up to `cap` entries into `entries`,
+ * fastest first (*n_entries = number written). Every candidate must give the
+ * same skeleton and the same SepSets; otherwise CUPC_E_STATE. The caller
+ * stores the winner (e.g. in a table keyed by the batch's shape class) and
+ * passes it through opts->chunk, opts->ctas_per_sm and opts->corr_kps. */
+cupc_status cupc_batch_autotune(cupc_ctx* ctx, int nprob, const void* const* X, int dtype, int layout,
+                                int on_device, const int64_t* n_samples, const int64_t* p,
+                                const double* alpha, const cupc_options* base, int reps,
+                                cupc_tune_entry* entries, int cap, int* n_entries);
 
 /* Number of variables of a result. */
 cupc_status cupc_result_p(const cupc_result* res, int64_t* p);

@@ -50,6 +50,10 @@ _SIGNATURES = {
     "cupc_pcor_batch": ("status", ["vp", "vp", "int", "i64", "vp", "i64", "int", "vp"]),
     "cupc_fisher_threshold": ("status", ["dbl", "i64", "int", "vp", "vp"]),
     "cupc_correlation_noalloc": ("status", ["vp", "int", "int", "i64", "i64", "i64", "vp", "vp"]),
+    "cupc_skeleton_batch": ("status", ["vp", "int", "vp", "int", "int", "int", "vp", "vp", "vp", "opts_p", "vp",
+                                       "vp"]),
+    "cupc_batch_autotune": ("status", ["vp", "int", "vp", "int", "int", "int", "vp", "vp", "vp", "opts_p", "int",
+                                       "vp", "int", "vp"]),
     "cupc_mlp_set_weights": ("status", ["vp", "vp"]),
     "cupc_mlp_get_weights": ("status", ["vp", "vp"]),
     "cupc_mlp_grad": ("status", ["vp", "vp", "vp", "i64", "vp", "vp"]),
@@ -68,7 +72,8 @@ class CupcError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("canonical_sepset", ctypes.c_int), ("learned_order", ctypes.c_int),
                 ("max_level", ctypes.c_int), ("recheck_margin", ctypes.c_double),
-                ("threads_per_block", ctypes.c_int), ("chunk", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("threads_per_block", ctypes.c_int), ("chunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("corr_kps", ctypes.c_int), ("batch_direct", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -80,7 +85,13 @@ class Stats(ctypes.Structure):
                 ("edges_final", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
                 ("kernel_ms", ctypes.c_float * 8), ("kernel_count", ctypes.c_int32 * 8),
-                ("ci_block_entries", ctypes.c_int64 * L), ("phase_ms", (ctypes.c_float * 4) * L)]
+                ("ci_block_entries", ctypes.c_int64 * L), ("phase_ms", (ctypes.c_float * 4) * L),
+                ("cuda_graph", ctypes.c_int32)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("chunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("corr_kps", ctypes.c_int),
+                ("ms", ctypes.c_float)]
 
 
 _LIB = None
@@ -166,6 +177,20 @@ def _describe(X):
     raise TypeError("X must be a numpy array or a torch tensor")
 
 
+def _stats_dict(s: Stats) -> dict:
+    L = s.levels
+    return {"levels": L, "tests": list(s.tests[:L]), "serial_tests": list(s.serial_tests[:L]),
+            "removed": list(s.removed[:L]), "rechecks": list(s.rechecks[:L]),
+            "edges_start": list(s.edges_start[:L]), "max_degree": list(s.max_degree[:L]),
+            "level_ms": list(s.level_ms[:L]), "prep_ms": s.prep_ms, "total_ms": s.total_ms,
+            "edges_final": s.edges_final, "kernel_launches": s.kernel_launches,
+            "h2d_bytes": s.h2d_bytes, "d2h_bytes": s.d2h_bytes,
+            "kernel_ms": dict(zip(KERNEL_CLASSES, list(s.kernel_ms))),
+            "kernel_count": dict(zip(KERNEL_CLASSES, list(s.kernel_count))),
+            "ci_block_entries": list(s.ci_block_entries[:L]),
+            "phase_ms": [list(s.phase_ms[q]) for q in range(L)], "cuda_graph": s.cuda_graph}
+
+
 class Result:
     """Skeleton and SepSets of one call; owns library memory until free()."""
 
@@ -218,17 +243,7 @@ class Result:
     def stats(self) -> dict:
         s = Stats()
         self._check(load().cupc_result_stats(self._h, ctypes.byref(s)), "cupc_result_stats")
-        L = s.levels
-        return {"levels": L, "tests": list(s.tests[:L]), "serial_tests": list(s.serial_tests[:L]),
-                "removed": list(s.removed[:L]), "rechecks": list(s.rechecks[:L]),
-                "edges_start": list(s.edges_start[:L]), "max_degree": list(s.max_degree[:L]),
-                "level_ms": list(s.level_ms[:L]), "prep_ms": s.prep_ms, "total_ms": s.total_ms,
-                "edges_final": s.edges_final, "kernel_launches": s.kernel_launches,
-                "h2d_bytes": s.h2d_bytes, "d2h_bytes": s.d2h_bytes,
-                "kernel_ms": dict(zip(KERNEL_CLASSES, list(s.kernel_ms))),
-                "kernel_count": dict(zip(KERNEL_CLASSES, list(s.kernel_count))),
-                "ci_block_entries": list(s.ci_block_entries[:L]),
-                "phase_ms": [list(s.phase_ms[q]) for q in range(L)]}
+        return _stats_dict(s)
 
     def free(self):
         if self._h:
@@ -268,7 +283,8 @@ class Context:
 
     @staticmethod
     def options(mode=MODE_FP32_RECHECK, canonical=True, max_level=-1, recheck_margin=0.0,
-                threads_per_block=0, chunk=0, learned_order=False) -> Options:
+                threads_per_block=0, chunk=0, learned_order=False, ctas_per_sm=0, corr_kps=0,
+                batch_direct=False) -> Options:
         o = Options()
         load().cupc_options_default(ctypes.byref(o))
         o.mode = mode
@@ -278,7 +294,65 @@ class Context:
         o.threads_per_block = threads_per_block
         o.chunk = chunk
         o.learned_order = 1 if learned_order else 0
+        o.ctas_per_sm = ctas_per_sm
+        o.corr_kps = corr_kps
+        o.batch_direct = 1 if batch_direct else 0
         return o
+
+    @staticmethod
+    def _batch_args(Xs, alphas):
+        """Pointer, size and alpha arrays for a list of dense n x p arrays/tensors."""
+        if len(Xs) == 0:
+            raise ValueError("empty batch")
+        descs = [_describe(X) for X in Xs]
+        dts = {d[1] for d in descs}
+        lays = {d[2] for d in descs}
+        devs = {d[3] for d in descs}
+        if len(dts) != 1 or len(lays) != 1 or len(devs) != 1:
+            raise ValueError("all problems of a batch share dtype, layout and location")
+        layout = lays.pop()
+        for d in descs:
+            dense = d[6] == (d[5] if layout == SAMPLE_MAJOR else d[4])
+            if not dense:
+                raise ValueError("batch inputs must be dense (ld = row length)")
+        k = len(descs)
+        ptrs = (ctypes.c_void_p * k)(*[d[0] for d in descs])
+        ns = (ctypes.c_int64 * k)(*[d[4] for d in descs])
+        ps = (ctypes.c_int64 * k)(*[d[5] for d in descs])
+        if np.isscalar(alphas):
+            alphas = [float(alphas)] * k
+        al = (ctypes.c_double * k)(*[float(a) for a in alphas])
+        keep = [d[7] for d in descs]
+        return k, ptrs, dts.pop(), layout, devs.pop(), ns, ps, al, keep
+
+    def skeleton_batch(self, Xs, alphas, opts: Options | None = None, **kw):
+        """Skeletons of independent problems (list of n_k x p_k arrays or tensors,
+        all host or all device, one dtype and layout) in one batched pass.
+        Returns (list of Result, batch stats dict)."""
+        k, ptrs, dt, layout, on_dev, ns, ps, al, keep = self._batch_args(Xs, alphas)
+        o = opts if opts is not None else self.options(**kw)
+        outs = (ctypes.c_void_p * k)()
+        bst = Stats()
+        st = load().cupc_skeleton_batch(self._h, k, ptrs, dt, layout, on_dev, ns, ps, al, ctypes.byref(o), outs,
+                                        ctypes.byref(bst))
+        self._check(st, "cupc_skeleton_batch")
+        del keep
+        return [Result(self, outs[q]) for q in range(k)], _stats_dict(bst)
+
+    def autotune_batch(self, Xs, alphas, opts: Options | None = None, reps: int = 2, **kw):
+        """Launch configurations of a batch, fastest first:
+        [{"chunk", "ctas_per_sm", "corr_kps", "ms"}, ...]."""
+        k, ptrs, dt, layout, on_dev, ns, ps, al, keep = self._batch_args(Xs, alphas)
+        o = opts if opts is not None else self.options(**kw)
+        cap = 64
+        ents = (TuneEntry * cap)()
+        cnt = ctypes.c_int()
+        st = load().cupc_batch_autotune(self._h, k, ptrs, dt, layout, on_dev, ns, ps, al, ctypes.byref(o), reps,
+                                        ents, cap, ctypes.byref(cnt))
+        self._check(st, "cupc_batch_autotune")
+        del keep
+        return [{"chunk": e.chunk, "ctas_per_sm": e.ctas_per_sm, "corr_kps": e.corr_kps, "ms": e.ms}
+                for e in ents[:cnt.value]]
 
     def skeleton(self, X, alpha: float, opts: Options | None = None, **kw) -> Result:
         """Algorithm 1 on data X (n x p numpy array or torch tensor, host or device)."""

@@ -15,17 +15,6 @@ using namespace cupc;
 
 namespace {
 
-constexpr double kBand0 = 2e-5;        // level 0 FP32 band on |C_ij|
-constexpr double kBandAbs = 4e-6;      // levels >= 1 FP32 band on |rho|
-constexpr double kBandRel = 4e-6;      // widening per 1/(pivot^2 * min conditional variance)
-constexpr double kPivFloor = 1e-3;     // FP32: smaller pivot^2 goes to FP64
-constexpr double kRankTol64 = 1e-12;   // FP64: pivot^2 at or below -> dependent member
-constexpr double kRankTol32 = 1e-6;
-
-}  // namespace
-
-namespace {
-
 void ctx_release(cupc_ctx* c);
 
 cupc_status fail(cupc_ctx* c, cupc_status s, const std::string& what, cudaError_t e = cudaSuccess)
@@ -320,6 +309,7 @@ cupc_status validate_opts(cupc_ctx* ctx, const cupc_options& o)
     if (o.threads_per_block != 0 && (o.threads_per_block % 32 != 0 || o.threads_per_block > 256))
         return fail(ctx, CUPC_E_INVALID, "threads_per_block must be a multiple of 32 up to 256");
     if (o.chunk < 0) return fail(ctx, CUPC_E_INVALID, "chunk must be >= 0");
+    if (o.ctas_per_sm < 0 || o.corr_kps < 0) return fail(ctx, CUPC_E_INVALID, "ctas_per_sm, corr_kps must be >= 0");
     return CUPC_OK;
 }
 
@@ -503,6 +493,8 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         LP.bits = R->bits;
         LP.W = W;
         LP.p = p;
+        LP.nwords = (long long)p * W;
+        LP.ctas_per_sm = o.ctas_per_sm;
         LP.backup = fp32 ? (unsigned*)ctx->backup[0].p : nullptr;
         LP.deg = (int*)ctx->deg.p;
         LP.row_off = (long long*)ctx->row_off.p;
@@ -684,6 +676,7 @@ void ctx_release(cupc_ctx* c)
                   &c->part};
     for (Buf* b : all) free_buf(ctx, *b);
     for (auto& kv : c->named) free_buf(ctx, kv.second);
+    if (c->batch_free) c->batch_free(c);
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
@@ -727,6 +720,15 @@ cupc_status build_host_records(const cupc_result* r)
 }  // namespace
 
 cupc_status ctx_ensure(cupc_ctx* ctx, Buf* b, size_t bytes) { return ensure(ctx, *b, bytes); }
+void ctx_free(cupc_ctx* ctx, Buf* b) { free_buf(ctx, *b); }
+double ctx_fisher_tau(double alpha, int64_t n, int l) { return fisher_tau(alpha, n, l); }
+cupc_status ctx_binom(cupc_ctx* ctx, int m_needed, Binom* out)
+{
+    cupc_status s = ensure_binom(ctx, m_needed);
+    if (s == CUPC_OK) *out = binom_view(ctx);
+    return s;
+}
+cupc_status ctx_validate(cupc_ctx* ctx, const cupc_options& o) { return validate_opts(ctx, o); }
 Buf* ctx_buf(cupc_ctx* ctx, const char* name) { return &ctx->named[name]; }
 int ctx_num_sms(cupc_ctx* ctx) { return ctx->num_sms; }
 cudaStream_t ctx_stream(cupc_ctx* ctx) { return ctx->stream; }
@@ -862,10 +864,14 @@ cupc_status cupc_result_adjacency(const cupc_result* r, uint8_t* out)
     if (!r || !out) return CUPC_E_INVALID;
     cupc_ctx* ctx = r->ctx;
     const size_t bytes = (size_t)r->p * r->W * 4;
-    std::vector<unsigned> h(bytes / 4);
-    CU(cudaMemcpyAsync(h.data(), r->bits, bytes, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
-    ctx->d2h += bytes;
+    std::vector<unsigned> hd;
+    if (!r->on_host) {
+        hd.resize(bytes / 4);
+        CU(cudaMemcpyAsync(hd.data(), r->bits, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        ctx->d2h += bytes;
+    }
+    const std::vector<unsigned>& h = r->on_host ? r->hbits : hd;
     const int64_t p = r->p;
     for (int64_t i = 0; i < p; ++i)
         for (int64_t j = 0; j < p; ++j) out[i * p + j] = (uint8_t)((h[i * r->W + (j >> 5)] >> (j & 31)) & 1u);
@@ -877,10 +883,14 @@ cupc_status cupc_result_sep_levels(const cupc_result* r, int16_t* out)
     if (!r || !out) return CUPC_E_INVALID;
     cupc_ctx* ctx = r->ctx;
     const size_t bytes = (size_t)r->p * r->W * 4;
-    std::vector<unsigned> h0(bytes / 4);
-    CU(cudaMemcpyAsync(h0.data(), r->bits0, bytes, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
-    ctx->d2h += bytes;
+    std::vector<unsigned> hd;
+    if (!r->on_host) {
+        hd.resize(bytes / 4);
+        CU(cudaMemcpyAsync(hd.data(), r->bits0, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        ctx->d2h += bytes;
+    }
+    const std::vector<unsigned>& h0 = r->on_host ? r->hbits0 : hd;
     cupc_status s = build_host_records(r);
     if (s != CUPC_OK) return fail(ctx, s, "record download");
     const int64_t p = r->p;
@@ -916,7 +926,8 @@ cupc_status cupc_result_sepset(const cupc_result* r, int64_t i, int64_t j, int32
     }
     // not a level >= 1 removal: present, or removed at level 0
     unsigned w0 = 0;
-    CU(cudaMemcpy(&w0, r->bits0 + a * r->W + (b >> 5), 4, cudaMemcpyDeviceToHost));
+    if (r->on_host) w0 = r->hbits0[(size_t)a * r->W + (b >> 5)];
+    else CU(cudaMemcpy(&w0, r->bits0 + a * r->W + (b >> 5), 4, cudaMemcpyDeviceToHost));
     *len = ((w0 >> (b & 31)) & 1u) ? -1 : 0;
     return CUPC_OK;
 }

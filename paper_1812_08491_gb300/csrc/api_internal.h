@@ -8,6 +8,15 @@
 
 #include "kernels.cuh"
 
+namespace cupc {
+constexpr double kBand0 = 2e-5;        // level 0 FP32 band on |C_ij|
+constexpr double kBandAbs = 4e-6;      // levels >= 1 FP32 band on |rho|
+constexpr double kBandRel = 4e-6;      // widening per 1/(pivot^2 * min conditional variance)
+constexpr double kPivFloor = 1e-3;     // FP32: smaller pivot^2 goes to FP64
+constexpr double kRankTol64 = 1e-12;   // FP64: pivot^2 at or below -> dependent member
+constexpr double kRankTol32 = 1e-6;
+}  // namespace cupc
+
 struct Buf {
     void* p = nullptr;
     size_t cap = 0;
@@ -38,6 +47,8 @@ struct cupc_ctx {
     std::map<std::string, Buf> named;   // further device buffers (network state)
     int mlp_ready = 0;                  // network weights loaded
     int mlp_step = 0;                   // Adam steps taken
+    void* batch = nullptr;              // batch plan (api_batch.cu)
+    void (*batch_free)(cupc_ctx*) = nullptr;
 };
 
 struct cupc_result {
@@ -50,6 +61,8 @@ struct cupc_result {
     int64_t rec_ints = 0;
     size_t rec_cap = 0;
     cupc_stats stats{};
+    bool on_host = false;                                           // batch results: bitsets on the host
+    std::vector<unsigned> hbits, hbits0;
     mutable bool host_ready = false;
     mutable std::vector<int32_t> hrec;                              // sorted records
     mutable std::vector<std::pair<uint64_t, int64_t>> index;        // (i*p+j) -> offset
@@ -58,6 +71,10 @@ struct cupc_result {
 
 // helpers with external linkage for the other host files
 cupc_status ctx_ensure(cupc_ctx* ctx, Buf* b, size_t bytes);
+void ctx_free(cupc_ctx* ctx, Buf* b);
+double ctx_fisher_tau(double alpha, int64_t n, int l);
+cupc_status ctx_binom(cupc_ctx* ctx, int m_needed, cupc::Binom* out);
+cupc_status ctx_validate(cupc_ctx* ctx, const cupc_options& o);
 Buf* ctx_buf(cupc_ctx* ctx, const char* name);
 int ctx_num_sms(cupc_ctx* ctx);
 cudaStream_t ctx_stream(cupc_ctx* ctx);

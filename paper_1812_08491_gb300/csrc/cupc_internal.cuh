@@ -202,6 +202,13 @@ __device__ __forceinline__ void bitset_clear_pair(unsigned* bits, int W, int i, 
     atomicAnd(bits + (size_t)j * W + (i >> 5), ~(1u << (i & 31)));
 }
 
+// Same with the row starts given (rb_i: word of column 0 in row i).
+__device__ __forceinline__ void bitset_clear_pair_at(unsigned* bits, long long rb_i, long long rb_j, int i, int j)
+{
+    atomicAnd(bits + rb_i + (j >> 5), ~(1u << (j & 31)));
+    atomicAnd(bits + rb_j + (i >> 5), ~(1u << (i & 31)));
+}
+
 __device__ __forceinline__ bool bitset_test(const unsigned* bits, int W, int i, int j)
 {
     return (bits[(size_t)i * W + (j >> 5)] >> (j & 31)) & 1u;

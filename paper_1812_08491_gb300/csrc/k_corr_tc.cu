@@ -22,6 +22,8 @@
 //
 // Every mbarrier wait is bounded in time; on expiry the thread raises an error
 // flag, the others stop at their next wait, TMEM is freed and the kernel ends.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -163,9 +165,21 @@ __device__ __forceinline__ void tile_of(int t, int& bi, int& bj)
     bi = t - j * (j + 1) / 2;
 }
 
+// Work unit of a batch (a list of independent products in one launch): the
+// operand rows of the A and B tiles, the K steps [g0, g1) of its 3 kt, and
+// the workspace slot of its partial tile.
+struct __align__(16) CorrWork {
+    int ra, rb, g0, g1, kt, slot, pad0, pad1;
+};
+
+// Output tile of a batch: problem, tile coordinates, its partials' slots.
+struct __align__(16) CorrTile {
+    int prob, bi, bj, slot0, nsplit, pad0, pad1, pad2;
+};
+
 __global__ void __launch_bounds__(THREADS, 1)
 k_corr_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmL, int kt, int kps,
-          int tiles, float* __restrict__ ws, int* err)
+          int tiles, float* __restrict__ ws, int* err, const CorrWork* __restrict__ work)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -178,11 +192,26 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUten
     uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x, split = blockIdx.y;
-    int bi, bj;
-    tile_of(t, bi, bj);
-    const int g0 = split * kps;
-    const int g1 = min(g0 + kps, 3 * kt);
+    int ra, rb, g0, g1;
+    long long slot;
+    if (work) {
+        const CorrWork w = work[blockIdx.x];
+        ra = w.ra;
+        rb = w.rb;
+        g0 = w.g0;
+        g1 = w.g1;
+        kt = w.kt;
+        slot = w.slot;
+    } else {
+        const int t = blockIdx.x, split = blockIdx.y;
+        int bi, bj;
+        tile_of(t, bi, bj);
+        ra = bi * BM;
+        rb = bj * BN;
+        g0 = split * kps;
+        g1 = min(g0 + kps, 3 * kt);
+        slot = (long long)split * tiles + t;
+    }
     const int nsteps = g1 - g0;
     const int ngroups = (nsteps + GROUP - 1) / GROUP;
 
@@ -216,8 +245,8 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUten
             if (!mbar_wait(&empty[s], ph ^ 1u, err)) break;
             const int g = g0 + k, seg = g / kt, kk = g - seg * kt;
             mbar_expect_tx(&full[s], STAGE_BYTES);
-            tma_load_2d(sA + s * TILE_BYTES, seg == 2 ? &tmL : &tmH, kk * BK, bi * BM, &full[s]);
-            tma_load_2d(sB + s * TILE_BYTES, seg == 1 ? &tmL : &tmH, kk * BK, bj * BN, &full[s]);
+            tma_load_2d(sA + s * TILE_BYTES, seg == 2 ? &tmL : &tmH, kk * BK, ra, &full[s]);
+            tma_load_2d(sB + s * TILE_BYTES, seg == 1 ? &tmL : &tmH, kk * BK, rb, &full[s]);
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: group g accumulates into TMEM columns [128 (g & 1), +128)
@@ -268,7 +297,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUten
             if (lane == 0) mbar_arrive(&acc_empty[b]);
         }
         if (ok) {
-            float4* out = (float4*)(ws + (((size_t)split * tiles + t) * BM + row) * BN);
+            float4* out = (float4*)(ws + ((size_t)slot * BM + row) * BN);
 #pragma unroll
             for (int c = 0; c < BN / 4; ++c) out[c] = make_float4(R[4 * c], R[4 * c + 1], R[4 * c + 2], R[4 * c + 3]);
         }
@@ -285,13 +314,10 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUten
 // value is written to (i, j) and, through a shared-memory transpose, to
 // (j, i); the diagonal is 1. Block (tile, 8-row band): 256 threads.
 constexpr int RROWS = 8;
-__global__ void __launch_bounds__(256) k_corr_reduce(const float* __restrict__ ws, int tiles, int nsplit, int p,
-                                                     double inv_n, float* __restrict__ C)
+__device__ __forceinline__ void reduce_band(const float* __restrict__ ws, long long slot0, long long stride,
+                                            int nsplit, int bi, int bj, int p, double inv_n, float* __restrict__ C,
+                                            float (*sm)[BN + 1])
 {
-    __shared__ float sm[RROWS][BN + 1];
-    const int t = blockIdx.x;
-    int bi, bj;
-    tile_of(t, bi, bj);
     const int r0 = blockIdx.y * RROWS;
     const int rr = threadIdx.x >> 5;            // row of the band (8 warps)
     const int lane = threadIdx.x & 31;
@@ -305,7 +331,7 @@ __global__ void __launch_bounds__(256) k_corr_reduce(const float* __restrict__ w
                 v = 1.0f;
             } else {
                 double acc = 0.0;
-                for (int s = 0; s < nsplit; ++s) acc += (double)ws[(((size_t)s * tiles + t) * BM + r) * BN + c];
+                for (int s = 0; s < nsplit; ++s) acc += (double)ws[((size_t)(slot0 + s * stride) * BM + r) * BN + c];
                 v = (float)(acc * inv_n);
             }
             C[(size_t)gi * p + gj] = v;
@@ -320,6 +346,28 @@ __global__ void __launch_bounds__(256) k_corr_reduce(const float* __restrict__ w
         const float v = sm[k][c];
         if (gj < p && gi2 < p && gj != gi2 && !(__float_as_int(v) == 0x7fc00001)) C[(size_t)gj * p + gi2] = v;
     }
+}
+
+__global__ void __launch_bounds__(256) k_corr_reduce(const float* __restrict__ ws, int tiles, int nsplit, int p,
+                                                     double inv_n, float* __restrict__ C)
+{
+    __shared__ float sm[RROWS][BN + 1];
+    const int t = blockIdx.x;
+    int bi, bj;
+    tile_of(t, bi, bj);
+    reduce_band(ws, t, tiles, nsplit, bi, bj, p, inv_n, C, sm);
+}
+
+// Batch form: block x = output tile of the table, written into its problem's
+// p x p block of the packed C.
+__global__ void __launch_bounds__(256) k_corr_reduce_batch(const float* __restrict__ ws,
+                                                           const CorrTile* __restrict__ tt,
+                                                           const ProbDesc* __restrict__ probs, float* __restrict__ C)
+{
+    __shared__ float sm[RROWS][BN + 1];
+    const CorrTile T = tt[blockIdx.x];
+    const ProbDesc& D = probs[T.prob];
+    reduce_band(ws, T.slot0, 1, T.nsplit, T.bi, T.bj, D.p, 1.0 / (double)D.n, C + D.c_off, sm);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -393,10 +441,105 @@ cudaError_t launch_corr_tc(const void* hi, const void* lo, long long ldk, int p,
         attr_set = true;
     }
     const int kt = (int)(ldk / BK);
-    k_corr_tc<<<dim3(tiles, nsplit), THREADS, SMEM_BYTES, st>>>(mh, ml, kt, kps, tiles, ws, err);
+    k_corr_tc<<<dim3(tiles, nsplit), THREADS, SMEM_BYTES, st>>>(mh, ml, kt, kps, tiles, ws, err, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_corr_reduce<<<dim3(tiles, BM / RROWS), 256, 0, st>>>(ws, tiles, nsplit, p, 1.0 / n, C);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batch: the products of many problems in one launch. The operands hold every
+// problem's standardised rows at its vertex offset (ld = ldk for all); each
+// problem's upper-triangle tiles are cut into K slices of at most kps steps
+// (never past its own 3 kt_k steps), the work units ordered longest first.
+// ---------------------------------------------------------------------------
+void corr_tc_batch_plan(const std::vector<ProbDesc>& probs, int num_sms, int kps_req,
+                        std::vector<CorrBatchUnit>& units, std::vector<CorrBatchTile>& tiles, size_t* ws_bytes,
+                        int* kps_out)
+{
+    units.clear();
+    tiles.clear();
+    long long steps_total = 0;
+    for (const ProbDesc& D : probs) {
+        const int nt = (D.p + BM - 1) / BM;
+        const int kt = (D.n + BK - 1) / BK;
+        steps_total += (long long)nt * (nt + 1) / 2 * 3 * kt;
+    }
+    // slice length: whole waves of one CTA per SM, at least 16 steps a unit
+    int best_kps = 16;
+    double best_cost = 1e300;
+    for (int kps = 16; kps <= 4096; kps *= 2) {
+        long long n_units = 0, longest = 0;
+        for (const ProbDesc& D : probs) {
+            const int nt = (D.p + BM - 1) / BM;
+            const int kt = (D.n + BK - 1) / BK;
+            n_units += (long long)nt * (nt + 1) / 2 * ((3 * kt + kps - 1) / kps);
+            longest = std::max<long long>(longest, std::min(kps, 3 * kt));
+        }
+        // a bound on the makespan: the average load per SM (+4 steps of fill per
+        // unit) or the longest unit
+        const double load = (double)(steps_total + 4 * n_units) / num_sms;
+        const double cost = std::max(load, (double)(longest + 4)) + 0.02 * (double)n_units / num_sms;
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best_kps = kps;
+        }
+    }
+    if (kps_req > 0) best_kps = kps_req;
+    *kps_out = best_kps;
+    int slot = 0;
+    for (int k = 0; k < (int)probs.size(); ++k) {
+        const ProbDesc& D = probs[k];
+        const int nt = (D.p + BM - 1) / BM;
+        const int kt = (D.n + BK - 1) / BK;
+        const int ns = (3 * kt + best_kps - 1) / best_kps;
+        for (int bj = 0; bj < nt; ++bj)
+            for (int bi = 0; bi <= bj; ++bi) {
+                CorrBatchTile T{};
+                T.prob = k;
+                T.bi = bi;
+                T.bj = bj;
+                T.slot0 = slot;
+                T.nsplit = ns;
+                tiles.push_back(T);
+                for (int q = 0; q < ns; ++q) {
+                    CorrBatchUnit U{};
+                    U.ra = D.off + bi * BM;
+                    U.rb = D.off + bj * BN;
+                    U.g0 = q * best_kps;
+                    U.g1 = std::min(3 * kt, (q + 1) * best_kps);
+                    U.kt = kt;
+                    U.slot = slot++;
+                    units.push_back(U);
+                }
+            }
+    }
+    std::stable_sort(units.begin(), units.end(),
+                     [](const CorrBatchUnit& a, const CorrBatchUnit& b) { return a.g1 - a.g0 > b.g1 - b.g0; });
+    *ws_bytes = (size_t)slot * BM * BN * sizeof(float);
+}
+
+cudaError_t launch_corr_tc_batch(const void* hi, const void* lo, long long ldk, int rows, const void* units,
+                                 int n_units, const void* tiles, int n_tiles, const ProbDesc* probs, float* ws,
+                                 float* C, int* err, cudaStream_t st)
+{
+    static_assert(sizeof(CorrBatchUnit) == sizeof(CorrWork), "work unit layout");
+    static_assert(sizeof(CorrBatchTile) == sizeof(CorrTile), "tile layout");
+    if (n_units == 0) return cudaSuccess;
+    if (ldk % BK != 0 || ((uintptr_t)hi & 15) || ((uintptr_t)lo & 15)) return cudaErrorInvalidValue;
+    CUtensorMap mh, ml;
+    if (!make_map(&mh, hi, rows, ldk) || !make_map(&ml, lo, rows, ldk)) return cudaErrorInvalidValue;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_corr_tc<<<n_units, THREADS, SMEM_BYTES, st>>>(mh, ml, 0, 0, 0, ws, err, (const CorrWork*)units);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_corr_reduce_batch<<<dim3(n_tiles, BM / RROWS), 256, 0, st>>>(ws, (const CorrTile*)tiles, probs, C);
     return cudaGetLastError();
 }
 

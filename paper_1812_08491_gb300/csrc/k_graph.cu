@@ -11,19 +11,28 @@ namespace cupc {
 // monotone). In FP32 mode |C_ij| within band0 of the threshold keeps the
 // edge for now and queues the pair (once, from the i < j side) for FP64.
 // ---------------------------------------------------------------------------
+// In a batch (descriptors given) row i reads its problem's block of C, its
+// threshold, and writes only its problem's words; padding rows stay empty.
 template <typename T, bool FP32>
 __global__ void k_level0(const T* __restrict__ C, int p, int W, double r0, double band0, unsigned* __restrict__ bits,
-                         QEntry* __restrict__ q, unsigned long long qcap, Meta* meta)
+                         QEntry* __restrict__ q, unsigned long long qcap, Meta* meta, const int* __restrict__ vprob,
+                         const ProbDesc* __restrict__ probs, int nrows)
 {
     const int lane = threadIdx.x & 31;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= p) return;
-    const T* row = C + (size_t)i * p;
+    if (i >= nrows) return;
+    const ProbDesc* D = prob_of(vprob, probs, i);
+    const int off = D ? D->off : 0, pp = D ? D->p : p;
+    const int wlo = D ? D->wlo : 0, whi = D ? D->whi : W;
+    const long long rb = rowbase(D, W, i);
+    const bool live = i - off < pp;
+    const T* row = C + (D ? D->c_off : 0) + (long long)(i - off) * pp - off;
+    if (D) r0 = D->r[0];
     const T hi = (T)(r0 + band0), lo = (T)(r0 - band0);  // FP32 band edges
-    for (int w = 0; w < W; ++w) {
+    for (int w = wlo; w < whi; ++w) {
         const int j = (w << 5) + lane;
         bool keep = false;
-        if (j < p && j != i) {
+        if (live && j - off < pp && j != i) {
             const T c = row[j] < T(0) ? -row[j] : row[j];
             if (!FP32) {
                 keep = !(c <= (T)r0);
@@ -44,18 +53,22 @@ __global__ void k_level0(const T* __restrict__ C, int p, int W, double r0, doubl
             }
         }
         const unsigned word = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) bits[(size_t)i * W + w] = word;
+        if (lane == 0) bits[rb + w] = word;
     }
 }
 
 cudaError_t launch_level0(int fp32, const void* C, int p, int W, double r0, double band0, unsigned* bits,
-                          QEntry* q, unsigned long long qcap, Meta* meta, cudaStream_t st)
+                          QEntry* q, unsigned long long qcap, Meta* meta, cudaStream_t st, const int* vprob,
+                          const ProbDesc* probs, int nrows)
 {
-    const int block = 256, grid = (p * 32 + block - 1) / block;
+    if (!vprob) nrows = p;
+    const int block = 256, grid = (int)(((long long)nrows * 32 + block - 1) / block);
     if (fp32)
-        k_level0<float, true><<<grid, block, 0, st>>>((const float*)C, p, W, r0, band0, bits, q, qcap, meta);
+        k_level0<float, true><<<grid, block, 0, st>>>((const float*)C, p, W, r0, band0, bits, q, qcap, meta, vprob,
+                                                      probs, nrows);
     else
-        k_level0<double, false><<<grid, block, 0, st>>>((const double*)C, p, W, r0, band0, bits, q, qcap, meta);
+        k_level0<double, false><<<grid, block, 0, st>>>((const double*)C, p, W, r0, band0, bits, q, qcap, meta,
+                                                        vprob, probs, nrows);
     return cudaGetLastError();
 }
 
@@ -63,13 +76,17 @@ cudaError_t launch_level0(int fp32, const void* C, int p, int W, double r0, doub
 // Compaction (Sec. 3.3 "Compact"): degrees, one block scan for the CSR offsets
 // and the work-item offsets, then each row's sorted neighbour list.
 // ---------------------------------------------------------------------------
-__global__ void k_degree(const unsigned* __restrict__ bits, int p, int W, int* __restrict__ deg, Meta* meta)
+__global__ void k_degree(const unsigned* __restrict__ bits, int p, int W, int* __restrict__ deg, Meta* meta,
+                         const int* __restrict__ vprob, const ProbDesc* __restrict__ probs)
 {
     const int lane = threadIdx.x & 31;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= p) return;
+    const ProbDesc* D = prob_of(vprob, probs, i);
+    const int wlo = D ? D->wlo : 0, whi = D ? D->whi : W;
+    const long long rb = rowbase(D, W, i);
     int c = 0;
-    for (int w = lane; w < W; w += 32) c += __popc(bits[(size_t)i * W + w]);
+    for (int w = wlo + lane; w < whi; w += 32) c += __popc(bits[rb + w]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if (lane == 0) {
@@ -78,10 +95,11 @@ __global__ void k_degree(const unsigned* __restrict__ bits, int p, int W, int* _
     }
 }
 
-cudaError_t launch_degree(const unsigned* bits, int p, int W, int* deg, Meta* meta, cudaStream_t st)
+cudaError_t launch_degree(const unsigned* bits, int p, int W, int* deg, Meta* meta, cudaStream_t st,
+                          const int* vprob, const ProbDesc* probs)
 {
-    const int block = 256, grid = (p * 32 + block - 1) / block;
-    k_degree<<<grid, block, 0, st>>>(bits, p, W, deg, meta);
+    const int block = 256, grid = (int)(((long long)p * 32 + block - 1) / block);
+    k_degree<<<grid, block, 0, st>>>(bits, p, W, deg, meta, vprob, probs);
     return cudaGetLastError();
 }
 
@@ -179,11 +197,20 @@ __global__ void __launch_bounds__(RC_THREADS) k_recheck0(Recheck0Params P)
     unsigned long long done = 0;
     for (long long qi = blockIdx.x; qi < (long long)nq; qi += gridDim.x) {
         const QEntry E = P.queue[qi];
-        const int V[2] = {E.a, E.b};
+        const ProbDesc* D = prob_of(P.vprob, P.probs, E.a);
         double G[1];
-        c_block<2, RC_THREADS>(P.c64, P.p, P.z64, P.ldz, P.n, V, 2, G, red);
+        if (D) {
+            // the problem's own rows: local ids, its sample count
+            const int V[2] = {E.a - D->off, E.b - D->off};
+            c_block<2, RC_THREADS>(nullptr, D->p, P.z64 + D->z_off, D->n, D->n, V, 2, G, red);
+        } else {
+            const int V[2] = {E.a, E.b};
+            c_block<2, RC_THREADS>(P.c64, P.p, P.z64, P.ldz, P.n, V, 2, G, red);
+        }
         // independent iff rho^2 <= tanh(tau_0)^2
-        if (threadIdx.x == 0 && G[0] * G[0] <= P.r2) bitset_clear_pair(P.bits, P.W, E.a, E.b);
+        const double r2 = D ? D->r2[0] : P.r2;
+        if (threadIdx.x == 0 && G[0] * G[0] <= r2)
+            bitset_clear_pair_at(P.bits, rowbase(D, P.W, E.a), rowbase(D, P.W, E.b), E.a, E.b);
         ++done;
     }
     if (threadIdx.x == 0 && done) atomicAdd(&P.meta->rechecks, done);

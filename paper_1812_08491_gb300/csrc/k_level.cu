@@ -48,6 +48,61 @@ __device__ __forceinline__ unsigned long long gtimer()
 
 __device__ __forceinline__ unsigned long long ld_cg(const unsigned long long* p) { return __ldcg(p); }
 
+// View of the correlation block of vertex v's problem, indexed by global ids.
+template <typename T>
+struct CView {
+    const T* base;
+    int off, p;
+    __device__ __forceinline__ const T* row(int a) const { return base + (long long)(a - off) * p - off; }
+};
+
+template <typename T>
+__device__ __forceinline__ CView<T> cview(const LevelParams& P, int v)
+{
+    CView<T> c;
+    const ProbDesc* D = prob_of(P.vprob, P.probs, v);
+    c.base = (const T*)P.C + (D ? D->c_off : 0);
+    c.off = D ? D->off : 0;
+    c.p = D ? D->p : P.p;
+    return c;
+}
+
+// Bitset words of row v that can hold neighbours, and the row's base.
+__device__ __forceinline__ void word_range(const LevelParams& P, int v, int& lo, int& hi, long long& rb)
+{
+    const ProbDesc* D = prob_of(P.vprob, P.probs, v);
+    lo = D ? D->wlo : 0;
+    hi = D ? D->whi : P.W;
+    rb = rowbase(D, P.W, v);
+}
+
+__device__ __forceinline__ long long row_base(const LevelParams& P, int v)
+{
+    return rowbase(prob_of(P.vprob, P.probs, v), P.W, v);
+}
+
+// Degree of row i as far as this level's work items go: 0 for a problem whose
+// threshold or level limit ends before this level.
+__device__ __forceinline__ int item_deg(const LevelParams& P, int i)
+{
+    const int d = P.deg[i];
+    if (P.vprob && P.l > P.probs[P.vprob[i]].lmax) return 0;
+    return d;
+}
+
+// tanh(tau_l) of vertex v's problem and its square.
+__device__ __forceinline__ void thresholds(const LevelParams& P, int v, double& r, double& r2)
+{
+    if (P.vprob) {
+        const ProbDesc& D = P.probs[P.vprob[v]];
+        r = D.r[P.l];
+        r2 = D.r2[P.l];
+    } else {
+        r = P.r;
+        r2 = P.r2;
+    }
+}
+
 // Grid-wide barrier for a cooperative launch. Returns false (uniformly in the
 // CTA) when the kernel must stop: a wait expired or an error was raised.
 __device__ bool grid_sync(LevelMeta* lm)
@@ -93,22 +148,25 @@ __device__ void phase_prefix(const LevelParams& P, bool fp32)
     const int gw = (bid * NT + threadIdx.x) >> 5;
     const int nwarps = (nb * NT) >> 5;
     for (int i = gw; i < P.p; i += nwarps) {
+        int wlo, whi;
+        long long rb;
+        word_range(P, i, wlo, whi, rb);
         int base = 0;
-        for (int w0 = 0; w0 < P.W; w0 += 32) {
+        for (int w0 = wlo; w0 < whi; w0 += 32) {
             const int q = w0 + lane;
-            const int c = (q < P.W) ? __popc(P.bits[(size_t)i * P.W + q]) : 0;
+            const int c = (q < whi) ? __popc(P.bits[rb + q]) : 0;
             int incl = c;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int x = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += x;
             }
-            if (q < P.W) P.wpre[(size_t)i * P.W + q] = base + incl - c;
+            if (q < whi) P.wpre[rb + q] = base + incl - c;
             base += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
     if (fp32) {
-        const size_t words = (size_t)P.p * P.W;
+        const size_t words = (size_t)P.nwords;
         for (size_t k = (size_t)bid * NT + threadIdx.x; k < words; k += (size_t)nb * NT)
             P.backup[k] = P.bits[k];
     }
@@ -142,7 +200,7 @@ __device__ void phase_scan(const LevelParams& P, bool learned)
     if (learned) {
         unsigned long long c = 0;
         for (int i = lo; i < hi; ++i) {
-            const int d = P.deg[i];
+            const int d = item_deg(P, i);
             if (d >= l + 1) c += (unsigned long long)d * (unsigned long long)(d - 1);
         }
         c = warp_sum_u64(c);
@@ -162,7 +220,7 @@ __device__ void phase_scan(const LevelParams& P, bool learned)
     for (int it = 0; it < 48; ++it) {
         unsigned long long b = 0;
         for (int i = lo; i < hi; ++i) {
-            const int d = P.deg[i];
+            const int d = item_deg(P, i);
             if (d >= l + 1 && P.B(d, l) == ~0ull) rng = 1;
             b += row_items(P.B, d, l, chunk, lrn);
         }
@@ -185,9 +243,9 @@ __device__ void phase_scan(const LevelParams& P, bool learned)
     unsigned long long sq = 0;
     int dmax = 0;
     for (int i = lo; i < hi; ++i) {
-        const int d = P.deg[i];
+        const int d = item_deg(P, i);
         dmax = max(dmax, d);
-        a += d;
+        a += P.deg[i];
         b += (long long)row_items(P.B, d, l, chunk, lrn);
         if (d >= l + 1) {
             sq += (unsigned long long)(d + 1) * (unsigned long long)(d + 1);
@@ -228,11 +286,11 @@ __device__ void phase_scan(const LevelParams& P, bool learned)
     long long eb = ib - b + (w > 0 ? sb[w - 1] : 0);
     long long ec = ic - c + (w > 0 ? sc[w - 1] : 0);
     for (int i = lo; i < hi; ++i) {
-        const int d = P.deg[i];
+        const int d = item_deg(P, i);
         P.row_off[i] = ea;
         P.item_off[i] = eb;
         if (P.poff) P.poff[i] = ec;
-        ea += d;
+        ea += P.deg[i];
         eb += (long long)row_items(P.B, d, l, chunk, lrn);
         if (lrn && d >= l + 1) ec += (long long)d * (d - 1);
     }
@@ -258,9 +316,12 @@ __device__ void phase_fill(const LevelParams& P)
     const int nwarps = (gridDim.x * NT) >> 5;
     for (int i = gw; i < P.p; i += nwarps) {
         long long base = P.row_off[i];
-        for (int w0 = 0; w0 < P.W; w0 += 32) {
+        int wlo, whi;
+        long long rb;
+        word_range(P, i, wlo, whi, rb);
+        for (int w0 = wlo; w0 < whi; w0 += 32) {
             const int q = w0 + lane;
-            unsigned word = (q < P.W) ? P.bits[(size_t)i * P.W + q] : 0u;
+            unsigned word = (q < whi) ? P.bits[rb + q] : 0u;
             const int c = __popc(word);
             int incl = c;
 #pragma unroll
@@ -276,8 +337,9 @@ __device__ void phase_fill(const LevelParams& P)
                 P.cols[pos] = j;
                 P.srow[pos] = i;
                 // slot of (j, i): row j's offset + neighbours of j below i
-                const unsigned wj = P.bits[(size_t)j * P.W + (i >> 5)];
-                P.partner[pos] = (int)(P.row_off[j] + P.wpre[(size_t)j * P.W + (i >> 5)] +
+                const long long rbj = row_base(P, j);
+                const unsigned wj = P.bits[rbj + (i >> 5)];
+                P.partner[pos] = (int)(P.row_off[j] + P.wpre[rbj + (i >> 5)] +
                                        __popc(wj & ((1u << (i & 31)) - 1u)));
                 ++pos;
             }
@@ -295,19 +357,20 @@ __device__ void phase_fill(const LevelParams& P)
 // ---------------------------------------------------------------------------
 // 0 dependent, 1 independent, 2 undecided in FP32 (sent to the FP64 recheck)
 template <typename T, bool FP32>
-__device__ __forceinline__ int ci_decide(T H11, T H12, T H22, T minpiv2, const LevelParams& P)
+__device__ __forceinline__ int ci_decide(T H11, T H12, T H22, T minpiv2, const LevelParams& P, double r_,
+                                         double r2_)
 {
     if (!FP32) {
         // zero conditional variance (rounding level of the unit diagonal): V_i or
         // V_j is a linear function of S -> independent
         if (!(H11 > T(kVarZero)) || !(H22 > T(kVarZero))) return 1;
-        return (H12 * H12 <= (T)P.r2 * H11 * H22) ? 1 : 0;
+        return (H12 * H12 <= (T)r2_ * H11 * H22) ? 1 : 0;
     } else {
         if (!(minpiv2 >= (T)P.piv_floor) || !(H11 > T(1e-4)) || !(H22 > T(1e-4))) return 2;
         const float rho = fabsf((float)H12) * rsqrtf((float)(H11 * H22));
         const float band =
             (float)P.band_abs + (float)P.band_rel / ((float)minpiv2 * fminf((float)H11, (float)H22));
-        const float r = (float)P.r;
+        const float r = (float)r_;
         if (rho > r + band) return 0;
         if (rho < r - band) return 1;
         return 2;
@@ -318,8 +381,7 @@ template <typename T, int LB, bool FP32>
 __device__ void phase_ci(const LevelParams& P)
 {
     const int lane = threadIdx.x & 31;
-    const T* __restrict__ C = (const T*)P.C;
-    const int p = P.p, l = P.l;
+    const int l = P.l;
     const unsigned long long n_items = P.lm->items[l];
     const int chunk = P.lm->chunk[l];
     unsigned long long ntests = 0;
@@ -335,7 +397,10 @@ __device__ void phase_ci(const LevelParams& P)
         const unsigned long long nsets = P.B(d, l);
         const unsigned long long s0 = (unsigned long long)k * (unsigned long long)chunk;
         const unsigned long long s1 = min(s0 + (unsigned long long)chunk, nsets);
-        const T* __restrict__ Ci = C + (size_t)i * p;
+        const CView<T> CV = cview<T>(P, i);
+        double thr, thr2;
+        thresholds(P, i, thr, thr2);
+        const T* __restrict__ Ci = CV.row(i);
         for (unsigned long long base = s0; base < s1; base += 32) {
             const unsigned long long s = base + lane;
             const bool active = s < s1;
@@ -349,7 +414,7 @@ __device__ void phase_ci(const LevelParams& P)
                 for (int c = 0; c < LB; ++c)
                     if (c < l) Sx[c] = P.cols[off + Pos[c]];
                 factor_build<T, LB>(
-                    F, l, (T)P.rank_tol, [&](int a, int b) { return __ldg(C + (size_t)Sx[a] * p + Sx[b]); },
+                    F, l, (T)P.rank_tol, [&](int a, int b) { return __ldg(CV.row(Sx[a]) + Sx[b]); },
                     [&](int a) { return __ldg(Ci + Sx[a]); });
             }
             // the row's per-j data in chunks of 32: lane q loads j-position jc + q
@@ -381,11 +446,11 @@ __device__ void phase_ci(const LevelParams& P)
                         if (c < l && Pos[c] == jp) t = false;
                     if (t) {
                         T H12, H22;
-                        const T* __restrict__ Cj = C + (size_t)j * p;
+                        const T* __restrict__ Cj = CV.row(j);
                         factor_apply<T, LB>(F, l, cij, [&](int a) { return __ldg(Cj + Sx[a]); }, H12, H22);
                         const T H11 = T(1) - F.uu;
                         ++ntests;
-                        const int dec = ci_decide<T, FP32>(H11, H12, H22, F.minpiv2, P);
+                        const int dec = ci_decide<T, FP32>(H11, H12, H22, F.minpiv2, P, thr, thr2);
                         const long long e = off + jp;
                         if (dec == 1) {
                             atomicMin(P.best + e, s);
@@ -435,13 +500,13 @@ __device__ void phase_score(const LevelParams& P)
     __shared__ float sc[NW][MCAP];
     for (int q = threadIdx.x; q < MLP_NP; q += NT) Wsm[q] = ((const __nv_bfloat16*)P.mlp_w)[q];
     __syncthreads();
-    const float* __restrict__ C = (const float*)P.C;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int gw = (blockIdx.x * NT + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * NT) >> 5;
     const long long nnz = P.row_off[P.p];
     for (long long e = gw; e < nnz; e += nwarps) {
         const int i = P.srow[e], j = P.cols[e];
+        const CView<float> CV = cview<float>(P, i);
         const long long off = P.row_off[i];
         const int m = (int)(P.row_off[i + 1] - off) - 1;
         if (m < P.l) continue;
@@ -451,11 +516,11 @@ __device__ void phase_score(const LevelParams& P)
             for (int c = lane; c < m; c += 32) dst[c] = P.cols[off + (c < pj ? c : c + 1)];
             continue;
         }
-        const float cij = C[(size_t)i * P.p + j];
+        const float cij = CV.row(i)[j];
         for (int c = lane; c < m; c += 32) {
             const int k = P.cols[off + (c < pj ? c : c + 1)];
             float x[MLP_IN];
-            mlp_features(cij, C[(size_t)i * P.p + k], C[(size_t)j * P.p + k], P.l, x);
+            mlp_features(cij, CV.row(i)[k], CV.row(j)[k], P.l, x);
             const float y = mlp_score(Wsm, x);
             sc[w][c] = (y == y) ? y : -INFINITY;
         }
@@ -477,8 +542,7 @@ template <typename T, int LB, bool FP32>
 __device__ void phase_ci_edge(const LevelParams& P)
 {
     const int lane = threadIdx.x & 31;
-    const T* __restrict__ C = (const T*)P.C;
-    const int p = P.p, l = P.l;
+    const int l = P.l;
     const unsigned long long n_items = P.lm->items[l];
     const int chunk = P.lm->chunk[l];
     unsigned long long ntests = 0;
@@ -491,6 +555,9 @@ __device__ void phase_ci_edge(const LevelParams& P)
         const long long k = (long long)item - P.item_off[i];
         const long long off = P.row_off[i];
         const int m = (int)(P.row_off[i + 1] - off) - 1;
+        const CView<T> CV = cview<T>(P, i);
+        double thr, thr2;
+        thresholds(P, i, thr, thr2);
         const unsigned long long total = P.B(m, l);
         const long long per_edge = (long long)((total + chunk - 1) / chunk);
         const long long q = k / per_edge, cidx = k % per_edge;
@@ -499,8 +566,8 @@ __device__ void phase_ci_edge(const LevelParams& P)
         const int* __restrict__ cand = side_perm(P, i, e);
         const unsigned long long s0 = (unsigned long long)cidx * (unsigned long long)chunk;
         const unsigned long long s1 = min(s0 + (unsigned long long)chunk, total);
-        const T* __restrict__ Ci = C + (size_t)i * p;
-        const T* __restrict__ Cj = C + (size_t)j * p;
+        const T* __restrict__ Ci = CV.row(i);
+        const T* __restrict__ Cj = CV.row(j);
         const T cij = Ci[j];
         const bool watch_partner = !P.canonical || i > j;
         for (unsigned long long base = s0; base < s1; base += 32) {
@@ -522,13 +589,13 @@ __device__ void phase_ci_edge(const LevelParams& P)
                 for (int c = 0; c < LB; ++c) Sx[c] = (c < l) ? cand[Q[c]] : 0;
                 Factor<T, LB> F;
                 factor_build<T, LB>(
-                    F, l, (T)P.rank_tol, [&](int a, int b) { return __ldg(C + (size_t)Sx[a] * p + Sx[b]); },
+                    F, l, (T)P.rank_tol, [&](int a, int b) { return __ldg(CV.row(Sx[a]) + Sx[b]); },
                     [&](int a) { return __ldg(Ci + Sx[a]); });
                 T H12, H22;
                 factor_apply<T, LB>(F, l, cij, [&](int a) { return __ldg(Cj + Sx[a]); }, H12, H22);
                 const T H11 = T(1) - F.uu;
                 ++ntests;
-                const int dec = ci_decide<T, FP32>(H11, H12, H22, F.minpiv2, P);
+                const int dec = ci_decide<T, FP32>(H11, H12, H22, F.minpiv2, P, thr, thr2);
                 if (dec == 1) {
                     atomicMin(P.best + e, r);
                 } else if (FP32 && dec == 2) {
@@ -561,15 +628,34 @@ __device__ void phase_ci_edge(const LevelParams& P)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int recheck_slices(int n) { return max(1, min(8, n / 2048)); }
 
+// FP64 rows of vertex v's problem: sample count, first global vertex, offset
+// of its rows and their stride.
+__device__ __forceinline__ void zview(const LevelParams& P, int v, int& n, int& off, long long& base, long long& ld)
+{
+    if (P.vprob) {
+        const ProbDesc& D = P.probs[P.vprob[v]];
+        n = D.n;
+        off = D.off;
+        base = D.z_off;
+        ld = D.n;
+    } else {
+        n = P.n;
+        off = 0;
+        base = 0;
+        ld = P.ldz;
+    }
+}
+
 template <int LB>
 __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
 {
     constexpr int M = LB + 2;
     constexpr int D = M * (M - 1) / 2;
     __shared__ double red[NW * D];
-    const int S = recheck_slices(P.n);
+    // slices per test: one count for the level (batches mix sample counts; the
+    // slices then follow the largest n, the same for every test of the level)
+    const int S = recheck_slices(P.vprob ? P.nmax : P.n);
     const long long batch = (long long)P.part_tests;
-    const double inv_n = 1.0 / (double)P.n;
     for (long long q0 = 0; q0 < (long long)nq; q0 += batch) {
         const long long nb = min(batch, (long long)nq - q0);
         // partial sums
@@ -585,14 +671,17 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
 #pragma unroll
             for (int c = 0; c < LB; ++c) V[2 + c] = (c < P.l) ? E->S[c] : i;
             const int m = P.l + 2;
-            const int k0 = (int)((long long)P.n * k / S), k1 = (int)((long long)P.n * (k + 1) / S);
+            int zn, zoff;
+            long long zbase, zld;
+            zview(P, i, zn, zoff, zbase, zld);
+            const int k0 = (int)((long long)zn * k / S), k1 = (int)((long long)zn * (k + 1) / S);
             double G[D];
 #pragma unroll
             for (int t = 0; t < D; ++t) G[t] = 0.0;
             if (P.c64 == nullptr) {
                 const double* rows[M];
 #pragma unroll
-                for (int a = 0; a < M; ++a) rows[a] = P.z64 + (size_t)(a < m ? V[a] : V[0]) * P.ldz;
+                for (int a = 0; a < M; ++a) rows[a] = P.z64 + zbase + (long long)((a < m ? V[a] : V[0]) - zoff) * zld;
 #pragma unroll 4
                 for (int kk = k0 + (int)threadIdx.x; kk < k1; kk += NT) {
                     double x[M];
@@ -641,6 +730,10 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
                     for (int a = 0; a < b2; ++a)
                         G[b2 * (b2 - 1) / 2 + a] = (b2 < P.l + 2) ? P.c64[(size_t)V[a] * P.p + V[b2]] : 0.0;
             } else {
+                int zn, zoff;
+                long long zbase, zld;
+                zview(P, i, zn, zoff, zbase, zld);
+                const double inv_n = 1.0 / (double)zn;
 #pragma unroll
                 for (int x = 0; x < D; ++x) {
                     double g = 0.0;
@@ -656,7 +749,9 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
             double H12, H22;
             factor_apply<double, LB>(F, P.l, G[0], [&](int a) { return G[(a + 2) * (a + 1) / 2 + 1]; }, H12, H22);
             const double H11 = 1.0 - F.uu;
-            const bool indep = (!(H11 > kVarZero) || !(H22 > kVarZero)) ? true : (H12 * H12 <= P.r2 * H11 * H22);
+            double thr, thr2;
+            thresholds(P, i, thr, thr2);
+            const bool indep = (!(H11 > kVarZero) || !(H22 > kVarZero)) ? true : (H12 * H12 <= thr2 * H11 * H22);
             if (indep) atomicMin(P.best + e, E->s);
         }
         if (!grid_sync(P.lm)) return false;
@@ -736,7 +831,7 @@ __device__ void phase_finalize(const LevelParams& P, bool lrn)
                 else if (by != RANK_NONE) { side = y; rank = by; slot = f; }
                 if (side >= 0) {
                     removed = true;
-                    bitset_clear_pair(P.bits, P.W, x, y);
+                    bitset_clear_pair_at(P.bits, row_base(P, x), row_base(P, y), x, y);
                     atomicSub(P.deg + x, 1);
                     atomicSub(P.deg + y, 1);
                     int S[LB];
@@ -756,6 +851,7 @@ __device__ void phase_finalize(const LevelParams& P, bool lrn)
                 if (P.canonical) {
                     serial = side_serial<LB>(P, x, e, bx, lrn);
                     if (bx == RANK_NONE) serial += side_serial<LB>(P, y, f, by, lrn);
+                    if (P.prob_serial && serial) atomicAdd(P.prob_serial + (size_t)P.vprob[x] * LV + l, serial);
                 }
             }
         }
@@ -852,10 +948,19 @@ cudaError_t launch_level_t(const LevelParams& P, int num_sms, cudaStream_t st)
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         per_sm = per_sm > 2 ? 2 : per_sm;
     }
-    const int grid = num_sms * per_sm;
-    LevelParams arg = P;
-    void* args[] = {&arg};
-    return cudaLaunchCooperativeKernel((const void*)k_level<T, LB, FP32, LEARNED>, dim3(grid), dim3(NT), args, 0, st);
+    // CTAs per SM: as many as fit, at most 2, or fewer when asked
+    const int k = (P.ctas_per_sm > 0 && P.ctas_per_sm < per_sm) ? P.ctas_per_sm : per_sm;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(num_sms * k);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs resident: the grid barrier relies on it
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_level<T, LB, FP32, LEARNED>, P);
 }
 
 template <typename T, bool FP32, bool LEARNED>

@@ -28,6 +28,29 @@ __global__ void k_transpose(const T* __restrict__ X, long long ld, int n, int p,
     }
 }
 
+// Batch form: block z transposes problem z's n x p sample-major block at
+// x_off into its p x n variable-major block at the same offset of Xt.
+template <typename T>
+__global__ void k_transpose_batch(const T* __restrict__ X, const ProbDesc* __restrict__ probs, T* __restrict__ Xt)
+{
+    __shared__ T tile[32][33];
+    const ProbDesc& D = probs[blockIdx.z];
+    const int n = D.n, p = D.p;
+    const int v0 = blockIdx.x * 32, s0 = blockIdx.y * 32;
+    if (v0 >= p || s0 >= n) return;
+    const T* src = X + D.x_off;
+    T* dst = Xt + D.x_off;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int s = s0 + r, v = v0 + threadIdx.x;
+        if (s < n && v < p) tile[r][threadIdx.x] = src[(size_t)s * p + v];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int v = v0 + r, s = s0 + threadIdx.x;
+        if (s < n && v < p) dst[(size_t)v * n + s] = tile[threadIdx.x][r];
+    }
+}
+
 // One block per variable. Moments in FP64 in one pass over shifted values
 // (shift K = the variable's first sample, so the centred sums do not cancel):
 // S1 = sum (x - K), S2 = sum (x - K)^2, mean = K + S1/n,
@@ -38,12 +61,36 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
                                                     double* __restrict__ mu, double* __restrict__ isd,
                                                     double* __restrict__ z64, long long ldz,
                                                     __nv_bfloat16* __restrict__ zhi, __nv_bfloat16* __restrict__ zlo,
-                                                    long long ldb, Meta* meta)
+                                                    long long ldb, Meta* meta, const int* __restrict__ vprob,
+                                                    const ProbDesc* __restrict__ probs)
 {
     __shared__ double red[2][NT / 32];
     const int v = blockIdx.x;
     if (v >= p) return;
     const T* row = Xv + (size_t)v * ld;
+    double* zrow = z64 ? z64 + (size_t)v * ldz : nullptr;
+    if (vprob) {
+        // batch: global vertex v of problem D, whose variable-major rows (ld = its
+        // n) start at x_off and whose FP64 rows start at z_off; a padding vertex
+        // gets zero bf16 rows
+        const ProbDesc& D = probs[vprob[v]];
+        const int loc = v - D.off;
+        if (loc >= D.p) {
+            if (threadIdx.x == 0) {
+                mu[v] = 0.0;
+                isd[v] = 0.0;
+            }
+            if (zhi)
+                for (int k = threadIdx.x; k < ldb; k += NT) {
+                    zhi[(size_t)v * ldb + k] = __float2bfloat16(0.f);
+                    zlo[(size_t)v * ldb + k] = __float2bfloat16(0.f);
+                }
+            return;
+        }
+        n = D.n;
+        row = Xv + D.x_off + (size_t)loc * n;
+        if (z64) zrow = z64 + D.z_off + (long long)loc * n;
+    }
     const double K = (double)row[0];
     double s1 = 0.0, s2 = 0.0;
     for (int k = threadIdx.x; k < n; k += NT) {
@@ -84,7 +131,7 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
     const float fi = (float)inv;
     for (int k = threadIdx.x; k < n; k += NT) {
         const double d = (double)row[k] - mean;
-        if (z64) z64[(size_t)v * ldz + k] = d * inv;
+        if (zrow) zrow[k] = d * inv;
         if (zhi) {
             const float z = (float)d * fi;
             const __nv_bfloat16 h = __float2bfloat16_rn(z);
@@ -186,15 +233,28 @@ cudaError_t launch_transpose(int dtype, const void* X, long long ld, int n, int 
 
 cudaError_t launch_standardize(int dtype, const void* Xv, long long ld, int n, int p, double* mu, double* isd,
                                double* z64, long long ldz, void* zhi, void* zlo, long long ldb, Meta* meta,
-                               cudaStream_t st)
+                               cudaStream_t st, const int* vprob, const ProbDesc* probs)
 {
     constexpr int NT = 256;
     if (dtype == CUPC_F64)
         k_standardize<double, NT><<<p, NT, 0, st>>>((const double*)Xv, ld, n, p, mu, isd, z64, ldz,
-                                                    (__nv_bfloat16*)zhi, (__nv_bfloat16*)zlo, ldb, meta);
+                                                    (__nv_bfloat16*)zhi, (__nv_bfloat16*)zlo, ldb, meta, vprob,
+                                                    probs);
     else
         k_standardize<float, NT><<<p, NT, 0, st>>>((const float*)Xv, ld, n, p, mu, isd, z64, ldz,
-                                                   (__nv_bfloat16*)zhi, (__nv_bfloat16*)zlo, ldb, meta);
+                                                   (__nv_bfloat16*)zhi, (__nv_bfloat16*)zlo, ldb, meta, vprob,
+                                                   probs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_batch(int dtype, const void* X, const ProbDesc* probs, int nprob, int pmax, int nmax,
+                                   void* Xt, cudaStream_t st)
+{
+    dim3 grid((pmax + 31) / 32, (nmax + 31) / 32, nprob), block(32, 8);
+    if (dtype == CUPC_F64)
+        k_transpose_batch<double><<<grid, block, 0, st>>>((const double*)X, probs, (double*)Xt);
+    else
+        k_transpose_batch<float><<<grid, block, 0, st>>>((const float*)X, probs, (float*)Xt);
     return cudaGetLastError();
 }
 

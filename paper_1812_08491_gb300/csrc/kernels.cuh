@@ -1,6 +1,8 @@
 // kernels.cuh -- launcher declarations shared by the host driver and the kernel files.
 #pragma once
 
+#include <vector>
+
 #include "cupc_internal.cuh"
 
 namespace cupc {
@@ -29,10 +31,41 @@ struct LevelMeta {
     unsigned bar_count, bar_gen;           // grid barrier state
 };
 
+// One problem of a batch. The batch runs as one graph whose connected
+// blocks are the problems: problem k owns the global vertex ids
+// [off, off + P32) with P32 = p rounded up to 32 (ids past off + p are
+// padding and stay isolated). Its adjacency is its own P32 x W bitset (W =
+// P32 / 32 words a row) stored from word bw, so row v of the batch bitset
+// starts at word rowbase(v) = bw + (v - off) W - wlo and the word holding
+// global column c is rowbase(v) + (c >> 5), c >> 5 in [wlo, whi).
+struct ProbDesc {
+    int off, p, n;
+    int wlo, whi;                  // off / 32, (off + P32) / 32
+    int lmax;                      // last level its threshold allows (n - 4, max_level)
+    long long bw;                  // first word of its bitset block
+    long long c_off;               // its p x p correlation in the packed C
+    long long z_off;               // its p x n standardised rows (FP64) in the packed rows
+    long long x_off;               // its data (elements) in the packed input
+    double r[LV], r2[LV];          // tanh(tau_l) for its n and alpha, and the square
+};
+
+// Problem of vertex v (nullptr descriptors: one problem, no batch).
+__device__ __forceinline__ const ProbDesc* prob_of(const int* vprob, const ProbDesc* probs, int v)
+{
+    return vprob ? probs + vprob[v] : nullptr;
+}
+
+// Word offset such that bits[rowbase + (c >> 5)] holds column c of row v.
+__device__ __forceinline__ long long rowbase(const ProbDesc* D, int W, int v)
+{
+    return D ? D->bw + (long long)(v - D->off) * (D->whi - D->wlo) - D->wlo : (long long)v * W;
+}
+
 // Parameters of one level (l >= 1) of the fused level kernel.
 struct LevelParams {
-    unsigned* bits;                // live A_G bitset, p rows of W words
+    unsigned* bits;                // live A_G bitset, p rows of W words (batch: packed blocks)
     int W, p;
+    long long nwords;              // words of the bitset
     unsigned* backup;              // FP32 mode: A_G at level start (for a rerun after queue overflow)
     int* deg;
     long long* row_off;            // p + 1 CSR offsets of A'_G
@@ -59,6 +92,7 @@ struct LevelParams {
     const double* z64;             // FP64 standardised rows for the rechecks (or c64)
     long long ldz;
     int n;
+    int nmax;                      // batch: largest sample count
     const double* c64;
     double* part;                  // recheck partial Gram sums: part_tests x slices x D doubles
     unsigned long long part_tests; // queued tests per recheck batch
@@ -66,6 +100,11 @@ struct LevelParams {
     unsigned long long rec_cap;
     LevelMeta* lm;
     int* host_flags;               // device view of pinned host flags: [l] = 1 runs, 2 loop ended
+    // batch: problem of each global vertex, and the problems (nullptr: one problem)
+    const int* vprob;
+    const ProbDesc* probs;
+    unsigned long long* prob_serial;   // batch: serial-order tests per problem and level (nprob x LV)
+    int ctas_per_sm;               // launch shape (0: as many as fit, at most 2)
     // learned ordering (levels >= 2, FP32 mode)
     int learned;                   // requested
     const void* mlp_w;             // bf16 network parameters
@@ -87,22 +126,42 @@ struct Recheck0Params {
     Meta* meta;
     unsigned* bits;
     int W;
+    const int* vprob;              // batch: problem of each vertex (nullptr: one problem)
+    const ProbDesc* probs;
 };
 
 cudaError_t launch_transpose(int dtype, const void* X, long long ld, int n, int p, void* Xt, cudaStream_t st);
 cudaError_t launch_standardize(int dtype, const void* Xv, long long ld, int n, int p, double* mu, double* isd,
                                double* z64, long long ldz, void* zhi, void* zlo, long long ldb, Meta* meta,
-                               cudaStream_t st);
+                               cudaStream_t st, const int* vprob = nullptr, const ProbDesc* probs = nullptr);
+cudaError_t launch_transpose_batch(int dtype, const void* X, const ProbDesc* probs, int nprob, int pmax, int nmax,
+                                   void* Xt, cudaStream_t st);
 cudaError_t launch_syrk_f64(const double* Z, long long ldz, int n, int p, double* C, cudaStream_t st);
 void corr_tc_plan(int p, long long ldk, int num_sms, int* tiles, int* nsplit, int* kps, size_t* ws_bytes);
 cudaError_t launch_corr_tc(const void* hi, const void* lo, long long ldk, int p, int n, float* ws, float* C,
                            int num_sms, int* err, cudaStream_t st);
+// Batched correlation: host-side plan (work units and output tiles, copied to
+// the device by the caller) and the launch.
+struct CorrBatchUnit {
+    int ra, rb, g0, g1, kt, slot, pad0, pad1;
+};
+struct CorrBatchTile {
+    int prob, bi, bj, slot0, nsplit, pad0, pad1, pad2;
+};
+void corr_tc_batch_plan(const std::vector<ProbDesc>& probs, int num_sms, int kps_req,
+                        std::vector<CorrBatchUnit>& units, std::vector<CorrBatchTile>& tiles, size_t* ws_bytes,
+                        int* kps_out);
+cudaError_t launch_corr_tc_batch(const void* hi, const void* lo, long long ldk, int rows, const void* units,
+                                 int n_units, const void* tiles, int n_tiles, const ProbDesc* probs, float* ws,
+                                 float* C, int* err, cudaStream_t st);
 cudaError_t launch_symmetrize(int dtype, const void* Cin, long long ld, int p, double* C64, float* C32,
                               cudaStream_t st);
 
 cudaError_t launch_level0(int fp32, const void* C, int p, int W, double r0, double band0, unsigned* bits,
-                          QEntry* q, unsigned long long qcap, Meta* meta, cudaStream_t st);
-cudaError_t launch_degree(const unsigned* bits, int p, int W, int* deg, Meta* meta, cudaStream_t st);
+                          QEntry* q, unsigned long long qcap, Meta* meta, cudaStream_t st,
+                          const int* vprob = nullptr, const ProbDesc* probs = nullptr, int nrows = 0);
+cudaError_t launch_degree(const unsigned* bits, int p, int W, int* deg, Meta* meta, cudaStream_t st,
+                          const int* vprob = nullptr, const ProbDesc* probs = nullptr);
 cudaError_t launch_scan(const int* deg, int p, int l, int chunk, Binom B, long long* row_off,
                         long long* item_off, Meta* meta, cudaStream_t st);
 cudaError_t launch_recheck0(const Recheck0Params& P, int grid, cudaStream_t st);

@@ -121,8 +121,10 @@ def run_reference(args, workload_name):
     if rank != 0:
         return 0
     from synth import sem
-    s = sem.workload(workload_name)
     cores = os.cpu_count() or 1
+    if workload_name in BATCH_WORKLOADS:
+        return run_reference_batch(args, workload_name, cores)
+    s = sem.workload(workload_name)
     for _ in range(args.warmup):
         cpu_oracle_run(s, cores)
     secs, units = 0.0, 0
@@ -138,6 +140,32 @@ def run_reference(args, workload_name):
             "config": _config(workload_name, s, "cpu oracle"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"whole {workload_name} skeleton per step (correlation + all levels)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference_batch(args, name, cores):
+    """Oracle on a batch workload: each step runs a bounded sample of its problems
+    (the first 16), one after another."""
+    from synth import sem
+    probs = sem.batch_workload(BATCH_WORKLOADS[name], 0)[:16]
+    for _ in range(args.warmup):
+        cpu_oracle_run(probs[0], cores)
+    secs, units = 0.0, 0
+    for _ in range(args.steps):
+        for s in probs:
+            t, u = cpu_oracle_run(s, cores)
+            secs += t
+            units += u
+    value = units / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded linear-Gaussian SEMs)",
+            "config": _batch_config(name, probs, "cpu oracle, first 16 problems per step"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "first 16 of the 64 problems per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -202,6 +230,176 @@ def kernel_rooflines(st, s, mode, peaks):
     return out
 
 
+BATCH_WORKLOADS = {"batch64": 64}
+
+
+def _batch_config(name, probs, form):
+    ps = [s.p for s in probs]
+    ns = [s.n for s in probs]
+    return {"workload": name, "problems": len(probs), "p_range": [min(ps), max(ps)], "n_range": [min(ns), max(ns)],
+            "sum_p": int(sum(ps)), "family": "random", "degree": "U[2,6]", "alpha": probs[0].alpha,
+            "input_dtype": "float32", "form": form, "launch": "one CUDA graph per step",
+            "l2": "inputs (%.0f MB) larger than L2; 256 MiB write between steps" %
+                  (sum(p * n for p, n in zip(ps, ns)) * 4 / 1e6)}
+
+
+def batch_rooflines(bst, probs, peaks):
+    """Roofline of each stage of one batch step (its stats; CUDA-event stage times).
+
+      standardize  read X (float32), write the FP64 rows and the two bf16 rows
+      correlation  3 bf16 products over each problem's upper triangle, 2 n p (p+1)/2 each
+      level0       read every problem's C (FP32) once, write the bitsets; FP64 rechecks of the band
+      level        per level: the C sub-blocks its tests read (FP32), the bitsets, the CSR arrays
+    """
+    km = bst["kernel_ms"]
+    hbm = peaks["hbm_gbs"]
+    out = {}
+
+    def mem(name, ms, byts):
+        if ms <= 0:
+            return
+        ach = byts / (ms * 1e-3) / 1e9
+        out[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "ms": ms,
+                     "launches": 1, "alg_bytes_per_launch": byts, "traffic": None}
+
+    words = sum(((s.p + 31) // 32 * 32) ** 2 // 32 for s in probs)
+    mem("standardize", km["standardize"], sum(s.n * s.p * (4 + 8 + 4) for s in probs))
+    mem("level0", km["level0"], sum(s.p * s.p * 4 for s in probs) + words * 4)
+    lv = bst["levels"]
+    byts = 0
+    for l in range(1, lv):
+        byts += bst["ci_block_entries"][l] * 4 + 3 * words * 4 + 2 * bst["edges_start"][l] * 40
+    mem("level", bst["level_ms"][1] if lv > 1 else 0.0, byts)
+    ms = km["correlation"]
+    if ms > 0:
+        flops = sum(3 * 2.0 * s.n * s.p * (s.p + 1) / 2 for s in probs)
+        ach = flops / (ms * 1e-3) / 1e12
+        out["correlation"] = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                              "frac": ach / peaks["bf16_tflops"], "ms": ms, "launches": 1,
+                              "peak_src": "bf16 dense, measured burst", "traffic": None}
+    return out
+
+
+def main_batch(args, world, rank, local, dist):
+    """The batched workload: a step is one skeleton_batch call over all problems."""
+    import numpy as np
+    import torch
+
+    import paper_1812_08491_gb300 as cupc
+    from synth import sem
+
+    dev = torch.device("cuda", local)
+    cupc.build_library()
+    probs = sem.batch_workload(BATCH_WORKLOADS[args.workload], 0)
+    alphas = [s.alpha for s in probs]
+    Xd = [torch.from_numpy(s.Xt.astype(np.float32)).to(dev).T for s in probs]   # variable-major n x p
+    ctx = cupc.Context(local)
+    tune = {}
+    if args.tune:
+        table = ctx.autotune_batch(Xd, alphas, reps=2)
+        tune = {k: table[0][k] for k in ("chunk", "ctas_per_sm", "corr_kps")}
+    res, bst = ctx.skeleton_batch(Xd, alphas, **tune)
+    units = int(sum(bst["serial_tests"]))
+    edges = int(bst["edges_final"])
+    for r in res:
+        r.free()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        for r in ctx.skeleton_batch(Xd, alphas, **tune)[0]:
+            r.free()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms, launches, stats = 0.0, 0, []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            rs, st = ctx.skeleton_batch(Xd, alphas, **tune)
+            for r in rs:
+                r.free()
+            total_ms += st["total_ms"]
+            launches += st["kernel_launches"]
+            stats.append(st)
+    if dist:
+        dist.barrier()
+    clocks = clk.summary()
+    t = torch.tensor([total_ms], device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = units * world * args.steps / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+
+    e2e = None
+    if not args.no_e2e:
+        Xh = [torch.from_numpy(s.Xt.astype(np.float32)).pin_memory().T for s in probs]
+        for r in ctx.skeleton_batch(Xh, alphas, **tune)[0]:
+            r.free()
+        secs, h2d, d2h = 0.0, 0, 0
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            rs, st = ctx.skeleton_batch(Xh, alphas, **tune)
+            for r in rs:
+                r.adjacency()
+                r.records_raw()
+            secs += time.perf_counter() - t0
+            for r in rs:
+                r.free()
+            h2d += st["h2d_bytes"]
+            d2h += st["d2h_bytes"]
+        e2e = {"value": units * args.steps / secs, "unit": UNIT, "ms_per_step": 1e3 * secs / args.steps,
+               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+
+    peaks = _peaks()
+    kern_all = [batch_rooflines(st, probs, peaks) for st in stats]
+    kern = {}
+    for nm in kern_all[0]:
+        rs = [k[nm] for k in kern_all if nm in k]
+        d = dict(rs[0])
+        d["ms"] = sum(x["ms"] for x in rs) / len(rs)
+        d["achieved"] = sum(x["achieved"] for x in rs) / len(rs)
+        d["frac"] = d["achieved"] / d["peak"]
+        kern[nm] = d
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    roof = {k: kern[dom][k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    roof["kernel"] = dom
+    roof["ms_per_step"] = kern[dom]["ms"]
+    phases = {k: round(sum(st["kernel_ms"][k] for st in stats) / len(stats), 4) for k in stats[0]["kernel_ms"]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        secs, cu, used = 0.0, 0, 0
+        for s in probs:                       # a bounded sample: problems in order until 15 s
+            t_, u_ = cpu_oracle_run(s, cores)
+            secs += t_
+            cu += u_
+            used += 1
+            if secs > 15.0:
+                break
+        cpu = {"value": cu / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {used} of {len(probs)} problems, one by one, {secs:.2f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic (seeded linear-Gaussian SEMs, device-resident input)",
+                "config": _batch_config(args.workload, probs, "FP32 bulk + FP64 recheck, batched"),
+                "skeleton_wall_s": ms_per_step / 1e3, "serial_tests_per_step": units, "edges": edges,
+                "cuda_graph": stats[0]["cuda_graph"], "tuned": tune or None,
+                "e2e": e2e, "gpu_launches": launches, "phase_ms_per_step": phases,
+                "roofline": roof,
+                "kernel_rooflines": {k: {"frac": round(v["frac"], 5), "achieved": round(v["achieved"], 3),
+                                         "unit": v["unit"], "bound": v["bound"], "ms": round(v["ms"], 4)}
+                                     for k, v in kern.items()},
+                "cpu_baseline": cpu, "clocks": clocks}
+        print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -213,6 +411,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP64 form")
+    ap.add_argument("--tune", action="store_true", help="batch workloads: autotune the launch configuration")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.workload)
@@ -232,6 +431,11 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.workload in BATCH_WORKLOADS:
+        rc = main_batch(args, world, rank, local, dist)
+        if dist:
+            dist.destroy_process_group()
+        return rc
 
     cupc.build_library()
     s = sem.workload(args.workload)

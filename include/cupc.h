@@ -210,8 +210,13 @@ cupc_status cupc_skeleton_corr(cupc_ctx* ctx, const void* C, int dtype, int on_d
  *                with cupc_result_free). Their stats hold per problem:
  *                serial_tests (canonical runs), removed, edges_start,
  *                edges_final and levels; tests and rechecks per problem are -1.
- *   batch_stats  NULL, or receives the whole batch's counters and timings
- *                (total_ms = device time of the batch's kernels).
+ *   batch_stats  NULL, or receives the whole batch's counters and timings:
+ *                total_ms = device time from the input copies to the end of
+ *                the last level; kernel_ms[UPLOAD], [STANDARDIZE],
+ *                [CORRELATION], [LEVEL0] the stages (event-timed, the level-0
+ *                stage includes its rechecks and the degree pass); prep_ms
+ *                standardisation + correlation; level_ms[1] every level >= 1
+ *                together; phase_ms per level from the device clock.
  * Errors as cupc_skeleton; on error every out[k] is NULL. */
 cupc_status cupc_skeleton_batch(cupc_ctx* ctx, int nprob, const void* const* X, int dtype, int layout,
                                 int on_device, const int64_t* n_samples, const int64_t* p,

@@ -200,12 +200,16 @@ cupc_status readback(cupc_ctx* ctx)
     return CUPC_OK;
 }
 
-// Standardise + correlation. On return exactly one of (c64, c32) is the matrix
-// the CI kernels read; z64 / c64 feed the FP64 rechecks.
-// Data the FP64 rechecks read: the FP64 standardised rows.
+// Standardise + correlation. On return *Cuse is the matrix the CI kernels
+// read; c64 (correlation input) or the data view feeds the FP64 rechecks.
+// Data the FP64 rechecks read: the variable-major data rows and the moments of
+// the standardisation (z is recomputed from them bit for bit).
 struct DataView {
-    const double* z64 = nullptr;
-    long long ldz = 0;
+    const void* xv = nullptr;
+    long long ldx = 0;
+    int xf64 = 0;
+    const double* mu = nullptr;
+    const double* isd = nullptr;
 };
 
 cupc_status prepare(cupc_ctx* ctx, const Input& in, bool fp32, const void** Cuse, const double** c64_out,
@@ -266,17 +270,21 @@ cupc_status prepare(cupc_ctx* ctx, const Input& in, bool fp32, const void** Cuse
     cupc_status s;
     if ((s = ensure(ctx, ctx->mu, (size_t)p * 8)) != CUPC_OK) return s;
     if ((s = ensure(ctx, ctx->isd, (size_t)p * 8)) != CUPC_OK) return s;
-    if ((s = ensure(ctx, ctx->z64, (size_t)p * ldz * 8)) != CUPC_OK) return s;
+    // FP64 rows only for the FP64 product (plain mode); FP32 mode keeps the bf16 split
+    if (!fp32 && (s = ensure(ctx, ctx->z64, (size_t)p * ldz * 8)) != CUPC_OK) return s;
     if (fp32) {
         if ((s = ensure(ctx, ctx->zhi, (size_t)p * ldb * 2)) != CUPC_OK) return s;
         if ((s = ensure(ctx, ctx->zlo, (size_t)p * ldb * 2)) != CUPC_OK) return s;
     }
     TIMED(CUPC_K_STANDARDIZE,
           launch_standardize(in.dtype, xv, ldv, n, p, (double*)ctx->mu.p, (double*)ctx->isd.p,
-                             (double*)ctx->z64.p, ldz, fp32 ? ctx->zhi.p : nullptr,
+                             fp32 ? nullptr : (double*)ctx->z64.p, ldz, fp32 ? ctx->zhi.p : nullptr,
                              fp32 ? ctx->zlo.p : nullptr, ldb, meta, ctx->stream));
-    dv->z64 = (const double*)ctx->z64.p;
-    dv->ldz = ldz;
+    dv->xv = xv;
+    dv->ldx = ldv;
+    dv->xf64 = in.dtype == CUPC_F64 ? 1 : 0;
+    dv->mu = (const double*)ctx->mu.p;
+    dv->isd = (const double*)ctx->isd.p;
     if (!fp32) {
         if ((s = ensure(ctx, ctx->c64, (size_t)p * p * 8)) != CUPC_OK) return s;
         TIMED(CUPC_K_CORRELATION,
@@ -392,8 +400,11 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     const int grid_wide = std::max(1, ctx->num_sms * 8);
     auto recheck0_params = [&]() {
         Recheck0Params rp{};
-        rp.z64 = dv.z64;
-        rp.ldz = dv.ldz;
+        rp.xv = dv.xv;
+        rp.ldx = dv.ldx;
+        rp.xf64 = dv.xf64;
+        rp.mu = dv.mu;
+        rp.isd = dv.isd;
         rp.n = (int)n;
         rp.c64 = c64;
         rp.p = p;
@@ -479,10 +490,8 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         if ((s = ensure(ctx, ctx->item_row, (size_t)item_cap * 4)) != CUPC_OK) return s;
         if ((s = ensure_binom(ctx, M.maxdeg + 2)) != CUPC_OK) return s;
         if ((s = ensure(ctx, ctx->lmeta, sizeof(LevelMeta))) != CUPC_OK) return s;
-        // recheck partials: a batch of 8 tests per SM, 8 sample slices, the largest Gram block
-        const unsigned long long part_tests = 8ull * ctx->num_sms * 2;
-        const size_t dmax = (size_t)(CUPC_MAX_LEVEL + 2) * (CUPC_MAX_LEVEL + 1) / 2;
-        if (fp32 && (s = ensure(ctx, ctx->part, part_tests * 8 * dmax * sizeof(double))) != CUPC_OK) return s;
+        // recheck partials: batches of queued tests sized to this buffer per level
+        if (fp32 && (s = ensure(ctx, ctx->part, kPartBytes)) != CUPC_OK) return s;
         // SepSet pool: room for every edge present after level 0 with the largest set
         rec_len_cap = (size_t)M.edges * (3 + lmax) + 16;
         if ((s = dalloc(ctx, (void**)&R->rec, rec_len_cap * 4)) != CUPC_OK) return s;
@@ -515,12 +524,15 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         LP.band_rel = kBandRel;
         LP.rank_tol = fp32 ? kRankTol32 : kRankTol64;
         LP.piv_floor = kPivFloor;
-        LP.z64 = dv.z64;
-        LP.ldz = dv.ldz;
+        LP.xv = dv.xv;
+        LP.ldx = dv.ldx;
+        LP.xf64 = dv.xf64;
+        LP.mu = dv.mu;
+        LP.isd = dv.isd;
         LP.n = (int)n;
         LP.c64 = c64;
         LP.part = fp32 ? (double*)ctx->part.p : nullptr;
-        LP.part_tests = 8ull * ctx->num_sms * 2;
+        LP.part_cap = kPartBytes / sizeof(double);
         LP.rec = R->rec;
         LP.rec_cap = rec_len_cap;
         LP.lm = lm;

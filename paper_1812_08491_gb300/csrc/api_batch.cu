@@ -48,14 +48,14 @@ struct BatchKey {
 struct BatchPlan {
     BatchKey key;
     std::vector<ProbDesc> probs;
-    std::vector<int> vprob;
+    std::vector<int> vprob, vlmax;
     std::vector<CorrBatchUnit> units;
     std::vector<CorrBatchTile> tiles;
     int P = 0, pmax = 0, nmax = 0, lmax = 0, lmax_need = 0, kps = 0;
     long long words = 0, xelems = 0, zelems = 0, celems = 0, ldb = 0;
     size_t ws_bytes = 0;
-    unsigned long long nnz_cap = 0, item_cap = 0, qcap = 0, rec_cap = 0, part_tests = 0;
-    Buf d_probs, d_vprob, d_units, d_tiles, x_in, xt, mu, isd, z64, zhi, zlo, ws, c32, bits, bits0, backup;
+    unsigned long long nnz_cap = 0, item_cap = 0, qcap = 0, rec_cap = 0;
+    Buf d_probs, d_vprob, d_vlmax, d_units, d_tiles, x_in, xt, mu, isd, zhi, zlo, ws, c32, bits, bits0, backup;
     Buf deg, row_off, item_off, item_row, cols, srow, partner, wpre, best, queue, part, rec, meta, lmeta, pserial;
     Binom binom{};
     // pinned host copies written at the end of each run
@@ -64,9 +64,11 @@ struct BatchPlan {
     LevelMeta* h_lm = nullptr;
     Meta* h_meta = nullptr;
     unsigned long long* h_ps = nullptr;
+    ProbDesc* h_probs = nullptr;   // pinned: the descriptors uploaded before each run
     cudaStream_t gs = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr, ein = nullptr;
+    cudaEvent_t ts[5] = {};  // stage boundaries: start, standardised, C formed, level 0 done, levels done
     int launches = 0;      // kernels one run launches
     bool graph_ok = false;
 };
@@ -78,8 +80,8 @@ void plan_destroy(cupc_ctx* ctx, BatchPlan* B)
     if (!B) return;
     if (B->gs) cudaStreamSynchronize(B->gs);
     if (B->exec) cudaGraphExecDestroy(B->exec);
-    Buf* all[] = {&B->d_probs, &B->d_vprob, &B->d_units, &B->d_tiles, &B->x_in, &B->xt,      &B->mu,
-                  &B->isd,     &B->z64,     &B->zhi,     &B->zlo,     &B->ws,   &B->c32,     &B->bits,
+    Buf* all[] = {&B->d_probs, &B->d_vprob, &B->d_vlmax, &B->d_units, &B->d_tiles, &B->x_in, &B->xt,      &B->mu,
+                  &B->isd,     &B->zhi,     &B->zlo,     &B->ws,   &B->c32,     &B->bits,
                   &B->bits0,   &B->backup,  &B->deg,     &B->row_off, &B->item_off, &B->item_row, &B->cols,
                   &B->srow,    &B->partner, &B->wpre,    &B->best,    &B->queue, &B->part,   &B->rec,
                   &B->meta,    &B->lmeta,   &B->pserial};
@@ -89,9 +91,12 @@ void plan_destroy(cupc_ctx* ctx, BatchPlan* B)
     if (B->h_lm) cudaFreeHost(B->h_lm);
     if (B->h_meta) cudaFreeHost(B->h_meta);
     if (B->h_ps) cudaFreeHost(B->h_ps);
+    if (B->h_probs) cudaFreeHost(B->h_probs);
     if (B->e0) cudaEventDestroy(B->e0);
     if (B->e1) cudaEventDestroy(B->e1);
     if (B->ein) cudaEventDestroy(B->ein);
+    for (cudaEvent_t e : B->ts)
+        if (e) cudaEventDestroy(e);
     if (B->gs) cudaStreamDestroy(B->gs);
     delete B;
 }
@@ -153,10 +158,14 @@ void lay_out(cupc_ctx* ctx, BatchPlan& B)
     B.xelems = B.zelems = xo;
     B.ldb = ((long long)B.nmax + 63) / 64 * 64;
     B.vprob.assign(B.P, 0);
+    B.vlmax.assign(B.P, 0);
     for (int k = 0; k < K.nprob; ++k) {
         const ProbDesc& D = B.probs[k];
         const int p32 = (D.whi - D.wlo) * 32;
-        for (int v = 0; v < p32; ++v) B.vprob[D.off + v] = k;
+        for (int v = 0; v < p32; ++v) {
+            B.vprob[D.off + v] = k;
+            B.vlmax[D.off + v] = D.lmax;
+        }
     }
     B.lmax = std::min(B.lmax_need, CUPC_MAX_LEVEL);
 }
@@ -174,18 +183,16 @@ cupc_status allocate(cupc_ctx* ctx, BatchPlan& B)
     for (const ProbDesc& D : B.probs) pairs2 += (unsigned long long)D.p * (D.p - 1);
     B.nnz_cap = std::max<unsigned long long>(pairs2, 1);
     B.item_cap = 1ull << 22;
-    B.part_tests = 16ull * ctx_num_sms(ctx);
-    const size_t dmax = (size_t)(CUPC_MAX_LEVEL + 2) * (CUPC_MAX_LEVEL + 1) / 2;
     const Req reqs[] = {
         {&B.d_probs, B.probs.size() * sizeof(ProbDesc)},
         {&B.d_vprob, (size_t)B.P * 4},
+        {&B.d_vlmax, (size_t)B.P * 4},
         {&B.d_units, std::max<size_t>(B.units.size(), 1) * sizeof(CorrBatchUnit)},
         {&B.d_tiles, std::max<size_t>(B.tiles.size(), 1) * sizeof(CorrBatchTile)},
-        {&B.x_in, (size_t)B.xelems * es},
+        {&B.x_in, K.on_device ? 0 : (size_t)B.xelems * es},
         {&B.xt, K.layout == CUPC_LAYOUT_SAMPLE_MAJOR ? (size_t)B.xelems * es : 0},
         {&B.mu, (size_t)B.P * 8},
         {&B.isd, (size_t)B.P * 8},
-        {&B.z64, (size_t)B.zelems * 8},
         {&B.zhi, (size_t)B.P * B.ldb * 2},
         {&B.zlo, (size_t)B.P * B.ldb * 2},
         {&B.ws, B.ws_bytes},
@@ -203,7 +210,7 @@ cupc_status allocate(cupc_ctx* ctx, BatchPlan& B)
         {&B.partner, (size_t)B.nnz_cap * 4},
         {&B.best, (size_t)B.nnz_cap * 8},
         {&B.queue, (size_t)B.qcap * sizeof(QEntry)},
-        {&B.part, (size_t)B.part_tests * 8 * dmax * sizeof(double)},
+        {&B.part, kPartBytes},
         {&B.rec, (size_t)B.rec_cap * 4},
         {&B.meta, sizeof(Meta)},
         {&B.lmeta, sizeof(LevelMeta)},
@@ -221,11 +228,13 @@ cupc_status allocate(cupc_ctx* ctx, BatchPlan& B)
         BCU(cudaHostAlloc((void**)&B.h_lm, sizeof(LevelMeta), cudaHostAllocDefault));
         BCU(cudaHostAlloc((void**)&B.h_meta, sizeof(Meta), cudaHostAllocDefault));
         BCU(cudaHostAlloc((void**)&B.h_ps, (size_t)K.nprob * LV * 8, cudaHostAllocDefault));
+        BCU(cudaHostAlloc((void**)&B.h_probs, B.probs.size() * sizeof(ProbDesc), cudaHostAllocDefault));
     }
-    // descriptor tables (the pool allocations above are ordered on the context stream)
+    // descriptor tables (the pool allocations above are ordered on the context
+    // stream; the problem descriptors are uploaded before each run)
     cudaStream_t st = ctx_stream(ctx);
-    BCU(cudaMemcpyAsync(B.d_probs.p, B.probs.data(), B.probs.size() * sizeof(ProbDesc), cudaMemcpyHostToDevice, st));
     BCU(cudaMemcpyAsync(B.d_vprob.p, B.vprob.data(), (size_t)B.P * 4, cudaMemcpyHostToDevice, st));
+    BCU(cudaMemcpyAsync(B.d_vlmax.p, B.vlmax.data(), (size_t)B.P * 4, cudaMemcpyHostToDevice, st));
     if (!B.units.empty())
         BCU(cudaMemcpyAsync(B.d_units.p, B.units.data(), B.units.size() * sizeof(CorrBatchUnit),
                             cudaMemcpyHostToDevice, st));
@@ -238,7 +247,7 @@ cupc_status allocate(cupc_ctx* ctx, BatchPlan& B)
 
 // The device work of one batch run, issued on stream st (recorded into the
 // graph, or launched directly).
-cupc_status issue(cupc_ctx* ctx, BatchPlan& B, cudaStream_t st)
+cupc_status issue(cupc_ctx* ctx, BatchPlan& B, cudaStream_t st, bool capturing)
 {
     const BatchKey& K = B.key;
     const int* vprob = (const int*)B.d_vprob.p;
@@ -249,26 +258,34 @@ cupc_status issue(cupc_ctx* ctx, BatchPlan& B, cudaStream_t st)
     BCU(cudaMemsetAsync(meta, 0, sizeof(Meta), st));
     BCU(cudaMemsetAsync(lm, 0, sizeof(LevelMeta), st));
     BCU(cudaMemsetAsync(B.pserial.p, 0, (size_t)K.nprob * LV * 8, st));
-    // standardise every problem's variables (variable-major first)
-    const void* xv = B.x_in.p;
+    // stage boundaries (event nodes of the graph when recorded)
+    auto stage = [&](int q) {
+        return capturing ? cudaEventRecordWithFlags(B.ts[q], st, cudaEventRecordExternal) : cudaEventRecord(B.ts[q], st);
+    };
+    BCU(stage(0));
+    // standardise every problem's variables (its variable-major rows: the data
+    // itself, or its transpose)
     if (K.layout == CUPC_LAYOUT_SAMPLE_MAJOR) {
-        BCU(launch_transpose_batch(K.dtype, B.x_in.p, probs, K.nprob, B.pmax, B.nmax, B.xt.p, st));
+        BCU(launch_transpose_batch(K.dtype, probs, K.nprob, B.pmax, B.nmax, B.xt.p, st));
         ++launches;
-        xv = B.xt.p;
     }
-    BCU(launch_standardize(K.dtype, xv, 0, 0, B.P, (double*)B.mu.p, (double*)B.isd.p, (double*)B.z64.p, 0,
-                           B.zhi.p, B.zlo.p, B.ldb, meta, st, vprob, probs));
+    BCU(launch_standardize(K.dtype, nullptr, 0, 0, B.P, (double*)B.mu.p, (double*)B.isd.p, nullptr, 0, B.zhi.p, B.zlo.p,
+                           B.ldb, meta, st, vprob, probs));
     ++launches;
+    BCU(stage(1));
     // every problem's C on the tensor cores
     BCU(launch_corr_tc_batch(B.zhi.p, B.zlo.p, B.ldb, B.P, B.d_units.p, (int)B.units.size(), B.d_tiles.p,
                              (int)B.tiles.size(), probs, (float*)B.ws.p, (float*)B.c32.p, &meta->error, st));
     launches += 2;
+    BCU(stage(2));
     // level 0 and its FP64 rechecks
     BCU(launch_level0(1, B.c32.p, B.P, 0, 0.0, kBand0, (unsigned*)B.bits.p, (QEntry*)B.queue.p, B.qcap, meta, st,
                       vprob, probs, B.P));
     ++launches;
     Recheck0Params rp{};
-    rp.z64 = (const double*)B.z64.p;
+    rp.xf64 = K.dtype == CUPC_F64 ? 1 : 0;
+    rp.mu = (const double*)B.mu.p;
+    rp.isd = (const double*)B.isd.p;
     rp.p = B.P;
     rp.queue = (const QEntry*)B.queue.p;
     rp.qcap = B.qcap;
@@ -281,6 +298,7 @@ cupc_status issue(cupc_ctx* ctx, BatchPlan& B, cudaStream_t st)
     BCU(cudaMemcpyAsync(B.bits0.p, B.bits.p, (size_t)B.words * 4, cudaMemcpyDeviceToDevice, st));
     BCU(launch_degree((const unsigned*)B.bits.p, B.P, 0, (int*)B.deg.p, meta, st, vprob, probs));
     ++launches;
+    BCU(stage(3));
     // levels 1 .. lmax of the union graph
     LevelParams LP{};
     LP.bits = (unsigned*)B.bits.p;
@@ -309,15 +327,18 @@ cupc_status issue(cupc_ctx* ctx, BatchPlan& B, cudaStream_t st)
     LP.piv_floor = kPivFloor;
     LP.queue = (QEntry*)B.queue.p;
     LP.qcap = B.qcap;
-    LP.z64 = (const double*)B.z64.p;
+    LP.xf64 = K.dtype == CUPC_F64 ? 1 : 0;
+    LP.mu = (const double*)B.mu.p;
+    LP.isd = (const double*)B.isd.p;
     LP.nmax = B.nmax;
     LP.part = (double*)B.part.p;
-    LP.part_tests = B.part_tests;
+    LP.part_cap = kPartBytes / sizeof(double);
     LP.rec = (int*)B.rec.p;
     LP.rec_cap = B.rec_cap;
     LP.lm = lm;
     LP.vprob = vprob;
     LP.probs = probs;
+    LP.vlmax = (const int*)B.d_vlmax.p;
     LP.prob_serial = (unsigned long long*)B.pserial.p;
     LP.ctas_per_sm = K.ctas;
     for (int l = 1; l <= B.lmax; ++l) {
@@ -325,6 +346,7 @@ cupc_status issue(cupc_ctx* ctx, BatchPlan& B, cudaStream_t st)
         BCU(launch_level(1, LP, ctx_num_sms(ctx), st));
         ++launches;
     }
+    BCU(stage(4));
     // results to pinned host memory
     BCU(cudaMemcpyAsync(B.h_meta, meta, sizeof(Meta), cudaMemcpyDeviceToHost, st));
     BCU(cudaMemcpyAsync(B.h_lm, lm, sizeof(LevelMeta), cudaMemcpyDeviceToHost, st));
@@ -350,7 +372,7 @@ cupc_status capture(cupc_ctx* ctx, BatchPlan& B)
         cudaGetLastError();
         return CUPC_OK;
     }
-    cupc_status s = issue(ctx, B, B.gs);
+    cupc_status s = issue(ctx, B, B.gs, true);
     cudaError_t e = cudaStreamEndCapture(B.gs, &g);
     if (s != CUPC_OK || e != cudaSuccess || !g) {
         if (g) cudaGraphDestroy(g);
@@ -380,7 +402,9 @@ cupc_status build_plan(cupc_ctx* ctx, const BatchKey& key, BatchPlan** out)
     cupc_status s;
     if (cudaStreamCreateWithFlags(&B->gs, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&B->e0) != cudaSuccess || cudaEventCreate(&B->e1) != cudaSuccess ||
-        cudaEventCreateWithFlags(&B->ein, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&B->ein, cudaEventDisableTiming) != cudaSuccess || cudaEventCreate(&B->ts[0]) ||
+        cudaEventCreate(&B->ts[1]) || cudaEventCreate(&B->ts[2]) || cudaEventCreate(&B->ts[3]) ||
+        cudaEventCreate(&B->ts[4])) {
         plan_destroy(ctx, B);
         return ctx_fail(ctx, CUPC_E_CUDA, "batch stream/events");
     }
@@ -416,18 +440,29 @@ cupc_status run_once(cupc_ctx* ctx, BatchPlan& B, const void* const* X, float* m
     BCU(cudaEventRecord(B.ein, ctx_stream(ctx)));
     BCU(cudaStreamWaitEvent(B.gs, B.ein, 0));
     BCU(cudaEventRecord(B.e0, B.gs));
+    // inputs: host data is copied into the packed input buffer; device data is
+    // read where it is. The descriptors carry this call's data pointers.
     for (int k = 0; k < K.nprob; ++k) {
-        const ProbDesc& D = B.probs[k];
-        BCU(cudaMemcpyAsync((char*)B.x_in.p + (size_t)D.x_off * es, X[k], (size_t)D.p * D.n * es,
-                            cudaMemcpyDefault, B.gs));
+        ProbDesc& D = B.probs[k];
+        if (K.on_device) {
+            D.xs = X[k];
+        } else {
+            D.xs = (const char*)B.x_in.p + (size_t)D.x_off * es;
+            BCU(cudaMemcpyAsync((void*)D.xs, X[k], (size_t)D.p * D.n * es, cudaMemcpyHostToDevice, B.gs));
+        }
+        D.xv = (K.layout == CUPC_LAYOUT_SAMPLE_MAJOR) ? (const void*)((const char*)B.xt.p + (size_t)D.x_off * es)
+                                                      : D.xs;
     }
+    std::memcpy(B.h_probs, B.probs.data(), B.probs.size() * sizeof(ProbDesc));
+    BCU(cudaMemcpyAsync(B.d_probs.p, B.h_probs, B.probs.size() * sizeof(ProbDesc), cudaMemcpyHostToDevice, B.gs));
     if (B.graph_ok) {
         BCU(cudaGraphLaunch(B.exec, B.gs));
     } else {
-        cupc_status s = issue(ctx, B, B.gs);
+        cupc_status s = issue(ctx, B, B.gs, false);
         if (s != CUPC_OK) return s;
     }
     BCU(cudaEventRecord(B.e1, B.gs));
+    BCU(cudaStreamWaitEvent(ctx_stream(ctx), B.e1, 0));  // later work on the context stream follows the batch
     BCU(cudaStreamSynchronize(B.gs));
     *ms = 0.f;
     cudaEventElapsedTime(ms, B.e0, B.e1);
@@ -618,6 +653,16 @@ cupc_status make_results(cupc_ctx* ctx, BatchPlan& B, float ms, cupc_result** ou
         S.kernel_ms[CUPC_K_CI] += 1e-6f * (float)H.phase_ns[l][1];
         S.kernel_ms[CUPC_K_RECHECK] += 1e-6f * (float)H.phase_ns[l][2];
         S.kernel_ms[CUPC_K_FINALIZE] += 1e-6f * (float)H.phase_ns[l][3];
+    }
+    {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, B.e0, B.ts[0]) == cudaSuccess) S.kernel_ms[CUPC_K_UPLOAD] = t;
+        if (cudaEventElapsedTime(&t, B.ts[0], B.ts[1]) == cudaSuccess) S.kernel_ms[CUPC_K_STANDARDIZE] = t;
+        if (cudaEventElapsedTime(&t, B.ts[1], B.ts[2]) == cudaSuccess) S.kernel_ms[CUPC_K_CORRELATION] = t;
+        if (cudaEventElapsedTime(&t, B.ts[2], B.ts[3]) == cudaSuccess) S.kernel_ms[CUPC_K_LEVEL0] = t;
+        if (cudaEventElapsedTime(&t, B.ts[0], B.ts[2]) == cudaSuccess) S.prep_ms = t;
+        if (cudaEventElapsedTime(&t, B.ts[3], B.ts[4]) == cudaSuccess) S.level_ms[1] = t;  // all levels >= 1
+        cudaGetLastError();
     }
     S.kernel_count[CUPC_K_STANDARDIZE] = K.layout == CUPC_LAYOUT_SAMPLE_MAJOR ? 2 : 1;
     S.kernel_count[CUPC_K_CORRELATION] = 2;

@@ -15,6 +15,7 @@ constexpr double kBandRel = 4e-6;      // widening per 1/(pivot^2 * min conditio
 constexpr double kPivFloor = 1e-3;     // FP32: smaller pivot^2 goes to FP64
 constexpr double kRankTol64 = 1e-12;   // FP64: pivot^2 at or below -> dependent member
 constexpr double kRankTol32 = 1e-6;
+constexpr size_t kPartBytes = size_t(32) << 20;  // FP64 recheck partial sums per batch of tests
 }  // namespace cupc
 
 struct Buf {

@@ -215,37 +215,40 @@ __device__ __forceinline__ bool bitset_test(const unsigned* bits, int W, int i, 
 }
 
 // ---------------------------------------------------------------------------
-// FP64 block of C for the rechecks: for the m variables V, the strictly lower
-// packed entries G[b(b-1)/2 + a] = C[V_a, V_b] (a < b). From the resident FP64
-// correlation when there is one; otherwise by the definition
-// C_ab = sum_s z_as z_bs / n over the FP64 standardised rows, every pair in one
-// pass (threads of the block stride the samples, four in flight each), then a
-// fixed-order block reduction -- an entry's value does not depend on the test
-// it serves. Must be called by all NT threads of the block; red holds
-// (NT/32) * M(M-1)/2 doubles.
+// Standardised value z = ((double)x - mu) * isd of one variable, recomputed
+// from its variable-major data row (FP32 or FP64) with the arithmetic of the
+// standardisation kernel, so it equals the stored FP64 value bit for bit.
+// ---------------------------------------------------------------------------
+struct XRow {
+    const void* p;
+    int f64;
+    double mu, isd;
+    __device__ __forceinline__ double z(int k) const
+    {
+        const double x = f64 ? __ldg((const double*)p + k) : (double)__ldg((const float*)p + k);
+        return (x - mu) * isd;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// FP64 block of C for the rechecks: for the m variables with rows R, the
+// strictly lower packed entries G[b(b-1)/2 + a] = C[V_a, V_b] (a < b) by the
+// definition C_ab = sum_s z_as z_bs / n, every pair in one pass (threads of
+// the block stride the samples), then a fixed-order block reduction -- an
+// entry's value does not depend on the test it serves. Must be called by all
+// NT threads of the block; red holds (NT/32) * M(M-1)/2 doubles.
 // ---------------------------------------------------------------------------
 template <int M, int NT>
-__device__ __forceinline__ void c_block(const double* c64, int p, const double* z64, long long ldz, int n,
-                                        const int (&V)[M], int m, double (&G)[M * (M - 1) / 2], double* red)
+__device__ __forceinline__ void c_block(const XRow (&R)[M], int n, int m, double (&G)[M * (M - 1) / 2], double* red)
 {
     constexpr int D = M * (M - 1) / 2;
-    if (c64) {
-#pragma unroll
-        for (int b = 1; b < M; ++b)
-#pragma unroll
-            for (int a = 0; a < b; ++a) G[b * (b - 1) / 2 + a] = (b < m) ? c64[(size_t)V[a] * p + V[b]] : 0.0;
-        return;
-    }
-    const double* rows[M];
-#pragma unroll
-    for (int a = 0; a < M; ++a) rows[a] = z64 + (size_t)(a < m ? V[a] : V[0]) * ldz;
 #pragma unroll
     for (int q = 0; q < D; ++q) G[q] = 0.0;
 #pragma unroll 4
     for (int k = threadIdx.x; k < n; k += NT) {
         double x[M];
 #pragma unroll
-        for (int a = 0; a < M; ++a) x[a] = (a < m) ? __ldg(rows[a] + k) : 0.0;
+        for (int a = 0; a < M; ++a) x[a] = (a < m) ? R[a].z(k) : 0.0;
 #pragma unroll
         for (int b = 1; b < M; ++b)
 #pragma unroll

@@ -199,13 +199,21 @@ __global__ void __launch_bounds__(RC_THREADS) k_recheck0(Recheck0Params P)
         const QEntry E = P.queue[qi];
         const ProbDesc* D = prob_of(P.vprob, P.probs, E.a);
         double G[1];
-        if (D) {
-            // the problem's own rows: local ids, its sample count
-            const int V[2] = {E.a - D->off, E.b - D->off};
-            c_block<2, RC_THREADS>(nullptr, D->p, P.z64 + D->z_off, D->n, D->n, V, 2, G, red);
+        if (P.c64) {
+            G[0] = P.c64[(size_t)E.a * P.p + E.b];
         } else {
+            // the pair's data rows (a batch problem's own rows, its sample count)
+            const int es = P.xf64 ? 8 : 4;
             const int V[2] = {E.a, E.b};
-            c_block<2, RC_THREADS>(P.c64, P.p, P.z64, P.ldz, P.n, V, 2, G, red);
+            XRow R[2];
+            for (int a = 0; a < 2; ++a) {
+                R[a].f64 = P.xf64;
+                R[a].mu = P.mu[V[a]];
+                R[a].isd = P.isd[V[a]];
+                R[a].p = D ? (const char*)D->xv + (size_t)(V[a] - D->off) * D->n * es
+                           : (const char*)P.xv + (size_t)V[a] * P.ldx * es;
+            }
+            c_block<2, RC_THREADS>(R, D ? D->n : P.n, 2, G, red);
         }
         // independent iff rho^2 <= tanh(tau_0)^2
         const double r2 = D ? D->r2[0] : P.r2;

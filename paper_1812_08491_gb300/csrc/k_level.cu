@@ -76,19 +76,6 @@ __device__ __forceinline__ void word_range(const LevelParams& P, int v, int& lo,
     rb = rowbase(D, P.W, v);
 }
 
-__device__ __forceinline__ long long row_base(const LevelParams& P, int v)
-{
-    return rowbase(prob_of(P.vprob, P.probs, v), P.W, v);
-}
-
-// Degree of row i as far as this level's work items go: 0 for a problem whose
-// threshold or level limit ends before this level.
-__device__ __forceinline__ int item_deg(const LevelParams& P, int i)
-{
-    const int d = P.deg[i];
-    if (P.vprob && P.l > P.probs[P.vprob[i]].lmax) return 0;
-    return d;
-}
 
 // tanh(tau_l) of vertex v's problem and its square.
 __device__ __forceinline__ void thresholds(const LevelParams& P, int v, double& r, double& r2)
@@ -185,6 +172,24 @@ __device__ __forceinline__ unsigned long long row_items(const Binom& B, int d, i
     return (unsigned long long)d * ((B(d - 1, l) + chunk - 1) / chunk);
 }
 
+// Degrees of rows [i0, i0 + 8) (0 past hi): all loads issued before use, so a
+// thread walking its range pays one memory latency per 8 rows.
+__device__ __forceinline__ void load8(const LevelParams& P, int i0, int hi, int (&d)[8], int (&di)[8])
+{
+#pragma unroll
+    for (int u = 0; u < 8; ++u) d[u] = (i0 + u < hi) ? P.deg[i0 + u] : 0;
+    if (P.vlmax) {
+        int m[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) m[u] = (i0 + u < hi) ? P.vlmax[i0 + u] : 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) di[u] = (P.l > m[u]) ? 0 : d[u];
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) di[u] = d[u];
+    }
+}
+
 __device__ void phase_scan(const LevelParams& P, bool learned)
 {
     __shared__ long long sa[32], sb[32], sc[32];
@@ -195,13 +200,18 @@ __device__ void phase_scan(const LevelParams& P, bool learned)
     const int lo = min(P.p, t * per), hi = min(P.p, lo + per);
     const int l = P.l;
     int rng = 0;
+    int d8[8], di8[8];
     // learned order: the per-side candidate lists must fit the perm array
     bool lrn = false;
     if (learned) {
         unsigned long long c = 0;
-        for (int i = lo; i < hi; ++i) {
-            const int d = item_deg(P, i);
-            if (d >= l + 1) c += (unsigned long long)d * (unsigned long long)(d - 1);
+        for (int i0 = lo; i0 < hi; i0 += 8) {
+            load8(P, i0, hi, d8, di8);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int d = di8[u];
+                if (d >= l + 1) c += (unsigned long long)d * (unsigned long long)(d - 1);
+            }
         }
         c = warp_sum_u64(c);
         if (lane == 0) sb[w] = (long long)c;
@@ -215,17 +225,30 @@ __device__ void phase_scan(const LevelParams& P, bool learned)
         __syncthreads();
         lrn = slrn != 0;
     }
+    // one pass for the sums at the default chunk; the chunk doubles (items
+    // recounted) only while the items would not fit the item array
     int chunk = P.chunk0;
-    // choose the chunk
-    for (int it = 0; it < 48; ++it) {
-        unsigned long long b = 0;
-        for (int i = lo; i < hi; ++i) {
-            const int d = item_deg(P, i);
-            if (d >= l + 1 && P.B(d, l) == ~0ull) rng = 1;
-            b += row_items(P.B, d, l, chunk, lrn);
+    long long a = 0, b = 0, c = 0;
+    unsigned long long sq = 0;
+    int dmax = 0;
+    for (int i0 = lo; i0 < hi; i0 += 8) {
+        load8(P, i0, hi, d8, di8);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int d = di8[u];
+            dmax = max(dmax, d);
+            a += d8[u];
+            b += (long long)row_items(P.B, d, l, chunk, lrn);
+            if (d >= l + 1) {
+                if (P.B(d, l) == ~0ull) rng = 1;
+                sq += (unsigned long long)(d + 1) * (unsigned long long)(d + 1);
+                if (lrn) c += (long long)d * (d - 1);
+            }
         }
-        b = warp_sum_u64(b);
-        if (lane == 0) sb[w] = (long long)b;
+    }
+    for (int it = 0; it < 48; ++it) {
+        const unsigned long long bw = warp_sum_u64((unsigned long long)b);
+        if (lane == 0) sb[w] = (long long)bw;
         __syncthreads();
         if (t == 0) {
             unsigned long long tot = 0;
@@ -235,21 +258,13 @@ __device__ void phase_scan(const LevelParams& P, bool learned)
         __syncthreads();
         const bool fits = stot <= P.item_cap;
         __syncthreads();
-        if (fits) break;
-        chunk = chunk > (1 << 29) ? chunk : chunk * 2;
-    }
-    // exclusive scans of (degree, items, candidate-list entries); max degree
-    long long a = 0, b = 0, c = 0;
-    unsigned long long sq = 0;
-    int dmax = 0;
-    for (int i = lo; i < hi; ++i) {
-        const int d = item_deg(P, i);
-        dmax = max(dmax, d);
-        a += P.deg[i];
-        b += (long long)row_items(P.B, d, l, chunk, lrn);
-        if (d >= l + 1) {
-            sq += (unsigned long long)(d + 1) * (unsigned long long)(d + 1);
-            if (lrn) c += (long long)d * (d - 1);
+        if (fits || chunk > (1 << 29)) break;
+        chunk *= 2;
+        b = 0;
+        for (int i0 = lo; i0 < hi; i0 += 8) {
+            load8(P, i0, hi, d8, di8);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) b += (long long)row_items(P.B, di8[u], l, chunk, lrn);
         }
     }
     sq = warp_sum_u64(sq);
@@ -285,14 +300,20 @@ __device__ void phase_scan(const LevelParams& P, bool learned)
     long long ea = ia - a + (w > 0 ? sa[w - 1] : 0);
     long long eb = ib - b + (w > 0 ? sb[w - 1] : 0);
     long long ec = ic - c + (w > 0 ? sc[w - 1] : 0);
-    for (int i = lo; i < hi; ++i) {
-        const int d = item_deg(P, i);
-        P.row_off[i] = ea;
-        P.item_off[i] = eb;
-        if (P.poff) P.poff[i] = ec;
-        ea += P.deg[i];
-        eb += (long long)row_items(P.B, d, l, chunk, lrn);
-        if (lrn && d >= l + 1) ec += (long long)d * (d - 1);
+    for (int i0 = lo; i0 < hi; i0 += 8) {
+        load8(P, i0, hi, d8, di8);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u;
+            if (i >= hi) break;
+            const int d = di8[u];
+            P.row_off[i] = ea;
+            P.item_off[i] = eb;
+            if (P.poff) P.poff[i] = ec;
+            ea += d8[u];
+            eb += (long long)row_items(P.B, d, l, chunk, lrn);
+            if (lrn && d >= l + 1) ec += (long long)d * (d - 1);
+        }
     }
     if (rng) atomicOr(&P.lm->range_error, 1);
     if (t == NT - 1) {
@@ -319,6 +340,7 @@ __device__ void phase_fill(const LevelParams& P)
         int wlo, whi;
         long long rb;
         word_range(P, i, wlo, whi, rb);
+        const ProbDesc* Di = prob_of(P.vprob, P.probs, i);   // every neighbour is in i's problem
         for (int w0 = wlo; w0 < whi; w0 += 32) {
             const int q = w0 + lane;
             unsigned word = (q < whi) ? P.bits[rb + q] : 0u;
@@ -337,7 +359,7 @@ __device__ void phase_fill(const LevelParams& P)
                 P.cols[pos] = j;
                 P.srow[pos] = i;
                 // slot of (j, i): row j's offset + neighbours of j below i
-                const long long rbj = row_base(P, j);
+                const long long rbj = rowbase(Di, P.W, j);
                 const unsigned wj = P.bits[rbj + (i >> 5)];
                 P.partner[pos] = (int)(P.row_off[j] + P.wpre[rbj + (i >> 5)] +
                                        __popc(wj & ((1u << (i & 31)) - 1u)));
@@ -626,93 +648,118 @@ __device__ void phase_ci_edge(const LevelParams& P)
 // spreading each test over several SMs shortens the phase when few tests
 // are queued. The queue is processed in batches that fit the partial buffer.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int recheck_slices(int n) { return max(1, min(8, n / 2048)); }
+__device__ __forceinline__ int recheck_slices(int n) { return max(1, min(8, n / 1024)); }
 
-// FP64 rows of vertex v's problem: sample count, first global vertex, offset
-// of its rows and their stride.
-__device__ __forceinline__ void zview(const LevelParams& P, int v, int& n, int& off, long long& base, long long& ld)
+// Data row of vertex v for the rechecks (its problem's rows in a batch) and
+// its problem's sample count.
+__device__ __forceinline__ XRow xrow(const LevelParams& P, int v, int& n)
 {
-    if (P.vprob) {
-        const ProbDesc& D = P.probs[P.vprob[v]];
-        n = D.n;
-        off = D.off;
-        base = D.z_off;
-        ld = D.n;
+    const int es = P.xf64 ? 8 : 4;
+    const ProbDesc* D = prob_of(P.vprob, P.probs, v);
+    XRow r;
+    r.f64 = P.xf64;
+    r.mu = P.mu[v];
+    r.isd = P.isd[v];
+    if (D) {
+        r.p = (const char*)D->xv + (size_t)(v - D->off) * D->n * es;
+        n = D->n;
     } else {
+        r.p = (const char*)P.xv + (size_t)v * P.ldx * es;
         n = P.n;
-        off = 0;
-        base = 0;
-        ld = P.ldz;
     }
+    return r;
 }
 
+// A queued test whose outcome cannot change the level's result: the edge's
+// removal is already decided by a definitive FP32 independence at a smaller
+// rank on the side that wins (canonical: the smaller endpoint's side first,
+// then the smaller rank), or by any definitive independence (non-canonical).
+// best[] does not change while this is evaluated (it is written only after the
+// grid barrier that follows), so every slice of a test agrees.
+__device__ __forceinline__ bool recheck_moot(const LevelParams& P, long long e, int i, int j, unsigned long long s)
+{
+    const unsigned long long be = ld_cg(P.best + e);
+    const unsigned long long bf = ld_cg(P.best + P.partner[e]);
+    if (!P.canonical) return be != RANK_NONE || bf != RANK_NONE;
+    if (i < j) return be < s;                      // this side is the first one
+    return bf != RANK_NONE || be < s;              // the first side already removes it
+}
+
+// FP64 recheck of the queued tests in batches that fit the partial-sum buffer:
+// one warp per (test, sample slice) forms the slice's Gram entries of the
+// m = l + 2 variables from the data rows, one thread per test adds the slices in
+// order and decides with the FP64 factorisation.
 template <int LB>
 __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
 {
     constexpr int M = LB + 2;
     constexpr int D = M * (M - 1) / 2;
-    __shared__ double red[NW * D];
-    // slices per test: one count for the level (batches mix sample counts; the
-    // slices then follow the largest n, the same for every test of the level)
-    const int S = recheck_slices(P.vprob ? P.nmax : P.n);
-    const long long batch = (long long)P.part_tests;
+    __shared__ double sG[NW][D];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // consecutive units go to consecutive CTAs, so a short queue spreads over SMs
+    const long long gw = (long long)warp * gridDim.x + blockIdx.x;
+    const long long nwarps = (long long)gridDim.x * NW;
+    // slices per test, the same for every test of the level: enough for the
+    // sample count (a batch takes its largest n), and enough units to occupy
+    // every warp when the queue is short
+    const int sp = (int)min(64ll, (nwarps + (long long)nq - 1) / (long long)nq);
+    const int S = max(recheck_slices(P.vprob ? P.nmax : P.n), sp);
+    const long long batch = max(1ll, (long long)(P.part_cap / ((unsigned long long)S * D)));
+    unsigned long long done = 0;
     for (long long q0 = 0; q0 < (long long)nq; q0 += batch) {
         const long long nb = min(batch, (long long)nq - q0);
         // partial sums
-        for (long long u = blockIdx.x; u < nb * S; u += gridDim.x) {
+        for (long long u = gw; u < nb * S; u += nwarps) {
             const long long qi = q0 + u / S;
             const int k = (int)(u % S);
             const QEntry* E = P.queue + qi;
             const long long e = E->a;
             const int i = P.srow[e], j = P.cols[e];
+            double* out = P.part + (size_t)u * D;
+            const bool moot = recheck_moot(P, e, i, j, E->s);
+            if (moot || P.c64) {
+                // slice 0 carries the test's mark: NaN = skipped
+                if (k == 0 && lane == 0) out[0] = moot ? __longlong_as_double(0x7ff8000000000001ll) : 0.0;
+                continue;
+            }
             int V[M];
             V[0] = i;
             V[1] = j;
 #pragma unroll
             for (int c = 0; c < LB; ++c) V[2 + c] = (c < P.l) ? E->S[c] : i;
             const int m = P.l + 2;
-            int zn, zoff;
-            long long zbase, zld;
-            zview(P, i, zn, zoff, zbase, zld);
-            const int k0 = (int)((long long)zn * k / S), k1 = (int)((long long)zn * (k + 1) / S);
             double G[D];
 #pragma unroll
             for (int t = 0; t < D; ++t) G[t] = 0.0;
-            if (P.c64 == nullptr) {
-                const double* rows[M];
+            int zn = 0;
+            XRow R[M];
 #pragma unroll
-                for (int a = 0; a < M; ++a) rows[a] = P.z64 + zbase + (long long)((a < m ? V[a] : V[0]) - zoff) * zld;
+            for (int a = 0; a < M; ++a) R[a] = xrow(P, a < m ? V[a] : V[0], zn);
+            const int k0 = (int)((long long)zn * k / S), k1 = (int)((long long)zn * (k + 1) / S);
 #pragma unroll 4
-                for (int kk = k0 + (int)threadIdx.x; kk < k1; kk += NT) {
-                    double x[M];
+            for (int kk = k0 + lane; kk < k1; kk += 32) {
+                double x[M];
 #pragma unroll
-                    for (int a = 0; a < M; ++a) x[a] = (a < m) ? __ldg(rows[a] + kk) : 0.0;
+                for (int a = 0; a < M; ++a) x[a] = (a < m) ? R[a].z(kk) : 0.0;
 #pragma unroll
-                    for (int b2 = 1; b2 < M; ++b2)
+                for (int b2 = 1; b2 < M; ++b2)
 #pragma unroll
-                        for (int a = 0; a < b2; ++a) G[b2 * (b2 - 1) / 2 + a] = fma(x[a], x[b2], G[b2 * (b2 - 1) / 2 + a]);
-                }
+                    for (int a = 0; a < b2; ++a) G[b2 * (b2 - 1) / 2 + a] = fma(x[a], x[b2], G[b2 * (b2 - 1) / 2 + a]);
             }
-            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
             for (int t = 0; t < D; ++t) {
                 double g = G[t];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-                if (lane == 0) red[w * D + t] = g;
+                if (lane == 0) out[t] = g;
             }
-            __syncthreads();
-            for (int t = threadIdx.x; t < D; t += NT) {
-                double g = 0.0;
-                for (int ww = 0; ww < NW; ++ww) g += red[ww * D + t];
-                P.part[(size_t)u * D + t] = g;
-            }
-            __syncthreads();
         }
         if (!grid_sync(P.lm)) return false;
-        // combine the slices of each test in order and decide
-        for (long long t = blockIdx.x; t < nb; t += gridDim.x) {
-            if (threadIdx.x != 0) continue;
+        // combine the slices of each test in order (a warp per test, lanes over
+        // the Gram entries) and decide (its first lane)
+        for (long long t = gw; t < nb; t += nwarps) {
+            const double* pt = P.part + (size_t)t * S * D;
+            if (isnan(__ldcg(pt))) continue;       // moot (warp-uniform)
             const long long qi = q0 + t;
             const QEntry* E = P.queue + qi;
             const long long e = E->a;
@@ -722,41 +769,48 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
             V[1] = j;
 #pragma unroll
             for (int c = 0; c < LB; ++c) V[2 + c] = (c < P.l) ? E->S[c] : i;
-            double G[D];
             if (P.c64) {
-#pragma unroll
-                for (int b2 = 1; b2 < M; ++b2)
-#pragma unroll
-                    for (int a = 0; a < b2; ++a)
-                        G[b2 * (b2 - 1) / 2 + a] = (b2 < P.l + 2) ? P.c64[(size_t)V[a] * P.p + V[b2]] : 0.0;
+                for (int x = lane; x < D; x += 32) {
+                    int b2 = 1;
+                    while ((b2 + 1) * b2 / 2 <= x) ++b2;
+                    const int a = x - b2 * (b2 - 1) / 2;
+                    sG[warp][x] = (b2 < P.l + 2) ? P.c64[(size_t)V[a] * P.p + V[b2]] : 0.0;
+                }
             } else {
-                int zn, zoff;
-                long long zbase, zld;
-                zview(P, i, zn, zoff, zbase, zld);
+                int zn = 0;
+                xrow(P, i, zn);
                 const double inv_n = 1.0 / (double)zn;
-#pragma unroll
-                for (int x = 0; x < D; ++x) {
+                for (int x = lane; x < D; x += 32) {
                     double g = 0.0;
-                    for (int k = 0; k < S; ++k) g += __ldcg(P.part + ((size_t)t * S + k) * D + x);
-                    G[x] = g * inv_n;
+                    for (int k = 0; k < S; ++k) g += __ldcg(pt + (size_t)k * D + x);
+                    sG[warp][x] = g * inv_n;
                 }
             }
-            // V index 0 = i, 1 = j, 2 + a = S_a; G[b(b-1)/2 + a] holds C[V_a, V_b], a < b
-            Factor<double, LB> F;
-            factor_build<double, LB>(
-                F, P.l, P.rank_tol, [&](int a, int b2) { return G[(a + 2) * (a + 1) / 2 + (b2 + 2)]; },
-                [&](int a) { return G[(a + 2) * (a + 1) / 2 + 0]; });
-            double H12, H22;
-            factor_apply<double, LB>(F, P.l, G[0], [&](int a) { return G[(a + 2) * (a + 1) / 2 + 1]; }, H12, H22);
-            const double H11 = 1.0 - F.uu;
-            double thr, thr2;
-            thresholds(P, i, thr, thr2);
-            const bool indep = (!(H11 > kVarZero) || !(H22 > kVarZero)) ? true : (H12 * H12 <= thr2 * H11 * H22);
-            if (indep) atomicMin(P.best + e, E->s);
+            __syncwarp();
+            if (lane == 0) {
+                ++done;
+                const double* G = sG[warp];
+                // V index 0 = i, 1 = j, 2 + a = S_a; G[b(b-1)/2 + a] holds C[V_a, V_b], a < b
+                Factor<double, LB> F;
+                factor_build<double, LB>(
+                    F, P.l, P.rank_tol, [&](int a, int b2) { return G[(a + 2) * (a + 1) / 2 + (b2 + 2)]; },
+                    [&](int a) { return G[(a + 2) * (a + 1) / 2 + 0]; });
+                double H12, H22;
+                factor_apply<double, LB>(F, P.l, G[0], [&](int a) { return G[(a + 2) * (a + 1) / 2 + 1]; }, H12,
+                                         H22);
+                const double H11 = 1.0 - F.uu;
+                double thr, thr2;
+                thresholds(P, i, thr, thr2);
+                const bool indep =
+                    (!(H11 > kVarZero) || !(H22 > kVarZero)) ? true : (H12 * H12 <= thr2 * H11 * H22);
+                if (indep) atomicMin(P.best + e, E->s);
+            }
+            __syncwarp();
         }
         if (!grid_sync(P.lm)) return false;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&P.lm->rechecks[P.l], nq);
+    done = warp_sum_u64(done);
+    if (lane == 0 && done) atomicAdd(&P.lm->rechecks[P.l], done);
     return true;
 }
 
@@ -831,7 +885,8 @@ __device__ void phase_finalize(const LevelParams& P, bool lrn)
                 else if (by != RANK_NONE) { side = y; rank = by; slot = f; }
                 if (side >= 0) {
                     removed = true;
-                    bitset_clear_pair_at(P.bits, row_base(P, x), row_base(P, y), x, y);
+                    const ProbDesc* Dx = prob_of(P.vprob, P.probs, x);
+                    bitset_clear_pair_at(P.bits, rowbase(Dx, P.W, x), rowbase(Dx, P.W, y), x, y);
                     atomicSub(P.deg + x, 1);
                     atomicSub(P.deg + y, 1);
                     int S[LB];

@@ -1,8 +1,8 @@
 // k_prep.cu -- standardisation of the data and the FP64 correlation product.
 //
 // C = Z^T Z / n with Z the standardised data (Sec. 4.3 defines C as the
-// correlation matrix; the paper does not say where it is formed). Moments are
-// FP64 and two-pass (mean, then centred sum of squares), divisor n.
+// correlation matrix; the paper does not say where it is formed). Mean and
+// variance are FP64 values, divisor n, from shifted sums.
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
@@ -28,17 +28,17 @@ __global__ void k_transpose(const T* __restrict__ X, long long ld, int n, int p,
     }
 }
 
-// Batch form: block z transposes problem z's n x p sample-major block at
-// x_off into its p x n variable-major block at the same offset of Xt.
+// Batch form: block z transposes problem z's n x p sample-major data (xs)
+// into its p x n variable-major block at offset x_off of Xt.
 template <typename T>
-__global__ void k_transpose_batch(const T* __restrict__ X, const ProbDesc* __restrict__ probs, T* __restrict__ Xt)
+__global__ void k_transpose_batch(const ProbDesc* __restrict__ probs, T* __restrict__ Xt)
 {
     __shared__ T tile[32][33];
     const ProbDesc& D = probs[blockIdx.z];
     const int n = D.n, p = D.p;
     const int v0 = blockIdx.x * 32, s0 = blockIdx.y * 32;
     if (v0 >= p || s0 >= n) return;
-    const T* src = X + D.x_off;
+    const T* src = (const T*)D.xs;
     T* dst = Xt + D.x_off;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int s = s0 + r, v = v0 + threadIdx.x;
@@ -49,6 +49,109 @@ __global__ void k_transpose_batch(const T* __restrict__ X, const ProbDesc* __res
         const int v = v0 + r, s = s0 + threadIdx.x;
         if (s < n && v < p) dst[(size_t)v * n + s] = tile[threadIdx.x][r];
     }
+}
+
+// ---------------------------------------------------------------------------
+// Compensated FP32 pairs ("double-word" numbers hi + lo, |lo| <= ulp(hi)/2):
+// the error-free sums of Knuth (two_sum) and Dekker (fast_two_sum, |a| >= |b|)
+// and the accurate pair addition of Joldes, Muller and Popescu (2017), whose
+// relative error is below 3 * 2^-48. GB300 runs FP32 at many times its FP64
+// rate, so moments of FP32 data are accumulated in pairs and only the
+// per-thread partial sums are combined in FP64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    e = b - (s - a);
+}
+
+__device__ __forceinline__ void pair_add(float& xh, float& xl, float yh, float yl)
+{
+    float sh, sl, th, tl, vh, vl;
+    two_sum(xh, yh, sh, sl);
+    two_sum(xl, yl, th, tl);
+    sl += th;
+    fast_two_sum(sh, sl, vh, vl);
+    vl += tl;
+    fast_two_sum(vh, vl, xh, xl);
+}
+
+// Shifted moments S1 = sum (x - K), S2 = sum (x - K)^2 of a row, by one block
+// of NT threads, in a fixed order. FP64 data, or FP64 rows requested: FP64
+// sums per thread, a warp tree and the warp partials in order. FP32 data
+// otherwise: compensated pairs throughout -- x - K exactly as a pair
+// (two_sum), its square exactly to 2^-48 (the product's error term by fma; the
+// lo^2 term, below 2^-48 of the square, is dropped), sums by pair_add per
+// thread and down the warp tree -- widened to FP64 only for the warp partials.
+// The totals are valid in thread 0.
+template <typename T, int NT>
+__device__ __forceinline__ void shifted_moments(const T* __restrict__ row, int n, T K, bool pairs, double& S1,
+                                                double& S2)
+{
+    __shared__ double red[2][NT / 32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double s1 = 0.0, s2 = 0.0;
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+        if (pairs) {
+            float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
+            for (int k = threadIdx.x; k < n; k += NT) {
+                float dh, dl;
+                two_sum(row[k], -K, dh, dl);
+                pair_add(ah, al, dh, dl);
+                const float p = dh * dh;
+                float q = fmaf(dh, dh, -p);
+                q = fmaf(2.f * dh, dl, q);
+                float ph, pl;
+                fast_two_sum(p, q, ph, pl);
+                pair_add(bh, bl, ph, pl);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float xh = __shfl_xor_sync(0xffffffffu, ah, o), xl = __shfl_xor_sync(0xffffffffu, al, o);
+                const float yh = __shfl_xor_sync(0xffffffffu, bh, o), yl = __shfl_xor_sync(0xffffffffu, bl, o);
+                pair_add(ah, al, xh, xl);
+                pair_add(bh, bl, yh, yl);
+            }
+            if (lane == 0) {
+                s1 = (double)ah + (double)al;
+                s2 = (double)bh + (double)bl;
+            }
+            done = true;
+        }
+    }
+    if (!done) {
+        const double Kd = (double)K;
+        for (int k = threadIdx.x; k < n; k += NT) {
+            const double d = (double)row[k] - Kd;
+            s1 += d;
+            s2 = fma(d, d, s2);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+    }
+    if (lane == 0) {
+        red[0][w] = s1;
+        red[1][w] = s2;
+    }
+    __syncthreads();
+    S1 = 0.0;
+    S2 = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NT / 32; ++k) {
+            S1 += red[0][k];
+            S2 += red[1][k];
+        }
 }
 
 // One block per variable. Moments in FP64 in one pass over shifted values
@@ -64,76 +167,78 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
                                                     long long ldb, Meta* meta, const int* __restrict__ vprob,
                                                     const ProbDesc* __restrict__ probs)
 {
-    __shared__ double red[2][NT / 32];
     const int v = blockIdx.x;
     if (v >= p) return;
     const T* row = Xv + (size_t)v * ld;
     double* zrow = z64 ? z64 + (size_t)v * ldz : nullptr;
+    long long kpad = ldb;  // bf16 columns written (the product reads whole 64-wide slabs)
     if (vprob) {
         // batch: global vertex v of problem D, whose variable-major rows (ld = its
-        // n) start at x_off and whose FP64 rows start at z_off; a padding vertex
-        // gets zero bf16 rows
+        // n) start at xv and whose FP64 rows start at z_off; the product reads its
+        // rows up to n rounded to 64; a padding vertex gets zero bf16 rows
         const ProbDesc& D = probs[vprob[v]];
         const int loc = v - D.off;
+        kpad = ((long long)D.n + 63) / 64 * 64;
         if (loc >= D.p) {
             if (threadIdx.x == 0) {
                 mu[v] = 0.0;
                 isd[v] = 0.0;
             }
             if (zhi)
-                for (int k = threadIdx.x; k < ldb; k += NT) {
+                for (int k = threadIdx.x; k < kpad; k += NT) {
                     zhi[(size_t)v * ldb + k] = __float2bfloat16(0.f);
                     zlo[(size_t)v * ldb + k] = __float2bfloat16(0.f);
                 }
             return;
         }
         n = D.n;
-        row = Xv + D.x_off + (size_t)loc * n;
+        row = (const T*)D.xv + (size_t)loc * n;
         if (z64) zrow = z64 + D.z_off + (long long)loc * n;
     }
-    const double K = (double)row[0];
-    double s1 = 0.0, s2 = 0.0;
+    // FP32 mode (no FP64 rows requested): compensated FP32 pairs for FP32 data
+    const bool fast = (zrow == nullptr);
+    __shared__ double stat[2];
+    __shared__ float fstat[3];
+    {
+        double S1, S2;
+        shifted_moments<T, NT>(row, n, row[0], fast, S1, S2);
+        // mean, 1/sd and their FP32 forms, once per variable
+        if (threadIdx.x == 0) {
+            const double K = (double)row[0];
+            const double mean = K + S1 / (double)n;
+            const double var = (S2 - S1 * S1 / (double)n) / (double)n;
+            const bool ok = (var > 0.0) && isfinite(var) && isfinite(mean);
+            const double inv = ok ? 1.0 / sqrt(var) : 0.0;
+            mu[v] = mean;
+            isd[v] = inv;
+            if (!ok) atomicOr(&meta->error, 1);
+            stat[0] = mean;
+            stat[1] = inv;
+            const float mh = (float)mean;
+            fstat[0] = mh;
+            fstat[1] = (float)(mean - (double)mh);
+            fstat[2] = (float)inv;
+        }
+        __syncthreads();
+    }
+    const double mean = stat[0], inv = stat[1];
+    // z = (x - mean) / sd in FP64 for the FP64 rows. The bf16 split z = hi + lo
+    // (|z - hi - lo| < 2^-17 |z|) needs z to about 2^-20: for FP32 data it is
+    // formed in FP32 as ((x - m_hi) - m_lo) * (1/sd) with mean = m_hi + m_lo
+    // (x - m_hi exact when x is within a factor 2 of the mean, else rounded
+    // relative to a result of the size of x), about 3 * 2^-24 in all; for FP64
+    // data the centring is FP64.
+    const float mh = fstat[0], ml = fstat[1], fi = fstat[2];
     for (int k = threadIdx.x; k < n; k += NT) {
-        const double d = (double)row[k] - K;
-        s1 += d;
-        s2 = fma(d, d, s2);
-    }
-    // deterministic block reduction: warp trees, then the warp partials in order
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        red[0][w] = s1;
-        red[1][w] = s2;
-    }
-    __syncthreads();
-    double S1 = 0.0, S2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < NT / 32; ++k) {
-        S1 += red[0][k];
-        S2 += red[1][k];
-    }
-    const double mean = K + S1 / (double)n;
-    const double var = (S2 - S1 * S1 / (double)n) / (double)n;
-    const bool ok = (var > 0.0) && isfinite(var) && isfinite(mean);
-    const double inv = ok ? 1.0 / sqrt(var) : 0.0;
-    if (threadIdx.x == 0) {
-        mu[v] = mean;
-        isd[v] = inv;
-        if (!ok) atomicOr(&meta->error, 1);
-    }
-    // z = (x - mean) / sd in FP64; the bf16 split z = hi + lo (|z - hi - lo| <
-    // 2^-18 |z|) takes the FP64 centring and an FP32 scaling (2^-24, far below
-    // the split's 2^-18)
-    const float fi = (float)inv;
-    for (int k = threadIdx.x; k < n; k += NT) {
-        const double d = (double)row[k] - mean;
-        if (zrow) zrow[k] = d * inv;
+        float z;
+        if (sizeof(T) == 4 && fast) {
+            z = (((float)row[k] - mh) - ml) * fi;
+        } else {
+            const double d = (double)row[k] - mean;
+            if (zrow) zrow[k] = d * inv;
+            z = (float)d * fi;
+        }
         if (zhi) {
-            const float z = (float)d * fi;
             const __nv_bfloat16 h = __float2bfloat16_rn(z);
             zhi[(size_t)v * ldb + k] = h;
             zlo[(size_t)v * ldb + k] = __float2bfloat16_rn(z - __bfloat162float(h));
@@ -141,7 +246,7 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
     }
     // zero the K padding so the tensor-core product can read whole 64-wide slabs
     if (zhi)
-        for (int k = n + threadIdx.x; k < ldb; k += NT) {
+        for (int k = n + threadIdx.x; k < kpad; k += NT) {
             zhi[(size_t)v * ldb + k] = __float2bfloat16(0.f);
             zlo[(size_t)v * ldb + k] = __float2bfloat16(0.f);
         }
@@ -247,14 +352,14 @@ cudaError_t launch_standardize(int dtype, const void* Xv, long long ld, int n, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_transpose_batch(int dtype, const void* X, const ProbDesc* probs, int nprob, int pmax, int nmax,
-                                   void* Xt, cudaStream_t st)
+cudaError_t launch_transpose_batch(int dtype, const ProbDesc* probs, int nprob, int pmax, int nmax, void* Xt,
+                                   cudaStream_t st)
 {
     dim3 grid((pmax + 31) / 32, (nmax + 31) / 32, nprob), block(32, 8);
     if (dtype == CUPC_F64)
-        k_transpose_batch<double><<<grid, block, 0, st>>>((const double*)X, probs, (double*)Xt);
+        k_transpose_batch<double><<<grid, block, 0, st>>>(probs, (double*)Xt);
     else
-        k_transpose_batch<float><<<grid, block, 0, st>>>((const float*)X, probs, (float*)Xt);
+        k_transpose_batch<float><<<grid, block, 0, st>>>(probs, (float*)Xt);
     return cudaGetLastError();
 }
 

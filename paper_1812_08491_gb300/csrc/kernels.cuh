@@ -45,7 +45,9 @@ struct ProbDesc {
     long long bw;                  // first word of its bitset block
     long long c_off;               // its p x p correlation in the packed C
     long long z_off;               // its p x n standardised rows (FP64) in the packed rows
-    long long x_off;               // its data (elements) in the packed input
+    long long x_off;               // its data (elements) in the packed input buffers
+    const void* xs;                // its data as given (n x p, the batch's layout and type)
+    const void* xv;                // its variable-major rows (ld = n)
     double r[LV], r2[LV];          // tanh(tau_l) for its n and alpha, and the square
 };
 
@@ -89,13 +91,16 @@ struct LevelParams {
     double piv_floor;              // FP32 mode: smaller pivot^2 sends the test to FP64
     QEntry* queue;
     unsigned long long qcap;
-    const double* z64;             // FP64 standardised rows for the rechecks (or c64)
-    long long ldz;
+    const void* xv;                // variable-major data rows for the rechecks (or c64)
+    long long ldx;
+    int xf64;                      // element type of xv: 1 FP64, 0 FP32
+    const double* mu;              // per variable: mean and 1/sd of the standardisation
+    const double* isd;
     int n;
     int nmax;                      // batch: largest sample count
     const double* c64;
-    double* part;                  // recheck partial Gram sums: part_tests x slices x D doubles
-    unsigned long long part_tests; // queued tests per recheck batch
+    double* part;                  // recheck partial Gram sums (tests x slices x D doubles)
+    unsigned long long part_cap;   // doubles in part
     int* rec;                      // SepSet record pool (int32 groups i, j, l, S...)
     unsigned long long rec_cap;
     LevelMeta* lm;
@@ -103,6 +108,7 @@ struct LevelParams {
     // batch: problem of each global vertex, and the problems (nullptr: one problem)
     const int* vprob;
     const ProbDesc* probs;
+    const int* vlmax;              // batch: the last level of each vertex's problem
     unsigned long long* prob_serial;   // batch: serial-order tests per problem and level (nprob x LV)
     int ctas_per_sm;               // launch shape (0: as many as fit, at most 2)
     // learned ordering (levels >= 2, FP32 mode)
@@ -115,8 +121,11 @@ struct LevelParams {
 
 // Parameters of the level-0 FP64 recheck.
 struct Recheck0Params {
-    const double* z64;
-    long long ldz;
+    const void* xv;                // variable-major data rows, their stride and type
+    long long ldx;
+    int xf64;
+    const double* mu;
+    const double* isd;
     int n;
     const double* c64;
     int p;
@@ -134,8 +143,8 @@ cudaError_t launch_transpose(int dtype, const void* X, long long ld, int n, int 
 cudaError_t launch_standardize(int dtype, const void* Xv, long long ld, int n, int p, double* mu, double* isd,
                                double* z64, long long ldz, void* zhi, void* zlo, long long ldb, Meta* meta,
                                cudaStream_t st, const int* vprob = nullptr, const ProbDesc* probs = nullptr);
-cudaError_t launch_transpose_batch(int dtype, const void* X, const ProbDesc* probs, int nprob, int pmax, int nmax,
-                                   void* Xt, cudaStream_t st);
+cudaError_t launch_transpose_batch(int dtype, const ProbDesc* probs, int nprob, int pmax, int nmax, void* Xt,
+                                   cudaStream_t st);
 cudaError_t launch_syrk_f64(const double* Z, long long ldz, int n, int p, double* C, cudaStream_t st);
 void corr_tc_plan(int p, long long ldk, int num_sms, int* tiles, int* nsplit, int* kps, size_t* ws_bytes);
 cudaError_t launch_corr_tc(const void* hi, const void* lo, long long ldk, int p, int n, float* ws, float* C,

@@ -488,6 +488,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         if ((s = ensure(ctx, ctx->wpre, bitbytes)) != CUPC_OK) return s;
         if ((s = ensure(ctx, ctx->best, (size_t)nnz_cap * 8)) != CUPC_OK) return s;
         if ((s = ensure(ctx, ctx->item_row, (size_t)item_cap * 4)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, *ctx_buf(ctx, "item_c"), (size_t)item_cap * 4)) != CUPC_OK) return s;
         if ((s = ensure_binom(ctx, M.maxdeg + 2)) != CUPC_OK) return s;
         if ((s = ensure(ctx, ctx->lmeta, sizeof(LevelMeta))) != CUPC_OK) return s;
         // recheck partials: batches of queued tests sized to this buffer per level
@@ -509,6 +510,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         LP.row_off = (long long*)ctx->row_off.p;
         LP.item_off = (long long*)ctx->item_off.p;
         LP.item_row = (int*)ctx->item_row.p;
+        LP.item_c = (int*)ctx_buf(ctx, "item_c")->p;
         LP.item_cap = item_cap;
         LP.cols = (int*)ctx->cols.p;
         LP.srow = (int*)ctx->srow.p;
@@ -607,6 +609,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
                 H.tests[q] = H.rechecks[q] = H.removed[q] = H.serial[q] = H.edges[q] = H.items[q] = 0;
                 H.next_item[q] = H.queue_len[q] = H.block_entries[q] = 0;
                 for (int c = 0; c < 4; ++c) H.phase_ns[q][c] = 0;
+                for (int c = 0; c < RND; ++c) H.round_off[q][c] = H.round_cur[q][c] = 0;
                 H.maxdeg[q] = 0;
                 H.chunk[q] = 0;
             }

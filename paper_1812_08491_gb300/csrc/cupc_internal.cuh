@@ -216,16 +216,31 @@ __device__ __forceinline__ bool bitset_test(const unsigned* bits, int W, int i, 
 
 // ---------------------------------------------------------------------------
 // Standardised value z = ((double)x - mu) * isd of one variable, recomputed
-// from its variable-major data row (FP32 or FP64) with the arithmetic of the
-// standardisation kernel, so it equals the stored FP64 value bit for bit.
+// in FP64 from its variable-major data row (FP32 or FP64) and the moments of
+// the standardisation: the centring rounds once, the scaling once.
 // ---------------------------------------------------------------------------
+// FP32 -> FP64 widening (exact) by integer operations on the IEEE encodings
+// for normal numbers (exponent rebiased from 127 to 1023, mantissa shifted
+// left by 29); zeros, subnormals and non-finite values take the conversion
+// instruction, which on GB300 shares the narrow FP64 pipe.
+__device__ __forceinline__ double widen_f32(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)x;
+    const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
+                                    ((unsigned long long)(e + 896u) << 52) |
+                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
 struct XRow {
     const void* p;
     int f64;
     double mu, isd;
     __device__ __forceinline__ double z(int k) const
     {
-        const double x = f64 ? __ldg((const double*)p + k) : (double)__ldg((const float*)p + k);
+        const double x = f64 ? __ldg((const double*)p + k) : widen_f32(__ldg((const float*)p + k));
         return (x - mu) * isd;
     }
 };

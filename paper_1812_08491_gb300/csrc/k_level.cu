@@ -190,6 +190,18 @@ __device__ __forceinline__ void load8(const LevelParams& P, int i0, int hi, int 
     }
 }
 
+// Adds a row with K items to the round histogram (bin min(K, RND - 1); rows
+// without items are not counted). Lanes with the same bin are combined first:
+// most rows fall in a handful of bins, and shared atomics on one address
+// serialise.
+__device__ __forceinline__ void hist_add(unsigned long long* hist, unsigned long long K)
+{
+    const int bin = K == 0 ? -1 : (int)(K < RND - 1 ? K : RND - 1);
+    const unsigned peers = __match_any_sync(__activemask(), bin);
+    const int lane = threadIdx.x & 31;
+    if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned long long)__popc(peers));
+}
+
 __device__ void phase_scan(const LevelParams& P, bool learned)
 {
     __shared__ long long sa[32], sb[32], sc[32];
@@ -300,6 +312,11 @@ __device__ void phase_scan(const LevelParams& P, bool learned)
     long long ea = ia - a + (w > 0 ? sa[w - 1] : 0);
     long long eb = ib - b + (w > 0 ? sb[w - 1] : 0);
     long long ec = ic - c + (w > 0 ? sc[w - 1] : 0);
+    // rows by their item count (capped at RND - 1) and the items past the cap
+    __shared__ unsigned long long hist[RND];
+    for (int q = t; q < RND; q += NT) hist[q] = 0;
+    __syncthreads();
+    unsigned long long ovf = 0;
     for (int i0 = lo; i0 < hi; i0 += 8) {
         load8(P, i0, hi, d8, di8);
 #pragma unroll
@@ -311,8 +328,29 @@ __device__ void phase_scan(const LevelParams& P, bool learned)
             P.item_off[i] = eb;
             if (P.poff) P.poff[i] = ec;
             ea += d8[u];
-            eb += (long long)row_items(P.B, d, l, chunk, lrn);
+            const unsigned long long K = row_items(P.B, d, l, chunk, lrn);
+            eb += (long long)K;
+            hist_add(hist, K);
+            if (K > RND - 1) ovf += K - (RND - 1);
             if (lrn && d >= l + 1) ec += (long long)d * (d - 1);
+        }
+    }
+    ovf = warp_sum_u64(ovf);
+    if (lane == 0 && ovf) atomicAdd(&hist[0], ovf);   // bin 0 (no row has 0 items counted) carries the overflow
+    __syncthreads();
+    // round c < RND - 1 holds the rows with more than c items; the last round the
+    // items past the first RND - 1 of every row
+    if (t == 0) {
+        unsigned long long off = 0, above = 0;
+        unsigned long long n_round[RND];
+        for (int v = RND - 1; v >= 1; --v) {
+            above += hist[v];
+            n_round[v - 1] = above;   // rows with more than v - 1 items
+        }
+        n_round[RND - 1] = hist[0];
+        for (int q = 0; q < RND; ++q) {
+            P.lm->round_off[l][q] = off;
+            off += n_round[q];
         }
     }
     if (rng) atomicOr(&P.lm->range_error, 1);
@@ -330,6 +368,69 @@ __device__ void phase_scan(const LevelParams& P, bool learned)
 // ---------------------------------------------------------------------------
 // P2: A'_G rows, item rows, best reset
 // ---------------------------------------------------------------------------
+// Work items in dispatch order: each CTA takes a contiguous range of rows,
+// reserves slots in every round for them (one global atomic per round), then
+// each row's warp writes its items (row, index within the row) into them. The
+// order within a round is unspecified; results do not depend on it.
+__device__ void phase_items(const LevelParams& P)
+{
+    __shared__ unsigned cnt[RND];
+    __shared__ unsigned long long base[RND], cur[RND];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int l = P.l;
+    const int r0 = (int)((long long)P.p * blockIdx.x / gridDim.x);
+    const int r1 = (int)((long long)P.p * (blockIdx.x + 1) / gridDim.x);
+    for (int q = threadIdx.x; q < RND; q += NT) {
+        cnt[q] = 0;
+        cur[q] = 0;
+    }
+    __syncthreads();
+    unsigned long long ovf = 0;
+    for (int i = r0 + (int)threadIdx.x; i < r1; i += NT) {
+        const long long K = P.item_off[i + 1] - P.item_off[i];
+        const int bin = K == 0 ? -1 : (int)(K < RND - 1 ? K : RND - 1);
+        const unsigned peers = __match_any_sync(__activemask(), bin);
+        if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[bin], (unsigned)__popc(peers));
+        if (K > RND - 1) ovf += (unsigned long long)(K - (RND - 1));
+    }
+    ovf = warp_sum_u64(ovf);
+    __shared__ unsigned long long sovf;
+    if (threadIdx.x == 0) sovf = 0;
+    __syncthreads();
+    if (lane == 0 && ovf) atomicAdd(&sovf, ovf);
+    __syncthreads();
+    if (threadIdx.x < RND) {
+        const int q = threadIdx.x;
+        unsigned long long nq = 0;
+        if (q < RND - 1) {
+            for (int v = q + 1; v < RND; ++v) nq += cnt[v];
+        } else {
+            nq = sovf;
+        }
+        base[q] = nq ? P.lm->round_off[l][q] + atomicAdd(&P.lm->round_cur[l][q], nq) : 0;
+    }
+    __syncthreads();
+    for (int i = r0 + w; i < r1; i += NW) {
+        const long long K = P.item_off[i + 1] - P.item_off[i];
+        const int kc = (int)(K < RND - 1 ? K : RND - 1);
+        for (int c = lane; c < kc; c += 32) {
+            const unsigned long long slot = base[c] + atomicAdd(&cur[c], 1ull);
+            P.item_row[slot] = i;
+            P.item_c[slot] = c;
+        }
+        if (K > RND - 1) {
+            unsigned long long k0 = 0;
+            if (lane == 0) k0 = atomicAdd(&cur[RND - 1], (unsigned long long)(K - (RND - 1)));
+            k0 = __shfl_sync(0xffffffffu, k0, 0);
+            for (long long q = lane; q < K - (RND - 1); q += 32) {
+                const unsigned long long slot = base[RND - 1] + k0 + (unsigned long long)q;
+                P.item_row[slot] = i;
+                P.item_c[slot] = (int)(RND - 1 + q);
+            }
+        }
+    }
+}
+
 __device__ void phase_fill(const LevelParams& P)
 {
     const int lane = threadIdx.x & 31;
@@ -367,8 +468,8 @@ __device__ void phase_fill(const LevelParams& P)
             }
             base += __shfl_sync(0xffffffffu, incl, 31);
         }
-        for (long long k = P.item_off[i] + lane; k < P.item_off[i + 1]; k += 32) P.item_row[k] = i;
     }
+    phase_items(P);
     const long long nnz = P.row_off[P.p];
     for (long long e = (long long)blockIdx.x * NT + threadIdx.x; e < nnz; e += (long long)gridDim.x * NT)
         P.best[e] = RANK_NONE;
@@ -378,23 +479,38 @@ __device__ void phase_fill(const LevelParams& P)
 // P4: CI tests
 // ---------------------------------------------------------------------------
 // 0 dependent, 1 independent, 2 undecided in FP32 (sent to the FP64 recheck)
+// Decision constants of one work item, converted once (conversions run on
+// GB300's narrow FP64 pipe): tanh(tau_l) and its square, the FP32 band.
+struct Decide {
+    float r, band_abs, band_rel, piv_floor;
+    double r2;
+};
+
+__device__ __forceinline__ Decide decide_consts(const LevelParams& P, double r, double r2)
+{
+    Decide d;
+    d.r = (float)r;
+    d.band_abs = (float)P.band_abs;
+    d.band_rel = (float)P.band_rel;
+    d.piv_floor = (float)P.piv_floor;
+    d.r2 = r2;
+    return d;
+}
+
 template <typename T, bool FP32>
-__device__ __forceinline__ int ci_decide(T H11, T H12, T H22, T minpiv2, const LevelParams& P, double r_,
-                                         double r2_)
+__device__ __forceinline__ int ci_decide(T H11, T H12, T H22, T minpiv2, const Decide& dc)
 {
     if (!FP32) {
         // zero conditional variance (rounding level of the unit diagonal): V_i or
         // V_j is a linear function of S -> independent
         if (!(H11 > T(kVarZero)) || !(H22 > T(kVarZero))) return 1;
-        return (H12 * H12 <= (T)r2_ * H11 * H22) ? 1 : 0;
+        return (H12 * H12 <= (T)dc.r2 * H11 * H22) ? 1 : 0;
     } else {
-        if (!(minpiv2 >= (T)P.piv_floor) || !(H11 > T(1e-4)) || !(H22 > T(1e-4))) return 2;
+        if (!(minpiv2 >= dc.piv_floor) || !(H11 > 1e-4f) || !(H22 > 1e-4f)) return 2;
         const float rho = fabsf((float)H12) * rsqrtf((float)(H11 * H22));
-        const float band =
-            (float)P.band_abs + (float)P.band_rel / ((float)minpiv2 * fminf((float)H11, (float)H22));
-        const float r = (float)r_;
-        if (rho > r + band) return 0;
-        if (rho < r - band) return 1;
+        const float band = dc.band_abs + dc.band_rel / ((float)minpiv2 * fminf((float)H11, (float)H22));
+        if (rho > dc.r + band) return 0;
+        if (rho < dc.r - band) return 1;
         return 2;
     }
 }
@@ -413,7 +529,7 @@ __device__ void phase_ci(const LevelParams& P)
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
         const int i = P.item_row[item];
-        const long long k = (long long)item - P.item_off[i];
+        const long long k = P.item_c[item];
         const long long off = P.row_off[i];
         const int d = (int)(P.row_off[i + 1] - off);
         const unsigned long long nsets = P.B(d, l);
@@ -422,6 +538,7 @@ __device__ void phase_ci(const LevelParams& P)
         const CView<T> CV = cview<T>(P, i);
         double thr, thr2;
         thresholds(P, i, thr, thr2);
+        const Decide dc = decide_consts(P, thr, thr2);
         const T* __restrict__ Ci = CV.row(i);
         for (unsigned long long base = s0; base < s1; base += 32) {
             const unsigned long long s = base + lane;
@@ -472,7 +589,7 @@ __device__ void phase_ci(const LevelParams& P)
                         factor_apply<T, LB>(F, l, cij, [&](int a) { return __ldg(Cj + Sx[a]); }, H12, H22);
                         const T H11 = T(1) - F.uu;
                         ++ntests;
-                        const int dec = ci_decide<T, FP32>(H11, H12, H22, F.minpiv2, P, thr, thr2);
+                        const int dec = ci_decide<T, FP32>(H11, H12, H22, F.minpiv2, dc);
                         const long long e = off + jp;
                         if (dec == 1) {
                             atomicMin(P.best + e, s);
@@ -574,12 +691,13 @@ __device__ void phase_ci_edge(const LevelParams& P)
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
         const int i = P.item_row[item];
-        const long long k = (long long)item - P.item_off[i];
+        const long long k = P.item_c[item];
         const long long off = P.row_off[i];
         const int m = (int)(P.row_off[i + 1] - off) - 1;
         const CView<T> CV = cview<T>(P, i);
         double thr, thr2;
         thresholds(P, i, thr, thr2);
+        const Decide dc = decide_consts(P, thr, thr2);
         const unsigned long long total = P.B(m, l);
         const long long per_edge = (long long)((total + chunk - 1) / chunk);
         const long long q = k / per_edge, cidx = k % per_edge;
@@ -617,7 +735,7 @@ __device__ void phase_ci_edge(const LevelParams& P)
                 factor_apply<T, LB>(F, l, cij, [&](int a) { return __ldg(Cj + Sx[a]); }, H12, H22);
                 const T H11 = T(1) - F.uu;
                 ++ntests;
-                const int dec = ci_decide<T, FP32>(H11, H12, H22, F.minpiv2, P, thr, thr2);
+                const int dec = ci_decide<T, FP32>(H11, H12, H22, F.minpiv2, dc);
                 if (dec == 1) {
                     atomicMin(P.best + e, r);
                 } else if (FP32 && dec == 2) {
@@ -780,10 +898,15 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
                 int zn = 0;
                 xrow(P, i, zn);
                 const double inv_n = 1.0 / (double)zn;
-                for (int x = lane; x < D; x += 32) {
-                    double g = 0.0;
-                    for (int k = 0; k < S; ++k) g += __ldcg(pt + (size_t)k * D + x);
-                    sG[warp][x] = g * inv_n;
+                // entry x: lane q holds slices q and q + 32 (S <= 64), then a fixed
+                // xor-shuffle tree; the loads of several entries are in flight at once
+#pragma unroll 4
+                for (int x = 0; x < D; ++x) {
+                    double g = (lane < S) ? __ldcg(pt + (size_t)lane * D + x) : 0.0;
+                    if (lane + 32 < S) g += __ldcg(pt + (size_t)(lane + 32) * D + x);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+                    if (lane == 0) sG[warp][x] = g * inv_n;
                 }
             }
             __syncwarp();

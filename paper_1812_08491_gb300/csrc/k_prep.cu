@@ -83,6 +83,18 @@ __device__ __forceinline__ void pair_add(float& xh, float& xl, float yh, float y
     fast_two_sum(vh, vl, xh, xl);
 }
 
+// bf16 bit pattern of a finite float, rounded to nearest with ties to even,
+// by integer arithmetic on the IEEE encoding (add half an ulp of the target
+// minus one, plus the kept lowest bit, and truncate). Conversion instructions
+// share GB300's narrow FP64 pipe; this keeps the split on the integer ALUs.
+__device__ __forceinline__ unsigned short bf16_bits_rn(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    return (unsigned short)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+}
+
+__device__ __forceinline__ float bf16_bits_to_float(unsigned short h) { return __uint_as_float((unsigned)h << 16); }
+
 // Shifted moments S1 = sum (x - K), S2 = sum (x - K)^2 of a row, by one block
 // of NT threads, in a fixed order. FP64 data, or FP64 rows requested: FP64
 // sums per thread, a warp tree and the warp partials in order. FP32 data
@@ -90,15 +102,16 @@ __device__ __forceinline__ void pair_add(float& xh, float& xl, float yh, float y
 // (two_sum), its square exactly to 2^-48 (the product's error term by fma; the
 // lo^2 term, below 2^-48 of the square, is dropped), sums by pair_add per
 // thread and down the warp tree -- widened to FP64 only for the warp partials.
-// The totals are valid in thread 0.
+// The totals are valid in thread fin.
 template <typename T, int NT>
-__device__ __forceinline__ void shifted_moments(const T* __restrict__ row, int n, T K, bool pairs, double& S1,
-                                                double& S2)
+__device__ __forceinline__ void shifted_moments(const T* __restrict__ row, int n, T K, bool pairs, int fin,
+                                                double& S1, double& S2)
 {
     __shared__ double red[2][NT / 32];
+    __shared__ float redp[4][NT / 32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double s1 = 0.0, s2 = 0.0;
-    bool done = false;
+    S1 = 0.0;
+    S2 = 0.0;
     if constexpr (sizeof(T) == 4) {
         if (pairs) {
             float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
@@ -121,33 +134,44 @@ __device__ __forceinline__ void shifted_moments(const T* __restrict__ row, int n
                 pair_add(bh, bl, yh, yl);
             }
             if (lane == 0) {
-                s1 = (double)ah + (double)al;
-                s2 = (double)bh + (double)bl;
+                redp[0][w] = ah;
+                redp[1][w] = al;
+                redp[2][w] = bh;
+                redp[3][w] = bl;
             }
-            done = true;
+            __syncthreads();
+            // the warp partials in order, still in pairs; widened once (by the
+            // block's finishing thread fin, which rotates over the warps)
+            if (threadIdx.x == fin) {
+                float sh = redp[0][0], sl = redp[1][0], th = redp[2][0], tl = redp[3][0];
+                for (int k = 1; k < NT / 32; ++k) {
+                    pair_add(sh, sl, redp[0][k], redp[1][k]);
+                    pair_add(th, tl, redp[2][k], redp[3][k]);
+                }
+                S1 = (double)sh + (double)sl;
+                S2 = (double)th + (double)tl;
+            }
+            return;
         }
     }
-    if (!done) {
-        const double Kd = (double)K;
-        for (int k = threadIdx.x; k < n; k += NT) {
-            const double d = (double)row[k] - Kd;
-            s1 += d;
-            s2 = fma(d, d, s2);
-        }
+    const double Kd = (double)K;
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = threadIdx.x; k < n; k += NT) {
+        const double d = (double)row[k] - Kd;
+        s1 += d;
+        s2 = fma(d, d, s2);
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        }
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     }
     if (lane == 0) {
         red[0][w] = s1;
         red[1][w] = s2;
     }
     __syncthreads();
-    S1 = 0.0;
-    S2 = 0.0;
-    if (threadIdx.x == 0)
+    if (threadIdx.x == fin)
         for (int k = 0; k < NT / 32; ++k) {
             S1 += red[0][k];
             S2 += red[1][k];
@@ -165,7 +189,7 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
                                                     double* __restrict__ z64, long long ldz,
                                                     __nv_bfloat16* __restrict__ zhi, __nv_bfloat16* __restrict__ zlo,
                                                     long long ldb, Meta* meta, const int* __restrict__ vprob,
-                                                    const ProbDesc* __restrict__ probs)
+                                                    const ProbDesc* __restrict__ probs, double inv_n)
 {
     const int v = blockIdx.x;
     if (v >= p) return;
@@ -186,12 +210,13 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
             }
             if (zhi)
                 for (int k = threadIdx.x; k < kpad; k += NT) {
-                    zhi[(size_t)v * ldb + k] = __float2bfloat16(0.f);
-                    zlo[(size_t)v * ldb + k] = __float2bfloat16(0.f);
+                    ((unsigned short*)zhi)[(size_t)v * ldb + k] = 0;
+                    ((unsigned short*)zlo)[(size_t)v * ldb + k] = 0;
                 }
             return;
         }
         n = D.n;
+        inv_n = D.inv_n;
         row = (const T*)D.xv + (size_t)loc * n;
         if (z64) zrow = z64 + D.z_off + (long long)loc * n;
     }
@@ -201,14 +226,19 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
     __shared__ float fstat[3];
     {
         double S1, S2;
-        shifted_moments<T, NT>(row, n, row[0], fast, S1, S2);
-        // mean, 1/sd and their FP32 forms, once per variable
-        if (threadIdx.x == 0) {
+        // the thread finishing this block's FP64 work: a different warp per block,
+        // so the FP64 work of consecutive blocks lands on different schedulers
+        const int fin = (int)(blockIdx.x % (NT / 32)) * 32;
+        shifted_moments<T, NT>(row, n, row[0], fast, fin, S1, S2);
+        // mean, 1/sd and their FP32 forms, once per variable (1/n from the host:
+        // a multiply instead of a divide on the FP64 pipe)
+        if (threadIdx.x == fin) {
             const double K = (double)row[0];
-            const double mean = K + S1 / (double)n;
-            const double var = (S2 - S1 * S1 / (double)n) / (double)n;
+            const double a = S1 * inv_n;
+            const double mean = K + a;
+            const double var = fma(-S1, a, S2) * inv_n;
             const bool ok = (var > 0.0) && isfinite(var) && isfinite(mean);
-            const double inv = ok ? 1.0 / sqrt(var) : 0.0;
+            const double inv = ok ? rsqrt(var) : 0.0;
             mu[v] = mean;
             isd[v] = inv;
             if (!ok) atomicOr(&meta->error, 1);
@@ -239,16 +269,16 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
             z = (float)d * fi;
         }
         if (zhi) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(z);
-            zhi[(size_t)v * ldb + k] = h;
-            zlo[(size_t)v * ldb + k] = __float2bfloat16_rn(z - __bfloat162float(h));
+            const unsigned short h = bf16_bits_rn(z);
+            ((unsigned short*)zhi)[(size_t)v * ldb + k] = h;
+            ((unsigned short*)zlo)[(size_t)v * ldb + k] = bf16_bits_rn(z - bf16_bits_to_float(h));
         }
     }
     // zero the K padding so the tensor-core product can read whole 64-wide slabs
     if (zhi)
         for (int k = n + threadIdx.x; k < kpad; k += NT) {
-            zhi[(size_t)v * ldb + k] = __float2bfloat16(0.f);
-            zlo[(size_t)v * ldb + k] = __float2bfloat16(0.f);
+            ((unsigned short*)zhi)[(size_t)v * ldb + k] = 0;
+            ((unsigned short*)zlo)[(size_t)v * ldb + k] = 0;
         }
 }
 
@@ -344,11 +374,11 @@ cudaError_t launch_standardize(int dtype, const void* Xv, long long ld, int n, i
     if (dtype == CUPC_F64)
         k_standardize<double, NT><<<p, NT, 0, st>>>((const double*)Xv, ld, n, p, mu, isd, z64, ldz,
                                                     (__nv_bfloat16*)zhi, (__nv_bfloat16*)zlo, ldb, meta, vprob,
-                                                    probs);
+                                                    probs, 1.0 / (double)(n > 0 ? n : 1));
     else
         k_standardize<float, NT><<<p, NT, 0, st>>>((const float*)Xv, ld, n, p, mu, isd, z64, ldz,
                                                    (__nv_bfloat16*)zhi, (__nv_bfloat16*)zlo, ldb, meta, vprob,
-                                                   probs);
+                                                   probs, 1.0 / (double)(n > 0 ? n : 1));
     return cudaGetLastError();
 }
 

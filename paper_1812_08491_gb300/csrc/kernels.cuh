@@ -9,6 +9,10 @@ namespace cupc {
 
 // Per-level counters of the fused level kernels (zeroed once per call).
 constexpr int LV = CUPC_MAX_LEVEL + 2;
+// Work items are dispatched in rounds: round c holds the c-th item (subset
+// ranks [c chunk, (c + 1) chunk)) of every row that has one, for c < RND - 1;
+// the last round holds every later item.
+constexpr int RND = 64;
 struct LevelMeta {
     unsigned long long tests[LV];          // CI tests executed
     unsigned long long rechecks[LV];       // FP64 rechecks performed
@@ -29,6 +33,8 @@ struct LevelMeta {
     int error;                             // 8: a grid barrier wait expired
     int range_error;                       // a subset count saturated 64 bits
     unsigned bar_count, bar_gen;           // grid barrier state
+    unsigned long long round_off[LV][RND]; // first dispatch slot of each round
+    unsigned long long round_cur[LV][RND]; // slots of each round handed to CTAs so far
 };
 
 // One problem of a batch. The batch runs as one graph whose connected
@@ -40,6 +46,7 @@ struct LevelMeta {
 // global column c is rowbase(v) + (c >> 5), c >> 5 in [wlo, whi).
 struct ProbDesc {
     int off, p, n;
+    double inv_n;                  // 1 / n
     int wlo, whi;                  // off / 32, (off + P32) / 32
     int lmax;                      // last level its threshold allows (n - 4, max_level)
     long long bw;                  // first word of its bitset block
@@ -71,8 +78,9 @@ struct LevelParams {
     unsigned* backup;              // FP32 mode: A_G at level start (for a rerun after queue overflow)
     int* deg;
     long long* row_off;            // p + 1 CSR offsets of A'_G
-    long long* item_off;           // p + 1: first CI work item of each row
-    int* item_row;                 // row of each work item
+    long long* item_off;           // p + 1: items of the rows before each row (row-major count)
+    int* item_row;                 // work items in dispatch order: the row of each
+    int* item_c;                   // and the item's index within its row
     unsigned long long item_cap;
     int* cols;                     // neighbour indices (increasing per row)
     int* srow;                     // row of each slot

@@ -127,6 +127,13 @@ typedef struct {
     int32_t cuda_graph;                          /* batch: 1 if the device work ran as a
                                                     replayed CUDA graph, 0 if launched
                                                     directly; single calls: 0 */
+    float recheck_ms[CUPC_STATS_LEVELS][3];      /* per level >= 1, the FP64 recheck phase
+                                                    split into partial sums and combine,
+                                                    and the first CTA's own partial sums
+                                                    (device clock) */
+    int64_t rechecks_queued[CUPC_STATS_LEVELS];  /* tests queued for the FP64 recheck (those
+                                                    whose outcome could no longer matter are
+                                                    skipped; rechecks counts the rest) */
 } cupc_stats;
 
 typedef struct cupc_ctx cupc_ctx;

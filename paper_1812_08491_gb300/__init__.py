@@ -86,7 +86,8 @@ class Stats(ctypes.Structure):
                 ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
                 ("kernel_ms", ctypes.c_float * 8), ("kernel_count", ctypes.c_int32 * 8),
                 ("ci_block_entries", ctypes.c_int64 * L), ("phase_ms", (ctypes.c_float * 4) * L),
-                ("cuda_graph", ctypes.c_int32)]
+                ("cuda_graph", ctypes.c_int32), ("recheck_ms", (ctypes.c_float * 3) * L),
+                ("rechecks_queued", ctypes.c_int64 * L)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -188,7 +189,9 @@ def _stats_dict(s: Stats) -> dict:
             "kernel_ms": dict(zip(KERNEL_CLASSES, list(s.kernel_ms))),
             "kernel_count": dict(zip(KERNEL_CLASSES, list(s.kernel_count))),
             "ci_block_entries": list(s.ci_block_entries[:L]),
-            "phase_ms": [list(s.phase_ms[q]) for q in range(L)], "cuda_graph": s.cuda_graph}
+            "phase_ms": [list(s.phase_ms[q]) for q in range(L)], "cuda_graph": s.cuda_graph,
+            "recheck_ms": [list(s.recheck_ms[q]) for q in range(L)],
+            "rechecks_queued": list(s.rechecks_queued[:L])}
 
 
 class Result:

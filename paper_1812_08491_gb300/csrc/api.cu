@@ -558,6 +558,11 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         // last level and they return at once.
         auto launch_levels = [&](int from) -> cupc_status {
             LP.queue = (QEntry*)ctx->queue.p;
+            if (fp32) {
+                cupc_status sl = ensure(ctx, *ctx_buf(ctx, "live"), qcap * sizeof(int));
+                if (sl != CUPC_OK) return sl;
+                LP.live = (int*)ctx_buf(ctx, "live")->p;
+            }
             LP.qcap = qcap;
             LP.host_flags = ctx->dflags;
             for (int q = 0; q < LV; ++q) ((volatile int*)ctx->hflags)[q] = 0;
@@ -610,12 +615,15 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
                 H.next_item[q] = H.queue_len[q] = H.block_entries[q] = 0;
                 for (int c = 0; c < 4; ++c) H.phase_ns[q][c] = 0;
                 for (int c = 0; c < RND; ++c) H.round_off[q][c] = H.round_cur[q][c] = 0;
+                H.recheck_ns[q][0] = H.recheck_ns[q][1] = H.recheck_ns[q][2] = 0;
+                H.live[q] = 0;
                 H.maxdeg[q] = 0;
                 H.chunk[q] = 0;
             }
             H.rec_ints = keep;
             H.overflow_level = 0;
             H.done_level = 0;
+            H.csr_level = 0;
             H.bar_count = 0;
             CU(cudaMemcpyAsync(lm, ctx->hlmeta, sizeof(LevelMeta), cudaMemcpyHostToDevice, ctx->stream));
             if ((s = launch_levels(ol)) != CUPC_OK) return s;
@@ -634,6 +642,8 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             R->stats.max_degree[l] = H.maxdeg[l];
             R->stats.ci_block_entries[l] = (int64_t)H.block_entries[l];
             for (int c = 0; c < 4; ++c) R->stats.phase_ms[l][c] = 1e-6f * (float)H.phase_ns[l][c];
+            for (int c = 0; c < 3; ++c) R->stats.recheck_ms[l][c] = 1e-6f * (float)H.recheck_ns[l][c];
+            R->stats.rechecks_queued[l] = (int64_t)H.queue_len[l];
         }
         for (int l = 1; l < LV; ++l) {
             R->stats.kernel_ms[CUPC_K_COMPACT] += 1e-6f * (float)H.phase_ns[l][0];

@@ -56,7 +56,7 @@ struct BatchPlan {
     size_t ws_bytes = 0;
     unsigned long long nnz_cap = 0, item_cap = 0, qcap = 0, rec_cap = 0;
     Buf d_probs, d_vprob, d_vlmax, d_units, d_tiles, x_in, xt, mu, isd, zhi, zlo, ws, c32, bits, bits0, backup;
-    Buf deg, row_off, item_off, item_row, item_c, cols, srow, partner, wpre, best, queue, part, rec, meta, lmeta, pserial;
+    Buf deg, row_off, item_off, item_row, item_c, live, cols, srow, partner, wpre, best, queue, part, rec, meta, lmeta, pserial;
     Binom binom{};
     // pinned host copies written at the end of each run
     unsigned* h_bits = nullptr;
@@ -82,7 +82,7 @@ void plan_destroy(cupc_ctx* ctx, BatchPlan* B)
     if (B->exec) cudaGraphExecDestroy(B->exec);
     Buf* all[] = {&B->d_probs, &B->d_vprob, &B->d_vlmax, &B->d_units, &B->d_tiles, &B->x_in, &B->xt,      &B->mu,
                   &B->isd,     &B->zhi,     &B->zlo,     &B->ws,   &B->c32,     &B->bits,
-                  &B->bits0,   &B->backup,  &B->deg,     &B->row_off, &B->item_off, &B->item_row, &B->item_c, &B->cols,
+                  &B->bits0,   &B->backup,  &B->deg,     &B->row_off, &B->item_off, &B->item_row, &B->item_c, &B->live, &B->cols,
                   &B->srow,    &B->partner, &B->wpre,    &B->best,    &B->queue, &B->part,   &B->rec,
                   &B->meta,    &B->lmeta,   &B->pserial};
     for (Buf* b : all) ctx_free(ctx, b);
@@ -212,6 +212,7 @@ cupc_status allocate(cupc_ctx* ctx, BatchPlan& B)
         {&B.partner, (size_t)B.nnz_cap * 4},
         {&B.best, (size_t)B.nnz_cap * 8},
         {&B.queue, (size_t)B.qcap * sizeof(QEntry)},
+        {&B.live, (size_t)B.qcap * sizeof(int)},
         {&B.part, kPartBytes},
         {&B.rec, (size_t)B.rec_cap * 4},
         {&B.meta, sizeof(Meta)},
@@ -329,6 +330,7 @@ cupc_status issue(cupc_ctx* ctx, BatchPlan& B, cudaStream_t st, bool capturing)
     LP.rank_tol = kRankTol32;
     LP.piv_floor = kPivFloor;
     LP.queue = (QEntry*)B.queue.p;
+    LP.live = (int*)B.live.p;
     LP.qcap = B.qcap;
     LP.xf64 = K.dtype == CUPC_F64 ? 1 : 0;
     LP.mu = (const double*)B.mu.p;
@@ -425,6 +427,7 @@ cupc_status grow(cupc_ctx* ctx, BatchPlan& B, unsigned long long qneed, unsigned
     if (qneed > B.qcap) {
         B.qcap = qneed + qneed / 2;
         ctx_free(ctx, &B.queue);
+        ctx_free(ctx, &B.live);
     }
     if (rneed > B.rec_cap) {
         B.rec_cap = rneed + rneed / 2;
@@ -650,6 +653,8 @@ cupc_status make_results(cupc_ctx* ctx, BatchPlan& B, float ms, cupc_result** ou
         S.max_degree[l] = H.maxdeg[l];
         S.ci_block_entries[l] = (int64_t)H.block_entries[l];
         for (int c = 0; c < 4; ++c) S.phase_ms[l][c] = 1e-6f * (float)H.phase_ns[l][c];
+        for (int c = 0; c < 3; ++c) S.recheck_ms[l][c] = 1e-6f * (float)H.recheck_ns[l][c];
+        S.rechecks_queued[l] = (int64_t)H.queue_len[l];
     }
     for (int l = 1; l < LV; ++l) {
         S.kernel_ms[CUPC_K_COMPACT] += 1e-6f * (float)H.phase_ns[l][0];

@@ -219,39 +219,54 @@ __device__ __forceinline__ bool bitset_test(const unsigned* bits, int W, int i, 
 // in FP64 from its variable-major data row (FP32 or FP64) and the moments of
 // the standardisation: the centring rounds once, the scaling once.
 // ---------------------------------------------------------------------------
-// FP32 -> FP64 widening (exact) by integer operations on the IEEE encodings
-// for normal numbers (exponent rebiased from 127 to 1023, mantissa shifted
-// left by 29); zeros, subnormals and non-finite values take the conversion
-// instruction, which on GB300 shares the narrow FP64 pipe.
+// FP32 -> FP64 widening (exact) by integer operations on the IEEE encodings:
+// normal numbers get the exponent rebiased from 127 to 1023 and the mantissa
+// shifted left by 29; zeros keep the sign; subnormals (m 2^-149) are
+// normalised at their leading one; infinities and NaNs keep the all-ones
+// exponent. GB300 issues the conversion instruction on its narrow FP64 pipe.
 __device__ __forceinline__ double widen_f32(float x)
 {
     const unsigned u = __float_as_uint(x);
     const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)x;
-    const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
-                                    ((unsigned long long)(e + 896u) << 52) |
-                                    ((unsigned long long)(u & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)bits);
+    const unsigned m = u & 0x7fffffu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    unsigned long long ex, man;
+    if (e != 0u) {
+        ex = (e == 0xffu) ? 2047ull : (unsigned long long)(e + 896u);
+        man = (unsigned long long)m << 29;
+    } else if (m != 0u) {
+        const int lead = 31 - __clz((int)m);                 // bit of the leading one, 0..22
+        ex = (unsigned long long)(lead + 874);               // 2^(lead - 149)
+        man = ((unsigned long long)m << (52 - lead)) & ((1ull << 52) - 1ull);
+    } else {
+        ex = 0ull;
+        man = 0ull;
+    }
+    return __longlong_as_double((long long)(sign | (ex << 52) | man));
 }
 
+// One variable's row for the rechecks: its variable-major data (FP32 or FP64)
+// and the moments of the standardisation, z = (x - mu) * isd. The Gram sums
+// below accumulate the centred values x - mu and apply isd_a isd_b once.
 struct XRow {
     const void* p;
     int f64;
     double mu, isd;
-    __device__ __forceinline__ double z(int k) const
+    __device__ __forceinline__ double centred(int k) const
     {
         const double x = f64 ? __ldg((const double*)p + k) : widen_f32(__ldg((const float*)p + k));
-        return (x - mu) * isd;
+        return x - mu;
     }
 };
 
 // ---------------------------------------------------------------------------
 // FP64 block of C for the rechecks: for the m variables with rows R, the
 // strictly lower packed entries G[b(b-1)/2 + a] = C[V_a, V_b] (a < b) by the
-// definition C_ab = sum_s z_as z_bs / n, every pair in one pass (threads of
-// the block stride the samples), then a fixed-order block reduction -- an
-// entry's value does not depend on the test it serves. Must be called by all
-// NT threads of the block; red holds (NT/32) * M(M-1)/2 doubles.
+// definition C_ab = sum_s z_as z_bs / n = isd_a isd_b sum_s (x_as - mu_a)
+// (x_bs - mu_b) / n, every pair in one pass (threads of the block stride the
+// samples), then a fixed-order block reduction -- an entry's value does not
+// depend on the test it serves. Must be called by all NT threads of the
+// block; red holds (NT/32) * M(M-1)/2 doubles.
 // ---------------------------------------------------------------------------
 template <int M, int NT>
 __device__ __forceinline__ void c_block(const XRow (&R)[M], int n, int m, double (&G)[M * (M - 1) / 2], double* red)
@@ -263,7 +278,7 @@ __device__ __forceinline__ void c_block(const XRow (&R)[M], int n, int m, double
     for (int k = threadIdx.x; k < n; k += NT) {
         double x[M];
 #pragma unroll
-        for (int a = 0; a < M; ++a) x[a] = (a < m) ? R[a].z(k) : 0.0;
+        for (int a = 0; a < M; ++a) x[a] = (a < m) ? R[a].centred(k) : 0.0;
 #pragma unroll
         for (int b = 1; b < M; ++b)
 #pragma unroll
@@ -280,12 +295,15 @@ __device__ __forceinline__ void c_block(const XRow (&R)[M], int n, int m, double
     __syncthreads();
     const double inv_n = 1.0 / (double)n;
 #pragma unroll
-    for (int q = 0; q < D; ++q) {
-        double g = 0.0;
+    for (int b = 1; b < M; ++b)
 #pragma unroll
-        for (int k = 0; k < NT / 32; ++k) g += red[k * D + q];
-        G[q] = g * inv_n;
-    }
+        for (int a = 0; a < b; ++a) {
+            const int q = b * (b - 1) / 2 + a;
+            double g = 0.0;
+#pragma unroll
+            for (int k = 0; k < NT / 32; ++k) g += red[k * D + q];
+            G[q] = g * (R[a].isd * R[b].isd) * inv_n;
+        }
     __syncthreads();
 }
 

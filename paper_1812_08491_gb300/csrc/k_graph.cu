@@ -29,11 +29,23 @@ __global__ void k_level0(const T* __restrict__ C, int p, int W, double r0, doubl
     const T* row = C + (D ? D->c_off : 0) + (long long)(i - off) * pp - off;
     if (D) r0 = D->r[0];
     const T hi = (T)(r0 + band0), lo = (T)(r0 - band0);  // FP32 band edges
-    for (int w = wlo; w < whi; ++w) {
+    // eight words at a time: their loads are issued before any is used
+    constexpr int U = 8;
+    for (int w0 = wlo; w0 < whi; w0 += U) {
+        T cv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = ((w0 + u) << 5) + lane;
+            cv[u] = (w0 + u < whi && live && j - off < pp && j != i) ? row[j] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+        const int w = w0 + u;
+        if (w >= whi) break;
         const int j = (w << 5) + lane;
         bool keep = false;
         if (live && j - off < pp && j != i) {
-            const T c = row[j] < T(0) ? -row[j] : row[j];
+            const T c = cv[u] < T(0) ? -cv[u] : cv[u];
             if (!FP32) {
                 keep = !(c <= (T)r0);
             } else {
@@ -54,6 +66,7 @@ __global__ void k_level0(const T* __restrict__ C, int p, int W, double r0, doubl
         }
         const unsigned word = __ballot_sync(0xffffffffu, keep);
         if (lane == 0) bits[rb + w] = word;
+        }
     }
 }
 

@@ -431,12 +431,12 @@ __device__ void phase_items(const LevelParams& P)
     }
 }
 
-__device__ void phase_fill(const LevelParams& P)
+__device__ void phase_fill(const LevelParams& P, bool reuse)
 {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * NT + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * NT) >> 5;
-    for (int i = gw; i < P.p; i += nwarps) {
+    for (int i = reuse ? P.p : gw; i < P.p; i += nwarps) {
         long long base = P.row_off[i];
         int wlo, whi;
         long long rb;
@@ -812,34 +812,45 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
 {
     constexpr int M = LB + 2;
     constexpr int D = M * (M - 1) / 2;
-    __shared__ double sG[NW][D];
+    __shared__ double sA[NW][M][M];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // consecutive units go to consecutive CTAs, so a short queue spreads over SMs
+    const bool timer = (blockIdx.x == 0 && threadIdx.x == 0);
+    unsigned long long tp = timer ? gtimer() : 0;
+    // the queued tests whose outcome can still matter, in queue order
+    for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < (long long)nq;
+         t += (long long)gridDim.x * NT) {
+        const QEntry* E = P.queue + t;
+        const long long e = E->a;
+        if (!recheck_moot(P, e, P.srow[e], P.cols[e], E->s)) {
+            const unsigned long long w = atomicAdd(&P.lm->live[P.l], 1ull);
+            P.live[w] = (int)t;
+        }
+    }
+    if (!grid_sync(P.lm)) return false;
+    const unsigned long long nl = ld_cg(&P.lm->live[P.l]);
+    if (nl == 0) return true;
+    // consecutive units go to consecutive CTAs, so a short list spreads over SMs
     const long long gw = (long long)warp * gridDim.x + blockIdx.x;
     const long long nwarps = (long long)gridDim.x * NW;
     // slices per test, the same for every test of the level: enough for the
     // sample count (a batch takes its largest n), and enough units to occupy
-    // every warp when the queue is short
-    const int sp = (int)min(64ll, (nwarps + (long long)nq - 1) / (long long)nq);
-    const int S = max(recheck_slices(P.vprob ? P.nmax : P.n), sp);
+    // every warp when the list is short
+    // (the combine sums S x D partials per test: a large Gram block takes fewer)
+    const int sp = (int)min((long long)max(1, 256 / D), (nwarps + (long long)nl - 1) / (long long)nl);
+    const int S = min(64, max(recheck_slices(P.vprob ? P.nmax : P.n), sp));
     const long long batch = max(1ll, (long long)(P.part_cap / ((unsigned long long)S * D)));
     unsigned long long done = 0;
-    for (long long q0 = 0; q0 < (long long)nq; q0 += batch) {
-        const long long nb = min(batch, (long long)nq - q0);
+    for (long long q0 = 0; q0 < (long long)nl; q0 += batch) {
+        const long long nb = min(batch, (long long)nl - q0);
         // partial sums
         for (long long u = gw; u < nb * S; u += nwarps) {
-            const long long qi = q0 + u / S;
+            const long long qi = P.live[q0 + u / S];
             const int k = (int)(u % S);
             const QEntry* E = P.queue + qi;
             const long long e = E->a;
             const int i = P.srow[e], j = P.cols[e];
             double* out = P.part + (size_t)u * D;
-            const bool moot = recheck_moot(P, e, i, j, E->s);
-            if (moot || P.c64) {
-                // slice 0 carries the test's mark: NaN = skipped
-                if (k == 0 && lane == 0) out[0] = moot ? __longlong_as_double(0x7ff8000000000001ll) : 0.0;
-                continue;
-            }
+            if (P.c64) continue;
             int V[M];
             V[0] = i;
             V[1] = j;
@@ -858,7 +869,7 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
             for (int kk = k0 + lane; kk < k1; kk += 32) {
                 double x[M];
 #pragma unroll
-                for (int a = 0; a < M; ++a) x[a] = (a < m) ? R[a].z(kk) : 0.0;
+                for (int a = 0; a < M; ++a) x[a] = (a < m) ? R[a].centred(kk) : 0.0;
 #pragma unroll
                 for (int b2 = 1; b2 < M; ++b2)
 #pragma unroll
@@ -872,56 +883,98 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
                 if (lane == 0) out[t] = g;
             }
         }
+        if (blockIdx.x == 0) {
+            __syncthreads();
+            if (timer) P.lm->recheck_ns[P.l][2] += gtimer() - tp;
+        }
         if (!grid_sync(P.lm)) return false;
+        if (timer) {
+            const unsigned long long t2 = gtimer();
+            P.lm->recheck_ns[P.l][0] += t2 - tp;
+            tp = t2;
+        }
         // combine the slices of each test in order (a warp per test, lanes over
-        // the Gram entries) and decide (its first lane)
+        // the Gram entries), then eliminate the members of S from the
+        // (l + 2) x (l + 2) correlation block of (S, i, j) with the warp: the
+        // trailing 2 x 2 Schur complement is the conditional covariance of
+        // (V_i, V_j) given S (Eq. PartialCorMat); a member whose remaining
+        // pivot is at or below the rank tolerance is linearly dependent on the
+        // members before it and is dropped (the pseudo-inverse's treatment)
         for (long long t = gw; t < nb; t += nwarps) {
             const double* pt = P.part + (size_t)t * S * D;
-            if (isnan(__ldcg(pt))) continue;       // moot (warp-uniform)
-            const long long qi = q0 + t;
+            const long long qi = P.live[q0 + t];
             const QEntry* E = P.queue + qi;
             const long long e = E->a;
             const int i = P.srow[e], j = P.cols[e];
+            const int l = P.l, m = l + 2;
             int V[M];
             V[0] = i;
             V[1] = j;
 #pragma unroll
-            for (int c = 0; c < LB; ++c) V[2 + c] = (c < P.l) ? E->S[c] : i;
+            for (int c = 0; c < LB; ++c) V[2 + c] = (c < l) ? E->S[c] : i;
+            double (*A)[M] = sA[warp];
+            // elimination position of Gram index g (0 = i, 1 = j, 2 + a = S_a)
+            auto pos = [&](int g) { return g >= 2 ? g - 2 : l + g; };
             if (P.c64) {
                 for (int x = lane; x < D; x += 32) {
                     int b2 = 1;
                     while ((b2 + 1) * b2 / 2 <= x) ++b2;
                     const int a = x - b2 * (b2 - 1) / 2;
-                    sG[warp][x] = (b2 < P.l + 2) ? P.c64[(size_t)V[a] * P.p + V[b2]] : 0.0;
+                    if (b2 < m) {
+                        const int pa = pos(a), pb = pos(b2);
+                        A[max(pa, pb)][min(pa, pb)] = P.c64[(size_t)V[a] * P.p + V[b2]];
+                    }
                 }
             } else {
+                // centred sums times isd_a isd_b / n; lane a holds isd of V_a
                 int zn = 0;
                 xrow(P, i, zn);
                 const double inv_n = 1.0 / (double)zn;
+                int vl = i;
+#pragma unroll
+                for (int a = 0; a < M; ++a)
+                    if (lane == a) vl = V[a];
+                const double isd_l = (lane < m) ? P.isd[vl] : 0.0;
                 // entry x: lane q holds slices q and q + 32 (S <= 64), then a fixed
                 // xor-shuffle tree; the loads of several entries are in flight at once
 #pragma unroll 4
                 for (int x = 0; x < D; ++x) {
+                    int b2 = 1;
+                    while ((b2 + 1) * b2 / 2 <= x) ++b2;
+                    const int a = x - b2 * (b2 - 1) / 2;
+                    const double sa = __shfl_sync(0xffffffffu, isd_l, a);
+                    const double sb = __shfl_sync(0xffffffffu, isd_l, b2);
                     double g = (lane < S) ? __ldcg(pt + (size_t)lane * D + x) : 0.0;
                     if (lane + 32 < S) g += __ldcg(pt + (size_t)(lane + 32) * D + x);
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-                    if (lane == 0) sG[warp][x] = g * inv_n;
+                    if (lane == 0 && b2 < m) {
+                        const int pa = pos(a), pb = pos(b2);
+                        A[max(pa, pb)][min(pa, pb)] = g * (sa * sb) * inv_n;
+                    }
                 }
             }
+            if (lane < m) A[lane][lane] = 1.0;
             __syncwarp();
+            // lower triangle only: step k updates A[a][b], k < b <= a < m
+            for (int k = 0; k < l; ++k) {
+                const double piv = A[k][k];
+                if (piv > P.rank_tol) {
+                    const double rp = 1.0 / piv;
+                    const int r = m - k - 1;
+                    for (int q = lane; q < r * (r + 1) / 2; q += 32) {
+                        int aa = 0;
+                        while ((aa + 1) * (aa + 2) / 2 <= q) ++aa;
+                        const int bb = q - aa * (aa + 1) / 2;
+                        const int a = k + 1 + aa, b = k + 1 + bb;
+                        A[a][b] = fma(-A[a][k] * rp, A[b][k], A[a][b]);
+                    }
+                }
+                __syncwarp();
+            }
             if (lane == 0) {
                 ++done;
-                const double* G = sG[warp];
-                // V index 0 = i, 1 = j, 2 + a = S_a; G[b(b-1)/2 + a] holds C[V_a, V_b], a < b
-                Factor<double, LB> F;
-                factor_build<double, LB>(
-                    F, P.l, P.rank_tol, [&](int a, int b2) { return G[(a + 2) * (a + 1) / 2 + (b2 + 2)]; },
-                    [&](int a) { return G[(a + 2) * (a + 1) / 2 + 0]; });
-                double H12, H22;
-                factor_apply<double, LB>(F, P.l, G[0], [&](int a) { return G[(a + 2) * (a + 1) / 2 + 1]; }, H12,
-                                         H22);
-                const double H11 = 1.0 - F.uu;
+                const double H11 = A[l][l], H12 = A[l + 1][l], H22 = A[l + 1][l + 1];
                 double thr, thr2;
                 thresholds(P, i, thr, thr2);
                 const bool indep =
@@ -931,6 +984,11 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
             __syncwarp();
         }
         if (!grid_sync(P.lm)) return false;
+        if (timer) {
+            const unsigned long long t2 = gtimer();
+            P.lm->recheck_ns[P.l][1] += t2 - tp;
+            tp = t2;
+        }
     }
     done = warp_sum_u64(done);
     if (lane == 0 && done) atomicAdd(&P.lm->rechecks[P.l], done);
@@ -1057,7 +1115,7 @@ __device__ __forceinline__ void signal_host(const LevelParams& P, int v)
 }
 
 template <typename T, int LB, bool FP32, bool LEARNED>
-__global__ void __launch_bounds__(NT) k_level(LevelParams P)
+__global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
 {
     LevelMeta* lm = P.lm;
     const int l = P.l;
@@ -1070,8 +1128,12 @@ __global__ void __launch_bounds__(NT) k_level(LevelParams P)
     const bool timer = (blockIdx.x == 0 && threadIdx.x == 0);
     if (timer) t0 = gtimer();
 
+    // A'_G of the previous level is still valid when that level removed no edge:
+    // the neighbour lists, partner slots and word prefixes are reused (the work
+    // items, which depend on l, are rebuilt)
+    const bool reuse = l >= 2 && ld_cg(&lm->removed[l - 1]) == 0ull && *(volatile int*)&lm->csr_level == l - 1;
     if (blockIdx.x == 0) phase_scan(P, LEARNED && P.learned && l >= 2);
-    if (blockIdx.x != 0 || gridDim.x == 1) phase_prefix(P, FP32);
+    if (!reuse && (blockIdx.x != 0 || gridDim.x == 1)) phase_prefix(P, FP32);
     if (!grid_sync(lm)) {
         if (timer) signal_host(P, 2);
         return;
@@ -1084,8 +1146,9 @@ __global__ void __launch_bounds__(NT) k_level(LevelParams P)
         return;
     }
     if (timer) signal_host(P, 1);
-    phase_fill(P);
+    phase_fill(P, reuse);
     if (!grid_sync(lm)) return;
+    if (timer) lm->csr_level = l;
     if (timer) { t1 = gtimer(); lm->phase_ns[l][0] += t1 - t0; t0 = t1; }
 
     const bool lrn = LEARNED && *(volatile int*)&lm->learned_on[l];

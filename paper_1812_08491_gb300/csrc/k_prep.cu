@@ -259,19 +259,27 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
     // relative to a result of the size of x), about 3 * 2^-24 in all; for FP64
     // data the centring is FP64.
     const float mh = fstat[0], ml = fstat[1], fi = fstat[2];
-    for (int k = threadIdx.x; k < n; k += NT) {
-        float z;
-        if (sizeof(T) == 4 && fast) {
-            z = (((float)row[k] - mh) - ml) * fi;
-        } else {
+    unsigned short* hrow = zhi ? (unsigned short*)zhi + (size_t)v * ldb : nullptr;
+    unsigned short* lrow = zlo ? (unsigned short*)zlo + (size_t)v * ldb : nullptr;
+    // two loops, not one with a branch inside: the compiler would evaluate both
+    // sides of a short branch, putting the FP64 side on every element
+    if (sizeof(T) == 4 && fast) {
+        for (int k = threadIdx.x; k < n; k += NT) {
+            const float z = (((float)row[k] - mh) - ml) * fi;
+            const unsigned short h = bf16_bits_rn(z);
+            hrow[k] = h;
+            lrow[k] = bf16_bits_rn(z - bf16_bits_to_float(h));
+        }
+    } else {
+        for (int k = threadIdx.x; k < n; k += NT) {
             const double d = (double)row[k] - mean;
             if (zrow) zrow[k] = d * inv;
-            z = (float)d * fi;
-        }
-        if (zhi) {
-            const unsigned short h = bf16_bits_rn(z);
-            ((unsigned short*)zhi)[(size_t)v * ldb + k] = h;
-            ((unsigned short*)zlo)[(size_t)v * ldb + k] = bf16_bits_rn(z - bf16_bits_to_float(h));
+            if (hrow) {
+                const float z = (float)d * fi;
+                const unsigned short h = bf16_bits_rn(z);
+                hrow[k] = h;
+                lrow[k] = bf16_bits_rn(z - bf16_bits_to_float(h));
+            }
         }
     }
     // zero the K padding so the tensor-core product can read whole 64-wide slabs

@@ -24,15 +24,19 @@ struct LevelMeta {
     unsigned long long queue_len[LV];      // recheck entries pushed (may exceed capacity)
     unsigned long long block_entries[LV];  // sum over rows with work of (n'_i + 1)^2
     unsigned long long phase_ns[LV][4];    // compaction, CI, recheck, finalisation (wall ns)
+    unsigned long long recheck_ns[LV][3];  // recheck partial sums, combine (wall ns, all batches),
+                                           // and block 0's own partial-sum work
     int maxdeg[LV];
     int chunk[LV];
     int learned_on[LV];                    // the level enumerated in the network's order
     unsigned long long rec_ints;           // SepSet record ints appended
     int done_level;                        // level whose termination test stopped the loop
+    int csr_level;                         // level whose A'_G arrays (cols, srow, partner, wpre) are current
     int overflow_level;                    // level whose recheck queue overflowed
     int error;                             // 8: a grid barrier wait expired
     int range_error;                       // a subset count saturated 64 bits
     unsigned bar_count, bar_gen;           // grid barrier state
+    unsigned long long live[LV];           // queued tests rechecked (not decided already)
     unsigned long long round_off[LV][RND]; // first dispatch slot of each round
     unsigned long long round_cur[LV][RND]; // slots of each round handed to CTAs so far
 };
@@ -108,6 +112,7 @@ struct LevelParams {
     int nmax;                      // batch: largest sample count
     const double* c64;
     double* part;                  // recheck partial Gram sums (tests x slices x D doubles)
+    int* live;                     // qcap: queue positions of the tests rechecked
     unsigned long long part_cap;   // doubles in part
     int* rec;                      // SepSet record pool (int32 groups i, j, l, S...)
     unsigned long long rec_cap;

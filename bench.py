@@ -51,6 +51,37 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_TFLOPS = 1.25
 
 
+LEVEL_SOURCES = ("paper_1812_08491_gb300/csrc/k_level.cu", "paper_1812_08491_gb300/csrc/kernels.cuh",
+                 "paper_1812_08491_gb300/csrc/cupc_internal.cuh")
+
+
+def level_source_hash():
+    """sha256 of the level kernel's sources (the ncu traffic figures are tied to it)."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in LEVEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(workload):
+    """DRAM bytes per level-kernel launch from the committed ncu summary of this
+    workload, or None when there is none or the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", f"k_level_{workload}.md")
+    try:
+        fields = {}
+        for line in open(path):
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+        if fields.get("source_hash") != level_source_hash():
+            return None
+        return float(fields["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clocks/throttle reasons sampled during the timed region."""
 
@@ -177,7 +208,7 @@ def _config(name, s, form):
             "form": form, "l2": "flushed between steps (256 MiB write)"}
 
 
-def kernel_rooflines(st, s, mode, peaks):
+def kernel_rooflines(st, s, mode, peaks, alu=None):
     """Roofline of each kernel of one skeleton call (stats of that call).
 
     Durations are CUDA-event times on the library's stream; algorithmic work:
@@ -213,6 +244,14 @@ def kernel_rooflines(st, s, mode, peaks):
         nnz = 2 * st["edges_start"][l]
         byts += st["ci_block_entries"][l] * cb + 3 * p * W * 4 + nnz * 40
     mem("level", lev_ms, max(1, lv - 1), byts)
+    # FP64 rechecks: per performed test the Gram block of its l + 2 variables over
+    # n samples (one FMA per pair, one centring subtraction per variable, per sample)
+    if alu and km.get("recheck", 0) > 0:
+        flops = sum(st["rechecks"][l] * n * (2.0 * (l + 2) * (l + 1) / 2 + (l + 2)) for l in range(1, lv))
+        ach = flops / (km["recheck"] * 1e-3) / 1e12
+        out["recheck"] = {"bound": "alu", "achieved": ach, "peak": alu["fp64_tflops"], "unit": "TFLOP/s",
+                          "frac": ach / alu["fp64_tflops"], "ms": km["recheck"], "launches": max(1, lv - 1),
+                          "peak_src": "FP64 FMA, measured by cupc_device_peaks", "traffic": None}
     ms = km["correlation"]
     if ms > 0:
         if mode == "fp32":
@@ -412,6 +451,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP64 form")
     ap.add_argument("--tune", action="store_true", help="batch workloads: autotune the launch configuration")
+    ap.add_argument("--once", action="store_true",
+                    help="run one skeleton of the workload and print its per-level stats (the command profiled)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.workload)
@@ -443,6 +484,16 @@ def main():
     X = Xd.T
     ctx = cupc.Context(local)
     mode = cupc.MODE_FP32_RECHECK if args.mode == "fp32" else cupc.MODE_PLAIN_FP64
+    if args.once:
+        r = ctx.skeleton(X, s.alpha, mode=mode, canonical=True, max_level=s.max_level)
+        st = r.stats()
+        r.free()
+        print(json.dumps({"workload": args.workload, "levels": st["levels"], "total_ms": st["total_ms"],
+                          "kernel_launches": st["kernel_launches"], "level_source_hash": level_source_hash(),
+                          "ci_block_entries": st["ci_block_entries"], "edges_start": st["edges_start"]}))
+        ctx.close()
+        return 0
+    peaks_alu = ctx.device_peaks()
     stream = torch.cuda.current_stream(dev)
 
     # the unit count: serial-order tests of the canonical run (equal to the oracle's)
@@ -479,7 +530,7 @@ def main():
             torch.cuda.synchronize()
             total_ms += a.elapsed_time(b)
             launches += st["kernel_launches"]
-            roofs.append((st, kernel_rooflines(st, s, args.mode, _peaks())))
+            roofs.append((st, kernel_rooflines(st, s, args.mode, _peaks(), peaks_alu)))
     if dist:
         dist.barrier()
     clocks = clk.summary()
@@ -541,10 +592,14 @@ def main():
         first["achieved"] = sum(x["achieved"] for x in rs) / len(rs)
         first["frac"] = first["achieved"] / first["peak"]
         kern[nm] = first
-    dom = max(kern, key=lambda k: kern[k]["ms"])
+    dom = max((k for k in kern if k != "recheck"), key=lambda k: kern[k]["ms"])
+    if "level" in kern:
+        kern["level"]["traffic"] = committed_traffic(args.workload)
     roof = {k: kern[dom][k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
     roof["kernel"] = dom
     roof["ms_per_step"] = kern[dom]["ms"]
+    roof["peak_src"] = "measured (MEASURED_PEAKS.json)" if _peaks()["src"] == "measured" else "fallback"
+    roof["alg_bytes_per_launch"] = kern[dom].get("alg_bytes_per_launch")
     kernels = {k: round(v["ms"], 4) for k, v in kern.items()}
     phases = {k: round(sum(st["kernel_ms"][k] for st, _ in roofs) / len(roofs), 4)
               for k in roofs[0][0]["kernel_ms"]}
@@ -572,7 +627,9 @@ def main():
                 "roofline": roof,
                 "kernel_rooflines": {k: {"frac": round(v["frac"], 5), "achieved": round(v["achieved"], 3),
                                          "unit": v["unit"], "bound": v["bound"]} for k, v in kern.items()},
-                "cpu_baseline": cpu, "clocks": clocks}
+                "cpu_baseline": cpu, "clocks": clocks,
+                "alu_peaks_measured": {k: round(v, 2) for k, v in peaks_alu.items()},
+                "level_source_hash": level_source_hash()}
         print(json.dumps(line))
     ctx.close()
     if dist:

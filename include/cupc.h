@@ -251,6 +251,14 @@ cupc_status cupc_batch_autotune(cupc_ctx* ctx, int nprob, const void* const* X, 
                                 const double* alpha, const cupc_options* base, int reps,
                                 cupc_tune_entry* entries, int cap, int* n_entries);
 
+/* Measured arithmetic peaks of the context's device, in TFLOP/s (2 flops per
+ * fused multiply-add): FP64 and FP32 FMA throughput of a grid filling every SM
+ * with four independent FMA chains per thread, best of three timed launches.
+ * They are the denominators of the rooflines of ALU-bound kernels (the FP64
+ * rechecks, the plain form's FP64 standardisation). The paper has no
+ * counterpart. Synchronises the context stream. */
+cupc_status cupc_device_peaks(cupc_ctx* ctx, double* fp64_tflops, double* fp32_tflops);
+
 /* Number of variables of a result. */
 cupc_status cupc_result_p(const cupc_result* res, int64_t* p);
 

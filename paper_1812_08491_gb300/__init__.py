@@ -52,6 +52,7 @@ _SIGNATURES = {
     "cupc_correlation_noalloc": ("status", ["vp", "int", "int", "i64", "i64", "i64", "vp", "vp"]),
     "cupc_skeleton_batch": ("status", ["vp", "int", "vp", "int", "int", "int", "vp", "vp", "vp", "opts_p", "vp",
                                        "vp"]),
+    "cupc_device_peaks": ("status", ["vp", "vp", "vp"]),
     "cupc_batch_autotune": ("status", ["vp", "int", "vp", "int", "int", "int", "vp", "vp", "vp", "opts_p", "int",
                                        "vp", "int", "vp"]),
     "cupc_mlp_set_weights": ("status", ["vp", "vp"]),
@@ -327,6 +328,12 @@ class Context:
         al = (ctypes.c_double * k)(*[float(a) for a in alphas])
         keep = [d[7] for d in descs]
         return k, ptrs, dts.pop(), layout, devs.pop(), ns, ps, al, keep
+
+    def device_peaks(self) -> dict:
+        """Measured FP64 / FP32 FMA throughput of the device (TFLOP/s)."""
+        f64, f32 = ctypes.c_double(), ctypes.c_double()
+        self._check(load().cupc_device_peaks(self._h, ctypes.byref(f64), ctypes.byref(f32)), "cupc_device_peaks")
+        return {"fp64_tflops": f64.value, "fp32_tflops": f32.value}
 
     def skeleton_batch(self, Xs, alphas, opts: Options | None = None, **kw):
         """Skeletons of independent problems (list of n_k x p_k arrays or tensors,

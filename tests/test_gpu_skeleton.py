@@ -244,3 +244,9 @@ def test_medium1000_full_size_parity(ctx):
         res = ctx.skeleton(Xd, s.alpha, mode=MODES[mode])
         _assert_same(res, ref)
         assert res.stats()["serial_tests"] == ref.tests
+
+
+def test_device_peaks(ctx):
+    pk = ctx.device_peaks()
+    # GB300: FP32 FMA throughput is tens of times the FP64 rate; both positive
+    assert pk["fp64_tflops"] > 0.1 and pk["fp32_tflops"] > 10 * pk["fp64_tflops"]

@@ -333,6 +333,14 @@ def main_batch(args, world, rank, local, dist):
     alphas = [s.alpha for s in probs]
     Xd = [torch.from_numpy(s.Xt.astype(np.float32)).to(dev).T for s in probs]   # variable-major n x p
     ctx = cupc.Context(local)
+    if args.once:
+        rs, st = ctx.skeleton_batch(Xd, alphas, batch_direct=True)
+        for r in rs:
+            r.free()
+        print(json.dumps({"workload": args.workload, "levels": st["levels"], "total_ms": st["total_ms"],
+                          "kernel_launches": st["kernel_launches"], "level_source_hash": level_source_hash()}))
+        ctx.close()
+        return 0
     tune = {}
     if args.tune:
         table = ctx.autotune_batch(Xd, alphas, reps=2)
@@ -369,6 +377,23 @@ def main_batch(args, world, rank, local, dist):
     total_ms = float(t.item())
     value = units * world * args.steps / (total_ms * 1e-3)
     ms_per_step = total_ms / args.steps
+
+    # the same problems one call each (FP32+recheck, and the plain FP64 form):
+    # device time of every skeleton summed
+    sequential = None
+    if not args.no_plain:
+        sequential = {}
+        for name, m in (("fp32_recheck", cupc.MODE_FP32_RECHECK), ("plain_fp64", cupc.MODE_PLAIN_FP64)):
+            for X in Xd[:2]:
+                ctx.skeleton(X, probs[0].alpha, mode=m).free()      # warm-up
+            tot = 0.0
+            for X, s in zip(Xd, probs):
+                r = ctx.skeleton(X, s.alpha, mode=m)
+                tot += r.stats()["total_ms"]
+                r.free()
+            sequential[name] = {"ms": round(tot, 3), "value": units / (tot * 1e-3), "unit": UNIT}
+        sequential["batched_speedup_vs_fp32_calls"] = round(sequential["fp32_recheck"]["ms"] / ms_per_step, 2)
+        sequential["batched_speedup_vs_plain_calls"] = round(sequential["plain_fp64"]["ms"] / ms_per_step, 2)
 
     e2e = None
     if not args.no_e2e:
@@ -427,7 +452,7 @@ def main_batch(args, world, rank, local, dist):
                 "data": "synthetic (seeded linear-Gaussian SEMs, device-resident input)",
                 "config": _batch_config(args.workload, probs, "FP32 bulk + FP64 recheck, batched"),
                 "skeleton_wall_s": ms_per_step / 1e3, "serial_tests_per_step": units, "edges": edges,
-                "cuda_graph": stats[0]["cuda_graph"], "tuned": tune or None,
+                "cuda_graph": stats[0]["cuda_graph"], "tuned": tune or None, "sequential_calls": sequential,
                 "e2e": e2e, "gpu_launches": launches, "phase_ms_per_step": phases,
                 "roofline": roof,
                 "kernel_rooflines": {k: {"frac": round(v["frac"], 5), "achieved": round(v["achieved"], 3),
@@ -451,6 +476,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP64 form")
     ap.add_argument("--tune", action="store_true", help="batch workloads: autotune the launch configuration")
+    ap.add_argument("--learned", action="store_true",
+                    help="learned subset ordering: train the network on 200 seeded p=500 instances first")
     ap.add_argument("--once", action="store_true",
                     help="run one skeleton of the workload and print its per-level stats (the command profiled)")
     args = ap.parse_args()
@@ -494,21 +521,41 @@ def main():
         ctx.close()
         return 0
     peaks_alu = ctx.device_peaks()
+    learned_info = None
+    if args.learned:
+        # the ordering network, trained on the GPU from the plain method's SepSets
+        from paper_1812_08491_gb300 import learned
+        t0 = time.perf_counter()
+        train_probs = [sem.mlp_training_instance(k) for k in range(200)]
+        Xtr, ttr = learned.collect(ctx, train_probs)
+        losses = learned.train(ctx, Xtr, ttr, epochs=6, batch=4096, lr=2e-3)
+        learned_info = {"train_instances": 200, "train_examples": int(Xtr.shape[0]),
+                        "positive_rate": round(float(ttr.mean()), 4),
+                        "loss_first_last": [round(float(losses[0]), 4), round(float(losses[-1]), 4)],
+                        "setup_s": round(time.perf_counter() - t0, 1)}
     stream = torch.cuda.current_stream(dev)
 
     # the unit count: serial-order tests of the canonical run (equal to the oracle's)
     ref = ctx.skeleton(X, s.alpha, mode=mode, canonical=True, max_level=s.max_level)
-    units = int(sum(ref.stats()["serial_tests"]))
+    ref_serial = list(ref.stats()["serial_tests"])
+    units = int(sum(ref_serial))
     edges = int(ref.stats()["edges_final"])
     ref.free()
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step(m):
-        res = ctx.skeleton(X, s.alpha, mode=m, canonical=True, max_level=s.max_level)
+        lo = bool(args.learned) and m == cupc.MODE_FP32_RECHECK
+        res = ctx.skeleton(X, s.alpha, mode=m, canonical=True, max_level=s.max_level, learned_order=lo)
         st = res.stats()
         res.free()
         return st
+
+    if args.learned:
+        st_l = step(mode)
+        learned_info["serial_tests_learned"] = int(sum(st_l["serial_tests"]))
+        learned_info["serial_tests_lexicographic"] = units
+        learned_info["serial_tests_saved_levels_ge2"] = int(sum(ref_serial[2:]) - sum(st_l["serial_tests"][2:]))
 
     for _ in range(args.warmup):
         step(mode)
@@ -564,12 +611,12 @@ def main():
     if not args.no_e2e:
         Xh = torch.from_numpy(s.Xt).pin_memory()
         Xhv = Xh.T
-        r = ctx.skeleton(Xhv, s.alpha, mode=mode, max_level=s.max_level)
+        r = ctx.skeleton(Xhv, s.alpha, mode=mode, max_level=s.max_level, learned_order=bool(args.learned))
         r.adjacency(); r.records_raw(); r.free()
         secs, h2d, d2h = 0.0, 0, 0
         for _ in range(args.steps):
             t0 = time.perf_counter()
-            r = ctx.skeleton(Xhv, s.alpha, mode=mode, max_level=s.max_level)
+            r = ctx.skeleton(Xhv, s.alpha, mode=mode, max_level=s.max_level, learned_order=bool(args.learned))
             adj = r.adjacency()
             recs = r.records_raw()
             secs += time.perf_counter() - t0
@@ -617,8 +664,10 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64" if args.mode == "fp32" else "f64",
                 "data": "synthetic (seeded linear-Gaussian SEM, device-resident input)",
-                "config": _config(args.workload, s, "FP32 bulk + FP64 recheck" if args.mode == "fp32"
-                                  else "plain FP64"),
+                "config": _config(args.workload, s, ("FP32 bulk + FP64 recheck" +
+                                                     (" + learned ordering" if args.learned else ""))
+                                  if args.mode == "fp32" else "plain FP64"),
+                "learned": learned_info,
                 "skeleton_wall_s": ms_per_step / 1e3, "serial_tests_per_step": units, "edges": edges,
                 "plain_form": plain,
                 "speedup_vs_plain": (plain["ms_per_step"] / ms_per_step) if plain else None,

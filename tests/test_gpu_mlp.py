@@ -150,3 +150,21 @@ def test_learned_order_gain(ctx, trained):
     print(f"serial tests at l >= 2: lexicographic {lex}, untrained {untrained}, trained {tr} "
           f"(gain vs lexicographic {100.0 * (lex - tr) / max(lex, 1):.2f} %)")
     assert tr <= untrained
+
+
+def test_learned_order_full_size_c3(ctx, trained):
+    """C3 at full size with the learned order: same skeleton and removal levels
+    as the oracle, and every stored SepSet separates."""
+    s = sem.workload("scalefree2500")
+    C = oracle.correlation(s.X, nthreads=16)
+    ref = oracle.pc_stable(C, s.n, s.alpha, max_level=s.max_level, nthreads=16)
+    ctx.mlp_set_weights(trained)
+    res = ctx.skeleton(torch.from_numpy(s.Xt).cuda().T, s.alpha, mode=cupc.MODE_FP32_RECHECK,
+                       learned_order=True, max_level=s.max_level)
+    assert np.array_equal(res.adjacency(), ref.adj)
+    assert np.array_equal(res.sep_levels(), ref.sep_level)
+    got = res.sepsets()
+    assert set(got) == set(ref.sepsets)
+    for (i, j), (l, S) in list(got.items())[::7]:          # a sample of the stored sets
+        ind, rho, z = oracle.ci_gauss(C, s.n, s.alpha, i, j, S)
+        assert ind, ((i, j), S, rho, z)

@@ -246,6 +246,34 @@ def test_medium1000_full_size_parity(ctx):
         assert res.stats()["serial_tests"] == ref.tests
 
 
+def _oracle_full(s, nthreads=16):
+    C = oracle.correlation(s.X, nthreads=nthreads)
+    return oracle.pc_stable(C, s.n, s.alpha, max_level=s.max_level, nthreads=nthreads)
+
+
+def test_scalefree2500_full_size_parity(ctx):
+    """C3 (p = 2500, n = 500, scale-free hubs), both forms, against the oracle."""
+    s = sem.workload("scalefree2500")
+    ref = _oracle_full(s)
+    Xd = torch.from_numpy(s.Xt).cuda().T
+    for mode in ("fp32", "plain"):
+        res = ctx.skeleton(Xd, s.alpha, mode=MODES[mode], max_level=s.max_level)
+        _assert_same(res, ref)
+        assert res.stats()["serial_tests"] == ref.tests
+
+
+def test_large10000_full_size_parity(ctx):
+    """C5 (p = 10^4, n = 1000, levels up to 6) in the benchmarked FP32 form."""
+    s = sem.workload("large10000")
+    ref = _oracle_full(s)
+    Xd = torch.from_numpy(s.Xt).cuda().T
+    res = ctx.skeleton(Xd, s.alpha, mode=MODES["fp32"], max_level=s.max_level)
+    assert np.array_equal(res.adjacency(), ref.adj)
+    assert np.array_equal(res.sep_levels(), ref.sep_level)
+    assert res.sepsets() == ref.sepsets
+    assert res.stats()["serial_tests"][:ref.levels_run] == list(ref.tests)
+
+
 def test_device_peaks(ctx):
     pk = ctx.device_peaks()
     # GB300: FP32 FMA throughput is tens of times the FP64 rate; both positive

@@ -2,6 +2,7 @@
 // of Algorithm 2 (level 0, then per level: compact A_G into A'_G, CI tests,
 // removal and SepSet records), results and their accessors.
 #include <algorithm>
+#include <cstddef>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -418,138 +419,126 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         return rp;
     };
 
-    // ---------------- level 0 (Algorithm 3) ----------------
-    auto run_level0 = [&]() -> cupc_status {
-        const double r0 = std::tanh(fisher_tau(alpha, n, 0));
-        TIMED(CUPC_K_LEVEL0,
-              launch_level0(fp32, Cuse, p, W, r0, kBand0, R->bits, (QEntry*)ctx->queue.p, qcap, meta, ctx->stream));
-        if (fp32) TIMED(CUPC_K_LEVEL0, launch_recheck0(recheck0_params(), grid_wide, ctx->stream));
-        CU(cudaMemcpyAsync(R->bits0, R->bits, bitbytes, cudaMemcpyDeviceToDevice, ctx->stream));
-        return CUPC_OK;
-    };
-    if ((s = run_level0()) != CUPC_OK) return s;
+    // ---------------- level 0 (Algorithm 3) and the levels (Algorithm 2 loop) ----------------
     const int64_t pairs = (int64_t)p * (p - 1) / 2;
     R->stats.tests[0] = pairs;
     R->stats.serial_tests[0] = pairs;
     R->stats.edges_start[0] = pairs;
     R->stats.max_degree[0] = p - 1;
-
-    // ---------------- buffer sizing from the graph after level 0 ----------------
-    const int chunk = o.chunk ? o.chunk : 32;
-    Meta M{};
-    for (int attempt = 0;; ++attempt) {
-        CU(cudaMemsetAsync(&meta->maxdeg, 0, 2 * sizeof(int), ctx->stream));
-        if ((s = ensure(ctx, ctx->deg, (size_t)p * 4)) != CUPC_OK) return s;
-        if ((s = ensure(ctx, ctx->row_off, (size_t)(p + 1) * 8)) != CUPC_OK) return s;
-        if ((s = ensure(ctx, ctx->item_off, (size_t)(p + 1) * 8)) != CUPC_OK) return s;
-        {
-            const int tk = tbegin(ctx, CUPC_K_COMPACT);
-            LAUNCH(launch_degree(R->bits, p, W, (int*)ctx->deg.p, meta, ctx->stream));
-            LAUNCH(launch_scan((const int*)ctx->deg.p, p, 1, chunk, binom_view(ctx), (long long*)ctx->row_off.p,
-                               (long long*)ctx->item_off.p, meta, ctx->stream));
-            tend(ctx, tk);
-            kcount[CUPC_K_COMPACT] += 2;
-        }
-        if ((s = readback(ctx)) != CUPC_OK) return s;
-        M = *ctx->hmeta;
-        if (M.error & 4) return fail(ctx, CUPC_E_TIMEOUT, "a bounded wait in the tensor-core product expired");
-        if (M.error) return fail(ctx, CUPC_E_NUMERIC, "a variable has zero variance or non-finite data");
-        if (!(fp32 && M.queue_len > qcap)) break;
-        // the level-0 recheck queue overflowed: enlarge it and run level 0 again
-        if (attempt >= 4) return fail(ctx, CUPC_E_RANGE, "recheck queue overflow persists");
-        qcap = (size_t)(M.queue_len * 2);
-        if ((s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
-        CU(cudaMemsetAsync(meta, 0, sizeof(Meta), ctx->stream));
-        if ((s = run_level0()) != CUPC_OK) return s;
-    }
-    R->stats.rechecks[0] = (int64_t)M.rechecks;
-    R->stats.removed[0] = pairs - (int64_t)M.edges;
-
-    // last level that can run: Algorithm 1 stops once max degree - 1 < l (degrees
-    // only shrink), Eq. (threshold) needs n - l - 3 > 0, and opts->max_level
-    int lmax = std::min<int64_t>(M.maxdeg - 1, n - 4);
+    // last level that may run: Eq. (threshold) needs n - l - 3 > 0, and opts->max_level;
+    // the loop ends earlier once max degree - 1 < l, decided on the device
+    int lmax = (int)std::min<int64_t>(n - 4, CUPC_MAX_LEVEL + 1);
     if (o.max_level >= 0) lmax = std::min(lmax, o.max_level);
     bool range_stop = false;
     if (lmax > CUPC_MAX_LEVEL) {
         lmax = CUPC_MAX_LEVEL;
         range_stop = true;  // an error unless the loop terminates by itself before
     }
+    const int chunk = o.chunk ? o.chunk : 32;
+    // Level buffers are sized without waiting for level 0: the context keeps the
+    // largest needs of its earlier calls (defaults on the first); a level that would
+    // overflow one reports it and the levels run again with room.
+    const unsigned long long all_slots = (unsigned long long)p * (unsigned long long)(p - 1);
+    unsigned long long nnz_cap = std::min<unsigned long long>(
+        all_slots, std::max<unsigned long long>({ctx->cap_nnz, 64ull * p, 1ull << 21}));
+    nnz_cap = std::max<unsigned long long>(nnz_cap, 1);
+    const unsigned long long item_cap = 1ull << 22;
+    size_t rec_len_cap =
+        16 + (ctx->cap_rec ? std::max<size_t>(ctx->cap_rec, (size_t)1 << 16)
+                           : std::min<size_t>((size_t)(3 + std::max(lmax, 0)) * (nnz_cap / 2), (size_t)1 << 22));
+    unsigned long long perm_cap = std::max<unsigned long long>(ctx->cap_perm, 1ull << 22);
+    LevelMeta* lm = nullptr;
+    LevelParams LP{};
     int levels_run = 1;
     int last_launched = 0;
-    size_t rec_len_cap = 0;
-    if (lmax >= 1) {
-        if (M.range_error) return fail(ctx, CUPC_E_RANGE, "subset count exceeds 64 bits");
-        const unsigned long long nnz_cap = std::max<unsigned long long>(M.nnz, 1);
-        const unsigned long long item_cap =
-            std::max<unsigned long long>({4ull * M.n_items, nnz_cap, 1ull << 16});
-        if ((s = ensure(ctx, ctx->cols, (size_t)nnz_cap * 4)) != CUPC_OK) return s;
-        if ((s = ensure(ctx, ctx->srow, (size_t)nnz_cap * 4)) != CUPC_OK) return s;
-        if ((s = ensure(ctx, ctx->partner, (size_t)nnz_cap * 4)) != CUPC_OK) return s;
-        if ((s = ensure(ctx, ctx->wpre, bitbytes)) != CUPC_OK) return s;
-        if ((s = ensure(ctx, ctx->best, (size_t)nnz_cap * 8)) != CUPC_OK) return s;
-        if ((s = ensure(ctx, ctx->item_row, (size_t)item_cap * 4)) != CUPC_OK) return s;
-        if ((s = ensure(ctx, *ctx_buf(ctx, "item_c"), (size_t)item_cap * 4)) != CUPC_OK) return s;
-        if ((s = ensure_binom(ctx, M.maxdeg + 2)) != CUPC_OK) return s;
-        if ((s = ensure(ctx, ctx->lmeta, sizeof(LevelMeta))) != CUPC_OK) return s;
-        // recheck partials: batches of queued tests sized to this buffer per level
-        if (fp32 && (s = ensure(ctx, ctx->part, kPartBytes)) != CUPC_OK) return s;
-        // SepSet pool: room for every edge present after level 0 with the largest set
-        rec_len_cap = (size_t)M.edges * (3 + lmax) + 16;
-        if ((s = dalloc(ctx, (void**)&R->rec, rec_len_cap * 4)) != CUPC_OK) return s;
-        LevelMeta* lm = (LevelMeta*)ctx->lmeta.p;
-        CU(cudaMemsetAsync(lm, 0, sizeof(LevelMeta), ctx->stream));
+    Meta M{};
+    for (int attempt = 0;; ++attempt) {
+        if (attempt > 6) return fail(ctx, CUPC_E_RANGE, "level buffers keep overflowing");
+        // level 0's counters (the error flags of the preparation stay)
+        CU(cudaMemsetAsync(meta, 0, offsetof(Meta, error), ctx->stream));
+        {
+            const double r0 = std::tanh(fisher_tau(alpha, n, 0));
+            TIMED(CUPC_K_LEVEL0, launch_level0(fp32, Cuse, p, W, r0, kBand0, R->bits, (QEntry*)ctx->queue.p, qcap,
+                                               meta, ctx->stream));
+            if (fp32) TIMED(CUPC_K_LEVEL0, launch_recheck0(recheck0_params(), grid_wide, ctx->stream));
+            CU(cudaMemcpyAsync(R->bits0, R->bits, bitbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        if ((s = ensure(ctx, ctx->deg, (size_t)p * 4)) != CUPC_OK) return s;
+        TIMED(CUPC_K_COMPACT, launch_degree(R->bits, p, W, (int*)ctx->deg.p, meta, ctx->stream));
+        last_launched = 0;
+        levels_run = 1;
+        if (lmax >= 1) {
+            if ((s = ensure(ctx, ctx->row_off, (size_t)(p + 1) * 8)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, ctx->item_off, (size_t)(p + 1) * 8)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, ctx->cols, (size_t)nnz_cap * 4)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, ctx->srow, (size_t)nnz_cap * 4)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, ctx->partner, (size_t)nnz_cap * 4)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, ctx->wpre, bitbytes)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, ctx->best, (size_t)nnz_cap * 8)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, ctx->item_row, (size_t)item_cap * 4)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, *ctx_buf(ctx, "item_c"), (size_t)item_cap * 4)) != CUPC_OK) return s;
+            if ((s = ensure_binom(ctx, p + 2)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, ctx->lmeta, sizeof(LevelMeta))) != CUPC_OK) return s;
+            // recheck partials: batches of queued tests sized to this buffer per level
+            if (fp32 && (s = ensure(ctx, ctx->part, kPartBytes)) != CUPC_OK) return s;
+            if (R->rec) cudaFreeAsync(R->rec, ctx->stream);
+            R->rec = nullptr;
+            if ((s = dalloc(ctx, (void**)&R->rec, rec_len_cap * 4)) != CUPC_OK) return s;
+            lm = (LevelMeta*)ctx->lmeta.p;
+            CU(cudaMemsetAsync(lm, 0, sizeof(LevelMeta), ctx->stream));
 
-        LevelParams LP{};
-        LP.bits = R->bits;
-        LP.W = W;
-        LP.p = p;
-        LP.nwords = (long long)p * W;
-        LP.ctas_per_sm = o.ctas_per_sm;
-        LP.backup = fp32 ? (unsigned*)ctx->backup[0].p : nullptr;
-        LP.deg = (int*)ctx->deg.p;
-        LP.row_off = (long long*)ctx->row_off.p;
-        LP.item_off = (long long*)ctx->item_off.p;
-        LP.item_row = (int*)ctx->item_row.p;
-        LP.item_c = (int*)ctx_buf(ctx, "item_c")->p;
-        LP.item_cap = item_cap;
-        LP.cols = (int*)ctx->cols.p;
-        LP.srow = (int*)ctx->srow.p;
-        LP.partner = (int*)ctx->partner.p;
-        LP.wpre = (int*)ctx->wpre.p;
-        LP.best = (unsigned long long*)ctx->best.p;
-        LP.nnz_cap = nnz_cap;
-        LP.C = Cuse;
-        LP.B = binom_view(ctx);
-        LP.chunk0 = chunk;
-        LP.canonical = o.canonical_sepset;
-        LP.band_abs = (o.recheck_margin > 0) ? o.recheck_margin : kBandAbs;
-        LP.band_rel = kBandRel;
-        LP.rank_tol = fp32 ? kRankTol32 : kRankTol64;
-        LP.piv_floor = kPivFloor;
-        LP.xv = dv.xv;
-        LP.ldx = dv.ldx;
-        LP.xf64 = dv.xf64;
-        LP.mu = dv.mu;
-        LP.isd = dv.isd;
-        LP.n = (int)n;
-        LP.c64 = c64;
-        LP.part = fp32 ? (double*)ctx->part.p : nullptr;
-        LP.part_cap = kPartBytes / sizeof(double);
-        LP.rec = R->rec;
-        LP.rec_cap = rec_len_cap;
-        LP.lm = lm;
-        LP.learned = o.learned_order ? 1 : 0;
-        if (o.learned_order) {
-            // per-slot candidate lists of levels >= 2 (sized from level 1; a level that
-            // would not fit keeps the increasing order)
-            const unsigned long long perm_cap =
-                std::min<unsigned long long>(std::max<unsigned long long>(M.block_entries, 1), 1ull << 26);
-            if ((s = ensure(ctx, *ctx_buf(ctx, "perm"), (size_t)perm_cap * 4)) != CUPC_OK) return s;
-            if ((s = ensure(ctx, *ctx_buf(ctx, "poff"), (size_t)(p + 1) * 8)) != CUPC_OK) return s;
-            LP.perm = (int*)ctx_buf(ctx, "perm")->p;
-            LP.poff = (long long*)ctx_buf(ctx, "poff")->p;
-            LP.perm_cap = perm_cap;
-            LP.mlp_w = ctx_buf(ctx, "mlp_Pb")->p;
+            LP = LevelParams{};
+            LP.bits = R->bits;
+            LP.W = W;
+            LP.p = p;
+            LP.nwords = (long long)p * W;
+            LP.ctas_per_sm = o.ctas_per_sm;
+            LP.backup = fp32 ? (unsigned*)ctx->backup[0].p : nullptr;
+            LP.deg = (int*)ctx->deg.p;
+            LP.row_off = (long long*)ctx->row_off.p;
+            LP.item_off = (long long*)ctx->item_off.p;
+            LP.item_row = (int*)ctx->item_row.p;
+            LP.item_c = (int*)ctx_buf(ctx, "item_c")->p;
+            LP.item_cap = item_cap;
+            LP.cols = (int*)ctx->cols.p;
+            LP.srow = (int*)ctx->srow.p;
+            LP.partner = (int*)ctx->partner.p;
+            LP.wpre = (int*)ctx->wpre.p;
+            LP.best = (unsigned long long*)ctx->best.p;
+            LP.nnz_cap = nnz_cap;
+            LP.C = Cuse;
+            LP.B = binom_view(ctx);
+            LP.chunk0 = chunk;
+            LP.canonical = o.canonical_sepset;
+            LP.band_abs = (o.recheck_margin > 0) ? o.recheck_margin : kBandAbs;
+            LP.band_rel = kBandRel;
+            LP.rank_tol = fp32 ? kRankTol32 : kRankTol64;
+            LP.piv_floor = kPivFloor;
+            LP.xv = dv.xv;
+            LP.ldx = dv.ldx;
+            LP.xf64 = dv.xf64;
+            LP.mu = dv.mu;
+            LP.isd = dv.isd;
+            LP.n = (int)n;
+            LP.c64 = c64;
+            LP.part = fp32 ? (double*)ctx->part.p : nullptr;
+            LP.part_cap = kPartBytes / sizeof(double);
+            LP.rec = R->rec;
+            LP.rec_cap = rec_len_cap;
+            LP.lm = lm;
+            LP.meta0 = meta;
+            LP.qcap0 = fp32 ? qcap : ~0ull;
+            LP.learned = o.learned_order ? 1 : 0;
+            if (o.learned_order) {
+                // per-slot candidate lists of levels >= 2 (a level whose lists would not
+                // fit keeps the increasing order)
+                if ((s = ensure(ctx, *ctx_buf(ctx, "perm"), (size_t)perm_cap * 4)) != CUPC_OK) return s;
+                if ((s = ensure(ctx, *ctx_buf(ctx, "poff"), (size_t)(p + 1) * 8)) != CUPC_OK) return s;
+                LP.perm = (int*)ctx_buf(ctx, "perm")->p;
+                LP.poff = (long long*)ctx_buf(ctx, "poff")->p;
+                LP.perm_cap = perm_cap;
+                LP.mlp_w = ctx_buf(ctx, "mlp_Pb")->p;
+            }
         }
 
         // Levels are launched with at most two in flight: level l is launched only
@@ -582,7 +571,6 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
                 const double r = std::tanh(fisher_tau(alpha, n, l));
                 LP.r = r;
                 LP.r2 = r * r;
-                LP.rank_tol = fp32 ? kRankTol32 : kRankTol64;
                 if (l < CUPC_STATS_LEVELS) CU(cudaEventRecord(ctx->ev[1 + l], ctx->stream));
                 LAUNCH(launch_level(fp32, LP, ctx->num_sms, ctx->stream));
                 kcount[CUPC_K_CI]++;
@@ -590,21 +578,52 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             }
             return CUPC_OK;
         };
-        if ((s = launch_levels(1)) != CUPC_OK) return s;
-        for (int attempt = 0;; ++attempt) {
+        if (lmax >= 1 && (s = launch_levels(1)) != CUPC_OK) return s;
+
+        // one readback: level 0's counters and, when levels ran, theirs
+        CU(cudaMemcpyAsync(ctx->hmeta, meta, sizeof(Meta), cudaMemcpyDeviceToHost, ctx->stream));
+        ctx->d2h += sizeof(Meta);
+        if (lmax >= 1) {
             CU(cudaMemcpyAsync(ctx->hlmeta, lm, sizeof(LevelMeta), cudaMemcpyDeviceToHost, ctx->stream));
-            CU(cudaStreamSynchronize(ctx->stream));
             ctx->d2h += sizeof(LevelMeta);
+        }
+        CU(cudaStreamSynchronize(ctx->stream));
+        M = *ctx->hmeta;
+        if (M.error & 4) return fail(ctx, CUPC_E_TIMEOUT, "a bounded wait in the tensor-core product expired");
+        if (M.error) return fail(ctx, CUPC_E_NUMERIC, "a variable has zero variance or non-finite data");
+        if (fp32 && M.queue_len > qcap) {
+            // the level-0 recheck queue overflowed (the levels stopped at entry):
+            // enlarge it and run level 0 again
+            qcap = (size_t)(M.queue_len * 2);
+            if ((s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
+            continue;
+        }
+        if (lmax < 1) break;
+        bool rerun = false;
+        for (int ov = 0;; ++ov) {
             LevelMeta& H = *ctx->hlmeta;
             if (H.error & 8) return fail(ctx, CUPC_E_TIMEOUT, "a grid barrier wait expired");
-            if (H.error) return fail(ctx, CUPC_E_RANGE, "level buffers too small");
             if (H.range_error) return fail(ctx, CUPC_E_RANGE, "subset count exceeds 64 bits");
+            unsigned long long nnz_need = 0;
+            for (int q = 1; q < LV; ++q) nnz_need = std::max(nnz_need, 2 * H.edges[q]);
+            if ((H.error & 16) || nnz_need > nnz_cap) {
+                // CSR arrays too small for some level: room for every slot seen, and again
+                nnz_cap = std::min<unsigned long long>(all_slots, nnz_need + nnz_need / 2 + 1024);
+                rerun = true;
+                break;
+            }
+            if (H.error) return fail(ctx, CUPC_E_RANGE, "level buffers too small");
+            if (H.rec_ints > rec_len_cap) {
+                rec_len_cap = (size_t)(H.rec_ints + H.rec_ints / 4 + 16);
+                rerun = true;
+                break;
+            }
             const int ol = H.overflow_level;
             if (ol == 0) break;
             // the recheck queue of level ol overflowed: restore A_G as it was at the
             // start of that level, enlarge the queue, clear that level's counters and
             // run the levels from ol again
-            if (attempt >= 4) return fail(ctx, CUPC_E_RANGE, "recheck queue overflow persists");
+            if (ov >= 4) return fail(ctx, CUPC_E_RANGE, "recheck queue overflow persists");
             qcap = (size_t)(H.queue_len[ol] * 2);
             if ((s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
             CU(cudaMemcpyAsync(R->bits, ctx->backup[0].p, bitbytes, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -627,7 +646,15 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             H.bar_count = 0;
             CU(cudaMemcpyAsync(lm, ctx->hlmeta, sizeof(LevelMeta), cudaMemcpyHostToDevice, ctx->stream));
             if ((s = launch_levels(ol)) != CUPC_OK) return s;
+            CU(cudaMemcpyAsync(ctx->hlmeta, lm, sizeof(LevelMeta), cudaMemcpyDeviceToHost, ctx->stream));
+            CU(cudaStreamSynchronize(ctx->stream));
+            ctx->d2h += sizeof(LevelMeta);
         }
+        if (!rerun) break;
+    }
+    R->stats.rechecks[0] = (int64_t)M.rechecks;
+    R->stats.removed[0] = pairs - (int64_t)(M.nnz / 2);
+    if (lmax >= 1) {
         const LevelMeta& H = *ctx->hlmeta;
         const int last = H.done_level ? H.done_level - 1 : lmax;  // last level that ran
         if (range_stop && H.done_level == 0)
@@ -652,8 +679,18 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             R->stats.kernel_ms[CUPC_K_FINALIZE] += 1e-6f * (float)H.phase_ns[l][3];
         }
         R->rec_ints = (int64_t)H.rec_ints;
+        // the needs the next call on this context is sized for
+        unsigned long long nnz_need = 0, blk = 0;
+        for (int q = 1; q < LV; ++q) {
+            nnz_need = std::max(nnz_need, 2 * H.edges[q]);
+            blk = std::max(blk, H.block_entries[q]);
+        }
+        ctx->cap_nnz = std::max<unsigned long long>(ctx->cap_nnz, nnz_need + nnz_need / 4);
+        ctx->cap_rec = std::max<size_t>(ctx->cap_rec, (size_t)(H.rec_ints + H.rec_ints / 4));
+        ctx->cap_perm = std::max<unsigned long long>(ctx->cap_perm, std::min<unsigned long long>(blk, 1ull << 26));
+    } else if (range_stop) {
+        return fail(ctx, CUPC_E_RANGE, "a level above CUPC_MAX_LEVEL would be needed");
     }
-    if (lmax < 1 && range_stop) return fail(ctx, CUPC_E_RANGE, "a level above CUPC_MAX_LEVEL would be needed");
     const int ev_end = std::min(std::max(levels_run, last_launched + 1), CUPC_STATS_LEVELS - 1) + 1;
     CU(cudaEventRecord(ctx->ev[ev_end], ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));

@@ -48,6 +48,10 @@ struct cupc_ctx {
     std::map<std::string, Buf> named;   // further device buffers (network state)
     int mlp_ready = 0;                  // network weights loaded
     int mlp_step = 0;                   // Adam steps taken
+    // largest level-buffer needs seen by this context's calls (CSR slots, SepSet
+    // ints, candidate-list entries): the next call is sized for them up front
+    unsigned long long cap_nnz = 0, cap_perm = 0;
+    size_t cap_rec = 0;
     void* batch = nullptr;              // batch plan (api_batch.cu)
     void (*batch_free)(cupc_ctx*) = nullptr;
 };

@@ -105,6 +105,7 @@ __global__ void k_degree(const unsigned* __restrict__ bits, int p, int W, int* _
     if (lane == 0) {
         deg[i] = c;
         atomicMax(&meta->maxdeg, c);
+        if (c) atomicAdd(&meta->nnz, (unsigned long long)c);
     }
 }
 
@@ -113,87 +114,6 @@ cudaError_t launch_degree(const unsigned* bits, int p, int W, int* deg, Meta* me
 {
     const int block = 256, grid = (int)(((long long)p * 32 + block - 1) / block);
     k_degree<<<grid, block, 0, st>>>(bits, p, W, deg, meta, vprob, probs);
-    return cudaGetLastError();
-}
-
-// Single-block exclusive scans of deg (CSR offsets) and of the per-row work
-// items (rows with n'_i >= l + 1 get ceil(C(n'_i, l) / chunk) items).
-__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ deg, int p, int l, int chunk, Binom B,
-                                               long long* __restrict__ row_off, long long* __restrict__ item_off,
-                                               Meta* meta)
-{
-    __shared__ long long sa[32], sb[32];
-    const int t = threadIdx.x, NT = blockDim.x;
-    const int per = (p + NT - 1) / NT;
-    const int lo = min(p, t * per), hi = min(p, lo + per);
-    long long a = 0, b = 0;
-    unsigned long long sq = 0;
-    int rng = 0;
-    for (int i = lo; i < hi; ++i) {
-        const int d = deg[i];
-        a += d;
-        if (d >= l + 1) {
-            const unsigned long long ns = B(d, l);
-            if (ns == ~0ull) rng = 1;
-            b += (long long)((ns + chunk - 1) / chunk);
-            sq += (unsigned long long)(d + 1) * (unsigned long long)(d + 1);
-        }
-    }
-    {
-        unsigned long long t2 = sq;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t2 += __shfl_xor_sync(0xffffffffu, t2, o);
-        if ((threadIdx.x & 31) == 0 && t2) atomicAdd(&meta->block_entries, t2);
-    }
-    // block exclusive scan of (a, b)
-    const int lane = t & 31, w = t >> 5;
-    long long ia = a, ib = b;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long xa = __shfl_up_sync(0xffffffffu, ia, o);
-        const long long xb = __shfl_up_sync(0xffffffffu, ib, o);
-        if (lane >= o) { ia += xa; ib += xb; }
-    }
-    if (lane == 31) { sa[w] = ia; sb[w] = ib; }
-    __syncthreads();
-    if (w == 0) {
-        long long va = (lane < NT / 32) ? sa[lane] : 0, vb = (lane < NT / 32) ? sb[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long xa = __shfl_up_sync(0xffffffffu, va, o);
-            const long long xb = __shfl_up_sync(0xffffffffu, vb, o);
-            if (lane >= o) { va += xa; vb += xb; }
-        }
-        sa[lane] = va;
-        sb[lane] = vb;
-    }
-    __syncthreads();
-    long long ea = ia - a + (w > 0 ? sa[w - 1] : 0);
-    long long eb = ib - b + (w > 0 ? sb[w - 1] : 0);
-    for (int i = lo; i < hi; ++i) {
-        const int d = deg[i];
-        row_off[i] = ea;
-        item_off[i] = eb;
-        ea += d;
-        if (d >= l + 1) {
-            const unsigned long long ns = B(d, l);
-            eb += (long long)((ns + chunk - 1) / chunk);
-        }
-    }
-    if (rng) atomicOr(&meta->range_error, 1);
-    if (t == NT - 1) {
-        row_off[p] = ea;
-        item_off[p] = eb;
-        meta->nnz = (unsigned long long)ea;
-        meta->edges = (unsigned long long)ea / 2;
-        meta->n_items = (unsigned long long)eb;
-    }
-}
-
-cudaError_t launch_scan(const int* deg, int p, int l, int chunk, Binom B, long long* row_off,
-                        long long* item_off, Meta* meta, cudaStream_t st)
-{
-    k_scan<<<1, 1024, 0, st>>>(deg, p, l, chunk, B, row_off, item_off, meta);
     return cudaGetLastError();
 }
 

@@ -836,7 +836,7 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
     // sample count (a batch takes its largest n), and enough units to occupy
     // every warp when the list is short
     // (the combine sums S x D partials per test: a large Gram block takes fewer)
-    const int sp = (int)min((long long)max(1, 256 / D), (nwarps + (long long)nl - 1) / (long long)nl);
+    const int sp = (int)min((long long)max(8, 1024 / D), (nwarps + (long long)nl - 1) / (long long)nl);
     const int S = min(64, max(recheck_slices(P.vprob ? P.nmax : P.n), sp));
     const long long batch = max(1ll, (long long)(P.part_cap / ((unsigned long long)S * D)));
     unsigned long long done = 0;
@@ -1119,8 +1119,12 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
 {
     LevelMeta* lm = P.lm;
     const int l = P.l;
-    // a previous level ended the loop (termination, overflow or error)
-    if (*(volatile int*)&lm->done_level || *(volatile int*)&lm->overflow_level || *(volatile int*)&lm->error) {
+    // a previous level ended the loop (termination, overflow or error), or level 0
+    // failed (an error, or its recheck queue overflowed: its decisions are incomplete)
+    const bool level0_bad =
+        P.meta0 && (*(volatile const int*)&P.meta0->error != 0 || ld_cg(&P.meta0->queue_len) > P.qcap0);
+    if (level0_bad || *(volatile int*)&lm->done_level || *(volatile int*)&lm->overflow_level ||
+        *(volatile int*)&lm->error) {
         if (blockIdx.x == 0 && threadIdx.x == 0) signal_host(P, 2);
         return;
     }

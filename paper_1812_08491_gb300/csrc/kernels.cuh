@@ -124,6 +124,8 @@ struct LevelParams {
     const int* vlmax;              // batch: the last level of each vertex's problem
     unsigned long long* prob_serial;   // batch: serial-order tests per problem and level (nprob x LV)
     int ctas_per_sm;               // launch shape (0: as many as fit, at most 2)
+    const Meta* meta0;             // level 0's counters: a level does not run after an error
+    unsigned long long qcap0;      // there, or an overflow of its recheck queue
     // learned ordering (levels >= 2, FP32 mode)
     int learned;                   // requested
     const void* mlp_w;             // bf16 network parameters
@@ -184,8 +186,6 @@ cudaError_t launch_level0(int fp32, const void* C, int p, int W, double r0, doub
                           const int* vprob = nullptr, const ProbDesc* probs = nullptr, int nrows = 0);
 cudaError_t launch_degree(const unsigned* bits, int p, int W, int* deg, Meta* meta, cudaStream_t st,
                           const int* vprob = nullptr, const ProbDesc* probs = nullptr);
-cudaError_t launch_scan(const int* deg, int p, int l, int chunk, Binom B, long long* row_off,
-                        long long* item_off, Meta* meta, cudaStream_t st);
 cudaError_t launch_recheck0(const Recheck0Params& P, int grid, cudaStream_t st);
 // One fused level kernel (cooperative launch). *grid receives the grid used.
 cudaError_t launch_level(int fp32, const LevelParams& P, int num_sms, cudaStream_t st);

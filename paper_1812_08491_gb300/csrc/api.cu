@@ -479,6 +479,8 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             if ((s = ensure(ctx, *ctx_buf(ctx, "item_c"), (size_t)item_cap * 4)) != CUPC_OK) return s;
             if ((s = ensure_binom(ctx, p + 2)) != CUPC_OK) return s;
             if ((s = ensure(ctx, ctx->lmeta, sizeof(LevelMeta))) != CUPC_OK) return s;
+            if ((s = ensure(ctx, *ctx_buf(ctx, "scan_part"), 4 * 1024 * sizeof(unsigned long long))) != CUPC_OK)
+                return s;
             // recheck partials: batches of queued tests sized to this buffer per level
             if (fp32 && (s = ensure(ctx, ctx->part, kPartBytes)) != CUPC_OK) return s;
             if (R->rec) cudaFreeAsync(R->rec, ctx->stream);
@@ -526,6 +528,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             LP.rec = R->rec;
             LP.rec_cap = rec_len_cap;
             LP.lm = lm;
+            LP.scan_part = (unsigned long long*)ctx_buf(ctx, "scan_part")->p;
             LP.meta0 = meta;
             LP.qcap0 = fp32 ? qcap : ~0ull;
             LP.learned = o.learned_order ? 1 : 0;
@@ -633,7 +636,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
                 H.tests[q] = H.rechecks[q] = H.removed[q] = H.serial[q] = H.edges[q] = H.items[q] = 0;
                 H.next_item[q] = H.queue_len[q] = H.block_entries[q] = 0;
                 for (int c = 0; c < 4; ++c) H.phase_ns[q][c] = 0;
-                for (int c = 0; c < RND; ++c) H.round_off[q][c] = H.round_cur[q][c] = 0;
+                for (int c = 0; c < RND; ++c) H.round_hist[q][c] = H.round_cur[q][c] = 0;
                 H.recheck_ns[q][0] = H.recheck_ns[q][1] = H.recheck_ns[q][2] = 0;
                 H.live[q] = 0;
                 H.maxdeg[q] = 0;

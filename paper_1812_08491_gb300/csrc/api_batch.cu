@@ -56,7 +56,7 @@ struct BatchPlan {
     size_t ws_bytes = 0;
     unsigned long long nnz_cap = 0, item_cap = 0, qcap = 0, rec_cap = 0;
     Buf d_probs, d_vprob, d_vlmax, d_units, d_tiles, x_in, xt, mu, isd, zhi, zlo, ws, c32, bits, bits0, backup;
-    Buf deg, row_off, item_off, item_row, item_c, live, cols, srow, partner, wpre, best, queue, part, rec, meta, lmeta, pserial;
+    Buf deg, row_off, item_off, item_row, item_c, live, scan_part, cols, srow, partner, wpre, best, queue, part, rec, meta, lmeta, pserial;
     Binom binom{};
     // pinned host copies written at the end of each run
     unsigned* h_bits = nullptr;
@@ -82,7 +82,7 @@ void plan_destroy(cupc_ctx* ctx, BatchPlan* B)
     if (B->exec) cudaGraphExecDestroy(B->exec);
     Buf* all[] = {&B->d_probs, &B->d_vprob, &B->d_vlmax, &B->d_units, &B->d_tiles, &B->x_in, &B->xt,      &B->mu,
                   &B->isd,     &B->zhi,     &B->zlo,     &B->ws,   &B->c32,     &B->bits,
-                  &B->bits0,   &B->backup,  &B->deg,     &B->row_off, &B->item_off, &B->item_row, &B->item_c, &B->live, &B->cols,
+                  &B->bits0,   &B->backup,  &B->deg,     &B->row_off, &B->item_off, &B->item_row, &B->item_c, &B->live, &B->scan_part, &B->cols,
                   &B->srow,    &B->partner, &B->wpre,    &B->best,    &B->queue, &B->part,   &B->rec,
                   &B->meta,    &B->lmeta,   &B->pserial};
     for (Buf* b : all) ctx_free(ctx, b);
@@ -207,6 +207,7 @@ cupc_status allocate(cupc_ctx* ctx, BatchPlan& B)
         {&B.item_off, (size_t)(B.P + 1) * 8},
         {&B.item_row, (size_t)B.item_cap * 4},
         {&B.item_c, (size_t)B.item_cap * 4},
+        {&B.scan_part, 4 * 1024 * sizeof(unsigned long long)},
         {&B.cols, (size_t)B.nnz_cap * 4},
         {&B.srow, (size_t)B.nnz_cap * 4},
         {&B.partner, (size_t)B.nnz_cap * 4},
@@ -341,6 +342,7 @@ cupc_status issue(cupc_ctx* ctx, BatchPlan& B, cudaStream_t st, bool capturing)
     LP.rec = (int*)B.rec.p;
     LP.rec_cap = B.rec_cap;
     LP.lm = lm;
+    LP.scan_part = (unsigned long long*)B.scan_part.p;
     LP.vprob = vprob;
     LP.probs = probs;
     LP.vlmax = (const int*)B.d_vlmax.p;

@@ -126,12 +126,12 @@ __device__ bool grid_sync(LevelMeta* lm)
 // P1 (blocks other than 0): exclusive prefix popcounts of each row's words,
 // wpre[i*W + w] = number of neighbours of i below 32 w; FP32 mode: A_G copy
 // ---------------------------------------------------------------------------
-__device__ void phase_prefix(const LevelParams& P, bool fp32)
+__device__ void phase_prefix(const LevelParams& P, bool fp32, int skip)
 {
     const int lane = threadIdx.x & 31;
-    // block 0 is scanning; with a single block it does this part too
-    const int nb = gridDim.x > 1 ? gridDim.x - 1 : 1;
-    const int bid = gridDim.x > 1 ? blockIdx.x - 1 : 0;
+    // (skip = 1: block 0 is scanning; with a single block it does this part too)
+    const int nb = (skip && gridDim.x > 1) ? gridDim.x - 1 : gridDim.x;
+    const int bid = (skip && gridDim.x > 1) ? blockIdx.x - 1 : blockIdx.x;
     const int gw = (bid * NT + threadIdx.x) >> 5;
     const int nwarps = (nb * NT) >> 5;
     for (int i = gw; i < P.p; i += nwarps) {
@@ -172,6 +172,18 @@ __device__ __forceinline__ unsigned long long row_items(const Binom& B, int d, i
     return (unsigned long long)d * ((B(d - 1, l) + chunk - 1) / chunk);
 }
 
+// Adds a row with K items to the round histogram (bin min(K, RND - 1); rows
+// without items are not counted). Lanes with the same bin are combined first:
+// most rows fall in a handful of bins, and shared atomics on one address
+// serialise.
+__device__ __forceinline__ void hist_add(unsigned long long* hist, unsigned long long K)
+{
+    const int bin = K == 0 ? -1 : (int)(K < RND - 1 ? K : RND - 1);
+    const unsigned peers = __match_any_sync(__activemask(), bin);
+    const int lane = threadIdx.x & 31;
+    if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned long long)__popc(peers));
+}
+
 // Degrees of rows [i0, i0 + 8) (0 past hi): all loads issued before use, so a
 // thread walking its range pays one memory latency per 8 rows.
 __device__ __forceinline__ void load8(const LevelParams& P, int i0, int hi, int (&d)[8], int (&di)[8])
@@ -190,19 +202,9 @@ __device__ __forceinline__ void load8(const LevelParams& P, int i0, int hi, int 
     }
 }
 
-// Adds a row with K items to the round histogram (bin min(K, RND - 1); rows
-// without items are not counted). Lanes with the same bin are combined first:
-// most rows fall in a handful of bins, and shared atomics on one address
-// serialise.
-__device__ __forceinline__ void hist_add(unsigned long long* hist, unsigned long long K)
-{
-    const int bin = K == 0 ? -1 : (int)(K < RND - 1 ? K : RND - 1);
-    const unsigned peers = __match_any_sync(__activemask(), bin);
-    const int lane = threadIdx.x & 31;
-    if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned long long)__popc(peers));
-}
-
-__device__ void phase_scan(const LevelParams& P, bool learned)
+// P1 for graphs of at most 32 NT rows: block 0 scans every row while the
+// other CTAs build the word prefixes (no second barrier).
+__device__ void phase_scan_one(const LevelParams& P, bool learned)
 {
     __shared__ long long sa[32], sb[32], sc[32];
     __shared__ unsigned long long stot;
@@ -338,21 +340,8 @@ __device__ void phase_scan(const LevelParams& P, bool learned)
     ovf = warp_sum_u64(ovf);
     if (lane == 0 && ovf) atomicAdd(&hist[0], ovf);   // bin 0 (no row has 0 items counted) carries the overflow
     __syncthreads();
-    // round c < RND - 1 holds the rows with more than c items; the last round the
-    // items past the first RND - 1 of every row
-    if (t == 0) {
-        unsigned long long off = 0, above = 0;
-        unsigned long long n_round[RND];
-        for (int v = RND - 1; v >= 1; --v) {
-            above += hist[v];
-            n_round[v - 1] = above;   // rows with more than v - 1 items
-        }
-        n_round[RND - 1] = hist[0];
-        for (int q = 0; q < RND; ++q) {
-            P.lm->round_off[l][q] = off;
-            off += n_round[q];
-        }
-    }
+    for (int q = t; q < RND; q += NT)
+        if (hist[q]) P.lm->round_hist[l][q] = hist[q];
     if (rng) atomicOr(&P.lm->range_error, 1);
     if (t == NT - 1) {
         P.row_off[P.p] = ea;
@@ -363,6 +352,196 @@ __device__ void phase_scan(const LevelParams& P, bool learned)
         P.lm->chunk[l] = chunk;
         if ((unsigned long long)ea > P.nnz_cap || (unsigned long long)eb > P.item_cap) atomicOr(&P.lm->error, 16);
     }
+}
+
+// Contiguous rows of this CTA (the scan's order).
+__device__ __forceinline__ void cta_rows(const LevelParams& P, int& r0, int& r1)
+{
+    r0 = (int)((long long)P.p * blockIdx.x / gridDim.x);
+    r1 = (int)((long long)P.p * (blockIdx.x + 1) / gridDim.x);
+}
+
+// Block-wide sum of four u64 values (fixed order); the result is valid in thread 0.
+__device__ __forceinline__ void block_sum4(unsigned long long (&v)[4], unsigned long long (*red)[4])
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = warp_sum_u64(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) red[w][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int q = 1; q < NW; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] += red[q][k];
+    __syncthreads();
+}
+
+// P1a (every CTA, its contiguous rows): CSR slots, work items at the default
+// chunk in both enumeration orders, candidate-list entries; max degree,
+// C sub-block entries and the 64-bit range check go to the level counters.
+__device__ void phase_scan_a(const LevelParams& P, bool learned)
+{
+    __shared__ unsigned long long red[NW][4];
+    const int l = P.l;
+    int r0, r1;
+    cta_rows(P, r0, r1);
+    unsigned long long v[4] = {0, 0, 0, 0};   // slots, items (S-shared), items (per edge), list entries
+    unsigned long long sq = 0;
+    int dmax = 0, rng = 0;
+    for (int i = r0 + (int)threadIdx.x; i < r1; i += NT) {
+        const int d = P.deg[i];
+        const int di = (P.vlmax && l > P.vlmax[i]) ? 0 : d;
+        v[0] += (unsigned long long)d;
+        v[1] += row_items(P.B, di, l, P.chunk0, false);
+        if (learned) v[2] += row_items(P.B, di, l, P.chunk0, true);
+        dmax = max(dmax, di);
+        if (di >= l + 1) {
+            if (P.B(di, l) == ~0ull) rng = 1;
+            sq += (unsigned long long)(di + 1) * (unsigned long long)(di + 1);
+            if (learned) v[3] += (unsigned long long)di * (unsigned long long)(di - 1);
+        }
+    }
+    sq = warp_sum_u64(sq);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        if (sq) atomicAdd(&P.lm->block_entries[l], sq);
+        if (dmax) atomicMax(&P.lm->maxdeg[l], dmax);
+    }
+    if (__any_sync(0xffffffffu, rng) && lane == 0) atomicOr(&P.lm->range_error, 1);
+    block_sum4(v, red);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) P.scan_part[(size_t)blockIdx.x * 4 + k] = v[k];
+}
+
+// P1b (every CTA, after a grid barrier): the enumeration order and chunk from
+// the totals (the chunk doubles while the items would not fit; each doubling
+// recounts and takes another barrier), then this CTA's rows' CSR offsets, item
+// offsets, candidate-list offsets and its part of the round histogram.
+// Returns false when a barrier failed.
+__device__ bool phase_scan_b(const LevelParams& P, bool learned, bool& lrn_out)
+{
+    __shared__ unsigned long long sbase[4], stot[4];
+    __shared__ unsigned long long rsum[NW][4];
+    __shared__ unsigned long long wsum[NW][3];
+    __shared__ unsigned long long hist[RND];
+    __shared__ int schunk, slrn;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int l = P.l;
+    int r0, r1;
+    cta_rows(P, r0, r1);
+    // totals of the CTAs, and the exclusive prefix for this CTA (fixed order)
+    // (thread c loads CTA c's partials; two block sums in a fixed order)
+    auto totals = [&]() {
+        unsigned long long v[4] = {0, 0, 0, 0}, u[4] = {0, 0, 0, 0};
+        if (t < (int)gridDim.x)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                v[k] = __ldcg(P.scan_part + (size_t)t * 4 + k);
+                u[k] = t < (int)blockIdx.x ? v[k] : 0ull;
+            }
+        block_sum4(v, rsum);
+        block_sum4(u, rsum);
+        if (t == 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                stot[k] = v[k];
+                sbase[k] = u[k];
+            }
+        __syncthreads();
+    };
+    totals();
+    if (t == 0) {
+        slrn = (learned && stot[3] <= P.perm_cap) ? 1 : 0;
+        schunk = P.chunk0;
+        if (learned && blockIdx.x == 0) P.lm->learned_on[l] = slrn;
+    }
+    __syncthreads();
+    const bool lrn = slrn != 0;
+    lrn_out = lrn;
+    int chunk = schunk;
+    for (int it = 0; it < 40 && stot[lrn ? 2 : 1] > P.item_cap && chunk <= (1 << 29); ++it) {
+        // recount this CTA's items at twice the chunk
+        chunk *= 2;
+        unsigned long long b = 0;
+        for (int i = r0 + t; i < r1; i += NT) {
+            const int di = (P.vlmax && l > P.vlmax[i]) ? 0 : P.deg[i];
+            b += row_items(P.B, di, l, chunk, lrn);
+        }
+        b = warp_sum_u64(b);
+        if (lane == 0) wsum[w][0] = b;
+        __syncthreads();
+        if (t == 0) {
+            unsigned long long x = 0;
+            for (int q = 0; q < NW; ++q) x += wsum[q][0];
+            P.scan_part[(size_t)blockIdx.x * 4 + (lrn ? 2 : 1)] = x;
+        }
+        if (!grid_sync(P.lm)) return false;
+        totals();
+    }
+    // this CTA's rows: exclusive scans of (slots, items, list entries), in tiles of NT rows
+    for (int q = t; q < RND; q += NT) hist[q] = 0;
+    __syncthreads();
+    unsigned long long ca = sbase[0], cb = sbase[lrn ? 2 : 1], cc = sbase[3];
+    unsigned long long ovf = 0;
+    for (int base = r0; base < r1; base += NT) {
+        const int i = base + t;
+        unsigned long long a = 0, b = 0, c = 0;
+        if (i < r1) {
+            const int d = P.deg[i];
+            const int di = (P.vlmax && l > P.vlmax[i]) ? 0 : d;
+            a = (unsigned long long)d;
+            b = row_items(P.B, di, l, chunk, lrn);
+            if (lrn && di >= l + 1) c = (unsigned long long)di * (unsigned long long)(di - 1);
+            if (b > RND - 1) ovf += b - (RND - 1);
+        }
+        hist_add(hist, b);
+        // inclusive warp scans, then the warp totals in order
+        unsigned long long ia = a, ib = b, ic = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long xa = __shfl_up_sync(0xffffffffu, ia, o);
+            const unsigned long long xb = __shfl_up_sync(0xffffffffu, ib, o);
+            const unsigned long long xc = __shfl_up_sync(0xffffffffu, ic, o);
+            if (lane >= o) { ia += xa; ib += xb; ic += xc; }
+        }
+        if (lane == 31) { wsum[w][0] = ia; wsum[w][1] = ib; wsum[w][2] = ic; }
+        __syncthreads();
+        unsigned long long pa = 0, pb = 0, pc = 0, ta = 0, tb = 0, tc = 0;
+        for (int q = 0; q < NW; ++q) {
+            if (q < w) { pa += wsum[q][0]; pb += wsum[q][1]; pc += wsum[q][2]; }
+            ta += wsum[q][0]; tb += wsum[q][1]; tc += wsum[q][2];
+        }
+        if (i < r1) {
+            P.row_off[i] = (long long)(ca + pa + ia - a);
+            P.item_off[i] = (long long)(cb + pb + ib - b);
+            if (P.poff) P.poff[i] = (long long)(cc + pc + ic - c);
+        }
+        ca += ta;
+        cb += tb;
+        cc += tc;
+        __syncthreads();
+    }
+    ovf = warp_sum_u64(ovf);
+    if (lane == 0 && ovf) atomicAdd(&hist[0], ovf);   // bin 0 carries the items past the first RND - 1
+    __syncthreads();
+    for (int q = t; q < RND; q += NT)
+        if (hist[q]) atomicAdd(&P.lm->round_hist[l][q], hist[q]);
+    if (blockIdx.x == gridDim.x - 1 && t == 0) {
+        const unsigned long long ea = stot[0], eb = stot[lrn ? 2 : 1], ec = stot[3];
+        P.row_off[P.p] = (long long)ea;
+        P.item_off[P.p] = (long long)eb;
+        if (P.poff) P.poff[P.p] = (long long)(lrn ? ec : 0);
+        P.lm->edges[l] = ea / 2;
+        P.lm->items[l] = eb;
+        P.lm->chunk[l] = chunk;
+        if (ea > P.nnz_cap || eb > P.item_cap) atomicOr(&P.lm->error, 16);
+    }
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -378,8 +557,8 @@ __device__ void phase_items(const LevelParams& P)
     __shared__ unsigned long long base[RND], cur[RND];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int l = P.l;
-    const int r0 = (int)((long long)P.p * blockIdx.x / gridDim.x);
-    const int r1 = (int)((long long)P.p * (blockIdx.x + 1) / gridDim.x);
+    int r0, r1;
+    cta_rows(P, r0, r1);
     for (int q = threadIdx.x; q < RND; q += NT) {
         cnt[q] = 0;
         cur[q] = 0;
@@ -399,6 +578,25 @@ __device__ void phase_items(const LevelParams& P)
     __syncthreads();
     if (lane == 0 && ovf) atomicAdd(&sovf, ovf);
     __syncthreads();
+    // first slot of each round, from the level's histogram of rows by item count
+    // (round c < RND - 1 holds the rows with more than c items, the last round
+    // the items past the first RND - 1 of every row)
+    __shared__ unsigned long long roff[RND], rh[RND];
+    for (int q = threadIdx.x; q < RND; q += NT) rh[q] = __ldcg(&P.lm->round_hist[l][q]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long n_round[RND], above = 0, off = 0;
+        for (int v = RND - 1; v >= 1; --v) {
+            above += rh[v];
+            n_round[v - 1] = above;
+        }
+        n_round[RND - 1] = rh[0];
+        for (int q = 0; q < RND; ++q) {
+            roff[q] = off;
+            off += n_round[q];
+        }
+    }
+    __syncthreads();
     if (threadIdx.x < RND) {
         const int q = threadIdx.x;
         unsigned long long nq = 0;
@@ -407,7 +605,7 @@ __device__ void phase_items(const LevelParams& P)
         } else {
             nq = sovf;
         }
-        base[q] = nq ? P.lm->round_off[l][q] + atomicAdd(&P.lm->round_cur[l][q], nq) : 0;
+        base[q] = nq ? roff[q] + atomicAdd(&P.lm->round_cur[l][q], nq) : 0;
     }
     __syncthreads();
     for (int i = r0 + w; i < r1; i += NW) {
@@ -1136,8 +1334,15 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
     // the neighbour lists, partner slots and word prefixes are reused (the work
     // items, which depend on l, are rebuilt)
     const bool reuse = l >= 2 && ld_cg(&lm->removed[l - 1]) == 0ull && *(volatile int*)&lm->csr_level == l - 1;
-    if (blockIdx.x == 0) phase_scan(P, LEARNED && P.learned && l >= 2);
-    if (!reuse && (blockIdx.x != 0 || gridDim.x == 1)) phase_prefix(P, FP32);
+    const bool want_lrn = LEARNED && P.learned && l >= 2;
+    const bool one = P.p <= 32 * NT;   // one CTA scans graphs up to 16384 rows (no second barrier)
+    if (one) {
+        if (blockIdx.x == 0) phase_scan_one(P, want_lrn);
+        if (!reuse && (blockIdx.x != 0 || gridDim.x == 1)) phase_prefix(P, FP32, 1);
+    } else {
+        phase_scan_a(P, want_lrn);
+        if (!reuse) phase_prefix(P, FP32, 0);
+    }
     if (!grid_sync(lm)) {
         if (timer) signal_host(P, 2);
         return;
@@ -1150,6 +1355,11 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
         return;
     }
     if (timer) signal_host(P, 1);
+    if (!one) {
+        bool lrn_scan = false;
+        if (!phase_scan_b(P, want_lrn, lrn_scan)) return;
+        if (!grid_sync(lm)) return;
+    }
     phase_fill(P, reuse);
     if (!grid_sync(lm)) return;
     if (timer) lm->csr_level = l;

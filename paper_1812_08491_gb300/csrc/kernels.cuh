@@ -37,7 +37,7 @@ struct LevelMeta {
     int range_error;                       // a subset count saturated 64 bits
     unsigned bar_count, bar_gen;           // grid barrier state
     unsigned long long live[LV];           // queued tests rechecked (not decided already)
-    unsigned long long round_off[LV][RND]; // first dispatch slot of each round
+    unsigned long long round_hist[LV][RND]; // rows by item count (bin 0: items past RND - 1)
     unsigned long long round_cur[LV][RND]; // slots of each round handed to CTAs so far
 };
 
@@ -124,6 +124,7 @@ struct LevelParams {
     const int* vlmax;              // batch: the last level of each vertex's problem
     unsigned long long* prob_serial;   // batch: serial-order tests per problem and level (nprob x LV)
     int ctas_per_sm;               // launch shape (0: as many as fit, at most 2)
+    unsigned long long* scan_part; // per CTA: CSR slots, items (two orders), list entries
     const Meta* meta0;             // level 0's counters: a level does not run after an error
     unsigned long long qcap0;      // there, or an overflow of its recheck queue
     // learned ordering (levels >= 2, FP32 mode)

@@ -211,6 +211,7 @@ struct DataView {
     int xf64 = 0;
     const double* mu = nullptr;
     const double* isd = nullptr;
+    const float2* mup = nullptr;   // the mean as an FP32 pair (FP32 mode)
 };
 
 cupc_status prepare(cupc_ctx* ctx, const Input& in, bool fp32, const void** Cuse, const double** c64_out,
@@ -271,6 +272,7 @@ cupc_status prepare(cupc_ctx* ctx, const Input& in, bool fp32, const void** Cuse
     cupc_status s;
     if ((s = ensure(ctx, ctx->mu, (size_t)p * 8)) != CUPC_OK) return s;
     if ((s = ensure(ctx, ctx->isd, (size_t)p * 8)) != CUPC_OK) return s;
+    if (fp32 && (s = ensure(ctx, ctx->mup, (size_t)p * 8)) != CUPC_OK) return s;
     // FP64 rows only for the FP64 product (plain mode); FP32 mode keeps the bf16 split
     if (!fp32 && (s = ensure(ctx, ctx->z64, (size_t)p * ldz * 8)) != CUPC_OK) return s;
     if (fp32) {
@@ -279,6 +281,7 @@ cupc_status prepare(cupc_ctx* ctx, const Input& in, bool fp32, const void** Cuse
     }
     TIMED(CUPC_K_STANDARDIZE,
           launch_standardize(in.dtype, xv, ldv, n, p, (double*)ctx->mu.p, (double*)ctx->isd.p,
+                             fp32 ? (float2*)ctx->mup.p : nullptr,
                              fp32 ? nullptr : (double*)ctx->z64.p, ldz, fp32 ? ctx->zhi.p : nullptr,
                              fp32 ? ctx->zlo.p : nullptr, ldb, meta, ctx->stream));
     dv->xv = xv;
@@ -286,6 +289,7 @@ cupc_status prepare(cupc_ctx* ctx, const Input& in, bool fp32, const void** Cuse
     dv->xf64 = in.dtype == CUPC_F64 ? 1 : 0;
     dv->mu = (const double*)ctx->mu.p;
     dv->isd = (const double*)ctx->isd.p;
+    dv->mup = fp32 ? (const float2*)ctx->mup.p : nullptr;
     if (!fp32) {
         if ((s = ensure(ctx, ctx->c64, (size_t)p * p * 8)) != CUPC_OK) return s;
         TIMED(CUPC_K_CORRELATION,
@@ -300,7 +304,7 @@ cupc_status prepare(cupc_ctx* ctx, const Input& in, bool fp32, const void** Cuse
         if ((s = ensure(ctx, ctx->cws, wsb)) != CUPC_OK) return s;
         TIMED(CUPC_K_CORRELATION, launch_corr_tc(ctx->zhi.p, ctx->zlo.p, ldb, p, n, (float*)ctx->cws.p,
                                                  (float*)ctx->c32.p, ctx->num_sms, &meta->error, ctx->stream));
-        kcount[CUPC_K_CORRELATION]++;  // the K-slice reduction
+        if (nsplit > 1) kcount[CUPC_K_CORRELATION]++;  // the K-slice reduction
         *Cuse = ctx->c32.p;
     }
     return CUPC_OK;
@@ -406,7 +410,9 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         rp.xf64 = dv.xf64;
         rp.mu = dv.mu;
         rp.isd = dv.isd;
+        rp.mup = dv.mup;
         rp.n = (int)n;
+        rp.inv_n = 1.0 / (double)n;
         rp.c64 = c64;
         rp.p = p;
         const double r = std::tanh(fisher_tau(alpha, n, 0));
@@ -521,7 +527,9 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             LP.xf64 = dv.xf64;
             LP.mu = dv.mu;
             LP.isd = dv.isd;
+            LP.mup = dv.mup;
             LP.n = (int)n;
+            LP.inv_n = 1.0 / (double)n;
             LP.c64 = c64;
             LP.part = fp32 ? (double*)ctx->part.p : nullptr;
             LP.part_cap = kPartBytes / sizeof(double);
@@ -735,7 +743,7 @@ void ctx_release(cupc_ctx* c)
     if (--c->refs > 0) return;
     cudaSetDevice(c->device);
     cupc_ctx* ctx = c;
-    Buf* all[] = {&c->xin, &c->xt, &c->mu, &c->isd, &c->z64, &c->zhi, &c->zlo, &c->cws, &c->c64, &c->c32, &c->cin,
+    Buf* all[] = {&c->xin, &c->xt, &c->mu, &c->isd, &c->mup, &c->z64, &c->zhi, &c->zlo, &c->cws, &c->c64, &c->c32, &c->cin,
                   &c->deg, &c->row_off, &c->item_off, &c->item_row, &c->cols, &c->srow, &c->partner, &c->wpre,
                   &c->best, &c->queue, &c->binom, &c->meta, &c->lmeta, &c->backup[0], &c->backup[1],
                   &c->part};

@@ -55,7 +55,7 @@ struct BatchPlan {
     long long words = 0, xelems = 0, zelems = 0, celems = 0, ldb = 0;
     size_t ws_bytes = 0;
     unsigned long long nnz_cap = 0, item_cap = 0, qcap = 0, rec_cap = 0;
-    Buf d_probs, d_vprob, d_vlmax, d_units, d_tiles, x_in, xt, mu, isd, zhi, zlo, ws, c32, bits, bits0, backup;
+    Buf d_probs, d_vprob, d_vlmax, d_units, d_tiles, x_in, xt, mu, isd, mup, zhi, zlo, ws, c32, bits, bits0, backup;
     Buf deg, row_off, item_off, item_row, item_c, live, scan_part, cols, srow, partner, wpre, best, queue, part, rec, meta, lmeta, pserial;
     Binom binom{};
     // pinned host copies written at the end of each run
@@ -81,7 +81,7 @@ void plan_destroy(cupc_ctx* ctx, BatchPlan* B)
     if (B->gs) cudaStreamSynchronize(B->gs);
     if (B->exec) cudaGraphExecDestroy(B->exec);
     Buf* all[] = {&B->d_probs, &B->d_vprob, &B->d_vlmax, &B->d_units, &B->d_tiles, &B->x_in, &B->xt,      &B->mu,
-                  &B->isd,     &B->zhi,     &B->zlo,     &B->ws,   &B->c32,     &B->bits,
+                  &B->isd,     &B->mup,     &B->zhi,     &B->zlo,     &B->ws,   &B->c32,     &B->bits,
                   &B->bits0,   &B->backup,  &B->deg,     &B->row_off, &B->item_off, &B->item_row, &B->item_c, &B->live, &B->scan_part, &B->cols,
                   &B->srow,    &B->partner, &B->wpre,    &B->best,    &B->queue, &B->part,   &B->rec,
                   &B->meta,    &B->lmeta,   &B->pserial};
@@ -194,6 +194,7 @@ cupc_status allocate(cupc_ctx* ctx, BatchPlan& B)
         {&B.xt, K.layout == CUPC_LAYOUT_SAMPLE_MAJOR ? (size_t)B.xelems * es : 0},
         {&B.mu, (size_t)B.P * 8},
         {&B.isd, (size_t)B.P * 8},
+        {&B.mup, (size_t)B.P * 8},
         {&B.zhi, (size_t)B.P * B.ldb * 2},
         {&B.zlo, (size_t)B.P * B.ldb * 2},
         {&B.ws, B.ws_bytes},
@@ -273,14 +274,15 @@ cupc_status issue(cupc_ctx* ctx, BatchPlan& B, cudaStream_t st, bool capturing)
         BCU(launch_transpose_batch(K.dtype, probs, K.nprob, B.pmax, B.nmax, B.xt.p, st));
         ++launches;
     }
-    BCU(launch_standardize(K.dtype, nullptr, 0, 0, B.P, (double*)B.mu.p, (double*)B.isd.p, nullptr, 0, B.zhi.p, B.zlo.p,
-                           B.ldb, meta, st, vprob, probs));
+    BCU(launch_standardize(K.dtype, nullptr, 0, 0, B.P, (double*)B.mu.p, (double*)B.isd.p, (float2*)B.mup.p, nullptr,
+                           0, B.zhi.p, B.zlo.p, B.ldb, meta, st, vprob, probs));
     ++launches;
     BCU(stage(1));
     // every problem's C on the tensor cores
     BCU(launch_corr_tc_batch(B.zhi.p, B.zlo.p, B.ldb, B.P, B.d_units.p, (int)B.units.size(), B.d_tiles.p,
-                             (int)B.tiles.size(), probs, (float*)B.ws.p, (float*)B.c32.p, &meta->error, st));
-    launches += 2;
+                             (int)B.tiles.size(), probs, (float*)B.ws.p, (float*)B.c32.p, ctx_num_sms(ctx),
+                             &meta->error, st));
+    launches += (B.units.empty() ? 0 : 1) + (B.tiles.empty() ? 0 : 1);
     BCU(stage(2));
     // level 0 and its FP64 rechecks
     BCU(launch_level0(1, B.c32.p, B.P, 0, 0.0, kBand0, (unsigned*)B.bits.p, (QEntry*)B.queue.p, B.qcap, meta, st,
@@ -290,6 +292,7 @@ cupc_status issue(cupc_ctx* ctx, BatchPlan& B, cudaStream_t st, bool capturing)
     rp.xf64 = K.dtype == CUPC_F64 ? 1 : 0;
     rp.mu = (const double*)B.mu.p;
     rp.isd = (const double*)B.isd.p;
+    rp.mup = (const float2*)B.mup.p;
     rp.p = B.P;
     rp.queue = (const QEntry*)B.queue.p;
     rp.qcap = B.qcap;
@@ -336,6 +339,7 @@ cupc_status issue(cupc_ctx* ctx, BatchPlan& B, cudaStream_t st, bool capturing)
     LP.xf64 = K.dtype == CUPC_F64 ? 1 : 0;
     LP.mu = (const double*)B.mu.p;
     LP.isd = (const double*)B.isd.p;
+    LP.mup = (const float2*)B.mup.p;
     LP.nmax = B.nmax;
     LP.part = (double*)B.part.p;
     LP.part_cap = kPartBytes / sizeof(double);

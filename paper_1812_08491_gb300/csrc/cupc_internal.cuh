@@ -245,6 +245,70 @@ __device__ __forceinline__ double widen_f32(float x)
     return __longlong_as_double((long long)(sign | (ex << 52) | man));
 }
 
+// ---------------------------------------------------------------------------
+// Compensated FP32 pairs ("double-word" numbers hi + lo): Knuth's two-sum,
+// Dekker's fast two-sum (|a| >= |b|) and the accurate pair addition of
+// Joldes, Muller and Popescu (2017), relative error below 3 * 2^-48. GB300
+// runs FP32 at many times its FP64 rate. The roundings are spelled out
+// (__fadd_rn, __fmul_rn), so no contraction into a fused multiply-add can
+// change an error-free transformation.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ void pair_add(float& xh, float& xl, float yh, float yl)
+{
+    float sh, sl, th, tl, vh, vl;
+    two_sum(xh, yh, sh, sl);
+    two_sum(xl, yl, th, tl);
+    sl = __fadd_rn(sl, th);
+    fast_two_sum(sh, sl, vh, vl);
+    vl = __fadd_rn(vl, tl);
+    fast_two_sum(vh, vl, xh, xl);
+}
+
+// S += (ah + al)(bh + bl) for a pair accumulator (Sh, Sl) kept in the
+// compensated-dot form of Ogita, Rump and Oishi (2005): the product's leading
+// float, its exact rounding error (fma) and the cross terms, the leading sum's
+// error by two-sum, all errors gathered in Sl. Sl is folded back into Sh
+// (two_sum) every few terms by the caller.
+__device__ __forceinline__ void pair_dot_acc(float& Sh, float& Sl, float ah, float al, float bh, float bl)
+{
+    const float ph = __fmul_rn(ah, bh);
+    float pe = fmaf(ah, bh, -ph);
+    pe = fmaf(ah, bl, pe);
+    pe = fmaf(al, bh, pe);
+    pe = fmaf(al, bl, pe);
+    float s, e;
+    two_sum(Sh, ph, s, e);
+    Sh = s;
+    Sl = __fadd_rn(Sl, __fadd_rn(e, pe));
+}
+
+// One FP32 variable's row for the compensated rechecks: x - mu as a pair
+// (dh, dl), the FP64 mean given as the pair mh + ml (2^-48 relative):
+// x - mh exactly by two-sum, then minus ml.
+struct XRowP {
+    const float* p;
+    float mh, ml;
+    __device__ __forceinline__ void centred(int k, float& dh, float& dl) const
+    {
+        float e;
+        two_sum(__ldg(p + k), -mh, dh, e);
+        dl = __fsub_rn(e, ml);
+    }
+};
+
 // One variable's row for the rechecks: its variable-major data (FP32 or FP64)
 // and the moments of the standardisation, z = (x - mu) * isd. The Gram sums
 // below accumulate the centred values x - mu and apply isd_a isd_b once.

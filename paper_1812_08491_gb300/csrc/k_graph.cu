@@ -119,12 +119,49 @@ cudaError_t launch_degree(const unsigned* bits, int p, int W, int* deg, Meta* me
 
 // ---------------------------------------------------------------------------
 // Level-0 FP64 rechecks: one block per queued pair (S empty: rho = C_ij).
+// FP32 data: the centred sum in compensated FP32 pairs (every thread strides
+// the samples in the compensated-dot form, folded every 8 samples; a fixed
+// xor tree per warp, the warps in order), widened to FP64 once; FP64 data:
+// the FP64 block sum.
 // ---------------------------------------------------------------------------
 constexpr int RC_THREADS = 256;
+
+__device__ __forceinline__ double pair_centred_dot(const XRowP& A, const XRowP& B, int n, float2* red)
+{
+    float sh = 0.f, sl = 0.f;
+    for (int kb = threadIdx.x; kb < n; kb += RC_THREADS * 8) {
+        const int ke = min(n, kb + RC_THREADS * 8);
+#pragma unroll 8
+        for (int k = kb; k < ke; k += RC_THREADS) {
+            float ah, al, bh, bl;
+            A.centred(k, ah, al);
+            B.centred(k, bh, bl);
+            pair_dot_acc(sh, sl, ah, al, bh, bl);
+        }
+        two_sum(sh, sl, sh, sl);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+        pair_add(sh, sl, oh, ol);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = make_float2(sh, sl);
+    __syncthreads();
+    double g = 0.0;
+    if (threadIdx.x == 0) {
+        float h = red[0].x, l = red[0].y;
+        for (int k = 1; k < RC_THREADS / 32; ++k) pair_add(h, l, red[k].x, red[k].y);
+        g = widen_f32(h) + widen_f32(l);
+    }
+    __syncthreads();
+    return g;  // valid in thread 0
+}
 
 __global__ void __launch_bounds__(RC_THREADS) k_recheck0(Recheck0Params P)
 {
     __shared__ double red[RC_THREADS / 32];
+    __shared__ float2 redp[RC_THREADS / 32];
     unsigned long long nq = P.meta->queue_len;
     if (nq > P.qcap) nq = P.qcap;
     unsigned long long done = 0;
@@ -134,17 +171,30 @@ __global__ void __launch_bounds__(RC_THREADS) k_recheck0(Recheck0Params P)
         double G[1];
         if (P.c64) {
             G[0] = P.c64[(size_t)E.a * P.p + E.b];
+        } else if (!P.xf64) {
+            // FP32 data rows of the pair (a batch problem's own rows, its sample count)
+            const int n = D ? D->n : P.n;
+            XRowP R[2];
+            const int V[2] = {E.a, E.b};
+            for (int a = 0; a < 2; ++a) {
+                const float2 m = P.mup[V[a]];
+                R[a].mh = m.x;
+                R[a].ml = m.y;
+                R[a].p = D ? (const float*)D->xv + (size_t)(V[a] - D->off) * D->n
+                           : (const float*)P.xv + (size_t)V[a] * P.ldx;
+            }
+            const double g = pair_centred_dot(R[0], R[1], n, redp);
+            G[0] = g * (P.isd[E.a] * P.isd[E.b]) * (D ? D->inv_n : P.inv_n);
         } else {
-            // the pair's data rows (a batch problem's own rows, its sample count)
-            const int es = P.xf64 ? 8 : 4;
+            // the pair's FP64 data rows
             const int V[2] = {E.a, E.b};
             XRow R[2];
             for (int a = 0; a < 2; ++a) {
-                R[a].f64 = P.xf64;
+                R[a].f64 = 1;
                 R[a].mu = P.mu[V[a]];
                 R[a].isd = P.isd[V[a]];
-                R[a].p = D ? (const char*)D->xv + (size_t)(V[a] - D->off) * D->n * es
-                           : (const char*)P.xv + (size_t)V[a] * P.ldx * es;
+                R[a].p = D ? (const char*)D->xv + (size_t)(V[a] - D->off) * D->n * 8
+                           : (const char*)P.xv + (size_t)V[a] * P.ldx * 8;
             }
             c_block<2, RC_THREADS>(R, D ? D->n : P.n, 2, G, red);
         }

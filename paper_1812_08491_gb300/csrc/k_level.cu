@@ -964,7 +964,6 @@ __device__ void phase_ci_edge(const LevelParams& P)
 // spreading each test over several SMs shortens the phase when few tests
 // are queued. The queue is processed in batches that fit the partial buffer.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int recheck_slices(int n) { return max(1, min(8, n / 1024)); }
 
 // Data row of vertex v for the rechecks (its problem's rows in a batch) and
 // its problem's sample count.
@@ -986,6 +985,138 @@ __device__ __forceinline__ XRow xrow(const LevelParams& P, int v, int& n)
     return r;
 }
 
+// FP32 data: the row as read by the compensated rechecks, and 1/n of v's problem.
+__device__ __forceinline__ XRowP xrowp(const LevelParams& P, int v, int& n)
+{
+    const ProbDesc* D = prob_of(P.vprob, P.probs, v);
+    XRowP r;
+    const float2 m = P.mup[v];
+    r.mh = m.x;
+    r.ml = m.y;
+    if (D) {
+        r.p = (const float*)D->xv + (size_t)(v - D->off) * D->n;
+        n = D->n;
+    } else {
+        r.p = (const float*)P.xv + (size_t)v * P.ldx;
+        n = P.n;
+    }
+    return r;
+}
+
+__device__ __forceinline__ double inv_n_of(const LevelParams& P, int v)
+{
+    const ProbDesc* D = prob_of(P.vprob, P.probs, v);
+    return D ? D->inv_n : P.inv_n;
+}
+
+__device__ __forceinline__ int n_of(const LevelParams& P, int v)
+{
+    const ProbDesc* D = prob_of(P.vprob, P.probs, v);
+    return D ? D->n : P.n;
+}
+
+// Lanes of a recheck warp: entry x of the Gram block (x = lane mod DP, DP = D
+// rounded up to a power of two, at most 32) and sample (or slice) group
+// g = lane / DP of G = 32 / DP; the rolled loops below keep the code small,
+// since a level runs this phase once, from a cold instruction cache.
+template <int LB>
+struct RecheckLanes {
+    static constexpr int M = LB + 2;
+    static constexpr int D = M * (M - 1) / 2;
+    static constexpr int DP = D <= 4 ? 4 : D <= 8 ? 8 : D <= 16 ? 16 : 32;
+    static constexpr int G = 32 / DP;
+};
+
+// Packed Gram index x -> (a, b2), a < b2: x = b2 (b2 - 1) / 2 + a.
+__device__ __forceinline__ void gram_pair(int x, int& a, int& b2)
+{
+    b2 = 1;
+    while ((b2 + 1) * b2 / 2 <= x) ++b2;
+    a = x - b2 * (b2 - 1) / 2;
+}
+
+// Asks L2 for the 128-byte lines of bytes [b0, b1) of a row, lines g, g + G,
+// ... of them, so that a lane's sequential walk through its slice does not
+// wait on one line at a time.
+__device__ __forceinline__ void prefetch_lines(const char* base, long long b0, long long b1, int g, int G)
+{
+    for (long long c = (b0 >> 7) + g; c <= ((b1 - 1) >> 7); c += G)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (c << 7)));
+}
+
+// Member g of the test's (i, j, S) list (0 = i, 1 = j, 2 + c = S_c).
+__device__ __forceinline__ int gram_var(const QEntry* E, int i, int j, int g)
+{
+    return g == 0 ? i : g == 1 ? j : E->S[g - 2];
+}
+
+// Gram entries sum_s (x_as - mu_a)(x_bs - mu_b) over sample slice k of S of
+// one queued test, by one warp: the lanes of entry x stride the slice by G and
+// a fixed xor tree adds the G groups. FP32 data: compensated FP32 pairs
+// (pair_dot_acc, folded every 8 samples; about 2^-48 relative per term like an
+// FP64 sum), out as the pair (hi, lo) per entry; FP64 data: FP64 fma, out as
+// a double.
+template <int LB, bool PAIRS>
+__device__ __forceinline__ void recheck_unit(const LevelParams& P, const QEntry* E, int i, int j, int k, int S,
+                                             double* out)
+{
+    using L = RecheckLanes<LB>;
+    const int lane = threadIdx.x & 31, g = lane / L::DP;
+    const int m = P.l + 2;
+    const int zn = n_of(P, i);
+    const int k0 = (int)((long long)zn * k / S), k1 = (int)((long long)zn * (k + 1) / S);
+    for (int x0 = 0; x0 < L::D; x0 += L::DP) {
+        const int x = x0 + lane % L::DP;
+        int a, b2;
+        gram_pair(x, a, b2);
+        const bool act = x < L::D && b2 < m;
+        int dummy;
+        if constexpr (PAIRS) {
+            float h = 0.f, lo = 0.f;
+            if (act) {
+                const XRowP A = xrowp(P, gram_var(E, i, j, a), dummy), B = xrowp(P, gram_var(E, i, j, b2), dummy);
+                if (k1 > k0) {
+                    prefetch_lines((const char*)A.p, 4ll * k0, 4ll * k1, g, L::G);
+                    prefetch_lines((const char*)B.p, 4ll * k0, 4ll * k1, g, L::G);
+                }
+                for (int kb = k0 + g; kb < k1; kb += L::G * 8) {
+                    const int ke = min(k1, kb + L::G * 8);
+#pragma unroll 2
+                    for (int kk = kb; kk < ke; kk += L::G) {
+                        float ah, al, bh, bl;
+                        A.centred(kk, ah, al);
+                        B.centred(kk, bh, bl);
+                        pair_dot_acc(h, lo, ah, al, bh, bl);
+                    }
+                    two_sum(h, lo, h, lo);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o >= L::DP; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+                pair_add(h, lo, oh, ol);
+            }
+            if (x < L::D && g == 0) ((float2*)out)[x] = make_float2(h, lo);
+        } else {
+            double acc = 0.0;
+            if (act) {
+                const XRow A = xrow(P, gram_var(E, i, j, a), dummy), B = xrow(P, gram_var(E, i, j, b2), dummy);
+                const double* pa = (const double*)A.p;
+                const double* pb = (const double*)B.p;
+                if (k1 > k0) {
+                    prefetch_lines((const char*)pa, 8ll * k0, 8ll * k1, g, L::G);
+                    prefetch_lines((const char*)pb, 8ll * k0, 8ll * k1, g, L::G);
+                }
+#pragma unroll 4
+                for (int kk = k0 + g; kk < k1; kk += L::G) acc = fma(__ldg(pa + kk) - A.mu, __ldg(pb + kk) - B.mu, acc);
+            }
+#pragma unroll
+            for (int o = 16; o >= L::DP; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (x < L::D && g == 0) out[x] = acc;
+        }
+    }
+}
+
 // A queued test whose outcome cannot change the level's result: the edge's
 // removal is already decided by a definitive FP32 independence at a smaller
 // rank on the side that wins (canonical: the smaller endpoint's side first,
@@ -1001,10 +1132,11 @@ __device__ __forceinline__ bool recheck_moot(const LevelParams& P, long long e, 
     return bf != RANK_NONE || be < s;              // the first side already removes it
 }
 
-// FP64 recheck of the queued tests in batches that fit the partial-sum buffer:
-// one warp per (test, sample slice) forms the slice's Gram entries of the
-// m = l + 2 variables from the data rows, one thread per test adds the slices in
-// order and decides with the FP64 factorisation.
+// Recheck of the queued tests in batches that fit the partial-sum buffer: one
+// warp per (test, sample slice) forms the slice's Gram entries of the
+// m = l + 2 variables from the data rows (FP64, or compensated FP32 pairs for
+// FP32 data), one warp per test adds the slices in a fixed order and decides
+// with the FP64 factorisation.
 template <int LB>
 __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
 {
@@ -1013,6 +1145,8 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
     __shared__ double sA[NW][M][M];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool timer = (blockIdx.x == 0 && threadIdx.x == 0);
+    // FP32 data: Gram sums in compensated FP32 pairs (GB300's FP64 pipe is narrow)
+    const bool pairs = !P.c64 && !P.xf64;
     unsigned long long tp = timer ? gtimer() : 0;
     // the queued tests whose outcome can still matter, in queue order
     for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < (long long)nq;
@@ -1030,12 +1164,12 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
     // consecutive units go to consecutive CTAs, so a short list spreads over SMs
     const long long gw = (long long)warp * gridDim.x + blockIdx.x;
     const long long nwarps = (long long)gridDim.x * NW;
-    // slices per test, the same for every test of the level: enough for the
-    // sample count (a batch takes its largest n), and enough units to occupy
-    // every warp when the list is short
-    // (the combine sums S x D partials per test: a large Gram block takes fewer)
-    const int sp = (int)min((long long)max(8, 1024 / D), (nwarps + (long long)nl - 1) / (long long)nl);
-    const int S = min(64, max(recheck_slices(P.vprob ? P.nmax : P.n), sp));
+    // slices per test, the same for every test of the level: about sqrt(n),
+    // which balances a lane's samples in a slice against its slices in the
+    // combine, but no more than about two units per warp
+    const int nref = P.vprob ? P.nmax : P.n;
+    const long long room = max(1ll, (2 * nwarps + (long long)nl - 1) / (long long)nl);
+    const int S = (int)max(1ll, min((long long)min(256, max(1, (int)sqrtf((float)nref))), room));
     const long long batch = max(1ll, (long long)(P.part_cap / ((unsigned long long)S * D)));
     unsigned long long done = 0;
     for (long long q0 = 0; q0 < (long long)nl; q0 += batch) {
@@ -1049,37 +1183,10 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
             const int i = P.srow[e], j = P.cols[e];
             double* out = P.part + (size_t)u * D;
             if (P.c64) continue;
-            int V[M];
-            V[0] = i;
-            V[1] = j;
-#pragma unroll
-            for (int c = 0; c < LB; ++c) V[2 + c] = (c < P.l) ? E->S[c] : i;
-            const int m = P.l + 2;
-            double G[D];
-#pragma unroll
-            for (int t = 0; t < D; ++t) G[t] = 0.0;
-            int zn = 0;
-            XRow R[M];
-#pragma unroll
-            for (int a = 0; a < M; ++a) R[a] = xrow(P, a < m ? V[a] : V[0], zn);
-            const int k0 = (int)((long long)zn * k / S), k1 = (int)((long long)zn * (k + 1) / S);
-#pragma unroll 4
-            for (int kk = k0 + lane; kk < k1; kk += 32) {
-                double x[M];
-#pragma unroll
-                for (int a = 0; a < M; ++a) x[a] = (a < m) ? R[a].centred(kk) : 0.0;
-#pragma unroll
-                for (int b2 = 1; b2 < M; ++b2)
-#pragma unroll
-                    for (int a = 0; a < b2; ++a) G[b2 * (b2 - 1) / 2 + a] = fma(x[a], x[b2], G[b2 * (b2 - 1) / 2 + a]);
-            }
-#pragma unroll
-            for (int t = 0; t < D; ++t) {
-                double g = G[t];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-                if (lane == 0) out[t] = g;
-            }
+            if (pairs)
+                recheck_unit<LB, true>(P, E, i, j, k, S, out);
+            else
+                recheck_unit<LB, false>(P, E, i, j, k, S, out);
         }
         if (blockIdx.x == 0) {
             __syncthreads();
@@ -1124,33 +1231,66 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
                     }
                 }
             } else {
-                // centred sums times isd_a isd_b / n; lane a holds isd of V_a
-                int zn = 0;
-                xrow(P, i, zn);
-                const double inv_n = 1.0 / (double)zn;
-                int vl = i;
+                // the slices of entry x in order within each of the G lane groups
+                // (slice g, g + G, ...), then a fixed xor tree over the groups;
+                // the entry's lane scales by isd_a isd_b / n (the diagonal holds
+                // isd until then). FP32 data: pairs, widened to FP64 once.
+                using RL = RecheckLanes<LB>;
+                const int g = lane / RL::DP;
+                const double inv_n = inv_n_of(P, i);
+                if (lane < m) A[pos(lane)][pos(lane)] = P.isd[gram_var(E, i, j, lane)];
+                __syncwarp();
+                for (int x0 = 0; x0 < D; x0 += RL::DP) {
+                    const int x = x0 + lane % RL::DP;
+                    int a, b2;
+                    gram_pair(x, a, b2);
+                    double v = 0.0;
+                    if (pairs) {
+                        const float2* pt2 = (const float2*)pt;
+                        float h = 0.f, lo = 0.f;
+                        if (x < D) {
+                            // sixteen loads in flight, then their pair additions in order
+                            int s2 = g;
+                            for (; s2 + 15 * RL::G < S; s2 += 16 * RL::G) {
+                                float2 w[16];
 #pragma unroll
-                for (int a = 0; a < M; ++a)
-                    if (lane == a) vl = V[a];
-                const double isd_l = (lane < m) ? P.isd[vl] : 0.0;
-                // entry x: lane q holds slices q and q + 32 (S <= 64), then a fixed
-                // xor-shuffle tree; the loads of several entries are in flight at once
-#pragma unroll 4
-                for (int x = 0; x < D; ++x) {
-                    int b2 = 1;
-                    while ((b2 + 1) * b2 / 2 <= x) ++b2;
-                    const int a = x - b2 * (b2 - 1) / 2;
-                    const double sa = __shfl_sync(0xffffffffu, isd_l, a);
-                    const double sb = __shfl_sync(0xffffffffu, isd_l, b2);
-                    double g = (lane < S) ? __ldcg(pt + (size_t)lane * D + x) : 0.0;
-                    if (lane + 32 < S) g += __ldcg(pt + (size_t)(lane + 32) * D + x);
+                                for (int u = 0; u < 16; ++u) w[u] = __ldcg(pt2 + (size_t)(s2 + u * RL::G) * D + x);
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-                    if (lane == 0 && b2 < m) {
+                                for (int u = 0; u < 16; ++u) pair_add(h, lo, w[u].x, w[u].y);
+                            }
+                            for (; s2 < S; s2 += RL::G) {
+                                const float2 w = __ldcg(pt2 + (size_t)s2 * D + x);
+                                pair_add(h, lo, w.x, w.y);
+                            }
+                        }
+#pragma unroll
+                        for (int o = 16; o >= RL::DP; o >>= 1) {
+                            const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+                            const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+                            pair_add(h, lo, oh, ol);
+                        }
+                        v = widen_f32(h) + widen_f32(lo);
+                    } else {
+                        if (x < D) {
+                            int s2 = g;
+                            for (; s2 + 15 * RL::G < S; s2 += 16 * RL::G) {
+                                double w[16];
+#pragma unroll
+                                for (int u = 0; u < 16; ++u) w[u] = __ldcg(pt + (size_t)(s2 + u * RL::G) * D + x);
+#pragma unroll
+                                for (int u = 0; u < 16; ++u) v += w[u];
+                            }
+                            for (; s2 < S; s2 += RL::G) v += __ldcg(pt + (size_t)s2 * D + x);
+                        }
+#pragma unroll
+                        for (int o = 16; o >= RL::DP; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    }
+                    if (x < D && g == 0 && b2 < m) {
                         const int pa = pos(a), pb = pos(b2);
-                        A[max(pa, pb)][min(pa, pb)] = g * (sa * sb) * inv_n;
+                        A[max(pa, pb)][min(pa, pb)] = v * (A[pa][pa] * A[pb][pb]) * inv_n;
                     }
                 }
+                __syncwarp();
             }
             if (lane < m) A[lane][lane] = 1.0;
             __syncwarp();

@@ -52,37 +52,9 @@ __global__ void k_transpose_batch(const ProbDesc* __restrict__ probs, T* __restr
 }
 
 // ---------------------------------------------------------------------------
-// Compensated FP32 pairs ("double-word" numbers hi + lo, |lo| <= ulp(hi)/2):
-// the error-free sums of Knuth (two_sum) and Dekker (fast_two_sum, |a| >= |b|)
-// and the accurate pair addition of Joldes, Muller and Popescu (2017), whose
-// relative error is below 3 * 2^-48. GB300 runs FP32 at many times its FP64
-// rate, so moments of FP32 data are accumulated in pairs and only the
-// per-thread partial sums are combined in FP64.
+// FP32 data: moments in compensated FP32 pairs (two_sum, pair_add of the
+// shared header); only the per-warp partial sums are widened to FP64.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
-{
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e)
-{
-    s = a + b;
-    e = b - (s - a);
-}
-
-__device__ __forceinline__ void pair_add(float& xh, float& xl, float yh, float yl)
-{
-    float sh, sl, th, tl, vh, vl;
-    two_sum(xh, yh, sh, sl);
-    two_sum(xl, yl, th, tl);
-    sl += th;
-    fast_two_sum(sh, sl, vh, vl);
-    vl += tl;
-    fast_two_sum(vh, vl, xh, xl);
-}
-
 // bf16 bit pattern of a finite float, rounded to nearest with ties to even,
 // by integer arithmetic on the IEEE encoding (add half an ulp of the target
 // minus one, plus the kept lowest bit, and truncate). Conversion instructions
@@ -119,7 +91,7 @@ __device__ __forceinline__ void shifted_moments(const T* __restrict__ row, int n
                 float dh, dl;
                 two_sum(row[k], -K, dh, dl);
                 pair_add(ah, al, dh, dl);
-                const float p = dh * dh;
+                const float p = __fmul_rn(dh, dh);
                 float q = fmaf(dh, dh, -p);
                 q = fmaf(2.f * dh, dl, q);
                 float ph, pl;
@@ -186,7 +158,7 @@ __device__ __forceinline__ void shifted_moments(const T* __restrict__ row, int n
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, long long ld, int n, int p,
                                                     double* __restrict__ mu, double* __restrict__ isd,
-                                                    double* __restrict__ z64, long long ldz,
+                                                    float2* __restrict__ mup, double* __restrict__ z64, long long ldz,
                                                     __nv_bfloat16* __restrict__ zhi, __nv_bfloat16* __restrict__ zlo,
                                                     long long ldb, Meta* meta, const int* __restrict__ vprob,
                                                     const ProbDesc* __restrict__ probs, double inv_n)
@@ -207,6 +179,7 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
             if (threadIdx.x == 0) {
                 mu[v] = 0.0;
                 isd[v] = 0.0;
+                if (mup) mup[v] = make_float2(0.f, 0.f);
             }
             if (zhi)
                 for (int k = threadIdx.x; k < kpad; k += NT) {
@@ -248,6 +221,7 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
             fstat[0] = mh;
             fstat[1] = (float)(mean - (double)mh);
             fstat[2] = (float)inv;
+            if (mup) mup[v] = make_float2(fstat[0], fstat[1]);
         }
         __syncthreads();
     }
@@ -375,16 +349,16 @@ cudaError_t launch_transpose(int dtype, const void* X, long long ld, int n, int 
 }
 
 cudaError_t launch_standardize(int dtype, const void* Xv, long long ld, int n, int p, double* mu, double* isd,
-                               double* z64, long long ldz, void* zhi, void* zlo, long long ldb, Meta* meta,
-                               cudaStream_t st, const int* vprob, const ProbDesc* probs)
+                               float2* mup, double* z64, long long ldz, void* zhi, void* zlo, long long ldb,
+                               Meta* meta, cudaStream_t st, const int* vprob, const ProbDesc* probs)
 {
     constexpr int NT = 256;
     if (dtype == CUPC_F64)
-        k_standardize<double, NT><<<p, NT, 0, st>>>((const double*)Xv, ld, n, p, mu, isd, z64, ldz,
+        k_standardize<double, NT><<<p, NT, 0, st>>>((const double*)Xv, ld, n, p, mu, isd, mup, z64, ldz,
                                                     (__nv_bfloat16*)zhi, (__nv_bfloat16*)zlo, ldb, meta, vprob,
                                                     probs, 1.0 / (double)(n > 0 ? n : 1));
     else
-        k_standardize<float, NT><<<p, NT, 0, st>>>((const float*)Xv, ld, n, p, mu, isd, z64, ldz,
+        k_standardize<float, NT><<<p, NT, 0, st>>>((const float*)Xv, ld, n, p, mu, isd, mup, z64, ldz,
                                                    (__nv_bfloat16*)zhi, (__nv_bfloat16*)zlo, ldb, meta, vprob,
                                                    probs, 1.0 / (double)(n > 0 ? n : 1));
     return cudaGetLastError();

@@ -108,7 +108,9 @@ struct LevelParams {
     int xf64;                      // element type of xv: 1 FP64, 0 FP32
     const double* mu;              // per variable: mean and 1/sd of the standardisation
     const double* isd;
+    const float2* mup;             // the mean as an FP32 pair (FP32 data: compensated rechecks)
     int n;
+    double inv_n;                  // 1 / n (one problem)
     int nmax;                      // batch: largest sample count
     const double* c64;
     double* part;                  // recheck partial Gram sums (tests x slices x D doubles)
@@ -142,7 +144,9 @@ struct Recheck0Params {
     int xf64;
     const double* mu;
     const double* isd;
+    const float2* mup;             // the mean as an FP32 pair (FP32 data)
     int n;
+    double inv_n;
     const double* c64;
     int p;
     double r2;
@@ -157,8 +161,9 @@ struct Recheck0Params {
 
 cudaError_t launch_transpose(int dtype, const void* X, long long ld, int n, int p, void* Xt, cudaStream_t st);
 cudaError_t launch_standardize(int dtype, const void* Xv, long long ld, int n, int p, double* mu, double* isd,
-                               double* z64, long long ldz, void* zhi, void* zlo, long long ldb, Meta* meta,
-                               cudaStream_t st, const int* vprob = nullptr, const ProbDesc* probs = nullptr);
+                               float2* mup, double* z64, long long ldz, void* zhi, void* zlo, long long ldb,
+                               Meta* meta, cudaStream_t st, const int* vprob = nullptr,
+                               const ProbDesc* probs = nullptr);
 cudaError_t launch_transpose_batch(int dtype, const ProbDesc* probs, int nprob, int pmax, int nmax, void* Xt,
                                    cudaStream_t st);
 cudaError_t launch_syrk_f64(const double* Z, long long ldz, int n, int p, double* C, cudaStream_t st);
@@ -168,7 +173,7 @@ cudaError_t launch_corr_tc(const void* hi, const void* lo, long long ldk, int p,
 // Batched correlation: host-side plan (work units and output tiles, copied to
 // the device by the caller) and the launch.
 struct CorrBatchUnit {
-    int ra, rb, g0, g1, kt, slot, pad0, pad1;
+    int ra, rb, g0, g1, kt, slot, prob, pad0;   // slot -1: the unit writes its tile of C
 };
 struct CorrBatchTile {
     int prob, bi, bj, slot0, nsplit, pad0, pad1, pad2;
@@ -178,7 +183,7 @@ void corr_tc_batch_plan(const std::vector<ProbDesc>& probs, int num_sms, int kps
                         int* kps_out);
 cudaError_t launch_corr_tc_batch(const void* hi, const void* lo, long long ldk, int rows, const void* units,
                                  int n_units, const void* tiles, int n_tiles, const ProbDesc* probs, float* ws,
-                                 float* C, int* err, cudaStream_t st);
+                                 float* C, int num_sms, int* err, cudaStream_t st);
 cudaError_t launch_symmetrize(int dtype, const void* Cin, long long ld, int p, double* C64, float* C32,
                               cudaStream_t st);
 

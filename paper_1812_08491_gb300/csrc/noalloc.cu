@@ -95,7 +95,7 @@ extern "C" cupc_status cupc_correlation_noalloc(const void* X, int dtype, int la
         xv = xt;
         ldv = n;
     }
-    if (launch_standardize(dtype, xv, ldv, n, pp, mu, isd, z64, n, nullptr, nullptr, 0, meta, st) != cudaSuccess)
+    if (launch_standardize(dtype, xv, ldv, n, pp, mu, isd, nullptr, z64, n, nullptr, nullptr, 0, meta, st) != cudaSuccess)
         return CUPC_E_CUDA;
     if (launch_syrk_f64(z64, n, n, pp, C_out, st) != cudaSuccess) return CUPC_E_CUDA;
     int err = 0;

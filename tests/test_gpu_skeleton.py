@@ -76,6 +76,22 @@ def test_correlation_f32_parity(ctx):
     assert np.array_equal(C, C.T)
 
 
+@pytest.mark.parametrize("p,n", [(130, 200), (1500, 200), (1501, 150), (700, 5000)])
+def test_correlation_f32_tile_shapes(ctx, p, n):
+    """Short sample counts make every tile one whole-K unit that writes C itself
+    (row segments and mirrored columns, vector or scalar stores by p mod 4); the
+    long one splits K and goes through the partial-sum reduction. Both must give
+    the same bound against the FP64 definition, exact symmetry and a unit
+    diagonal, ragged row and column blocks included."""
+    s = sem.generate(p, n, 700 + p, "random", degree=3.0)
+    ref = oracle.correlation(s.X, nthreads=8)
+    C = ctx.correlation(s.X, cupc.F32).cpu().numpy().astype(np.float64)
+    err = np.max(np.abs(C - ref))
+    assert err < 2e-5, err
+    assert np.array_equal(C, C.T)
+    assert np.all(np.diag(C) == 1.0)
+
+
 def test_correlation_float32_input(ctx):
     s = sem.generate(90, 500, 6, "random", degree=3.0, dtype=np.float32)
     ref = oracle.correlation(s.X.astype(np.float64))
@@ -130,6 +146,19 @@ def test_skeleton_medium(ctx, mode, p, n, fam, deg, alpha):
     s = sem.generate(p, n, 7 * p + n, fam, degree=deg, w_min=0.2)
     C, ref = _oracle_run(s.X, alpha)
     res = ctx.skeleton(s.X, alpha, mode=MODES[mode])
+    _assert_same(res, ref)
+    assert res.stats()["serial_tests"] == ref.tests
+
+
+@pytest.mark.parametrize("p,n,deg,alpha", [(150, 2000, 3.0, 0.01), (97, 300, 5.0, 0.05), (40, 120, 6.0, 0.2),
+                                          (200, 60, 8.0, 0.3)])
+def test_skeleton_float32_data(ctx, p, n, deg, alpha):
+    """FP32 data: the rechecks near the threshold form their Gram sums from the
+    data in compensated FP32 pairs; the skeleton, SepSets and serial counts must
+    still be the FP64 definition's (the oracle runs on the same float32 values)."""
+    s = sem.generate(p, n, 11 * p + n, "random", degree=deg, w_min=0.2, dtype=np.float32)
+    C, ref = _oracle_run(s.X.astype(np.float64), alpha)
+    res = ctx.skeleton(s.X, alpha)
     _assert_same(res, ref)
     assert res.stats()["serial_tests"] == ref.tests
 

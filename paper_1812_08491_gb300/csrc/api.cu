@@ -654,7 +654,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             H.overflow_level = 0;
             H.done_level = 0;
             H.csr_level = 0;
-            H.bar_count = 0;
+            H.bar = 0;
             CU(cudaMemcpyAsync(lm, ctx->hlmeta, sizeof(LevelMeta), cudaMemcpyHostToDevice, ctx->stream));
             if ((s = launch_levels(ol)) != CUPC_OK) return s;
             CU(cudaMemcpyAsync(ctx->hlmeta, lm, sizeof(LevelMeta), cudaMemcpyDeviceToHost, ctx->stream));

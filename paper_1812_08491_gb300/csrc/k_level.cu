@@ -91,27 +91,31 @@ __device__ __forceinline__ void thresholds(const LevelParams& P, int v, double& 
 }
 
 // Grid-wide barrier for a cooperative launch. Returns false (uniformly in the
-// CTA) when the kernel must stop: a wait expired or an error was raised.
+// CTA) when the kernel must stop: a wait expired or an error was raised. One
+// 64-bit word holds the arrivals and the generation: a CTA arrives with one
+// atomic add; the last one adds 2^32 - N, which returns the arrivals to 0 and
+// advances the generation in the same operation, and the others poll the
+// generation (the error flag and the clock every 64th poll).
 __device__ bool grid_sync(LevelMeta* lm)
 {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* vgen = &lm->bar_gen;
-        const unsigned g = *vgen;
         __threadfence();
-        const unsigned arrived = atomicAdd(&lm->bar_count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            atomicExch(&lm->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&lm->bar_gen, 1u);
+        const unsigned long long old = atomicAdd(&lm->bar, 1ull);
+        const unsigned g = (unsigned)(old >> 32);
+        if ((unsigned)old + 1u == gridDim.x) {
+            atomicAdd(&lm->bar, (1ull << 32) - (unsigned long long)gridDim.x);
         } else {
+            volatile unsigned long long* vb = &lm->bar;
             const unsigned long long t0 = gtimer();
-            while (*vgen == g) {
-                if (*(volatile int*)&lm->error) break;
-                if (gtimer() - t0 > kBarrierNs) {
-                    atomicOr(&lm->error, 8);
-                    break;
+            for (unsigned it = 1; (unsigned)(*vb >> 32) == g; ++it) {
+                if ((it & 63u) == 0) {
+                    if (*(volatile int*)&lm->error) break;
+                    if (gtimer() - t0 > kBarrierNs) {
+                        atomicOr(&lm->error, 8);
+                        break;
+                    }
                 }
             }
         }
@@ -1443,13 +1447,12 @@ __device__ void phase_finalize(const LevelParams& P, bool lrn)
 // ---------------------------------------------------------------------------
 // Tells the host whether this level runs (1) or the loop has ended (2),
 // through pinned host memory the host polls to decide on further launches.
+// The store is not fenced: the host only waits a little longer when it lands
+// late (at the latest when the kernel ends), while a system-scope fence would
+// hold this thread, and the barrier after it, for microseconds.
 __device__ __forceinline__ void signal_host(const LevelParams& P, int v)
 {
-    if (P.host_flags) {
-        __threadfence_system();
-        *(volatile int*)(P.host_flags + P.l) = v;
-        __threadfence_system();
-    }
+    if (P.host_flags) *(volatile int*)(P.host_flags + P.l) = v;
 }
 
 template <typename T, int LB, bool FP32, bool LEARNED>

@@ -35,7 +35,7 @@ struct LevelMeta {
     int overflow_level;                    // level whose recheck queue overflowed
     int error;                             // 8: a grid barrier wait expired
     int range_error;                       // a subset count saturated 64 bits
-    unsigned bar_count, bar_gen;           // grid barrier state
+    unsigned long long bar;                // grid barrier: arrivals (low 32 bits), generation (high 32)
     unsigned long long live[LV];           // queued tests rechecked (not decided already)
     unsigned long long round_hist[LV][RND]; // rows by item count (bin 0: items past RND - 1)
     unsigned long long round_cur[LV][RND]; // slots of each round handed to CTAs so far

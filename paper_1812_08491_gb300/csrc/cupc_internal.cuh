@@ -49,6 +49,16 @@ struct Binom {
     }
 };
 
+// C(m, k) for m < kBinomS from a copy in shared memory (a level's subset
+// unranking does a few dependent lookups per member).
+constexpr int kBinomS = 64;
+struct BinomS {
+    const unsigned long long* tab;   // shared: [k][m], m < kBinomS
+    __device__ __forceinline__ unsigned long long operator()(int m, int k) const {
+        return (m < 0 || k < 0) ? 0ull : tab[k * kBinomS + m];
+    }
+};
+
 // The t-th l-subset of the positions {0, .., d-1} in lexicographic order
 // (Sec. 4.2, Eq. comb). With k = l - 1 - c members still to place after place
 // c, the subsets whose place-c member is >= v number N(v) = C(d - v, k + 1)
@@ -56,8 +66,10 @@ struct Binom {
 // come first. So the member is the largest v with N(prev) - N(v) <= t, found by
 // binary search since N falls with v, and t drops by N(prev) - N(v).
 // Positions come out increasing; a rank beyond C(d, l) cannot leave the row.
-template <int LB>
-__device__ __forceinline__ void unrank_lex(unsigned long long t, int d, int l, const Binom& B, int (&P)[LB])
+// BT: the table in global memory (Binom) or its small-m part in shared
+// memory (BinomS).
+template <int LB, typename BT>
+__device__ __forceinline__ void unrank_lex(unsigned long long t, int d, int l, const BT& B, int (&P)[LB])
 {
     int prev = 0;
 #pragma unroll

@@ -722,6 +722,11 @@ __device__ void phase_ci(const LevelParams& P)
 {
     const int lane = threadIdx.x & 31;
     const int l = P.l;
+    // C(m, k) for small m, k <= LB + 1, in shared memory for the unranking
+    __shared__ unsigned long long sbin[(LB + 2) * kBinomS];
+    for (int q = threadIdx.x; q < (LB + 2) * kBinomS; q += NT) sbin[q] = P.B(q % kBinomS, q / kBinomS);
+    __syncthreads();
+    const BinomS BS{sbin};
     const unsigned long long n_items = P.lm->items[l];
     const int chunk = P.lm->chunk[l];
     unsigned long long ntests = 0;
@@ -742,6 +747,10 @@ __device__ void phase_ci(const LevelParams& P)
         thresholds(P, i, thr, thr2);
         const Decide dc = decide_consts(P, thr, thr2);
         const T* __restrict__ Ci = CV.row(i);
+        // complement mode when most of the row is in S (high levels): a broadcast j
+        // is then valid for few lanes' subsets, so each lane walks its own d - l
+        // non-members instead and all lanes test at once
+        const bool comp = 4 * (d - l) <= 3 * d;
         for (unsigned long long base = s0; base < s1; base += 32) {
             const unsigned long long s = base + lane;
             const bool active = s < s1;
@@ -750,13 +759,54 @@ __device__ void phase_ci(const LevelParams& P)
 #pragma unroll
             for (int c = 0; c < LB; ++c) { Pos[c] = -1; Sx[c] = 0; }
             if (active) {
-                unrank_lex<LB>(s, d, l, P.B, Pos);
+                if (d < kBinomS) unrank_lex<LB>(s, d, l, BS, Pos);
+                else unrank_lex<LB>(s, d, l, P.B, Pos);
 #pragma unroll
                 for (int c = 0; c < LB; ++c)
                     if (c < l) Sx[c] = P.cols[off + Pos[c]];
                 factor_build<T, LB>(
                     F, l, (T)P.rank_tol, [&](int a, int b) { return __ldg(CV.row(Sx[a]) + Sx[b]); },
                     [&](int a) { return __ldg(Ci + Sx[a]); });
+            }
+            // one test of this lane's subset against position jp (slot e = off + jp)
+            auto test = [&](int jp, int j, T cij) {
+                T H12, H22;
+                const T* __restrict__ Cj = CV.row(j);
+                factor_apply<T, LB>(F, l, cij, [&](int a) { return __ldg(Cj + Sx[a]); }, H12, H22);
+                const T H11 = T(1) - F.uu;
+                ++ntests;
+                const int dec = ci_decide<T, FP32>(H11, H12, H22, F.minpiv2, dc);
+                const long long e = off + jp;
+                if (dec == 1) {
+                    atomicMin(P.best + e, s);
+                } else if (FP32 && dec == 2) {
+                    const unsigned long long qq = atomicAdd(&P.lm->queue_len[l], 1ull);
+                    if (qq < P.qcap) {
+                        QEntry* Q = P.queue + qq;
+                        Q->a = (int)e;
+                        Q->b = 0;
+                        Q->s = s;
+#pragma unroll
+                        for (int c = 0; c < LB; ++c)
+                            if (c < l) Q->S[c] = Sx[c];
+                    }
+                }
+            };
+            if (comp) {
+                for (int v = 0; v < d - l; ++v) {
+                    // the v-th position outside S (Pos increasing)
+                    int jp = v;
+#pragma unroll
+                    for (int c = 0; c < LB; ++c)
+                        if (c < l && Pos[c] <= jp) ++jp;
+                    if (!active) continue;
+                    const long long e = off + jp;
+                    const int j = P.cols[e];
+                    const unsigned long long be = ld_cg(P.best + e);
+                    const unsigned long long pb = (!P.canonical || i > j) ? ld_cg(P.best + P.partner[e]) : RANK_NONE;
+                    if (pb == RANK_NONE && (P.canonical ? (be >= s) : (be == RANK_NONE))) test(jp, j, __ldg(Ci + j));
+                }
+                continue;
             }
             // the row's per-j data in chunks of 32: lane q loads j-position jc + q
             // (coalesced), then the chunk is broadcast one j at a time by shuffles
@@ -785,29 +835,7 @@ __device__ void phase_ci(const LevelParams& P)
 #pragma unroll
                     for (int c = 0; c < LB; ++c)
                         if (c < l && Pos[c] == jp) t = false;
-                    if (t) {
-                        T H12, H22;
-                        const T* __restrict__ Cj = CV.row(j);
-                        factor_apply<T, LB>(F, l, cij, [&](int a) { return __ldg(Cj + Sx[a]); }, H12, H22);
-                        const T H11 = T(1) - F.uu;
-                        ++ntests;
-                        const int dec = ci_decide<T, FP32>(H11, H12, H22, F.minpiv2, dc);
-                        const long long e = off + jp;
-                        if (dec == 1) {
-                            atomicMin(P.best + e, s);
-                        } else if (FP32 && dec == 2) {
-                            const unsigned long long qq = atomicAdd(&P.lm->queue_len[l], 1ull);
-                            if (qq < P.qcap) {
-                                QEntry* Q = P.queue + qq;
-                                Q->a = (int)e;
-                                Q->b = 0;
-                                Q->s = s;
-#pragma unroll
-                                for (int c = 0; c < LB; ++c)
-                                    if (c < l) Q->S[c] = Sx[c];
-                            }
-                        }
-                    }
+                    if (t) test(jp, j, cij);
                 }
             }
         }

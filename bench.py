@@ -212,7 +212,7 @@ def kernel_rooflines(st, s, mode, peaks, alu=None):
     """Roofline of each kernel of one skeleton call (stats of that call).
 
     Durations are CUDA-event times on the library's stream; algorithmic work:
-      standardize  read X once, write the FP64 rows (+ the two bf16 rows in FP32 mode)
+      standardize  read X once; write the two bf16 rows (FP32 mode) or the FP64 rows (plain)
       correlation  3 split-precision bf16 products over the upper triangle, 2 n p(p+1)/2 each
       level0       read C once, write the bitset
       level        per level: the C sub-blocks its tests read, sum over rows of (n'_i+1)^2
@@ -235,7 +235,7 @@ def kernel_rooflines(st, s, mode, peaks, alu=None):
                      "ms": ms, "launches": launches, "alg_bytes_per_launch": per, "traffic": None}
 
     mem("standardize", km["standardize"], kc["standardize"],
-        n * p * es_in + n * p * 8 + (n * p * 4 if mode == "fp32" else 0))
+        n * p * es_in + (n * p * 4 if mode == "fp32" else n * p * 8))
     mem("level0", km["level0"], 1, p * p * cb + p * W * 4)
     lv = st["levels"]
     lev_ms = sum(st["level_ms"][1:lv])
@@ -285,7 +285,7 @@ def _batch_config(name, probs, form):
 def batch_rooflines(bst, probs, peaks):
     """Roofline of each stage of one batch step (its stats; CUDA-event stage times).
 
-      standardize  read X (float32), write the FP64 rows and the two bf16 rows
+      standardize  read X (float32), write the two bf16 rows
       correlation  3 bf16 products over each problem's upper triangle, 2 n p (p+1)/2 each
       level0       read every problem's C (FP32) once, write the bitsets; FP64 rechecks of the band
       level        per level: the C sub-blocks its tests read (FP32), the bitsets, the CSR arrays
@@ -302,7 +302,7 @@ def batch_rooflines(bst, probs, peaks):
                      "launches": 1, "alg_bytes_per_launch": byts, "traffic": None}
 
     words = sum(((s.p + 31) // 32 * 32) ** 2 // 32 for s in probs)
-    mem("standardize", km["standardize"], sum(s.n * s.p * (4 + 8 + 4) for s in probs))
+    mem("standardize", km["standardize"], sum(s.n * s.p * (4 + 4) for s in probs))
     mem("level0", km["level0"], sum(s.p * s.p * 4 for s in probs) + words * 4)
     lv = bst["levels"]
     byts = 0

@@ -454,8 +454,11 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAH, const __grid_constant__ CUte
 // written to (i, j) and, through a shared-memory transpose, to (j, i); the
 // diagonal is 1. The slices are added with Knuth's two-sum (an FP32 pair: the
 // same result as an FP64 sum of these few terms, without GB300's narrow FP64
-// pipe), four loads in flight at a time. Block (tile, 8-row band): 256 threads.
+// pipe). Block (tile, 8-row band): 256 threads, warp = row of the band; a lane
+// owns columns 4 lane .. 4 lane + 3 and 128 + 4 lane .. 128 + 4 lane + 3 and
+// reads them as two float4 per slice, eight slices' loads in flight at a time.
 constexpr int RROWS = 8;
+constexpr int RSL = 8;                               // slices loaded per batch
 __device__ __forceinline__ void two_sum_acc(float& s, float& e, float v)
 {
     const float t = s + v, bb = t - s;
@@ -467,33 +470,49 @@ __device__ __forceinline__ void reduce_band(const float* __restrict__ ws, long l
                                             int nsplit, int bi, int bj, int p, float inv_n, float* __restrict__ C,
                                             float (*sm)[BN + 1])
 {
+    static_assert(BN == 256, "a lane covers two float4 groups of a 256-column row");
     const int r0 = blockIdx.y * RROWS;
     const int rr = threadIdx.x >> 5;            // row of the band (8 warps)
     const int lane = threadIdx.x & 31;
     const int r = r0 + rr, gi = bi * BM + r;
-    for (int c = lane; c < BN; c += 32) {
-        const int gj = bj * BN + c;
-        float v = 0.f;
-        const bool valid = gi < p && gj < p && gj >= gi;
-        if (valid) {
-            if (gi == gj) {
-                v = 1.0f;
-            } else {
-                const float* src = ws + ((size_t)slot0 * BM + r) * BN + c;
-                const size_t step = (size_t)stride * BM * BN;
-                float hs = 0.f, he = 0.f;
-                int k = 0;
-                for (; k + 4 <= nsplit; k += 4) {
-                    const float a0 = src[(size_t)k * step], a1 = src[(size_t)(k + 1) * step];
-                    const float a2 = src[(size_t)(k + 2) * step], a3 = src[(size_t)(k + 3) * step];
-                    two_sum_acc(hs, he, a0);
-                    two_sum_acc(hs, he, a1);
-                    two_sum_acc(hs, he, a2);
-                    two_sum_acc(hs, he, a3);
-                }
-                for (; k < nsplit; ++k) two_sum_acc(hs, he, src[(size_t)k * step]);
-                v = fmaf(hs, inv_n, he * inv_n);
+    const float4* src = (const float4*)(ws + ((size_t)slot0 * BM + r) * BN);
+    const size_t step = (size_t)stride * BM * BN / 4;
+    float hs[8], he[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) hs[u] = he[u] = 0.f;
+    // the whole band row is summed (entries past p or below the diagonal are
+    // finite partials of the tile and are discarded below)
+    for (int k0 = 0; k0 < nsplit; k0 += RSL) {
+        float4 a[RSL][2];
+#pragma unroll
+        for (int q = 0; q < RSL; ++q) {
+            if (k0 + q < nsplit) {
+                a[q][0] = __ldcs(src + (size_t)(k0 + q) * step + lane);
+                a[q][1] = __ldcs(src + (size_t)(k0 + q) * step + 32 + lane);
             }
+        }
+#pragma unroll
+        for (int q = 0; q < RSL; ++q) {
+            if (k0 + q < nsplit) {
+                two_sum_acc(hs[0], he[0], a[q][0].x);
+                two_sum_acc(hs[1], he[1], a[q][0].y);
+                two_sum_acc(hs[2], he[2], a[q][0].z);
+                two_sum_acc(hs[3], he[3], a[q][0].w);
+                two_sum_acc(hs[4], he[4], a[q][1].x);
+                two_sum_acc(hs[5], he[5], a[q][1].y);
+                two_sum_acc(hs[6], he[6], a[q][1].z);
+                two_sum_acc(hs[7], he[7], a[q][1].w);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int c = (u < 4 ? 0 : 128) + 4 * lane + (u & 3);
+        const int gj = bj * BN + c;
+        const bool valid = gi < p && gj < p && gj >= gi;
+        float v = 0.f;
+        if (valid) {
+            v = (gi == gj) ? 1.0f : fmaf(hs[u], inv_n, he[u] * inv_n);
             C[(size_t)gi * p + gj] = v;
         }
         sm[rr][c] = (valid && gj != gi) ? v : __int_as_float(0x7fc00001);

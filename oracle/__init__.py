@@ -8,8 +8,9 @@ compiled with gcc) plus the NumPy MLP reference in ``mlp.py``.
 Functions mirror the paper's definitions (Zarebavani et al., TPDS 2019):
 ``comb`` (Sec. 4.2, Eq. comb / Algorithm 6), ``pcor`` (Sec. 4.3, Eqs.
 PartialCorMat and RhoCal), ``tau`` (Eq. threshold), ``pinv_alg7`` (Sec. 4.4,
-Algorithm 7), and ``pc_stable`` (Algorithm 1 with the readings in the C file's
-header).
+Algorithm 7), ``pc_stable`` (Algorithm 1 with the readings in the C file's
+header) and ``orient`` (the second step of PC-stable, Sec. 2.4: v-structures
+and Meek's rules, giving the CPDAG of Sec. 2.2).
 """
 from __future__ import annotations
 
@@ -90,6 +91,8 @@ def _lib():
                      ("orc_run_pinv_used", i64), ("orc_run_rec_len", i64), ("orc_run_n_rec", i64)):
         getattr(L, name).restype = rt
         getattr(L, name).argtypes = [vp]
+    L.orc_orient.restype = i64
+    L.orc_orient.argtypes = [i32, vp, vp, vp, vp, vp, i64, vp]
     L.orc_run_copy.restype = None
     L.orc_run_copy.argtypes = [vp, vp, vp, vp, vp, vp]
     _LIB = L
@@ -295,3 +298,33 @@ def pc_stable_table(p: int, statements, max_level: int = -1) -> OracleResult:
         T[r, 3:3 + len(S)] = sorted(S)
     h = _lib().orc_pc_table(p, _ptr(T), len(statements), width, max_level)
     return _collect(h)
+
+
+# --------------------------------------------------------------------------
+# Second step of PC-stable: orientation
+# --------------------------------------------------------------------------
+
+MARK_NONE, MARK_ARROW, MARK_TAIL = 0, 1, 2
+
+
+def orient(res: OracleResult):
+    """Sec. 2.4, second step: v-structures from the SepSets of ``res``, then
+    Meek's rules R1-R3 in rounds (readings in pc_oracle.c). Returns
+    (mark, rounds): mark[a, b] = 0 no edge, 1 arrowhead at b, 2 tail at b."""
+    p = res.adj.shape[0]
+    items = sorted(res.sepsets.items())
+    keys = np.array([i * p + j for (i, j), _ in items] or [0], dtype=np.int64)
+    off = np.zeros(max(len(items), 1), dtype=np.int64)
+    mem = []
+    for r, (_, (l, S)) in enumerate(items):
+        off[r] = len(mem)
+        mem.extend(S)
+    members = np.array(mem or [0], dtype=np.int32)
+    adj = np.ascontiguousarray(res.adj, dtype=np.uint8)
+    sep = np.ascontiguousarray(res.sep_level, dtype=np.int16)
+    mark = np.zeros((p, p), dtype=np.uint8)
+    rounds = _lib().orc_orient(p, _ptr(adj), _ptr(sep), _ptr(keys), _ptr(off), _ptr(members), len(items),
+                               _ptr(mark))
+    if rounds < 0:
+        raise ValueError("a removed pair has no SepSet record")
+    return mark, int(rounds)

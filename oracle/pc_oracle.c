@@ -22,6 +22,8 @@
  *     independent iff Z <= tau.
  *   - Sec. 4.4, Algorithm 7: Moore-Penrose pseudo-inverse through the full-rank
  *     Cholesky factor of M2^T M2, used when M2 is not positive definite.
+ *   - Sec. 2.4 (second step of PC-stable) with the v-structures and the CPDAG
+ *     of Sec. 2.2: orc_orient, at the end of the file, with its readings.
  *
  * Readings where the paper is silent or garbled (each is listed in the design
  * notes of the repository):
@@ -758,4 +760,149 @@ void orc_run_copy(const orc_run* r, uint8_t* adj, int16_t* sep_level, int* rec,
     if (rec && r->rec_len) memcpy(rec, r->rec, (size_t)r->rec_len * sizeof(int));
     if (tests) memcpy(tests, r->tests, sizeof r->tests);
     if (removed) memcpy(removed, r->removed, sizeof r->removed);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Second step of PC-stable (Sec. 2.4): the v-structures V_i -> V_k <- V_j   */
+/* of Sec. 2.2, read off the SepSets, then Meek's orientation rules R1-R3,  */
+/* which give the CPDAG of Sec. 2.2.                                         */
+/*                                                                          */
+/* Edge marks: mark[a*p + b] = 0 when a and b are not adjacent; 1 when the   */
+/* edge a - b has an arrowhead at b; 2 when it has a tail at b. So a -> b is */
+/* (mark[a][b], mark[b][a]) = (1, 2), a - b is (2, 2), and two v-structures  */
+/* that disagree on an edge leave arrowheads at both ends, (1, 1).           */
+/*                                                                          */
+/* Readings (the paper only names the step): every unshielded triple         */
+/* i - k - j (i, j not adjacent) with k outside SepSet(i, j) is a            */
+/* v-structure, all of them applied together (order-free; conflicts give     */
+/* (1, 1)); the rules then run in rounds, each deciding from the marks at    */
+/* the start of the round and applying all its orientations together, until  */
+/* a round changes nothing; an edge that a round would orient both ways is   */
+/* left undirected. Only undirected edges are oriented, and only directed    */
+/* edges (1, 2) count as arrows in the rules' premises:                      */
+/*   R1  c -> a, a - b, c and b not adjacent            =>  a -> b          */
+/*   R2  a -> c -> b, a - b                             =>  a -> b          */
+/*   R3  a - c1 -> b, a - c2 -> b, c1 and c2 not adjacent, a - b => a -> b  */
+/* SepSets: sep_level[i*p + j] is the level that removed the pair (-1 when   */
+/* the edge is present); removals at level 0 have S empty; the others are    */
+/* found by key i*p + j (i < j) in the ascending keys[], with members        */
+/* members[off[r] .. off[r] + level).                                        */
+/* Returns the number of rule rounds run (the last one changed nothing), or  */
+/* -1 on bad input.                                                          */
+/* ------------------------------------------------------------------------ */
+static int sep_has(int64_t p, const int16_t* sep_level, const int64_t* keys, const int64_t* off,
+                   const int32_t* members, int64_t nkeys, int i, int j, int k)
+{
+    const int a = i < j ? i : j, b = i < j ? j : i;
+    const int lev = sep_level[(int64_t)a * p + b];
+    if (lev <= 0) return 0;
+    const int64_t key = (int64_t)a * p + b;
+    int64_t lo = 0, hi = nkeys;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (keys[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo >= nkeys || keys[lo] != key) return -1;
+    for (int c = 0; c < lev; ++c)
+        if (members[off[lo] + c] == k) return 1;
+    return 0;
+}
+
+static int is_dir(const uint8_t* mark, int64_t p, int x, int y)
+{
+    return mark[(int64_t)x * p + y] == 1 && mark[(int64_t)y * p + x] == 2;
+}
+
+static int is_und(const uint8_t* mark, int64_t p, int x, int y)
+{
+    return mark[(int64_t)x * p + y] == 2 && mark[(int64_t)y * p + x] == 2;
+}
+
+int64_t orc_orient(int p, const uint8_t* adj, const int16_t* sep_level, const int64_t* keys, const int64_t* off,
+                   const int32_t* members, int64_t nkeys, uint8_t* mark)
+{
+    const int64_t P = p;
+    /* neighbour lists of the skeleton (it does not change in this step) */
+    int64_t* nb_off = (int64_t*)malloc((size_t)(P + 1) * sizeof(int64_t));
+    int64_t tot = 0;
+    for (int64_t a = 0; a < P; ++a) {
+        nb_off[a] = tot;
+        for (int64_t b = 0; b < P; ++b) tot += (a != b && adj[a * P + b]) ? 1 : 0;
+    }
+    nb_off[P] = tot;
+    int* nb = (int*)malloc((size_t)(tot > 0 ? tot : 1) * sizeof(int));
+    for (int64_t a = 0, q = 0; a < P; ++a)
+        for (int64_t b = 0; b < P; ++b)
+            if (a != b && adj[a * P + b]) nb[q++] = (int)b;
+    for (int64_t x = 0; x < P * P; ++x) mark[x] = adj[x] ? 2 : 0;
+    for (int64_t a = 0; a < P; ++a) mark[a * P + a] = 0;
+
+    /* v-structures: unshielded triples i - k - j with k not in SepSet(i, j) */
+    int bad = 0;
+    for (int64_t k = 0; k < P; ++k) {
+        for (int64_t x = nb_off[k]; x < nb_off[k + 1]; ++x) {
+            for (int64_t y = x + 1; y < nb_off[k + 1]; ++y) {
+                const int i = nb[x], j = nb[y];
+                if (adj[(int64_t)i * P + j]) continue;
+                const int in = sep_has(P, sep_level, keys, off, members, nkeys, i, j, (int)k);
+                if (in < 0) bad = 1;
+                if (in == 0) {
+                    mark[(int64_t)i * P + k] = 1;
+                    mark[(int64_t)j * P + k] = 1;
+                }
+            }
+        }
+    }
+    if (bad) {
+        free(nb);
+        free(nb_off);
+        return -1;
+    }
+
+    /* Meek's rules R1-R3 in rounds */
+    uint8_t* prop = (uint8_t*)malloc((size_t)(P * P > 0 ? P * P : 1));
+    int64_t rounds = 0;
+    for (;;) {
+        memset(prop, 0, (size_t)(P * P));
+        for (int64_t a = 0; a < P; ++a) {
+            for (int64_t x = nb_off[a]; x < nb_off[a + 1]; ++x) {
+                const int b = nb[x];
+                if (!is_und(mark, P, (int)a, b)) continue;
+                int hit = 0;
+                for (int64_t y = nb_off[a]; y < nb_off[a + 1] && !hit; ++y) {
+                    const int c = nb[y];
+                    if (c == b) continue;
+                    /* R1 */
+                    if (is_dir(mark, P, c, (int)a) && !adj[(int64_t)c * P + b]) hit = 1;
+                    /* R2 */
+                    if (is_dir(mark, P, (int)a, c) && is_dir(mark, P, c, b)) hit = 1;
+                }
+                /* R3 */
+                for (int64_t y = nb_off[a]; y < nb_off[a + 1] && !hit; ++y) {
+                    const int c1 = nb[y];
+                    if (c1 == b || !is_und(mark, P, (int)a, c1) || !is_dir(mark, P, c1, b)) continue;
+                    for (int64_t z = y + 1; z < nb_off[a + 1] && !hit; ++z) {
+                        const int c2 = nb[z];
+                        if (c2 == b || !is_und(mark, P, (int)a, c2) || !is_dir(mark, P, c2, b)) continue;
+                        if (!adj[(int64_t)c1 * P + c2]) hit = 1;
+                    }
+                }
+                prop[a * P + b] = (uint8_t)hit;
+            }
+        }
+        int64_t changed = 0;
+        for (int64_t a = 0; a < P; ++a)
+            for (int64_t b = 0; b < P; ++b)
+                if (prop[a * P + b] && !prop[b * P + a]) {
+                    mark[a * P + b] = 1;
+                    ++changed;
+                }
+        ++rounds;
+        if (!changed) break;
+    }
+    free(prop);
+    free(nb);
+    free(nb_off);
+    return rounds;
 }

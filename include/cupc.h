@@ -262,6 +262,39 @@ cupc_status cupc_device_peaks(cupc_ctx* ctx, double* fp64_tflops, double* fp32_t
 /* Number of variables of a result. */
 cupc_status cupc_result_p(const cupc_result* res, int64_t* p);
 
+/* Counts of one orientation (cupc_result_orient). */
+typedef struct {
+    int64_t rounds;          /* rounds of Meek's rules run; the last one changed nothing */
+    int64_t directed;        /* edges with an arrowhead at exactly one end */
+    int64_t undirected;      /* edges with no arrowhead */
+    int64_t bidirected;      /* edges two v-structures disagree on (arrowheads at both ends) */
+    int64_t rule_conflicts;  /* edges a round proposed both ways (left undirected that round) */
+    float ms;                /* device time from the neighbour lists to the marks (CUDA events) */
+    int32_t reserved;
+} cupc_orient_stats;
+
+/* The second step of PC-stable (Sec. 2.4): the v-structures of Sec. 2.2 read
+ * off the result's skeleton and SepSets, then Meek's orientation rules R1-R3,
+ * giving the CPDAG of Sec. 2.2. Runs on the device (k_orient.cu).
+ *   marks  host buffer of p*p bytes (caller-owned; NULL: counts only), row-major:
+ *          marks[a*p + b] = 0 when a and b are not adjacent, 1 when the edge
+ *          a - b has an arrowhead at b, 2 when it has a tail at b; so a -> b
+ *          is (1, 2) at ([a][b], [b][a]), a - b is (2, 2), and an edge two
+ *          v-structures disagree on is (1, 1).
+ *   stats  may be NULL.
+ * Readings (the paper names the step only): every unshielded triple
+ * i - k - j (i, j not adjacent) with k outside SepSet(i, j) is a v-structure,
+ * all of them applied together; the rules run in rounds that decide from the
+ * marks at the start of the round and apply all their orientations together,
+ * until a round changes nothing; an edge proposed both ways in a round stays
+ * undirected; only undirected edges are oriented, and only directed edges
+ * count as arrows in the rules' premises. The result is independent of the
+ * variable order. Device scratch comes from the context's pool; the result
+ * itself is not changed. Synchronises the context stream once per round.
+ * Errors: CUPC_E_INVALID (NULL result), CUPC_E_STATE (a result without its
+ * skeleton or SepSet records), CUPC_E_NOMEM, CUPC_E_CUDA. */
+cupc_status cupc_result_orient(cupc_result* res, uint8_t* marks, cupc_orient_stats* stats);
+
 /* Copies the skeleton as a p x p uint8 matrix (1 = edge) into the host buffer
  * `out` (caller-owned, p*p bytes). Synchronises the context stream. */
 cupc_status cupc_result_adjacency(const cupc_result* res, uint8_t* out);

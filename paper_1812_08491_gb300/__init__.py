@@ -45,6 +45,7 @@ _SIGNATURES = {
     "cupc_result_sepset": ("status", ["vp", "i64", "i64", "vp", "vp"]),
     "cupc_result_sepset_records": ("status", ["vp", "vp", "i64", "vp"]),
     "cupc_result_stats": ("status", ["vp", "vp"]),
+    "cupc_result_orient": ("status", ["vp", "vp", "vp"]),
     "cupc_result_free": (None, ["vp"]),
     "cupc_correlation": ("status", ["vp", "vp", "int", "int", "int", "i64", "i64", "i64", "int", "vp"]),
     "cupc_pcor_batch": ("status", ["vp", "vp", "int", "i64", "vp", "i64", "int", "vp"]),
@@ -89,6 +90,12 @@ class Stats(ctypes.Structure):
                 ("ci_block_entries", ctypes.c_int64 * L), ("phase_ms", (ctypes.c_float * 4) * L),
                 ("cuda_graph", ctypes.c_int32), ("recheck_ms", (ctypes.c_float * 3) * L),
                 ("rechecks_queued", ctypes.c_int64 * L)]
+
+
+class OrientStats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("directed", ctypes.c_int64), ("undirected", ctypes.c_int64),
+                ("bidirected", ctypes.c_int64), ("rule_conflicts", ctypes.c_int64), ("ms", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -243,6 +250,16 @@ class Result:
             out[(i, j)] = (l, tuple(int(v) for v in raw[k + 3:k + 3 + l]))
             k += 3 + l
         return out
+
+    def orient(self, marks: bool = True):
+        """Second step of PC-stable on the device: (marks, stats). marks[a, b] = 0 no
+        edge, 1 arrowhead at b, 2 tail at b (None when marks=False)."""
+        out = np.empty((self.p, self.p), dtype=np.uint8) if marks else None
+        s = OrientStats()
+        self._check(load().cupc_result_orient(self._h, out.ctypes.data if marks else None, ctypes.byref(s)),
+                    "cupc_result_orient")
+        return out, {"rounds": s.rounds, "directed": s.directed, "undirected": s.undirected,
+                     "bidirected": s.bidirected, "rule_conflicts": s.rule_conflicts, "ms": s.ms}
 
     def stats(self) -> dict:
         s = Stats()

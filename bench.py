@@ -138,13 +138,38 @@ class ClockSampler:
         return out
 
 
-def cpu_oracle_run(sem_obj, nthreads):
-    """One full oracle skeleton (correlation + Algorithm 1): (seconds, serial tests)."""
+def cpu_oracle_run(sem_obj, nthreads, keep=None):
+    """One full oracle skeleton (correlation + Algorithm 1): (seconds, serial tests).
+    The oracle's result is stored in keep["res"] when a dict is given."""
     import oracle
     t0 = time.perf_counter()
     C = oracle.correlation(sem_obj.X, nthreads=nthreads)
     res = oracle.pc_stable(C, sem_obj.n, sem_obj.alpha, max_level=sem_obj.max_level, nthreads=nthreads)
+    if keep is not None:
+        keep["res"] = res
     return time.perf_counter() - t0, res.total_tests
+
+
+def orientation_line(ctx, X, s, mode, oracle_res=None, reps=5):
+    """The second step of PC-stable (v-structures + Meek's rules) on the device,
+    after one skeleton of the workload: device time (CUDA events inside the
+    library, median of reps) and edge counts; with the oracle's skeleton, the
+    oracle's orientation timed on the host beside it (one run)."""
+    r = ctx.skeleton(X, s.alpha, mode=mode, max_level=s.max_level)
+    times, st = [], None
+    for _ in range(reps + 1):
+        _, st = r.orient(marks=False)
+        times.append(st["ms"])
+    r.free()
+    out = {"device_ms": statistics.median(times[1:]), "rounds": st["rounds"], "directed": st["directed"],
+           "undirected": st["undirected"], "bidirected": st["bidirected"],
+           "note": "second step of PC-stable, outside the timed skeleton step"}
+    if oracle_res is not None:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.orient(oracle_res)
+        out["oracle_cpu_ms"] = 1e3 * (time.perf_counter() - t0)
+    return out
 
 
 def run_reference(args, workload_name):
@@ -544,9 +569,13 @@ def main():
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def step(m):
+    def step(m, done=None):
+        """One skeleton call; `done` (a CUDA event) is recorded as soon as the call
+        returns, before the result's statistics are read and its memory freed."""
         lo = bool(args.learned) and m == cupc.MODE_FP32_RECHECK
         res = ctx.skeleton(X, s.alpha, mode=m, canonical=True, max_level=s.max_level, learned_order=lo)
+        if done is not None:
+            done.record(stream)
         st = res.stats()
         res.free()
         return st
@@ -572,8 +601,7 @@ def main():
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            st = step(mode)
-            b.record(stream)
+            st = step(mode, b)
             torch.cuda.synchronize()
             total_ms += a.elapsed_time(b)
             launches += st["kernel_launches"]
@@ -600,8 +628,7 @@ def main():
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            step(cupc.MODE_PLAIN_FP64)
-            b.record(stream)
+            step(cupc.MODE_PLAIN_FP64, b)
             torch.cuda.synchronize()
             pm += a.elapsed_time(b)
         plain = {"value": units * k2 / (pm * 1e-3), "unit": UNIT, "ms_per_step": pm / k2, "steps": k2}
@@ -652,11 +679,13 @@ def main():
               for k in roofs[0][0]["kernel_ms"]}
 
     cpu = None
+    keep = {}
     if rank == 0 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        secs, cu = cpu_oracle_run(s, cores)
+        secs, cu = cpu_oracle_run(s, cores, keep)
         cpu = {"value": cu / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"whole {args.workload} skeleton once (correlation + all levels), {secs:.2f} s"}
+    orient = orientation_line(ctx, X, s, mode, keep.get("res")) if rank == 0 else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -676,7 +705,7 @@ def main():
                 "roofline": roof,
                 "kernel_rooflines": {k: {"frac": round(v["frac"], 5), "achieved": round(v["achieved"], 3),
                                          "unit": v["unit"], "bound": v["bound"]} for k, v in kern.items()},
-                "cpu_baseline": cpu, "clocks": clocks,
+                "cpu_baseline": cpu, "clocks": clocks, "orientation": orient,
                 "alu_peaks_measured": {k: round(v, 2) for k, v in peaks_alu.items()},
                 "level_source_hash": level_source_hash()}
         print(json.dumps(line))

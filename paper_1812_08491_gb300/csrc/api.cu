@@ -771,13 +771,30 @@ cupc_status build_host_records(const cupc_result* r)
         if (e != cudaSuccess) return CUPC_E_CUDA;
         r->ctx->d2h += (size_t)r->rec_ints * 4;
     }
-    std::vector<std::pair<uint64_t, int64_t>> idx;
-    for (int64_t k = 0; k < r->rec_ints;) {
-        const int i = raw[k], j = raw[k + 1], l = raw[k + 2];
-        idx.emplace_back((uint64_t)i * (uint64_t)r->p + (uint64_t)j, k);
-        k += 3 + l;
+    // records in (i, j) order: a counting sort on i, then each row's few
+    // records by j
+    const int64_t p = r->p;
+    std::vector<int64_t> row_cnt((size_t)p + 1, 0);
+    int64_t nrec = 0;
+    for (int64_t k = 0; k < r->rec_ints; k += 3 + raw[k + 2]) {
+        if (k + 2 >= r->rec_ints || raw[k] < 0 || raw[k] >= p || raw[k + 2] < 1 || raw[k + 2] > CUPC_MAX_LEVEL ||
+            k + 3 + raw[k + 2] > r->rec_ints)
+            return CUPC_E_STATE;
+        ++row_cnt[(size_t)raw[k] + 1];
+        ++nrec;
     }
-    std::sort(idx.begin(), idx.end());
+    for (int64_t i = 0; i < p; ++i) row_cnt[(size_t)i + 1] += row_cnt[(size_t)i];
+    std::vector<std::pair<uint64_t, int64_t>> idx((size_t)nrec);
+    {
+        std::vector<int64_t> fill(row_cnt.begin(), row_cnt.end() - 1);
+        for (int64_t k = 0; k < r->rec_ints; k += 3 + raw[k + 2]) {
+            const int i = raw[k], j = raw[k + 1];
+            idx[(size_t)fill[(size_t)i]++] = std::make_pair((uint64_t)i * (uint64_t)p + (uint64_t)j, k);
+        }
+    }
+    for (int64_t i = 0; i < p; ++i)
+        if (row_cnt[(size_t)i + 1] - row_cnt[(size_t)i] > 1)
+            std::sort(idx.begin() + row_cnt[(size_t)i], idx.begin() + row_cnt[(size_t)i + 1]);
     r->hrec.clear();
     r->hrec.reserve(raw.size());
     r->index.clear();
@@ -946,8 +963,21 @@ cupc_status cupc_result_adjacency(const cupc_result* r, uint8_t* out)
     }
     const std::vector<unsigned>& h = r->on_host ? r->hbits : hd;
     const int64_t p = r->p;
-    for (int64_t i = 0; i < p; ++i)
-        for (int64_t j = 0; j < p; ++j) out[i * p + j] = (uint8_t)((h[i * r->W + (j >> 5)] >> (j & 31)) & 1u);
+    // eight columns at a time: byte b of a row's bits -> its eight 0/1 bytes
+    static const auto table = [] {
+        std::vector<uint8_t> t(256 * 8);
+        for (int b = 0; b < 256; ++b)
+            for (int k = 0; k < 8; ++k) t[(size_t)b * 8 + k] = (uint8_t)((b >> k) & 1);
+        return t;
+    }();
+    for (int64_t i = 0; i < p; ++i) {
+        const unsigned* row = h.data() + i * r->W;
+        uint8_t* o = out + i * p;
+        for (int64_t j = 0; j < p; j += 8) {
+            const unsigned byte = (row[j >> 5] >> (j & 31)) & 0xffu;
+            std::memcpy(o + j, &table[(size_t)byte * 8], (size_t)std::min<int64_t>(8, p - j));
+        }
+    }
     return CUPC_OK;
 }
 

@@ -457,6 +457,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     LevelParams LP{};
     int levels_run = 1;
     int last_launched = 0;
+    int host_stop = 0;   // first level the host saw could not run (not launched)
     Meta M{};
     for (int attempt = 0;; ++attempt) {
         if (attempt > 6) return fail(ctx, CUPC_E_RANGE, "level buffers keep overflowing");
@@ -555,8 +556,11 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         // Levels are launched with at most two in flight: level l is launched only
         // once level l - 2 has reported (through pinned host memory, right after
         // its termination test) that it runs, so at most two launches follow the
-        // last level and they return at once.
+        // last level and they return at once. The report carries level l - 2's
+        // starting max degree: degrees only fall, so level l (which needs a node
+        // of degree >= l + 1) is not launched when that is below l + 1.
         auto launch_levels = [&](int from) -> cupc_status {
+            host_stop = 0;
             LP.queue = (QEntry*)ctx->queue.p;
             if (fp32) {
                 cupc_status sl = ensure(ctx, *ctx_buf(ctx, "live"), qcap * sizeof(int));
@@ -576,7 +580,12 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
                             if (*fl == 0) return fail(ctx, CUPC_E_TIMEOUT, "level flag not written");
                         }
                     }
-                    if (*fl == 2) break;
+                    const int fv = *fl;
+                    if ((fv & 3) == 2) break;
+                    if ((fv >> 4) - 1 < l) {
+                        host_stop = l;
+                        break;
+                    }
                 }
                 LP.l = l;
                 const double r = std::tanh(fisher_tau(alpha, n, l));
@@ -667,8 +676,10 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     R->stats.removed[0] = pairs - (int64_t)(M.nnz / 2);
     if (lmax >= 1) {
         const LevelMeta& H = *ctx->hlmeta;
-        const int last = H.done_level ? H.done_level - 1 : lmax;  // last level that ran
-        if (range_stop && H.done_level == 0)
+        // last level that ran: the one before the level whose termination test
+        // ended the loop, or before the level the host did not launch
+        const int last = H.done_level ? H.done_level - 1 : host_stop ? host_stop - 1 : lmax;
+        if (range_stop && H.done_level == 0 && host_stop == 0)
             return fail(ctx, CUPC_E_RANGE, "a level above CUPC_MAX_LEVEL would be needed");
         levels_run = last + 1;
         for (int l = 1; l <= last && l < CUPC_STATS_LEVELS; ++l) {

@@ -1473,8 +1473,9 @@ __device__ void phase_finalize(const LevelParams& P, bool lrn)
 // ---------------------------------------------------------------------------
 // The level kernel
 // ---------------------------------------------------------------------------
-// Tells the host whether this level runs (1) or the loop has ended (2),
-// through pinned host memory the host polls to decide on further launches.
+// Tells the host whether this level runs (1, with the level's starting max
+// degree in bits 4 and up) or the loop has ended (2), through pinned host
+// memory the host polls to decide on further launches.
 // The store is not fenced: the host only waits a little longer when it lands
 // late (at the latest when the kernel ends), while a system-scope fence would
 // hold this thread, and the barrier after it, for microseconds.
@@ -1525,7 +1526,7 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
         }
         return;
     }
-    if (timer) signal_host(P, 1);
+    if (timer) signal_host(P, 1 | (min(*(volatile int*)&lm->maxdeg[l], 1 << 26) << 4));
     if (!one) {
         bool lrn_scan = false;
         if (!phase_scan_b(P, want_lrn, lrn_scan)) return;

@@ -518,6 +518,9 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             LP.C = Cuse;
             LP.B = binom_view(ctx);
             LP.chunk0 = chunk;
+            // level 1 of a graph with few rows: split each row's j positions too, so
+            // the work items outnumber the warps and a hub row is not one long item
+            LP.jsplit = (p <= 4096) ? 1 : 0;
             LP.canonical = o.canonical_sepset;
             LP.band_abs = (o.recheck_margin > 0) ? o.recheck_margin : kBandAbs;
             LP.band_rel = kBandRel;

@@ -169,10 +169,16 @@ __device__ void phase_prefix(const LevelParams& P, bool fp32, int skip)
 // ---------------------------------------------------------------------------
 // Work items of a row with degree d at level l: the subset ranks of the row
 // (S shared across j) or, in the learned order, of each side's own candidates.
-__device__ __forceinline__ unsigned long long row_items(const Binom& B, int d, int l, int chunk, bool lrn)
+// With the j split (level 1), each subset chunk is further cut into the row's
+// j positions in ranges of 32: item k of the row is subset chunk k / J and
+// j range k % J, J = ceil(d / 32).
+__device__ __forceinline__ int j_ranges(int d, int l, bool js) { return (js && l == 1) ? (d + 31) >> 5 : 1; }
+
+__device__ __forceinline__ unsigned long long row_items(const Binom& B, int d, int l, int chunk, bool lrn,
+                                                        bool js = false)
 {
     if (d < l + 1) return 0;
-    if (!lrn) return (B(d, l) + chunk - 1) / chunk;
+    if (!lrn) return (B(d, l) + chunk - 1) / chunk * (unsigned long long)j_ranges(d, l, js);
     return (unsigned long long)d * ((B(d - 1, l) + chunk - 1) / chunk);
 }
 
@@ -256,7 +262,7 @@ __device__ void phase_scan_one(const LevelParams& P, bool learned)
             const int d = di8[u];
             dmax = max(dmax, d);
             a += d8[u];
-            b += (long long)row_items(P.B, d, l, chunk, lrn);
+            b += (long long)row_items(P.B, d, l, chunk, lrn, P.jsplit);
             if (d >= l + 1) {
                 if (P.B(d, l) == ~0ull) rng = 1;
                 sq += (unsigned long long)(d + 1) * (unsigned long long)(d + 1);
@@ -282,7 +288,7 @@ __device__ void phase_scan_one(const LevelParams& P, bool learned)
         for (int i0 = lo; i0 < hi; i0 += 8) {
             load8(P, i0, hi, d8, di8);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) b += (long long)row_items(P.B, di8[u], l, chunk, lrn);
+            for (int u = 0; u < 8; ++u) b += (long long)row_items(P.B, di8[u], l, chunk, lrn, P.jsplit);
         }
     }
     sq = warp_sum_u64(sq);
@@ -334,7 +340,7 @@ __device__ void phase_scan_one(const LevelParams& P, bool learned)
             P.item_off[i] = eb;
             if (P.poff) P.poff[i] = ec;
             ea += d8[u];
-            const unsigned long long K = row_items(P.B, d, l, chunk, lrn);
+            const unsigned long long K = row_items(P.B, d, l, chunk, lrn, P.jsplit);
             eb += (long long)K;
             hist_add(hist, K);
             if (K > RND - 1) ovf += K - (RND - 1);
@@ -398,7 +404,7 @@ __device__ void phase_scan_a(const LevelParams& P, bool learned)
         const int d = P.deg[i];
         const int di = (P.vlmax && l > P.vlmax[i]) ? 0 : d;
         v[0] += (unsigned long long)d;
-        v[1] += row_items(P.B, di, l, P.chunk0, false);
+        v[1] += row_items(P.B, di, l, P.chunk0, false, P.jsplit);
         if (learned) v[2] += row_items(P.B, di, l, P.chunk0, true);
         dmax = max(dmax, di);
         if (di >= l + 1) {
@@ -474,7 +480,7 @@ __device__ bool phase_scan_b(const LevelParams& P, bool learned, bool& lrn_out)
         unsigned long long b = 0;
         for (int i = r0 + t; i < r1; i += NT) {
             const int di = (P.vlmax && l > P.vlmax[i]) ? 0 : P.deg[i];
-            b += row_items(P.B, di, l, chunk, lrn);
+            b += row_items(P.B, di, l, chunk, lrn, P.jsplit);
         }
         b = warp_sum_u64(b);
         if (lane == 0) wsum[w][0] = b;
@@ -499,7 +505,7 @@ __device__ bool phase_scan_b(const LevelParams& P, bool learned, bool& lrn_out)
             const int d = P.deg[i];
             const int di = (P.vlmax && l > P.vlmax[i]) ? 0 : d;
             a = (unsigned long long)d;
-            b = row_items(P.B, di, l, chunk, lrn);
+            b = row_items(P.B, di, l, chunk, lrn, P.jsplit);
             if (lrn && di >= l + 1) c = (unsigned long long)di * (unsigned long long)(di - 1);
             if (b > RND - 1) ovf += b - (RND - 1);
         }
@@ -736,9 +742,13 @@ __device__ void phase_ci(const LevelParams& P)
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
         const int i = P.item_row[item];
-        const long long k = P.item_c[item];
+        const long long kr = P.item_c[item];
         const long long off = P.row_off[i];
         const int d = (int)(P.row_off[i + 1] - off);
+        // subset chunk k and j positions [jlo, jhi) of this item
+        const int nj = j_ranges(d, l, P.jsplit);
+        const long long k = kr / nj;
+        const int jlo = (int)(kr % nj) * 32, jhi = nj > 1 ? min(d, jlo + 32) : d;
         const unsigned long long nsets = P.B(d, l);
         const unsigned long long s0 = (unsigned long long)k * (unsigned long long)chunk;
         const unsigned long long s1 = min(s0 + (unsigned long long)chunk, nsets);
@@ -810,11 +820,11 @@ __device__ void phase_ci(const LevelParams& P)
             }
             // the row's per-j data in chunks of 32: lane q loads j-position jc + q
             // (coalesced), then the chunk is broadcast one j at a time by shuffles
-            for (int jc = 0; jc < d; jc += 32) {
+            for (int jc = jlo; jc < jhi; jc += 32) {
                 int j_l = 0;
                 unsigned long long b_l = RANK_NONE, pb_l = RANK_NONE;
                 T cij_l = T(0);
-                if (jc + lane < d) {
+                if (jc + lane < jhi) {
                     const long long e = off + jc + lane;
                     j_l = P.cols[e];
                     b_l = ld_cg(P.best + e);
@@ -823,7 +833,7 @@ __device__ void phase_ci(const LevelParams& P)
                     if (!P.canonical || i > j_l) pb_l = ld_cg(P.best + P.partner[e]);
                     cij_l = __ldg(Ci + j_l);
                 }
-                const int jn = min(32, d - jc);
+                const int jn = min(32, jhi - jc);
 #pragma unroll 4
                 for (int q = 0; q < jn; ++q) {
                     const int jp = jc + q;

@@ -95,6 +95,8 @@ struct LevelParams {
     const void* C;                 // p x p correlation (float or double), ld = p
     Binom B;
     int chunk0;                    // preferred subset ranks per work item
+    int jsplit;                    // level 1: a row's items also split its j positions in
+                                   // ranges of 32 (graphs with too few rows to fill the GPU)
     int canonical;
     int l;
     double r, r2;                  // tanh(tau_l) and its square

@@ -42,6 +42,7 @@ _SIGNATURES = {
     "cupc_result_p": ("status", ["vp", "vp"]),
     "cupc_result_adjacency": ("status", ["vp", "vp"]),
     "cupc_result_sep_levels": ("status", ["vp", "vp"]),
+    "cupc_result_edges": ("status", ["vp", "vp", "i64", "vp"]),
     "cupc_result_sepset": ("status", ["vp", "i64", "i64", "vp", "vp"]),
     "cupc_result_sepset_records": ("status", ["vp", "vp", "i64", "vp"]),
     "cupc_result_stats": ("status", ["vp", "vp"]),
@@ -219,6 +220,15 @@ class Result:
     def adjacency(self) -> np.ndarray:
         out = np.empty((self.p, self.p), dtype=np.uint8)
         self._check(load().cupc_result_adjacency(self._h, out.ctypes.data), "cupc_result_adjacency")
+        return out
+
+    def edges(self) -> np.ndarray:
+        """The skeleton's edges as an (m, 2) int32 array of pairs (i, j), i < j."""
+        L = load()
+        n = ctypes.c_int64()
+        self._check(L.cupc_result_edges(self._h, None, 0, ctypes.byref(n)), "cupc_result_edges")
+        out = np.empty((n.value, 2), dtype=np.int32)
+        self._check(L.cupc_result_edges(self._h, out.ctypes.data, n.value, ctypes.byref(n)), "cupc_result_edges")
         return out
 
     def sep_levels(self) -> np.ndarray:

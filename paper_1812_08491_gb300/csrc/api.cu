@@ -987,11 +987,49 @@ cupc_status cupc_result_adjacency(const cupc_result* r, uint8_t* out)
     for (int64_t i = 0; i < p; ++i) {
         const unsigned* row = h.data() + i * r->W;
         uint8_t* o = out + i * p;
-        for (int64_t j = 0; j < p; j += 8) {
-            const unsigned byte = (row[j >> 5] >> (j & 31)) & 0xffu;
-            std::memcpy(o + j, &table[(size_t)byte * 8], (size_t)std::min<int64_t>(8, p - j));
-        }
+        int64_t j = 0;
+        for (; j + 8 <= p; j += 8) std::memcpy(o + j, &table[(size_t)((row[j >> 5] >> (j & 31)) & 0xffu) * 8], 8);
+        if (j < p) std::memcpy(o + j, &table[(size_t)((row[j >> 5] >> (j & 31)) & 0xffu) * 8], (size_t)(p - j));
     }
+    return CUPC_OK;
+}
+
+cupc_status cupc_result_edges(const cupc_result* r, int32_t* out, int64_t cap, int64_t* n_edges)
+{
+    if (!r || !n_edges) return CUPC_E_INVALID;
+    cupc_ctx* ctx = r->ctx;
+    if (!r->edges_ready) {
+        const size_t bytes = (size_t)r->p * r->W * 4;
+        std::vector<unsigned> hd;
+        if (!r->on_host) {
+            hd.resize(bytes / 4);
+            CU(cudaMemcpyAsync(hd.data(), r->bits, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+            CU(cudaStreamSynchronize(ctx->stream));
+            ctx->d2h += bytes;
+        }
+        const std::vector<unsigned>& h = r->on_host ? r->hbits : hd;
+        const int64_t p = r->p;
+        const int W = r->W;
+        r->hedges.clear();
+        for (int64_t i = 0; i < p; ++i) {
+            const unsigned* row = h.data() + i * W;
+            const int w0 = (int)((i + 1) >> 5);
+            for (int w = w0; w < W; ++w) {
+                unsigned m = row[w];
+                if (w == w0) m &= ~0u << ((i + 1) & 31);   // columns j > i only
+                while (m) {
+                    const int64_t j = (int64_t)w * 32 + __builtin_ctz(m);
+                    m &= m - 1;
+                    if (j >= p) break;
+                    r->hedges.push_back((int32_t)i);
+                    r->hedges.push_back((int32_t)j);
+                }
+            }
+        }
+        r->edges_ready = true;
+    }
+    *n_edges = (int64_t)(r->hedges.size() / 2);
+    if (out) std::memcpy(out, r->hedges.data(), (size_t)std::min<int64_t>(cap, *n_edges) * 2 * 4);
     return CUPC_OK;
 }
 

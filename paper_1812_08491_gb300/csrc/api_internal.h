@@ -71,6 +71,8 @@ struct cupc_result {
     mutable bool host_ready = false;
     mutable std::vector<int32_t> hrec;                              // sorted records
     mutable std::vector<std::pair<uint64_t, int64_t>> index;        // (i*p+j) -> offset
+    mutable bool edges_ready = false;
+    mutable std::vector<int32_t> hedges;                            // edge list (i, j), i < j
 };
 
 

@@ -307,3 +307,20 @@ def test_device_peaks(ctx):
     pk = ctx.device_peaks()
     # GB300: FP32 FMA throughput is tens of times the FP64 rate; both positive
     assert pk["fp64_tflops"] > 0.1 and pk["fp32_tflops"] > 10 * pk["fp64_tflops"]
+
+
+def test_edge_list_matches_adjacency(ctx):
+    """cupc_result_edges: the pairs (i, j), i < j, of the skeleton in increasing order."""
+    for seed in range(3):
+        s = sem.workload("small20", seed)
+        res = ctx.skeleton(s.X, s.alpha)
+        adj = res.adjacency()
+        want = np.argwhere(np.triu(adj, 1)).astype(np.int32)
+        assert np.array_equal(res.edges(), want)
+        assert np.array_equal(res.edges(), want)          # cached on the second call
+    s = sem.generate(300, 500, 2100, "scale_free", w_min=0.2)
+    res = ctx.skeleton(s.X, s.alpha)
+    assert np.array_equal(res.edges(), np.argwhere(np.triu(res.adjacency(), 1)).astype(np.int32))
+    probs = [sem.generate(p, 600, 40 + p, "random", degree=3.0) for p in (33, 70)]
+    for r in ctx.skeleton_batch([q.X for q in probs], [q.alpha for q in probs])[0]:
+        assert np.array_equal(r.edges(), np.argwhere(np.triu(r.adjacency(), 1)).astype(np.int32))

@@ -785,37 +785,36 @@ cupc_status build_host_records(const cupc_result* r)
         if (e != cudaSuccess) return CUPC_E_CUDA;
         r->ctx->d2h += (size_t)r->rec_ints * 4;
     }
-    // records in (i, j) order: a counting sort on i, then each row's few
-    // records by j
+    // records in (i, j) order: a least-significant-digit radix sort of the
+    // record offsets, a stable counting sort on j and then on i
     const int64_t p = r->p;
-    std::vector<int64_t> row_cnt((size_t)p + 1, 0);
-    int64_t nrec = 0;
+    std::vector<int64_t> offs;
+    offs.reserve((size_t)(r->rec_ints / 4 + 1));
     for (int64_t k = 0; k < r->rec_ints; k += 3 + raw[k + 2]) {
-        if (k + 2 >= r->rec_ints || raw[k] < 0 || raw[k] >= p || raw[k + 2] < 1 || raw[k + 2] > CUPC_MAX_LEVEL ||
-            k + 3 + raw[k + 2] > r->rec_ints)
+        if (k + 2 >= r->rec_ints || raw[k] < 0 || raw[k] >= p || raw[k + 1] < 0 || raw[k + 1] >= p ||
+            raw[k + 2] < 1 || raw[k + 2] > CUPC_MAX_LEVEL || k + 3 + raw[k + 2] > r->rec_ints)
             return CUPC_E_STATE;
-        ++row_cnt[(size_t)raw[k] + 1];
-        ++nrec;
+        offs.push_back(k);
     }
-    for (int64_t i = 0; i < p; ++i) row_cnt[(size_t)i + 1] += row_cnt[(size_t)i];
-    std::vector<std::pair<uint64_t, int64_t>> idx((size_t)nrec);
-    {
-        std::vector<int64_t> fill(row_cnt.begin(), row_cnt.end() - 1);
-        for (int64_t k = 0; k < r->rec_ints; k += 3 + raw[k + 2]) {
-            const int i = raw[k], j = raw[k + 1];
-            idx[(size_t)fill[(size_t)i]++] = std::make_pair((uint64_t)i * (uint64_t)p + (uint64_t)j, k);
-        }
-    }
-    for (int64_t i = 0; i < p; ++i)
-        if (row_cnt[(size_t)i + 1] - row_cnt[(size_t)i] > 1)
-            std::sort(idx.begin() + row_cnt[(size_t)i], idx.begin() + row_cnt[(size_t)i + 1]);
-    r->hrec.clear();
-    r->hrec.reserve(raw.size());
-    r->index.clear();
-    for (auto& pr : idx) {
-        const int l = raw[pr.second + 2];
-        r->index.emplace_back(pr.first, (int64_t)r->hrec.size());
-        r->hrec.insert(r->hrec.end(), raw.begin() + pr.second, raw.begin() + pr.second + 3 + l);
+    const size_t m = offs.size();
+    std::vector<int64_t> cnt((size_t)p + 1), tmp(m), ord(m);
+    auto pass = [&](const std::vector<int64_t>& in, std::vector<int64_t>& out, int field) {
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (const int64_t k : in) ++cnt[(size_t)raw[k + field] + 1];
+        for (int64_t i = 0; i < p; ++i) cnt[(size_t)i + 1] += cnt[(size_t)i];
+        for (const int64_t k : in) out[(size_t)cnt[(size_t)raw[k + field]]++] = k;
+    };
+    pass(offs, tmp, 1);   // by j
+    pass(tmp, ord, 0);    // by i, stable
+    r->hrec.resize((size_t)r->rec_ints);
+    r->index.resize(m);
+    int64_t w = 0;
+    for (size_t q = 0; q < m; ++q) {
+        const int64_t k = ord[q];
+        const int ints = 3 + raw[k + 2];
+        r->index[q] = std::make_pair((uint64_t)raw[k] * (uint64_t)p + (uint64_t)raw[k + 1], w);
+        std::memcpy(r->hrec.data() + w, raw.data() + k, (size_t)ints * 4);
+        w += ints;
     }
     r->host_ready = true;
     return CUPC_OK;

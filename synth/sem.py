@@ -171,3 +171,22 @@ def batch_workload(count: int = 64, instance: int = 0):
     return [generate(int(ps[k]), int(ns[k]), 4000 * 1000 + 1000 * instance + k, "random",
                      degree=float(ds[k]), w_min=0.1, dtype=np.float64, alpha=0.05)
             for k in range(count)]
+
+
+def paper_density(p: int, n: int, d: float, seed: int, alpha: float = 0.01) -> SEM:
+    """The paper's scalability generator (Sec. 5.6): a lower-triangular random
+    weight matrix A with Bernoulli(d) support and U[0.1, 1] entries (all
+    positive), V_j -> V_i for A[i, j] != 0, and V_i = N_i + sum_{j < i} A[i, j] V_j
+    for i = 0 .. p - 1 with N_i ~ N(0, 1). The variables are labelled in
+    topological order. With positive weights the magnitudes grow
+    geometrically along that order, so the data is FP64."""
+    rng = np.random.default_rng(seed)
+    sup = rng.random((p, p)) < d
+    A = np.tril(sup, -1) * rng.uniform(0.1, 1.0, size=(p, p))
+    N = rng.standard_normal((p, n))
+    Xt = np.empty((p, n))
+    for i in range(p):
+        Xt[i] = N[i] + A[i, :i] @ Xt[:i]
+    dst, src = np.nonzero(A)
+    return SEM(Xt=Xt, src=src.astype(np.int64), dst=dst.astype(np.int64), weight=A[dst, src], p=p, n=n, seed=seed,
+               family="paper_density", alpha=alpha, meta={"density": d, "w_min": 0.1, "dtype": "float64"})

@@ -162,8 +162,18 @@ def orientation_line(ctx, X, s, mode, oracle_res=None, reps=5):
         _, st = r.orient(marks=False)
         times.append(st["ms"])
     r.free()
-    out = {"device_ms": statistics.median(times[1:]), "rounds": st["rounds"], "directed": st["directed"],
+    ms = statistics.median(times[1:])
+    # algorithmic bytes: the skeleton bitset read for the neighbour lists and the
+    # v-structures, per rule round the three bitsets (head, headT, proposals) read
+    # and the proposals written, and the p x p marks written
+    wbytes = s.p * ((s.p + 31) // 32) * 4
+    byts = 3 * wbytes + st["rounds"] * 4 * wbytes + s.p * s.p
+    ach = byts / (ms * 1e-3) / 1e9
+    hbm = _peaks()["hbm_gbs"]
+    out = {"device_ms": ms, "rounds": st["rounds"], "directed": st["directed"],
            "undirected": st["undirected"], "bidirected": st["bidirected"],
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                        "alg_bytes": byts, "note": "latency-bound: one host readback per rule round"},
            "note": "second step of PC-stable, outside the timed skeleton step"}
     if oracle_res is not None:
         import oracle

@@ -288,9 +288,13 @@ typedef struct {
  * marks at the start of the round and apply all their orientations together,
  * until a round changes nothing; an edge proposed both ways in a round stays
  * undirected; only undirected edges are oriented, and only directed edges
- * count as arrows in the rules' premises. The result is independent of the
- * variable order. Device scratch comes from the context's pool; the result
- * itself is not changed. Synchronises the context stream once per round.
+ * count as arrows in the rules' premises. Given the skeleton and the SepSets,
+ * the marks do not depend on the order in which triples or edges are visited
+ * (the SepSets themselves are the canonical ones of the serial order in
+ * canonical mode, and any separating sets otherwise, so the marks equal the
+ * oracle's for canonical results). Device scratch comes from the context's
+ * pool; the result itself is not changed. Synchronises the context stream
+ * once per round.
  * Errors: CUPC_E_INVALID (NULL result), CUPC_E_STATE (a result without its
  * skeleton or SepSet records), CUPC_E_NOMEM, CUPC_E_CUDA. */
 cupc_status cupc_result_orient(cupc_result* res, uint8_t* marks, cupc_orient_stats* stats);

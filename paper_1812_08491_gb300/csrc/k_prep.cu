@@ -67,6 +67,10 @@ __device__ __forceinline__ unsigned short bf16_bits_rn(float x)
 
 __device__ __forceinline__ float bf16_bits_to_float(unsigned short h) { return __uint_as_float((unsigned)h << 16); }
 
+// Row elements a thread loads before using them in the standardisation passes
+// (the element order of its sums is unchanged).
+constexpr int MU = 8;
+
 // Shifted moments S1 = sum (x - K), S2 = sum (x - K)^2 of a row, by one block
 // of NT threads, in a fixed order. FP64 data, or FP64 rows requested: FP64
 // sums per thread, a warp tree and the warp partials in order. FP32 data
@@ -87,16 +91,24 @@ __device__ __forceinline__ void shifted_moments(const T* __restrict__ row, int n
     if constexpr (sizeof(T) == 4) {
         if (pairs) {
             float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
-            for (int k = threadIdx.x; k < n; k += NT) {
-                float dh, dl;
-                two_sum(row[k], -K, dh, dl);
-                pair_add(ah, al, dh, dl);
-                const float p = __fmul_rn(dh, dh);
-                float q = fmaf(dh, dh, -p);
-                q = fmaf(2.f * dh, dl, q);
-                float ph, pl;
-                fast_two_sum(p, q, ph, pl);
-                pair_add(bh, bl, ph, pl);
+            // a thread's elements k, k + NT, ... in order; eight loads in flight
+            for (int k0 = threadIdx.x; k0 < n; k0 += NT * MU) {
+                float x[MU];
+#pragma unroll
+                for (int u = 0; u < MU; ++u) x[u] = (k0 + u * NT < n) ? row[k0 + u * NT] : 0.f;
+#pragma unroll
+                for (int u = 0; u < MU; ++u) {
+                    if (k0 + u * NT >= n) break;
+                    float dh, dl;
+                    two_sum(x[u], -K, dh, dl);
+                    pair_add(ah, al, dh, dl);
+                    const float p = __fmul_rn(dh, dh);
+                    float q = fmaf(dh, dh, -p);
+                    q = fmaf(2.f * dh, dl, q);
+                    float ph, pl;
+                    fast_two_sum(p, q, ph, pl);
+                    pair_add(bh, bl, ph, pl);
+                }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -128,10 +140,17 @@ __device__ __forceinline__ void shifted_moments(const T* __restrict__ row, int n
     }
     const double Kd = (double)K;
     double s1 = 0.0, s2 = 0.0;
-    for (int k = threadIdx.x; k < n; k += NT) {
-        const double d = (double)row[k] - Kd;
-        s1 += d;
-        s2 = fma(d, d, s2);
+    for (int k0 = threadIdx.x; k0 < n; k0 += NT * MU) {
+        T x[MU];
+#pragma unroll
+        for (int u = 0; u < MU; ++u) x[u] = (k0 + u * NT < n) ? row[k0 + u * NT] : T(0);
+#pragma unroll
+        for (int u = 0; u < MU; ++u) {
+            if (k0 + u * NT >= n) break;
+            const double d = (double)x[u] - Kd;
+            s1 += d;
+            s2 = fma(d, d, s2);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -237,22 +256,39 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
     unsigned short* lrow = zlo ? (unsigned short*)zlo + (size_t)v * ldb : nullptr;
     // two loops, not one with a branch inside: the compiler would evaluate both
     // sides of a short branch, putting the FP64 side on every element
+    // (eight loads in flight per thread, as in the moments)
     if (sizeof(T) == 4 && fast) {
-        for (int k = threadIdx.x; k < n; k += NT) {
-            const float z = (((float)row[k] - mh) - ml) * fi;
-            const unsigned short h = bf16_bits_rn(z);
-            hrow[k] = h;
-            lrow[k] = bf16_bits_rn(z - bf16_bits_to_float(h));
-        }
-    } else {
-        for (int k = threadIdx.x; k < n; k += NT) {
-            const double d = (double)row[k] - mean;
-            if (zrow) zrow[k] = d * inv;
-            if (hrow) {
-                const float z = (float)d * fi;
+        for (int k0 = threadIdx.x; k0 < n; k0 += NT * MU) {
+            T x[MU];
+#pragma unroll
+            for (int u = 0; u < MU; ++u) x[u] = (k0 + u * NT < n) ? row[k0 + u * NT] : T(0);
+#pragma unroll
+            for (int u = 0; u < MU; ++u) {
+                const int k = k0 + u * NT;
+                if (k >= n) break;
+                const float z = (((float)x[u] - mh) - ml) * fi;
                 const unsigned short h = bf16_bits_rn(z);
                 hrow[k] = h;
                 lrow[k] = bf16_bits_rn(z - bf16_bits_to_float(h));
+            }
+        }
+    } else {
+        for (int k0 = threadIdx.x; k0 < n; k0 += NT * MU) {
+            T x[MU];
+#pragma unroll
+            for (int u = 0; u < MU; ++u) x[u] = (k0 + u * NT < n) ? row[k0 + u * NT] : T(0);
+#pragma unroll
+            for (int u = 0; u < MU; ++u) {
+                const int k = k0 + u * NT;
+                if (k >= n) break;
+                const double d = (double)x[u] - mean;
+                if (zrow) zrow[k] = d * inv;
+                if (hrow) {
+                    const float z = (float)d * fi;
+                    const unsigned short h = bf16_bits_rn(z);
+                    hrow[k] = h;
+                    lrow[k] = bf16_bits_rn(z - bf16_bits_to_float(h));
+                }
             }
         }
     }

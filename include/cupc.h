@@ -303,8 +303,8 @@ cupc_status cupc_result_orient(cupc_result* res, uint8_t* marks, cupc_orient_sta
  * `out` (caller-owned, p*p bytes). Synchronises the context stream. */
 cupc_status cupc_result_adjacency(const cupc_result* res, uint8_t* out);
 
-/* The skeleton as an edge list: pairs (i, j) with i < j in increasing (i, j)
- * order, written to out[2k], out[2k + 1] (host buffer, caller-owned, room for
+/* The skeleton G that Algorithm 1 returns (Sec. 2.4), as an edge list: pairs
+ * (i, j) with i < j in increasing (i, j) order, written to out[2k], out[2k + 1] (host buffer, caller-owned, room for
  * `cap` pairs); *n_edges = the number of edges. With out == NULL only
  * *n_edges is set. The list is built once per result (one download of the
  * bitset) and kept until cupc_result_free. */

@@ -304,10 +304,11 @@ cupc_status cupc_result_orient(cupc_result* res, uint8_t* marks, cupc_orient_sta
 cupc_status cupc_result_adjacency(const cupc_result* res, uint8_t* out);
 
 /* The skeleton G that Algorithm 1 returns (Sec. 2.4), as an edge list: pairs
- * (i, j) with i < j in increasing (i, j) order, written to out[2k], out[2k + 1] (host buffer, caller-owned, room for
- * `cap` pairs); *n_edges = the number of edges. With out == NULL only
- * *n_edges is set. The list is built once per result (one download of the
- * bitset) and kept until cupc_result_free. */
+ * (i, j) with i < j in increasing (i, j) order, written to out[2k] and
+ * out[2k + 1] (host buffer, caller-owned, room for `cap` pairs); *n_edges =
+ * the number of edges. With out == NULL only *n_edges is set. The list is
+ * built once per result (one download of the bitset) and kept until
+ * cupc_result_free. */
 cupc_status cupc_result_edges(const cupc_result* res, int32_t* out, int64_t cap, int64_t* n_edges);
 
 /* Copies, into the host buffer `out` (p*p int16), the level at which each pair

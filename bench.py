@@ -696,6 +696,10 @@ def main():
         secs, cu = cpu_oracle_run(s, cores, keep)
         cpu = {"value": cu / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"whole {args.workload} skeleton once (correlation + all levels), {secs:.2f} s"}
+        # the oracle on one core (the serial analogue), when that stays within ~30 s
+        if secs * cores <= 30.0:
+            s1, cu1 = cpu_oracle_run(s, 1)
+            cpu["serial_1core"] = {"value": cu1 / s1, "unit": UNIT, "seconds": round(s1, 3)}
     orient = orientation_line(ctx, X, s, mode, keep.get("res")) if rank == 0 else None
 
     if rank == 0:

@@ -579,15 +579,35 @@ cupc_status make_results(cupc_ctx* ctx, BatchPlan& B, float ms, cupc_result** ou
         BCU(cudaMemcpyAsync(raw.data(), B.rec.p, raw.size() * 4, cudaMemcpyDeviceToHost, B.gs));
         BCU(cudaStreamSynchronize(B.gs));
     }
-    std::vector<std::vector<std::pair<uint64_t, size_t>>> idx(K.nprob);
+    for (int k = 0; k < K.nprob; ++k) out[k] = nullptr;
+    // each problem's record offsets in (i, j) order: a least-significant-digit
+    // radix sort, a stable counting sort on local j and then on local i
+    std::vector<std::vector<size_t>> idx(K.nprob);
     for (size_t q = 0; q < raw.size();) {
-        const int i = raw[q], j = raw[q + 1], l = raw[q + 2];
-        const int k = B.vprob[i];
-        const ProbDesc& D = B.probs[k];
-        idx[k].emplace_back((uint64_t)(i - D.off) * (uint64_t)D.p + (uint64_t)(j - D.off), q);
+        const int l = raw[q + 2];
+        if (l < 1 || l > CUPC_MAX_LEVEL || q + 3 + l > raw.size())
+            return ctx_fail(ctx, CUPC_E_STATE, "bad SepSet record");
+        idx[B.vprob[raw[q]]].push_back(q);
         q += 3 + l;
     }
-    for (int k = 0; k < K.nprob; ++k) out[k] = nullptr;
+    {
+        std::vector<size_t> cnt, tmp;
+        for (int k = 0; k < K.nprob; ++k) {
+            std::vector<size_t>& v = idx[k];
+            if (v.size() < 2) continue;
+            const ProbDesc& D = B.probs[k];
+            cnt.assign((size_t)D.p + 1, 0);
+            tmp.resize(v.size());
+            auto pass = [&](std::vector<size_t>& in, std::vector<size_t>& o, int field) {
+                std::fill(cnt.begin(), cnt.end(), 0);
+                for (const size_t q : in) ++cnt[(size_t)(raw[q + field] - D.off) + 1];
+                for (int i = 0; i < D.p; ++i) cnt[(size_t)i + 1] += cnt[(size_t)i];
+                for (const size_t q : in) o[cnt[(size_t)(raw[q + field] - D.off)]++] = q;
+            };
+            pass(v, tmp, 1);   // by local j
+            pass(tmp, v, 0);   // by local i, stable
+        }
+    }
     cupc_stats S{};
     S.levels = levels;
     for (int k = 0; k < K.nprob; ++k) {
@@ -601,17 +621,22 @@ cupc_status make_results(cupc_ctx* ctx, BatchPlan& B, float ms, cupc_result** ou
         const size_t nw = (size_t)D.p * R->W;
         R->hbits.assign(B.h_bits + D.bw, B.h_bits + D.bw + nw);
         R->hbits0.assign(B.h_bits0 + D.bw, B.h_bits0 + D.bw + nw);
-        std::sort(idx[k].begin(), idx[k].end());
-        R->hrec.reserve(idx[k].size() * 4);
+        size_t ints = 0;
+        for (const size_t q : idx[k]) ints += 3 + (size_t)raw[q + 2];
+        R->hrec.resize(ints);
+        R->index.resize(idx[k].size());
         std::vector<int64_t> rem(CUPC_STATS_LEVELS, 0);
-        for (auto& pr : idx[k]) {
-            const size_t q = pr.second;
+        size_t w = 0, r = 0;
+        for (const size_t q : idx[k]) {
             const int l = raw[q + 2];
-            R->index.emplace_back(pr.first, (int64_t)R->hrec.size());
-            R->hrec.push_back(raw[q] - D.off);
-            R->hrec.push_back(raw[q + 1] - D.off);
-            R->hrec.push_back(l);
-            for (int c = 0; c < l; ++c) R->hrec.push_back(raw[q + 3 + c] - D.off);
+            const int i = raw[q] - D.off, j = raw[q + 1] - D.off;
+            R->index[r++] = std::make_pair((uint64_t)i * (uint64_t)D.p + (uint64_t)j, (int64_t)w);
+            int32_t* o = R->hrec.data() + w;
+            o[0] = i;
+            o[1] = j;
+            o[2] = l;
+            for (int c = 0; c < l; ++c) o[3 + c] = raw[q + 3 + c] - D.off;
+            w += 3 + (size_t)l;
             if (l < CUPC_STATS_LEVELS) rem[l]++;
         }
         R->host_ready = true;

@@ -67,3 +67,13 @@ def test_create_fails_cleanly_without_gpu(lib):
     h = ctypes.c_void_p()
     st = lib.cupc_create(ctypes.byref(h), 0, None)
     assert st == -3 and not h.value
+
+
+def test_result_entry_points_reject_null_results(lib):
+    """The result accessors and the orientation step check their arguments
+    before any CUDA work (CUPC_E_INVALID = -1)."""
+    n = ctypes.c_int64()
+    assert lib.cupc_result_orient(None, None, None) == -1
+    assert lib.cupc_result_edges(None, None, 0, ctypes.byref(n)) == -1
+    assert lib.cupc_result_sepset_records(None, None, 0, ctypes.byref(n)) == -1
+    assert lib.cupc_result_adjacency(None, None) == -1

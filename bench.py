@@ -580,11 +580,15 @@ def main():
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    # the options of each form, built once (the public call takes them as given)
+    form_opts = {m: ctx.options(mode=m, canonical=True, max_level=s.max_level,
+                                learned_order=bool(args.learned) and m == cupc.MODE_FP32_RECHECK)
+                 for m in (cupc.MODE_FP32_RECHECK, cupc.MODE_PLAIN_FP64)}
+
     def step(m, done=None):
         """One skeleton call; `done` (a CUDA event) is recorded as soon as the call
         returns, before the result's statistics are read and its memory freed."""
-        lo = bool(args.learned) and m == cupc.MODE_FP32_RECHECK
-        res = ctx.skeleton(X, s.alpha, mode=m, canonical=True, max_level=s.max_level, learned_order=lo)
+        res = ctx.skeleton(X, s.alpha, form_opts[m])
         if done is not None:
             done.record(stream)
         st = res.stats()

@@ -204,7 +204,7 @@ def run_reference(args, workload_name):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded linear-Gaussian SEM)",
-            "config": _config(workload_name, s, "cpu oracle"),
+            "config": dict(_config(workload_name, s, "cpu oracle"), l2="not applicable (host cores)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"whole {workload_name} skeleton per step (correlation + all levels)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

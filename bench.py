@@ -653,12 +653,12 @@ def main():
     if not args.no_e2e:
         Xh = torch.from_numpy(s.Xt).pin_memory()
         Xhv = Xh.T
-        r = ctx.skeleton(Xhv, s.alpha, mode=mode, max_level=s.max_level, learned_order=bool(args.learned))
+        r = ctx.skeleton(Xhv, s.alpha, form_opts[mode])
         r.edges(); r.records_raw(); r.free()
         secs, h2d, d2h = 0.0, 0, 0
         for _ in range(args.steps):
             t0 = time.perf_counter()
-            r = ctx.skeleton(Xhv, s.alpha, mode=mode, max_level=s.max_level, learned_order=bool(args.learned))
+            r = ctx.skeleton(Xhv, s.alpha, form_opts[mode])
             r.edges()
             recs = r.records_raw()
             secs += time.perf_counter() - t0

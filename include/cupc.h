@@ -139,21 +139,26 @@ typedef struct {
 typedef struct cupc_ctx cupc_ctx;
 typedef struct cupc_result cupc_result;
 
-/* Fills *o with the defaults documented above. */
+/* Fills *o with the defaults documented above. The options are the library's
+ * own; the paper's inputs are only the data and alpha (Sec. 1, Sec. 4.3). */
 void cupc_options_default(cupc_options* o);
 
 /* Creates a context on CUDA device `device`. `stream` is a cudaStream_t (may be
  * NULL for the legacy default stream; a framework's stream handle may be passed).
- * The device must be sm_103 (GB300); otherwise CUPC_E_CUDA. */
+ * The device must be sm_103 (GB300); otherwise CUPC_E_CUDA. Resource
+ * management only: the paper has no counterpart (its program owns one GPU and
+ * its buffers for the whole run, Sec. 5.1). */
 cupc_status cupc_create(cupc_ctx** out, int device, void* stream);
 
-/* Changes the stream subsequent calls use. */
+/* Changes the stream subsequent calls use. The paper has no counterpart. */
 cupc_status cupc_set_stream(cupc_ctx* ctx, void* stream);
 
-/* Frees the context and its workspace. Results stay valid. */
+/* Frees the context and its workspace. Results stay valid. The paper has no
+ * counterpart. */
 void cupc_destroy(cupc_ctx* ctx);
 
-/* Message for the last error on this context ("" if none). Never NULL. */
+/* Message for the last error on this context ("" if none). Never NULL. The
+ * paper has no counterpart. */
 const char* cupc_last_error(const cupc_ctx* ctx);
 
 /* Algorithm 1 / Algorithm 2 on data: standardise X in FP64, form the
@@ -259,7 +264,8 @@ cupc_status cupc_batch_autotune(cupc_ctx* ctx, int nprob, const void* const* X, 
  * counterpart. Synchronises the context stream. */
 cupc_status cupc_device_peaks(cupc_ctx* ctx, double* fp64_tflops, double* fp32_tflops);
 
-/* Number of variables of a result. */
+/* Number of variables of a result (the n of the paper's problem statement,
+ * Sec. 1: the vertices of G). */
 cupc_status cupc_result_p(const cupc_result* res, int64_t* p);
 
 /* Counts of one orientation (cupc_result_orient). */
@@ -299,8 +305,10 @@ typedef struct {
  * skeleton or SepSet records), CUPC_E_NOMEM, CUPC_E_CUDA. */
 cupc_status cupc_result_orient(cupc_result* res, uint8_t* marks, cupc_orient_stats* stats);
 
-/* Copies the skeleton as a p x p uint8 matrix (1 = edge) into the host buffer
- * `out` (caller-owned, p*p bytes). Synchronises the context stream. */
+/* The skeleton G that Algorithm 1 returns (Sec. 2.4; the adjacency matrix A_G
+ * of Algorithm 2 and Sec. 3, at the end of the last level) as a p x p uint8 matrix (1 = edge)
+ * in the host buffer `out` (caller-owned, p*p bytes). Synchronises the context
+ * stream. */
 cupc_status cupc_result_adjacency(const cupc_result* res, uint8_t* out);
 
 /* The skeleton G that Algorithm 1 returns (Sec. 2.4), as an edge list: pairs
@@ -312,24 +320,31 @@ cupc_status cupc_result_adjacency(const cupc_result* res, uint8_t* out);
 cupc_status cupc_result_edges(const cupc_result* res, int32_t* out, int64_t cap, int64_t* n_edges);
 
 /* Copies, into the host buffer `out` (p*p int16), the level at which each pair
- * was removed, or -1 where the edge is present (the diagonal is -1). */
+ * was removed (|S| of its SepSet, Algorithm 1), or -1 where the edge is present
+ * (the diagonal is -1). */
 cupc_status cupc_result_sep_levels(const cupc_result* res, int16_t* out);
 
-/* SepSet of the pair (i, j): writes the members (increasing) to out[0..*len)
+/* SepSet(V_i, V_j) that Algorithm 1 stores when it removes the edge (the
+ * second output of the skeleton phase, Sec. 2.4): writes the members
+ * (increasing) to out[0..*len)
  * (caller-owned, at least CUPC_MAX_LEVEL entries) and the size to *len;
  * *len = -1 when the edge is present. Level-0 removals have *len = 0. */
 cupc_status cupc_result_sepset(const cupc_result* res, int64_t i, int64_t j, int32_t* out, int* len);
 
-/* All SepSet records of removals at levels >= 1, as consecutive int32 groups
+/* The SepSets of Algorithm 1 (Sec. 2.4) for every removal at level >= 1, as
+ * consecutive int32 groups
  * (i, j, l, S[0..l)) with i < j, sorted by (i, j). With out == NULL only
  * *n_ints is set; otherwise at most `cap` ints are written. */
 cupc_status cupc_result_sepset_records(const cupc_result* res, int32_t* out, int64_t cap,
                                        int64_t* n_ints);
 
-/* Per-level statistics of the call that produced `res`. */
+/* Per-level statistics of the call that produced `res`: the test counts of
+ * Algorithm 1 in serial order (the paper's Fig. 2 count convention), tests
+ * executed, removals, device times. The paper reports runtimes only (Sec. 5.3);
+ * the counters are the library's own. */
 cupc_status cupc_result_stats(const cupc_result* res, cupc_stats* out);
 
-/* Frees a result (NULL is ignored). */
+/* Frees a result (NULL is ignored). The paper has no counterpart. */
 void cupc_result_free(cupc_result* res);
 
 /* ---------------------------------------------------------------------------
@@ -410,7 +425,11 @@ cupc_status cupc_mlp_train(cupc_ctx* ctx, const float* X, const float* t, int64_
  * It calls no cudaMalloc, cudaFree or allocating library routine.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. Every call on a device shares the scratch: calls
+ * before any stream capture. The address is kept for the life of the process:
+ * it assumes the device's primary context (the one the CUDA runtime and
+ * PyTorch use) and no cudaDeviceReset() on that device afterwards; a caller
+ * that resets the device or makes another driver context current must not
+ * call this entry point again in that process. Every call on a device shares the scratch: calls
  * that overlap on the GPU (other threads or streams) race and must be
  * serialised by the caller; the error flag is cleared at the start of each
  * call. Errors: CUPC_E_INVALID, CUPC_E_RANGE, CUPC_E_NUMERIC (zero variance or

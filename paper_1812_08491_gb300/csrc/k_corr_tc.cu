@@ -25,8 +25,8 @@
 // the whole K range writes its tile of C directly: times 1/n, the i <= j
 // entries row by row and their mirror images (j, i) column by column, so C is
 // exactly symmetric; a unit that covers a K slice stores its partial tile, and
-// a second kernel adds the slices in a fixed order in FP64, scales by 1/n and
-// writes both triangles the same way.
+// a second kernel adds the slices in a fixed order as compensated FP32 pairs,
+// scales by 1/n and writes both triangles the same way.
 //
 // Every mbarrier wait is bounded in time; on expiry the thread raises an error
 // flag, the others stop at their next wait, TMEM is freed and the kernel ends.
@@ -452,9 +452,14 @@ k_corr_tc(const __grid_constant__ CUtensorMap tmAH, const __grid_constant__ CUte
 
 // Sum of the K-slice partials in slice order, times 1/n; the i < j value is
 // written to (i, j) and, through a shared-memory transpose, to (j, i); the
-// diagonal is 1. The slices are added with Knuth's two-sum (an FP32 pair: the
-// same result as an FP64 sum of these few terms, without GB300's narrow FP64
-// pipe). Block (tile, 8-row band): 256 threads, warp = row of the band; a lane
+// diagonal is 1. The slices are added with Knuth's two-sum, the rounding error
+// of each addition collected in a second FP32 word (the compensated sum Sum2 of
+// Ogita, Rump and Oishi, 2005): the result is within 2^-24 |sum| +
+// (k 2^-24)^2 sum|slice| of the exact sum of k slices. The second term is what
+// separates it from an FP64 sum (within k 2^-53 sum|slice|); it stays below the
+// output's own FP32 rounding while k^2 sum|slice| < 2^24 |sum|. GB300's FP64
+// pipe is narrow, so the pair is used instead. Block (tile, 8-row band): 256
+// threads, warp = row of the band; a lane
 // owns columns 4 lane .. 4 lane + 3 and 128 + 4 lane .. 128 + 4 lane + 3 and
 // reads them as two float4 per slice, eight slices' loads in flight at a time.
 constexpr int RROWS = 8;

@@ -194,6 +194,28 @@ def test_pcor_degenerate_conditional_variance():
     assert deg and math.isnan(rho)
 
 
+@pytest.mark.parametrize("h, degenerate", [(5e-11, True), (9e-11, True), (1e-9, False), (5e-9, False)])
+def test_pcor_near_zero_conditional_variance(h, degenerate):
+    # Var(V0 | V2) = 1 - C02^2 = h > 0. A conditional variance at or below 1e-10 is
+    # the rounding level of C's unit diagonal, where V0 is treated as a linear
+    # function of S (zero variance, independent); above it the test is an
+    # ordinary one and rho follows the level-1 textbook formula.
+    # Unit-variance V2 = Z2, V0 = c Z2 + sqrt(h) Z0, V1 = 0.3 Z2 + 0.4 Z0 + sqrt(0.75) Z1
+    # with independent standard Z: C02 = c = sqrt(1 - h), C12 = 0.3, C01 = 0.3 c + 0.4 sqrt(h),
+    # and rho(V0, V1 | V2) = 0.4 / sqrt(0.91) whatever h is.
+    c02 = math.sqrt(1.0 - h)
+    c01 = 0.3 * c02 + 0.4 * math.sqrt(h)
+    C = np.array([[1.0, c01, c02], [c01, 1.0, 0.3], [c02, 0.3, 1.0]])
+    rho, deg, _ = oracle.pcor(C, 0, 1, [2])
+    assert deg == degenerate
+    if degenerate:
+        assert math.isnan(rho)
+    else:
+        ref = (c01 - c02 * 0.3) / math.sqrt((1.0 - c02 * c02) * (1.0 - 0.09))
+        assert abs(ref - 0.4 / math.sqrt(0.91)) < 1e-5
+        assert abs(abs(rho) - ref) <= 1e-6 * ref, (rho, ref)
+
+
 # --------------------------------------------------------------------------
 # Sec. 4.4 / Algorithm 7
 # --------------------------------------------------------------------------

@@ -5,9 +5,10 @@ cupc_correlation_noalloc serves callers that may not allocate device memory
 cudaMalloc is not acceptable). Its scratch is a fixed device array inside the
 library, shared by all calls. This test calls it twice in a row through the C
 ABI, with different shapes and layouts, and compares each output with
-cupc_correlation's (FP64) within the correlation tolerance of the other tests
-(1e-13). It also checks that oversized inputs are refused. This file is
-collected last so a failure here never hides the other tests' results.
+cupc_correlation's (FP64) and with the FP64 CPU oracle's correlation, within
+the correlation tolerance of the other tests (1e-13). It also checks that
+oversized inputs are refused. This file is collected last so a failure here
+never hides the other tests' results.
 """
 import ctypes
 
@@ -17,6 +18,7 @@ import pytest
 cupc = pytest.importorskip("paper_1812_08491_gb300")
 torch = pytest.importorskip("torch")
 
+import oracle
 from synth import sem
 
 pytestmark = pytest.mark.gpu
@@ -49,6 +51,10 @@ def test_noalloc_matches_allocating_entry_point(cuda_device):
         assert st == 0, st
         err = (out - ref).abs().max().item()
         assert err <= 1e-13, err
+        # and against the FP64 oracle on the same values (float32 data widened)
+        C_or = oracle.correlation(np.asarray(s.X, dtype=np.float64))
+        err_or = np.max(np.abs(out.cpu().numpy() - C_or))
+        assert err_or <= 1e-13, err_or
     ctx.close()
 
 

@@ -397,7 +397,6 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     const size_t bitbytes = (size_t)p * W * 4;
     if ((s = dalloc(ctx, (void**)&R->bits, bitbytes)) != CUPC_OK) return s;
     if ((s = dalloc(ctx, (void**)&R->bits0, bitbytes)) != CUPC_OK) return s;
-    if (fp32 && (s = ensure(ctx, ctx->backup[0], bitbytes)) != CUPC_OK) return s;
     size_t qcap = std::max<size_t>(1u << 20, (size_t)4 * p);
     if (fp32 && (s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
     if ((s = ensure_binom(ctx, std::max(p + 1, 64))) != CUPC_OK) return s;
@@ -482,6 +481,17 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             if ((s = ensure(ctx, ctx->partner, (size_t)nnz_cap * 4)) != CUPC_OK) return s;
             if ((s = ensure(ctx, ctx->wpre, bitbytes)) != CUPC_OK) return s;
             if ((s = ensure(ctx, ctx->best, (size_t)nnz_cap * 8)) != CUPC_OK) return s;
+            // the second A'_G buffer, the per-slot survival flags and positions
+            if ((s = ensure(ctx, *ctx_buf(ctx, "row_off2"), (size_t)(p + 1) * 8)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, *ctx_buf(ctx, "cols2"), (size_t)nnz_cap * 4)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, *ctx_buf(ctx, "srow2"), (size_t)nnz_cap * 4)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, *ctx_buf(ctx, "partner2"), (size_t)nnz_cap * 4)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, *ctx_buf(ctx, "alive"), (size_t)nnz_cap)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, *ctx_buf(ctx, "nrank"), (size_t)nnz_cap * 4)) != CUPC_OK) return s;
+            // level 1 by conditioning variable when a C row fits the staging buffer
+            const size_t ce = fp32 ? 4 : 8;
+            const int l1_pivot = l1_buffers(p, (int)ce);
+            if (l1_pivot && (s = ensure(ctx, *ctx_buf(ctx, "cval"), (size_t)nnz_cap * ce)) != CUPC_OK) return s;
             if ((s = ensure(ctx, ctx->item_row, (size_t)item_cap * 4)) != CUPC_OK) return s;
             if ((s = ensure(ctx, *ctx_buf(ctx, "item_c"), (size_t)item_cap * 4)) != CUPC_OK) return s;
             if ((s = ensure_binom(ctx, p + 2)) != CUPC_OK) return s;
@@ -502,7 +512,6 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             LP.p = p;
             LP.nwords = (long long)p * W;
             LP.ctas_per_sm = o.ctas_per_sm;
-            LP.backup = fp32 ? (unsigned*)ctx->backup[0].p : nullptr;
             LP.deg = (int*)ctx->deg.p;
             LP.row_off = (long long*)ctx->row_off.p;
             LP.item_off = (long long*)ctx->item_off.p;
@@ -512,10 +521,19 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             LP.cols = (int*)ctx->cols.p;
             LP.srow = (int*)ctx->srow.p;
             LP.partner = (int*)ctx->partner.p;
+            LP.row_off2 = (long long*)ctx_buf(ctx, "row_off2")->p;
+            LP.cols2 = (int*)ctx_buf(ctx, "cols2")->p;
+            LP.srow2 = (int*)ctx_buf(ctx, "srow2")->p;
+            LP.partner2 = (int*)ctx_buf(ctx, "partner2")->p;
+            LP.alive = (unsigned char*)ctx_buf(ctx, "alive")->p;
+            LP.nrank = (int*)ctx_buf(ctx, "nrank")->p;
             LP.wpre = (int*)ctx->wpre.p;
             LP.best = (unsigned long long*)ctx->best.p;
             LP.nnz_cap = nnz_cap;
             LP.C = Cuse;
+            LP.l1_pivot = l1_pivot;
+            LP.pstage = p;
+            LP.cval = l1_pivot ? ctx_buf(ctx, "cval")->p : nullptr;
             LP.B = binom_view(ctx);
             LP.chunk0 = chunk;
             // level 1 of a graph with few rows: split each row's j positions too, so
@@ -569,6 +587,9 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
                 cupc_status sl = ensure(ctx, *ctx_buf(ctx, "live"), qcap * sizeof(int));
                 if (sl != CUPC_OK) return sl;
                 LP.live = (int*)ctx_buf(ctx, "live")->p;
+                sl = ensure(ctx, *ctx_buf(ctx, "rc_cnt"), (size_t)kRcCnt * sizeof(int));
+                if (sl != CUPC_OK) return sl;
+                LP.rc_cnt = (int*)ctx_buf(ctx, "rc_cnt")->p;
             }
             LP.qcap = qcap;
             LP.host_flags = ctx->dflags;
@@ -643,13 +664,13 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             }
             const int ol = H.overflow_level;
             if (ol == 0) break;
-            // the recheck queue of level ol overflowed: restore A_G as it was at the
-            // start of that level, enlarge the queue, clear that level's counters and
-            // run the levels from ol again
+            // the recheck queue of level ol overflowed: that level stopped before its
+            // removals and the later ones at entry, so A_G and the degrees are as at
+            // its start; enlarge the queue, clear the counters of the levels from ol
+            // and run them again (level ol rebuilds A'_G from A_G)
             if (ov >= 4) return fail(ctx, CUPC_E_RANGE, "recheck queue overflow persists");
             qcap = (size_t)(H.queue_len[ol] * 2);
             if ((s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
-            CU(cudaMemcpyAsync(R->bits, ctx->backup[0].p, bitbytes, cudaMemcpyDeviceToDevice, ctx->stream));
             unsigned long long keep = 0;
             for (int q = 1; q < ol; ++q) keep += H.removed[q] * (unsigned long long)(3 + q);
             for (int q = ol; q < LV; ++q) {
@@ -659,6 +680,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
                 for (int c = 0; c < RND; ++c) H.round_hist[q][c] = H.round_cur[q][c] = 0;
                 H.recheck_ns[q][0] = H.recheck_ns[q][1] = H.recheck_ns[q][2] = 0;
                 H.live[q] = 0;
+                H.rc_next[q] = 0;
                 H.maxdeg[q] = 0;
                 H.chunk[q] = 0;
             }
@@ -759,7 +781,7 @@ void ctx_release(cupc_ctx* c)
     cupc_ctx* ctx = c;
     Buf* all[] = {&c->xin, &c->xt, &c->mu, &c->isd, &c->mup, &c->z64, &c->zhi, &c->zlo, &c->cws, &c->c64, &c->c32, &c->cin,
                   &c->deg, &c->row_off, &c->item_off, &c->item_row, &c->cols, &c->srow, &c->partner, &c->wpre,
-                  &c->best, &c->queue, &c->binom, &c->meta, &c->lmeta, &c->backup[0], &c->backup[1],
+                  &c->best, &c->queue, &c->binom, &c->meta, &c->lmeta,
                   &c->part};
     for (Buf* b : all) free_buf(ctx, *b);
     for (auto& kv : c->named) free_buf(ctx, kv.second);

@@ -55,8 +55,8 @@ struct BatchPlan {
     long long words = 0, xelems = 0, zelems = 0, celems = 0, ldb = 0;
     size_t ws_bytes = 0;
     unsigned long long nnz_cap = 0, item_cap = 0, qcap = 0, rec_cap = 0;
-    Buf d_probs, d_vprob, d_vlmax, d_units, d_tiles, x_in, xt, mu, isd, mup, zhi, zlo, ws, c32, bits, bits0, backup;
-    Buf deg, row_off, item_off, item_row, item_c, live, scan_part, cols, srow, partner, wpre, best, queue, part, rec, meta, lmeta, pserial;
+    Buf d_probs, d_vprob, d_vlmax, d_units, d_tiles, x_in, xt, mu, isd, mup, zhi, zlo, ws, c32, bits, bits0;
+    Buf deg, row_off, item_off, item_row, item_c, live, rc_cnt, scan_part, cols, srow, partner, row_off2, cols2, srow2, partner2, alive, nrank, wpre, best, cval, queue, part, rec, meta, lmeta, pserial;
     Binom binom{};
     // pinned host copies written at the end of each run
     unsigned* h_bits = nullptr;
@@ -82,8 +82,8 @@ void plan_destroy(cupc_ctx* ctx, BatchPlan* B)
     if (B->exec) cudaGraphExecDestroy(B->exec);
     Buf* all[] = {&B->d_probs, &B->d_vprob, &B->d_vlmax, &B->d_units, &B->d_tiles, &B->x_in, &B->xt,      &B->mu,
                   &B->isd,     &B->mup,     &B->zhi,     &B->zlo,     &B->ws,   &B->c32,     &B->bits,
-                  &B->bits0,   &B->backup,  &B->deg,     &B->row_off, &B->item_off, &B->item_row, &B->item_c, &B->live, &B->scan_part, &B->cols,
-                  &B->srow,    &B->partner, &B->wpre,    &B->best,    &B->queue, &B->part,   &B->rec,
+                  &B->bits0,   &B->deg,     &B->row_off, &B->item_off, &B->item_row, &B->item_c, &B->live, &B->rc_cnt, &B->scan_part, &B->cols,
+                  &B->srow,    &B->partner, &B->row_off2, &B->cols2, &B->srow2, &B->partner2, &B->alive, &B->nrank, &B->wpre,    &B->best,    &B->cval,    &B->queue, &B->part,   &B->rec,
                   &B->meta,    &B->lmeta,   &B->pserial};
     for (Buf* b : all) ctx_free(ctx, b);
     if (B->h_bits) cudaFreeHost(B->h_bits);
@@ -201,7 +201,6 @@ cupc_status allocate(cupc_ctx* ctx, BatchPlan& B)
         {&B.c32, (size_t)B.celems * 4},
         {&B.bits, (size_t)B.words * 4},
         {&B.bits0, (size_t)B.words * 4},
-        {&B.backup, (size_t)B.words * 4},
         {&B.wpre, (size_t)B.words * 4},
         {&B.deg, (size_t)B.P * 4},
         {&B.row_off, (size_t)(B.P + 1) * 8},
@@ -212,9 +211,17 @@ cupc_status allocate(cupc_ctx* ctx, BatchPlan& B)
         {&B.cols, (size_t)B.nnz_cap * 4},
         {&B.srow, (size_t)B.nnz_cap * 4},
         {&B.partner, (size_t)B.nnz_cap * 4},
+        {&B.row_off2, (size_t)(B.P + 1) * 8},
+        {&B.cols2, (size_t)B.nnz_cap * 4},
+        {&B.srow2, (size_t)B.nnz_cap * 4},
+        {&B.partner2, (size_t)B.nnz_cap * 4},
+        {&B.alive, (size_t)B.nnz_cap},
+        {&B.nrank, (size_t)B.nnz_cap * 4},
         {&B.best, (size_t)B.nnz_cap * 8},
+        {&B.cval, (size_t)B.nnz_cap * 4},
         {&B.queue, (size_t)B.qcap * sizeof(QEntry)},
         {&B.live, (size_t)B.qcap * sizeof(int)},
+        {&B.rc_cnt, (size_t)kRcCnt * sizeof(int)},
         {&B.part, kPartBytes},
         {&B.rec, (size_t)B.rec_cap * 4},
         {&B.meta, sizeof(Meta)},
@@ -312,7 +319,6 @@ cupc_status issue(cupc_ctx* ctx, BatchPlan& B, cudaStream_t st, bool capturing)
     LP.W = 0;
     LP.p = B.P;
     LP.nwords = B.words;
-    LP.backup = (unsigned*)B.backup.p;
     LP.deg = (int*)B.deg.p;
     LP.row_off = (long long*)B.row_off.p;
     LP.item_off = (long long*)B.item_off.p;
@@ -322,10 +328,20 @@ cupc_status issue(cupc_ctx* ctx, BatchPlan& B, cudaStream_t st, bool capturing)
     LP.cols = (int*)B.cols.p;
     LP.srow = (int*)B.srow.p;
     LP.partner = (int*)B.partner.p;
+    LP.row_off2 = (long long*)B.row_off2.p;
+    LP.cols2 = (int*)B.cols2.p;
+    LP.srow2 = (int*)B.srow2.p;
+    LP.partner2 = (int*)B.partner2.p;
+    LP.alive = (unsigned char*)B.alive.p;
+    LP.nrank = (int*)B.nrank.p;
     LP.wpre = (int*)B.wpre.p;
     LP.best = (unsigned long long*)B.best.p;
     LP.nnz_cap = B.nnz_cap;
     LP.C = B.c32.p;
+    // level 1 by conditioning variable when the largest problem's C row fits
+    LP.l1_pivot = l1_buffers(B.pmax, 4);
+    LP.pstage = B.pmax;
+    LP.cval = B.cval.p;
     LP.B = B.binom;
     LP.chunk0 = K.chunk ? K.chunk : 32;
     LP.canonical = K.canonical;
@@ -335,6 +351,7 @@ cupc_status issue(cupc_ctx* ctx, BatchPlan& B, cudaStream_t st, bool capturing)
     LP.piv_floor = kPivFloor;
     LP.queue = (QEntry*)B.queue.p;
     LP.live = (int*)B.live.p;
+    LP.rc_cnt = (int*)B.rc_cnt.p;
     LP.qcap = B.qcap;
     LP.xf64 = K.dtype == CUPC_F64 ? 1 : 0;
     LP.mu = (const double*)B.mu.p;

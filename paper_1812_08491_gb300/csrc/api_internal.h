@@ -31,7 +31,7 @@ struct cupc_ctx {
     int refs = 1;
     int num_sms = 0;
     Buf xin, xt, mu, isd, mup, z64, zhi, zlo, cws, c64, c32, cin;
-    Buf deg, row_off, item_off, item_row, cols, srow, partner, wpre, best, queue, binom, meta, lmeta, backup[2];
+    Buf deg, row_off, item_off, item_row, cols, srow, partner, wpre, best, queue, binom, meta, lmeta;
     Buf part;
     cupc::Meta* hmeta = nullptr;
     cupc::LevelMeta* hlmeta = nullptr;

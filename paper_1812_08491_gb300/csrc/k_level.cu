@@ -48,6 +48,19 @@ __device__ __forceinline__ unsigned long long gtimer()
 
 __device__ __forceinline__ unsigned long long ld_cg(const unsigned long long* p) { return __ldcg(p); }
 
+// One of the two CSR buffers of A'_G.
+struct Csr {
+    long long* row_off;
+    int* cols;
+    int* srow;
+    int* partner;
+};
+
+__device__ __forceinline__ Csr csr_view(const LevelParams& P, int b)
+{
+    return b ? Csr{P.row_off2, P.cols2, P.srow2, P.partner2} : Csr{P.row_off, P.cols, P.srow, P.partner};
+}
+
 // View of the correlation block of vertex v's problem, indexed by global ids.
 template <typename T>
 struct CView {
@@ -130,7 +143,7 @@ __device__ bool grid_sync(LevelMeta* lm)
 // P1 (blocks other than 0): exclusive prefix popcounts of each row's words,
 // wpre[i*W + w] = number of neighbours of i below 32 w; FP32 mode: A_G copy
 // ---------------------------------------------------------------------------
-__device__ void phase_prefix(const LevelParams& P, bool fp32, int skip)
+__device__ void phase_prefix(const LevelParams& P, int skip)
 {
     const int lane = threadIdx.x & 31;
     // (skip = 1: block 0 is scanning; with a single block it does this part too)
@@ -156,10 +169,46 @@ __device__ void phase_prefix(const LevelParams& P, bool fp32, int skip)
             base += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
-    if (fp32) {
-        const size_t words = (size_t)P.nwords;
-        for (size_t k = (size_t)bid * NT + threadIdx.x; k < words; k += (size_t)nb * NT)
-            P.backup[k] = P.bits[k];
+}
+
+// P1 of a level whose A'_G is built from the previous level's (old buffer O):
+// per old row, the position of each surviving slot among the row's survivors
+// (-1 for a removed edge), from the alive flags the previous level's removal
+// phase wrote. Same CTA split as phase_prefix.
+__device__ void phase_rank(const LevelParams& P, const Csr& O, int skip)
+{
+    const int lane = threadIdx.x & 31;
+    const int nb = (skip && gridDim.x > 1) ? gridDim.x - 1 : gridDim.x;
+    const int bid = (skip && gridDim.x > 1) ? blockIdx.x - 1 : blockIdx.x;
+    const int gw = (bid * NT + threadIdx.x) >> 5;
+    const int nwarps = (nb * NT) >> 5;
+    for (int i = gw; i < P.p; i += nwarps) {
+        const long long off = O.row_off[i], end = O.row_off[i + 1];
+        int base = 0;
+        for (long long e0 = off; e0 < end; e0 += 32) {
+            const long long e = e0 + lane;
+            const bool a = e < end && P.alive[e] != 0;
+            const unsigned m = __ballot_sync(0xffffffffu, a);
+            if (e < end) P.nrank[e] = a ? base + __popc(m & ((1u << lane) - 1u)) : -1;
+            base += __popc(m);
+        }
+    }
+}
+
+// P2 of such a level: the surviving slots of the old A'_G, in order, into the
+// new buffer A (row offsets from the degree scan); a slot's partner is found
+// through the old partner's position.
+__device__ void phase_fill_incr(const LevelParams& P, const Csr& O, const Csr& A)
+{
+    const long long nnz_old = O.row_off[P.p];
+    for (long long e = (long long)blockIdx.x * NT + threadIdx.x; e < nnz_old; e += (long long)gridDim.x * NT) {
+        const int r = P.nrank[e];
+        if (r < 0) continue;
+        const int i = O.srow[e], j = O.cols[e];
+        const long long ne = A.row_off[i] + r;
+        A.cols[ne] = j;
+        A.srow[ne] = i;
+        A.partner[ne] = (int)(A.row_off[j] + P.nrank[O.partner[e]]);
     }
 }
 
@@ -214,7 +263,7 @@ __device__ __forceinline__ void load8(const LevelParams& P, int i0, int hi, int 
 
 // P1 for graphs of at most 32 NT rows: block 0 scans every row while the
 // other CTAs build the word prefixes (no second barrier).
-__device__ void phase_scan_one(const LevelParams& P, bool learned)
+__device__ void phase_scan_one(const LevelParams& P, const Csr& A, bool learned)
 {
     __shared__ long long sa[32], sb[32], sc[32];
     __shared__ unsigned long long stot;
@@ -336,7 +385,7 @@ __device__ void phase_scan_one(const LevelParams& P, bool learned)
             const int i = i0 + u;
             if (i >= hi) break;
             const int d = di8[u];
-            P.row_off[i] = ea;
+            A.row_off[i] = ea;
             P.item_off[i] = eb;
             if (P.poff) P.poff[i] = ec;
             ea += d8[u];
@@ -354,7 +403,7 @@ __device__ void phase_scan_one(const LevelParams& P, bool learned)
         if (hist[q]) P.lm->round_hist[l][q] = hist[q];
     if (rng) atomicOr(&P.lm->range_error, 1);
     if (t == NT - 1) {
-        P.row_off[P.p] = ea;
+        A.row_off[P.p] = ea;
         P.item_off[P.p] = eb;
         if (P.poff) P.poff[P.p] = ec;
         P.lm->edges[l] = (unsigned long long)ea / 2;
@@ -433,7 +482,7 @@ __device__ void phase_scan_a(const LevelParams& P, bool learned)
 // recounts and takes another barrier), then this CTA's rows' CSR offsets, item
 // offsets, candidate-list offsets and its part of the round histogram.
 // Returns false when a barrier failed.
-__device__ bool phase_scan_b(const LevelParams& P, bool learned, bool& lrn_out)
+__device__ bool phase_scan_b(const LevelParams& P, const Csr& A, bool learned, bool& lrn_out)
 {
     __shared__ unsigned long long sbase[4], stot[4];
     __shared__ unsigned long long rsum[NW][4];
@@ -527,7 +576,7 @@ __device__ bool phase_scan_b(const LevelParams& P, bool learned, bool& lrn_out)
             ta += wsum[q][0]; tb += wsum[q][1]; tc += wsum[q][2];
         }
         if (i < r1) {
-            P.row_off[i] = (long long)(ca + pa + ia - a);
+            A.row_off[i] = (long long)(ca + pa + ia - a);
             P.item_off[i] = (long long)(cb + pb + ib - b);
             if (P.poff) P.poff[i] = (long long)(cc + pc + ic - c);
         }
@@ -543,7 +592,7 @@ __device__ bool phase_scan_b(const LevelParams& P, bool learned, bool& lrn_out)
         if (hist[q]) atomicAdd(&P.lm->round_hist[l][q], hist[q]);
     if (blockIdx.x == gridDim.x - 1 && t == 0) {
         const unsigned long long ea = stot[0], eb = stot[lrn ? 2 : 1], ec = stot[3];
-        P.row_off[P.p] = (long long)ea;
+        A.row_off[P.p] = (long long)ea;
         P.item_off[P.p] = (long long)eb;
         if (P.poff) P.poff[P.p] = (long long)(lrn ? ec : 0);
         P.lm->edges[l] = ea / 2;
@@ -561,7 +610,7 @@ __device__ bool phase_scan_b(const LevelParams& P, bool learned, bool& lrn_out)
 // reserves slots in every round for them (one global atomic per round), then
 // each row's warp writes its items (row, index within the row) into them. The
 // order within a round is unspecified; results do not depend on it.
-__device__ void phase_items(const LevelParams& P)
+__device__ void phase_items(const LevelParams& P, const Csr& A)
 {
     __shared__ unsigned cnt[RND];
     __shared__ unsigned long long base[RND], cur[RND];
@@ -639,17 +688,23 @@ __device__ void phase_items(const LevelParams& P)
     }
 }
 
-__device__ void phase_fill(const LevelParams& P, bool reuse)
+template <typename T>
+__device__ void phase_fill(const LevelParams& P, const Csr& A, const Csr& O, bool reuse, bool incr, bool pivot)
 {
     const int lane = threadIdx.x & 31;
+    if (incr) {
+        phase_fill_incr(P, O, A);
+        reuse = true;                              // (the bitset walk below is skipped)
+    }
     const int gw = (blockIdx.x * NT + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * NT) >> 5;
     for (int i = reuse ? P.p : gw; i < P.p; i += nwarps) {
-        long long base = P.row_off[i];
+        long long base = A.row_off[i];
         int wlo, whi;
         long long rb;
         word_range(P, i, wlo, whi, rb);
         const ProbDesc* Di = prob_of(P.vprob, P.probs, i);   // every neighbour is in i's problem
+        const T* Crow = pivot ? cview<T>(P, i).row(i) : nullptr;
         for (int w0 = wlo; w0 < whi; w0 += 32) {
             const int q = w0 + lane;
             unsigned word = (q < whi) ? P.bits[rb + q] : 0u;
@@ -665,20 +720,21 @@ __device__ void phase_fill(const LevelParams& P, bool reuse)
                 const int b = __ffs(word) - 1;
                 word &= word - 1;
                 const int j = (q << 5) + b;
-                P.cols[pos] = j;
-                P.srow[pos] = i;
+                A.cols[pos] = j;
+                A.srow[pos] = i;
                 // slot of (j, i): row j's offset + neighbours of j below i
                 const long long rbj = rowbase(Di, P.W, j);
                 const unsigned wj = P.bits[rbj + (i >> 5)];
-                P.partner[pos] = (int)(P.row_off[j] + P.wpre[rbj + (i >> 5)] +
+                A.partner[pos] = (int)(A.row_off[j] + P.wpre[rbj + (i >> 5)] +
                                        __popc(wj & ((1u << (i & 31)) - 1u)));
+                if (pivot) ((T*)P.cval)[pos] = Crow[j];
                 ++pos;
             }
             base += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
-    phase_items(P);
-    const long long nnz = P.row_off[P.p];
+    if (!pivot) phase_items(P, A);
+    const long long nnz = A.row_off[P.p];
     for (long long e = (long long)blockIdx.x * NT + threadIdx.x; e < nnz; e += (long long)gridDim.x * NT)
         P.best[e] = RANK_NONE;
 }
@@ -724,7 +780,7 @@ __device__ __forceinline__ int ci_decide(T H11, T H12, T H22, T minpiv2, const D
 }
 
 template <typename T, int LB, bool FP32>
-__device__ void phase_ci(const LevelParams& P)
+__device__ void phase_ci(const LevelParams& P, const Csr& A)
 {
     const int lane = threadIdx.x & 31;
     const int l = P.l;
@@ -743,8 +799,8 @@ __device__ void phase_ci(const LevelParams& P)
         if (item >= n_items) break;
         const int i = P.item_row[item];
         const long long kr = P.item_c[item];
-        const long long off = P.row_off[i];
-        const int d = (int)(P.row_off[i + 1] - off);
+        const long long off = A.row_off[i];
+        const int d = (int)(A.row_off[i + 1] - off);
         // subset chunk k and j positions [jlo, jhi) of this item
         const int nj = j_ranges(d, l, P.jsplit);
         const long long k = kr / nj;
@@ -773,7 +829,7 @@ __device__ void phase_ci(const LevelParams& P)
                 else unrank_lex<LB>(s, d, l, P.B, Pos);
 #pragma unroll
                 for (int c = 0; c < LB; ++c)
-                    if (c < l) Sx[c] = P.cols[off + Pos[c]];
+                    if (c < l) Sx[c] = A.cols[off + Pos[c]];
                 factor_build<T, LB>(
                     F, l, (T)P.rank_tol, [&](int a, int b) { return __ldg(CV.row(Sx[a]) + Sx[b]); },
                     [&](int a) { return __ldg(Ci + Sx[a]); });
@@ -811,9 +867,9 @@ __device__ void phase_ci(const LevelParams& P)
                         if (c < l && Pos[c] <= jp) ++jp;
                     if (!active) continue;
                     const long long e = off + jp;
-                    const int j = P.cols[e];
+                    const int j = A.cols[e];
                     const unsigned long long be = ld_cg(P.best + e);
-                    const unsigned long long pb = (!P.canonical || i > j) ? ld_cg(P.best + P.partner[e]) : RANK_NONE;
+                    const unsigned long long pb = (!P.canonical || i > j) ? ld_cg(P.best + A.partner[e]) : RANK_NONE;
                     if (pb == RANK_NONE && (P.canonical ? (be >= s) : (be == RANK_NONE))) test(jp, j, __ldg(Ci + j));
                 }
                 continue;
@@ -826,11 +882,11 @@ __device__ void phase_ci(const LevelParams& P)
                 T cij_l = T(0);
                 if (jc + lane < jhi) {
                     const long long e = off + jc + lane;
-                    j_l = P.cols[e];
+                    j_l = A.cols[e];
                     b_l = ld_cg(P.best + e);
                     // the larger endpoint's side stops once the smaller side separates
                     // (free mode: either side stops the other)
-                    if (!P.canonical || i > j_l) pb_l = ld_cg(P.best + P.partner[e]);
+                    if (!P.canonical || i > j_l) pb_l = ld_cg(P.best + A.partner[e]);
                     cij_l = __ldg(Ci + j_l);
                 }
                 const int jn = min(32, jhi - jc);
@@ -855,6 +911,266 @@ __device__ void phase_ci(const LevelParams& P)
 }
 
 // ---------------------------------------------------------------------------
+// P4 at level 1, by conditioning variable. A test (i, j | k) with k in
+// adj(i) \ {j} (side i, S = {k}) reads C_ik, C_jk and C_ij only (Sec. 4.3 with
+// |S| = 1: H11 = 1 - C_ik^2, H22 = 1 - C_jk^2, H12 = C_ij - C_ik C_jk). Since k in
+// adj(i) iff i in adj(k), the tests sharing k are the slots (i, j) of the rows
+// i in adj(k): a CTA stages row k of C in shared memory with coalesced 16-byte
+// loads, then its warps walk those rows (lane q takes slot q of row i, reading
+// the row's neighbour list and its C_ij values contiguously), so C_ik and C_jk
+// come from shared memory and every row of C is read from memory once per
+// level instead of once per common neighbour. The rank of {k} on side i is k's
+// position in row i (the slot partner of (k, i)); the smallest separating rank
+// per slot is kept by atomicMin, which is the rank the serial order finds
+// first. Pivots are claimed in increasing order, so k's position in each of its
+// rows grows as the level proceeds: a test whose slot already holds a smaller
+// separating rank is skipped (read with the slot's other data), which cannot
+// change that minimum.
+// ---------------------------------------------------------------------------
+// Staging of pivot rows by the bulk-copy engine: one thread starts a
+// cp.async.bulk of the row's 16-byte-aligned middle into a shared buffer,
+// completing on an mbarrier; the few entries before and after it are loaded
+// by threads after the wait. The buffer holds the row from entry `mis` on, so
+// source and destination share their 16-byte alignment.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init1(unsigned long long* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of parity `parity`, at most kBarrierNs; false on expiry
+// (error flag 8 raised) or, with stop_on_error, when another CTA raised an
+// error. Without it the wait only ends on completion or expiry (used to drain
+// a copy in flight before the CTA leaves).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity, LevelMeta* lm,
+                                                  bool stop_on_error = true)
+{
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if ((it & 15u) == 0) {
+            if (stop_on_error && *(volatile int*)&lm->error) return false;
+            if (gtimer() - t0 > kBarrierNs) {
+                atomicOr(&lm->error, 8);
+                return false;
+            }
+        }
+    }
+}
+
+struct PivotRow {
+    int k;          // pivot (-1: none left)
+    int mis;        // entry of the buffer holding the row's first entry
+    int head;       // entries before the bulk-copied middle
+    int body;       // entries bulk-copied
+    int n;          // entries of the row
+};
+
+// Claims the next pivot with neighbours and starts copying its C row into buf
+// (thread 0 only).
+template <typename T>
+__device__ void pivot_issue(const LevelParams& P, const Csr& A, T* buf, unsigned long long* bar, PivotRow& R)
+{
+    constexpr int V = 16 / sizeof(T);
+    for (;;) {
+        const unsigned long long kk = atomicAdd(&P.lm->next_item[1], 1ull);
+        if (kk >= (unsigned long long)P.p) {
+            R.k = -1;
+            return;
+        }
+        const int k = (int)kk;
+        if (A.row_off[k + 1] == A.row_off[k] || (P.vlmax && P.vlmax[k] < 1)) continue;
+        const CView<T> CV = cview<T>(P, k);
+        const T* src = CV.row(k) + CV.off;
+        R.k = k;
+        R.n = CV.p;
+        R.mis = (int)(((uintptr_t)src & 15) / sizeof(T));
+        R.head = min(CV.p, (V - R.mis) % V);
+        R.body = ((CV.p - R.head) / V) * V;
+        const uint32_t bytes = (uint32_t)(R.body * sizeof(T));
+        if (bytes) {
+            // the buffer's previous contents were read through the generic proxy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_addr(buf + R.mis + R.head)),
+                "l"((unsigned long long)(src + R.head)), "r"(bytes), "r"(smem_addr(bar))
+                : "memory");
+        } else {
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+        }
+        return;
+    }
+}
+
+// Decision of a level-1 test (minpiv2 = 1) as ci_decide, with the band's
+// division by the smaller conditional variance done by the fast reciprocal
+// (the band is a safety margin; its few-ulp rounding only moves its edge).
+template <typename T, bool FP32>
+__device__ __forceinline__ int l1_decide(T H11, T H12, T H22, const Decide& dc)
+{
+    if (!FP32) return ci_decide<T, false>(H11, H12, H22, T(1), dc);
+    if (!(H22 > 1e-4f)) return 2;                  // (H11 is checked once per row)
+    const float rho = fabsf((float)H12) * rsqrtf((float)(H11 * H22));
+    const float band = dc.band_abs + __fdividef(dc.band_rel, fminf((float)H11, (float)H22));
+    if (rho > dc.r + band) return 0;
+    if (rho < dc.r - band) return 1;
+    return 2;
+}
+
+constexpr int kL1Nb = 256;   // neighbours of the pivot staged per round
+constexpr int kL1U = 4;      // slot loads in flight per lane
+
+template <typename T, bool FP32>
+__device__ void phase_l1_pivot(const LevelParams& P, const Csr& A, unsigned char* dyn)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ __align__(8) unsigned long long pbar[2];
+    __shared__ PivotRow prow[2];
+    __shared__ int sabort;
+    // the rows i in adj(k) of one round: slot offset, degree, position of k
+    __shared__ int nb_off[kL1Nb], nb_d[kL1Nb], nb_pos[kL1Nb], nb_i[kL1Nb];
+    const int nbuf = P.l1_pivot;
+    const size_t bbytes = l1_buf_bytes(P.pstage, sizeof(T));
+    T* buf[2] = {(T*)dyn, (T*)(dyn + (nbuf > 1 ? bbytes : 0))};
+    unsigned ntests = 0;
+    const T* __restrict__ cval = (const T*)P.cval;
+    if (threadIdx.x == 0) {
+        mbar_init1(&pbar[0]);
+        mbar_init1(&pbar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sabort = 0;
+        pivot_issue<T>(P, A, buf[0], &pbar[0], prow[0]);
+    }
+    __syncthreads();
+    uint32_t par[2] = {0u, 0u};
+    int b = 0;
+    for (;;) {
+        const PivotRow R = prow[b];
+        if (R.k < 0) break;
+        if (threadIdx.x == 0) {
+            // the next pivot's row streams into the other buffer meanwhile
+            if (nbuf > 1) pivot_issue<T>(P, A, buf[b ^ 1], &pbar[b ^ 1], prow[b ^ 1]);
+            if (!mbar_wait_bounded(&pbar[b], par[b], P.lm)) {
+                sabort = 1;
+                mbar_wait_bounded(&pbar[b], par[b], P.lm, false);   // this buffer's copy, drained
+            }
+        }
+        par[b] ^= 1u;
+        T* row = buf[b] + R.mis;
+        {
+            const T* src = cview<T>(P, R.k).row(R.k) + cview<T>(P, R.k).off;
+            const int tail0 = R.head + R.body;
+            for (int c = threadIdx.x; c < R.head; c += NT) row[c] = __ldg(src + c);
+            for (int c = tail0 + threadIdx.x; c < R.n; c += NT) row[c] = __ldg(src + c);
+        }
+        const int k = R.k;
+        const long long offk = A.row_off[k];
+        const int dk = (int)(A.row_off[k + 1] - offk);
+        double thr, thr2;
+        thresholds(P, k, thr, thr2);
+        const Decide dc = decide_consts(P, thr, thr2);
+        const T* __restrict__ sk_row = row - cview<T>(P, k).off;   // indexed by global column ids
+        for (int t0 = 0; t0 < dk; t0 += kL1Nb) {
+            const int nt = min(kL1Nb, dk - t0);
+            __syncthreads();                       // the previous round's metadata is no longer read
+            for (int t = threadIdx.x; t < nt; t += NT) {
+                const int i = A.cols[offk + t0 + t];
+                const long long offi = A.row_off[i];
+                nb_i[t] = i;
+                nb_off[t] = (int)offi;
+                nb_d[t] = (int)(A.row_off[i + 1] - offi);
+                nb_pos[t] = A.partner[offk + t0 + t] - (int)offi;   // slot (i, k) in row i
+            }
+            __syncthreads();                       // (the first one also publishes the staged row)
+            if (sabort) break;
+            for (int t = w; t < nt; t += NW) {
+                const int di = nb_d[t];
+                if (di < 2) continue;
+                const int offi = nb_off[t], posk = nb_pos[t];
+                const unsigned long long rk = (unsigned long long)posk;
+                const T cik = sk_row[nb_i[t]];
+                const T H11 = T(1) - cik * cik;
+                // (FP32: a tiny conditional variance sends every test of the row to FP64)
+                const bool h11_ok = !FP32 || (float)H11 > 1e-4f;
+                for (int q0 = 0; q0 < di; q0 += 32 * kL1U) {
+                    int jj[kL1U];
+                    T cv[kL1U];
+                    unsigned long long be[kL1U];
+#pragma unroll
+                    for (int u = 0; u < kL1U; ++u) {
+                        const int q = q0 + 32 * u + lane;
+                        const bool in = q < di && q != posk;
+                        jj[u] = in ? A.cols[offi + q] : 0;
+                        cv[u] = in ? cval[offi + q] : T(0);
+                        // the slot's smallest separating rank so far: a test of a
+                        // larger rank cannot change the result (canonical mode), nor
+                        // can any test once the slot has one (free mode)
+                        be[u] = in ? __ldcg(P.best + offi + q) : 0ull;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kL1U; ++u) {
+                        const bool go = P.canonical ? (be[u] > rk) : (be[u] == RANK_NONE);
+                        if (go) {
+                            const int e = offi + q0 + 32 * u + lane;
+                            const T cjk = sk_row[jj[u]];
+                            const T H12 = cv[u] - cik * cjk;
+                            const T H22 = T(1) - cjk * cjk;
+                            ++ntests;
+                            const int dec = h11_ok ? l1_decide<T, FP32>(H11, H12, H22, dc) : 2;
+                            if (dec == 1) {
+                                atomicMin(P.best + e, rk);
+                            } else if (FP32 && dec == 2) {
+                                const unsigned long long qq = atomicAdd(&P.lm->queue_len[1], 1ull);
+                                if (qq < P.qcap) {
+                                    QEntry* Q = P.queue + qq;
+                                    Q->a = e;
+                                    Q->b = 0;
+                                    Q->s = rk;
+                                    Q->S[0] = k;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();                           // buffer b and the metadata are no longer read
+        if (sabort) break;
+        if (nbuf > 1) {
+            b ^= 1;
+        } else if (threadIdx.x == 0) {
+            pivot_issue<T>(P, A, buf[0], &pbar[0], prow[0]);
+        }
+        __syncthreads();                           // the next pivot's descriptor is visible
+    }
+    if (sabort && threadIdx.x == 0 && nbuf > 1 && prow[b ^ 1].k >= 0) {
+        // a copy may still be in flight into the other buffer: wait for it
+        // (bounded) before the CTA leaves
+        mbar_wait_bounded(&pbar[b ^ 1], par[b ^ 1], P.lm, false);
+    }
+    const unsigned long long nt64 = warp_sum_u64((unsigned long long)ntests);
+    if (lane == 0 && nt64) atomicAdd(&P.lm->tests[1], nt64);
+}
+
+// ---------------------------------------------------------------------------
 // Learned ordering, levels l >= 2 (FP32 mode).
 // P3: for every slot (i, j), score each candidate k of adj(i) \ {j} with the
 // network and store the candidates by descending score (ties: increasing
@@ -866,14 +1182,14 @@ __device__ void phase_ci(const LevelParams& P)
 // ---------------------------------------------------------------------------
 constexpr int MCAP = 256;  // candidates scored per side; longer lists keep their increasing order
 
-__device__ __forceinline__ int* side_perm(const LevelParams& P, int i, long long e)
+__device__ __forceinline__ int* side_perm(const LevelParams& P, const Csr& A, int i, long long e)
 {
-    const long long off = P.row_off[i];
-    const int m = (int)(P.row_off[i + 1] - off) - 1;
+    const long long off = A.row_off[i];
+    const int m = (int)(A.row_off[i + 1] - off) - 1;
     return P.perm + P.poff[i] + (e - off) * (long long)m;
 }
 
-__device__ void phase_score(const LevelParams& P)
+__device__ void phase_score(const LevelParams& P, const Csr& A)
 {
     __shared__ __nv_bfloat16 Wsm[MLP_NP];
     __shared__ float sc[NW][MCAP];
@@ -882,22 +1198,22 @@ __device__ void phase_score(const LevelParams& P)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int gw = (blockIdx.x * NT + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * NT) >> 5;
-    const long long nnz = P.row_off[P.p];
+    const long long nnz = A.row_off[P.p];
     for (long long e = gw; e < nnz; e += nwarps) {
-        const int i = P.srow[e], j = P.cols[e];
+        const int i = A.srow[e], j = A.cols[e];
         const CView<float> CV = cview<float>(P, i);
-        const long long off = P.row_off[i];
-        const int m = (int)(P.row_off[i + 1] - off) - 1;
+        const long long off = A.row_off[i];
+        const int m = (int)(A.row_off[i + 1] - off) - 1;
         if (m < P.l) continue;
         const int pj = (int)(e - off);
-        int* dst = side_perm(P, i, e);
+        int* dst = side_perm(P, A, i, e);
         if (m > MCAP) {
-            for (int c = lane; c < m; c += 32) dst[c] = P.cols[off + (c < pj ? c : c + 1)];
+            for (int c = lane; c < m; c += 32) dst[c] = A.cols[off + (c < pj ? c : c + 1)];
             continue;
         }
         const float cij = CV.row(i)[j];
         for (int c = lane; c < m; c += 32) {
-            const int k = P.cols[off + (c < pj ? c : c + 1)];
+            const int k = A.cols[off + (c < pj ? c : c + 1)];
             float x[MLP_IN];
             mlp_features(cij, CV.row(i)[k], CV.row(j)[k], P.l, x);
             const float y = mlp_score(Wsm, x);
@@ -911,14 +1227,14 @@ __device__ void phase_score(const LevelParams& P)
                 const float y2 = sc[w][c2];
                 r += (y2 > y) || (y2 == y && c2 < c);
             }
-            dst[r] = P.cols[off + (c < pj ? c : c + 1)];
+            dst[r] = A.cols[off + (c < pj ? c : c + 1)];
         }
         __syncwarp();
     }
 }
 
 template <typename T, int LB, bool FP32>
-__device__ void phase_ci_edge(const LevelParams& P)
+__device__ void phase_ci_edge(const LevelParams& P, const Csr& A)
 {
     const int lane = threadIdx.x & 31;
     const int l = P.l;
@@ -932,8 +1248,8 @@ __device__ void phase_ci_edge(const LevelParams& P)
         if (item >= n_items) break;
         const int i = P.item_row[item];
         const long long k = P.item_c[item];
-        const long long off = P.row_off[i];
-        const int m = (int)(P.row_off[i + 1] - off) - 1;
+        const long long off = A.row_off[i];
+        const int m = (int)(A.row_off[i + 1] - off) - 1;
         const CView<T> CV = cview<T>(P, i);
         double thr, thr2;
         thresholds(P, i, thr, thr2);
@@ -942,8 +1258,8 @@ __device__ void phase_ci_edge(const LevelParams& P)
         const long long per_edge = (long long)((total + chunk - 1) / chunk);
         const long long q = k / per_edge, cidx = k % per_edge;
         const long long e = off + q;
-        const int j = P.cols[e];
-        const int* __restrict__ cand = side_perm(P, i, e);
+        const int j = A.cols[e];
+        const int* __restrict__ cand = side_perm(P, A, i, e);
         const unsigned long long s0 = (unsigned long long)cidx * (unsigned long long)chunk;
         const unsigned long long s1 = min(s0 + (unsigned long long)chunk, total);
         const T* __restrict__ Ci = CV.row(i);
@@ -954,7 +1270,7 @@ __device__ void phase_ci_edge(const LevelParams& P)
             unsigned long long be = 0, pb = 0;
             if (lane == 0) {
                 be = ld_cg(P.best + e);
-                pb = watch_partner ? ld_cg(P.best + P.partner[e]) : RANK_NONE;
+                pb = watch_partner ? ld_cg(P.best + A.partner[e]) : RANK_NONE;
             }
             be = __shfl_sync(0xffffffffu, be, 0);
             pb = __shfl_sync(0xffffffffu, pb, 0);
@@ -1165,213 +1481,235 @@ __device__ __forceinline__ void recheck_unit(const LevelParams& P, const QEntry*
 // then the smaller rank), or by any definitive independence (non-canonical).
 // best[] does not change while this is evaluated (it is written only after the
 // grid barrier that follows), so every slice of a test agrees.
-__device__ __forceinline__ bool recheck_moot(const LevelParams& P, long long e, int i, int j, unsigned long long s)
+__device__ __forceinline__ bool recheck_moot(const LevelParams& P, const Csr& A, long long e, int i, int j, unsigned long long s)
 {
     const unsigned long long be = ld_cg(P.best + e);
-    const unsigned long long bf = ld_cg(P.best + P.partner[e]);
+    const unsigned long long bf = ld_cg(P.best + A.partner[e]);
     if (!P.canonical) return be != RANK_NONE || bf != RANK_NONE;
     if (i < j) return be < s;                      // this side is the first one
     return bf != RANK_NONE || be < s;              // the first side already removes it
 }
 
-// Recheck of the queued tests in batches that fit the partial-sum buffer: one
-// warp per (test, sample slice) forms the slice's Gram entries of the
-// m = l + 2 variables from the data rows (FP64, or compensated FP32 pairs for
-// FP32 data), one warp per test adds the slices in a fixed order and decides
-// with the FP64 factorisation.
+// Gram entries of one slice of a queued test, summed over the NW warps of the
+// CTA in warp order by warp 0: out[x] (x < D) as an FP32 pair (pairs) or a
+// double. Must be called by the whole CTA.
 template <int LB>
-__device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
+__device__ __forceinline__ void recheck_slice(const LevelParams& P, const Csr& A, const QEntry* E, int i, int j, int s, int S,
+                                              bool pairs, double (*sred)[(LB + 2) * (LB + 1) / 2], double* out)
+{
+    constexpr int D = (LB + 2) * (LB + 1) / 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (pairs)
+        recheck_unit<LB, true>(P, E, i, j, s * NW + warp, S * NW, &sred[warp][0]);
+    else
+        recheck_unit<LB, false>(P, E, i, j, s * NW + warp, S * NW, &sred[warp][0]);
+    __syncthreads();
+    if (warp == 0) {
+        for (int x = lane; x < D; x += 32) {
+            if (pairs) {
+                float h = 0.f, lo = 0.f;
+                for (int w2 = 0; w2 < NW; ++w2) {
+                    const float2 t2 = ((const float2*)&sred[w2][0])[x];
+                    pair_add(h, lo, t2.x, t2.y);
+                }
+                ((float2*)out)[x] = make_float2(h, lo);
+            } else {
+                double v = 0.0;
+                for (int w2 = 0; w2 < NW; ++w2) v += sred[w2][x];
+                out[x] = v;
+            }
+        }
+    }
+}
+
+// Decision of a recheck by warp 0 from its Gram entries (slices already
+// added: g[x] as a pair or a double, or C64 when given): eliminates the
+// members of S from the (l + 2) x (l + 2) correlation block of (S, i, j); the
+// trailing 2 x 2 Schur complement is the conditional covariance of (V_i, V_j)
+// given S (Eq. PartialCorMat). A member whose remaining pivot is at or below
+// the rank tolerance is linearly dependent on the members before it and is
+// dropped (the pseudo-inverse's treatment). Returns independence (lane 0).
+template <int LB>
+__device__ __forceinline__ bool recheck_decide(const LevelParams& P, const Csr& A, const QEntry* E, int i, int j, bool pairs,
+                                               const double* g, double (*sA)[LB + 2])
 {
     constexpr int M = LB + 2;
     constexpr int D = M * (M - 1) / 2;
-    __shared__ double sA[NW][M][M];
+    const int lane = threadIdx.x & 31;
+    const int l = P.l, m = l + 2;
+    int V[M];
+    V[0] = i;
+    V[1] = j;
+#pragma unroll
+    for (int q = 0; q < LB; ++q) V[2 + q] = (q < l) ? E->S[q] : i;
+    // elimination position of Gram index x (0 = i, 1 = j, 2 + a = S_a)
+    auto pos = [&](int x) { return x >= 2 ? x - 2 : l + x; };
+    const double inv_n = inv_n_of(P, i);
+    for (int x = lane; x < D; x += 32) {
+        int a, b2;
+        gram_pair(x, a, b2);
+        if (b2 < m) {
+            const int pa = pos(a), pb = pos(b2);
+            double v;
+            if (P.c64) {
+                v = P.c64[(size_t)V[a] * P.p + V[b2]];
+            } else {
+                const double raw = pairs ? widen_f32(((const float2*)g)[x].x) + widen_f32(((const float2*)g)[x].y)
+                                         : g[x];
+                v = raw * (P.isd[V[a]] * P.isd[V[b2]]) * inv_n;
+            }
+            sA[max(pa, pb)][min(pa, pb)] = v;
+        }
+    }
+    if (lane < m) sA[lane][lane] = 1.0;
+    __syncwarp();
+    // lower triangle only: step k updates A[a][b], k < b <= a < m
+    for (int k = 0; k < l; ++k) {
+        const double piv = sA[k][k];
+        if (piv > P.rank_tol) {
+            const double rp = 1.0 / piv;
+            const int r = m - k - 1;
+            for (int q = lane; q < r * (r + 1) / 2; q += 32) {
+                int aa = 0;
+                while ((aa + 1) * (aa + 2) / 2 <= q) ++aa;
+                const int bb = q - aa * (aa + 1) / 2;
+                const int a = k + 1 + aa, b = k + 1 + bb;
+                sA[a][b] = fma(-sA[a][k] * rp, sA[b][k], sA[a][b]);
+            }
+        }
+        __syncwarp();
+    }
+    const double H11 = sA[l][l], H12 = sA[l + 1][l], H22 = sA[l + 1][l + 1];
+    double thr, thr2;
+    thresholds(P, i, thr, thr2);
+    __syncwarp();
+    return (!(H11 > kVarZero) || !(H22 > kVarZero)) ? true : (H12 * H12 <= thr2 * H11 * H22);
+}
+
+// FP64 rechecks of the queued tests. (1) The tests whose outcome can still
+// matter are listed (one grid barrier). (2) Each listed test is cut into S
+// sample slices, S = 1 when the tests outnumber the CTAs, else up to 16 so
+// that few tests still spread over many SMs; a CTA takes one (test, slice)
+// unit, its NW warps form the slice's Gram entries of the m = l + 2 variables
+// over NW sub-slices (FP64, or compensated FP32 pairs for FP32 data) and add
+// them in warp order. With S > 1 each CTA stores its slice's sums and the CTA
+// that completes a test (a counter per test) adds the S slices in slice order
+// and decides; no further grid barrier is needed. The slices depend on n and
+// S only, and S on the number of listed tests, so a test's FP64 value does not
+// depend on which CTAs compute it.
+template <int LB>
+__device__ bool phase_recheck(const LevelParams& P, const Csr& A, unsigned long long nq)
+{
+    constexpr int M = LB + 2;
+    constexpr int D = M * (M - 1) / 2;
+    constexpr int NA = LB <= 8 ? NW : 1;           // elimination blocks (one per warp in warp mode)
+    __shared__ double sA[NA][M][M];
+    __shared__ double sred[NW][D];                 // per warp: its sub-slice's Gram entries
+    __shared__ double sg[D];                       // the slice (or test) sums
+    __shared__ unsigned long long su;
+    __shared__ int slast;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool timer = (blockIdx.x == 0 && threadIdx.x == 0);
     // FP32 data: Gram sums in compensated FP32 pairs (GB300's FP64 pipe is narrow)
     const bool pairs = !P.c64 && !P.xf64;
-    unsigned long long tp = timer ? gtimer() : 0;
-    // the queued tests whose outcome can still matter, in queue order
-    for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < (long long)nq;
-         t += (long long)gridDim.x * NT) {
+    const unsigned long long tp = timer ? gtimer() : 0;
+    // (1) the queued tests whose outcome can still matter, in queue order
+    for (long long t = (long long)blockIdx.x * NT + threadIdx.x; t < (long long)nq; t += (long long)gridDim.x * NT) {
         const QEntry* E = P.queue + t;
         const long long e = E->a;
-        if (!recheck_moot(P, e, P.srow[e], P.cols[e], E->s)) {
+        if (!recheck_moot(P, A, e, A.srow[e], A.cols[e], E->s)) {
             const unsigned long long w = atomicAdd(&P.lm->live[P.l], 1ull);
             P.live[w] = (int)t;
+            if (w < (unsigned long long)kRcCnt) P.rc_cnt[w] = 0;
         }
     }
     if (!grid_sync(P.lm)) return false;
     const unsigned long long nl = ld_cg(&P.lm->live[P.l]);
-    if (nl == 0) return true;
-    // consecutive units go to consecutive CTAs, so a short list spreads over SMs
-    const long long gw = (long long)warp * gridDim.x + blockIdx.x;
-    const long long nwarps = (long long)gridDim.x * NW;
-    // slices per test, the same for every test of the level: about sqrt(n),
-    // which balances a lane's samples in a slice against its slices in the
-    // combine, but no more than about two units per warp
-    const int nref = P.vprob ? P.nmax : P.n;
-    const long long room = max(1ll, (2 * nwarps + (long long)nl - 1) / (long long)nl);
-    const int S = (int)max(1ll, min((long long)min(256, max(1, (int)sqrtf((float)nref))), room));
-    const long long batch = max(1ll, (long long)(P.part_cap / ((unsigned long long)S * D)));
     unsigned long long done = 0;
-    for (long long q0 = 0; q0 < (long long)nl; q0 += batch) {
-        const long long nb = min(batch, (long long)nl - q0);
-        // partial sums
-        for (long long u = gw; u < nb * S; u += nwarps) {
-            const long long qi = P.live[q0 + u / S];
-            const int k = (int)(u % S);
-            const QEntry* E = P.queue + qi;
+    if (LB <= 8 && nl >= (unsigned long long)gridDim.x) {
+        // (2') at least as many tests as CTAs: a warp takes a whole test (all
+        // samples in one slice) and decides it
+        const long long gw = (long long)warp * gridDim.x + blockIdx.x;
+        for (long long ti = gw; ti < (long long)nl; ti += (long long)gridDim.x * NW) {
+            const QEntry* E = P.queue + P.live[ti];
             const long long e = E->a;
-            const int i = P.srow[e], j = P.cols[e];
-            double* out = P.part + (size_t)u * D;
-            if (P.c64) continue;
-            if (pairs)
-                recheck_unit<LB, true>(P, E, i, j, k, S, out);
-            else
-                recheck_unit<LB, false>(P, E, i, j, k, S, out);
-        }
-        if (blockIdx.x == 0) {
-            __syncthreads();
-            if (timer) P.lm->recheck_ns[P.l][2] += gtimer() - tp;
-        }
-        if (!grid_sync(P.lm)) return false;
-        if (timer) {
-            const unsigned long long t2 = gtimer();
-            P.lm->recheck_ns[P.l][0] += t2 - tp;
-            tp = t2;
-        }
-        // combine the slices of each test in order (a warp per test, lanes over
-        // the Gram entries), then eliminate the members of S from the
-        // (l + 2) x (l + 2) correlation block of (S, i, j) with the warp: the
-        // trailing 2 x 2 Schur complement is the conditional covariance of
-        // (V_i, V_j) given S (Eq. PartialCorMat); a member whose remaining
-        // pivot is at or below the rank tolerance is linearly dependent on the
-        // members before it and is dropped (the pseudo-inverse's treatment)
-        for (long long t = gw; t < nb; t += nwarps) {
-            const double* pt = P.part + (size_t)t * S * D;
-            const long long qi = P.live[q0 + t];
-            const QEntry* E = P.queue + qi;
-            const long long e = E->a;
-            const int i = P.srow[e], j = P.cols[e];
-            const int l = P.l, m = l + 2;
-            int V[M];
-            V[0] = i;
-            V[1] = j;
-#pragma unroll
-            for (int c = 0; c < LB; ++c) V[2 + c] = (c < l) ? E->S[c] : i;
-            double (*A)[M] = sA[warp];
-            // elimination position of Gram index g (0 = i, 1 = j, 2 + a = S_a)
-            auto pos = [&](int g) { return g >= 2 ? g - 2 : l + g; };
-            if (P.c64) {
-                for (int x = lane; x < D; x += 32) {
-                    int b2 = 1;
-                    while ((b2 + 1) * b2 / 2 <= x) ++b2;
-                    const int a = x - b2 * (b2 - 1) / 2;
-                    if (b2 < m) {
-                        const int pa = pos(a), pb = pos(b2);
-                        A[max(pa, pb)][min(pa, pb)] = P.c64[(size_t)V[a] * P.p + V[b2]];
-                    }
-                }
-            } else {
-                // the slices of entry x in order within each of the G lane groups
-                // (slice g, g + G, ...), then a fixed xor tree over the groups;
-                // the entry's lane scales by isd_a isd_b / n (the diagonal holds
-                // isd until then). FP32 data: pairs, widened to FP64 once.
-                using RL = RecheckLanes<LB>;
-                const int g = lane / RL::DP;
-                const double inv_n = inv_n_of(P, i);
-                if (lane < m) A[pos(lane)][pos(lane)] = P.isd[gram_var(E, i, j, lane)];
-                __syncwarp();
-                for (int x0 = 0; x0 < D; x0 += RL::DP) {
-                    const int x = x0 + lane % RL::DP;
-                    int a, b2;
-                    gram_pair(x, a, b2);
-                    double v = 0.0;
-                    if (pairs) {
-                        const float2* pt2 = (const float2*)pt;
-                        float h = 0.f, lo = 0.f;
-                        if (x < D) {
-                            // sixteen loads in flight, then their pair additions in order
-                            int s2 = g;
-                            for (; s2 + 15 * RL::G < S; s2 += 16 * RL::G) {
-                                float2 w[16];
-#pragma unroll
-                                for (int u = 0; u < 16; ++u) w[u] = __ldcg(pt2 + (size_t)(s2 + u * RL::G) * D + x);
-#pragma unroll
-                                for (int u = 0; u < 16; ++u) pair_add(h, lo, w[u].x, w[u].y);
-                            }
-                            for (; s2 < S; s2 += RL::G) {
-                                const float2 w = __ldcg(pt2 + (size_t)s2 * D + x);
-                                pair_add(h, lo, w.x, w.y);
-                            }
-                        }
-#pragma unroll
-                        for (int o = 16; o >= RL::DP; o >>= 1) {
-                            const float oh = __shfl_xor_sync(0xffffffffu, h, o);
-                            const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
-                            pair_add(h, lo, oh, ol);
-                        }
-                        v = widen_f32(h) + widen_f32(lo);
-                    } else {
-                        if (x < D) {
-                            int s2 = g;
-                            for (; s2 + 15 * RL::G < S; s2 += 16 * RL::G) {
-                                double w[16];
-#pragma unroll
-                                for (int u = 0; u < 16; ++u) w[u] = __ldcg(pt + (size_t)(s2 + u * RL::G) * D + x);
-#pragma unroll
-                                for (int u = 0; u < 16; ++u) v += w[u];
-                            }
-                            for (; s2 < S; s2 += RL::G) v += __ldcg(pt + (size_t)s2 * D + x);
-                        }
-#pragma unroll
-                        for (int o = 16; o >= RL::DP; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    }
-                    if (x < D && g == 0 && b2 < m) {
-                        const int pa = pos(a), pb = pos(b2);
-                        A[max(pa, pb)][min(pa, pb)] = v * (A[pa][pa] * A[pb][pb]) * inv_n;
-                    }
-                }
-                __syncwarp();
+            const int i = A.srow[e], j = A.cols[e];
+            if (!P.c64) {
+                if (pairs)
+                    recheck_unit<LB, true>(P, E, i, j, 0, 1, &sred[warp][0]);
+                else
+                    recheck_unit<LB, false>(P, E, i, j, 0, 1, &sred[warp][0]);
             }
-            if (lane < m) A[lane][lane] = 1.0;
             __syncwarp();
-            // lower triangle only: step k updates A[a][b], k < b <= a < m
-            for (int k = 0; k < l; ++k) {
-                const double piv = A[k][k];
-                if (piv > P.rank_tol) {
-                    const double rp = 1.0 / piv;
-                    const int r = m - k - 1;
-                    for (int q = lane; q < r * (r + 1) / 2; q += 32) {
-                        int aa = 0;
-                        while ((aa + 1) * (aa + 2) / 2 <= q) ++aa;
-                        const int bb = q - aa * (aa + 1) / 2;
-                        const int a = k + 1 + aa, b = k + 1 + bb;
-                        A[a][b] = fma(-A[a][k] * rp, A[b][k], A[a][b]);
-                    }
-                }
-                __syncwarp();
-            }
+            const bool indep = recheck_decide<LB>(P, A, E, i, j, pairs, &sred[warp][0], sA[warp % NA]);
             if (lane == 0) {
                 ++done;
-                const double H11 = A[l][l], H12 = A[l + 1][l], H22 = A[l + 1][l + 1];
-                double thr, thr2;
-                thresholds(P, i, thr, thr2);
-                const bool indep =
-                    (!(H11 > kVarZero) || !(H22 > kVarZero)) ? true : (H12 * H12 <= thr2 * H11 * H22);
                 if (indep) atomicMin(P.best + e, E->s);
             }
             __syncwarp();
         }
-        if (!grid_sync(P.lm)) return false;
-        if (timer) {
-            const unsigned long long t2 = gtimer();
-            P.lm->recheck_ns[P.l][1] += t2 - tp;
-            tp = t2;
+        if (timer) P.lm->recheck_ns[P.l][0] += gtimer() - tp;
+        done = warp_sum_u64(done);
+        if (lane == 0 && done) atomicAdd(&P.lm->rechecks[P.l], done);
+        return true;
+    }
+    // (2) units (test, slice)
+    int S = 1;
+    if (!P.c64 && nl < (unsigned long long)gridDim.x && nl < (unsigned long long)kRcCnt) {
+        S = (int)min(16ull, (unsigned long long)gridDim.x / max(nl, 1ull));
+        // slice sums of every test must fit the partial buffer (pairs: one double each)
+        while (S > 1 && (unsigned long long)S * nl * D > P.part_cap) --S;
+    }
+    const unsigned long long units = nl * (unsigned long long)S;
+    for (;;) {
+        __syncthreads();                           // sg / sA of the previous unit are no longer read
+        if (threadIdx.x == 0) su = atomicAdd(&P.lm->rc_next[P.l], 1ull);
+        __syncthreads();
+        const unsigned long long u = su;
+        if (u >= units) break;
+        const unsigned long long ti = u / S;
+        const int sl = (int)(u % S);
+        const QEntry* E = P.queue + P.live[ti];
+        const long long e = E->a;
+        const int i = A.srow[e], j = A.cols[e];
+        if (!P.c64) recheck_slice<LB>(P, A, E, i, j, sl, S, pairs, sred, (S == 1) ? sg : P.part + (ti * S + sl) * D);
+        bool last = (S == 1);
+        if (S > 1) {
+            // publish this slice; the CTA that brings the test's count to S decides
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) slast = (atomicAdd(&P.rc_cnt[ti], 1) == S - 1) ? 1 : 0;
+            __syncthreads();
+            last = slast != 0;
+            if (last && warp == 0 && !P.c64) {
+                __threadfence();
+                for (int x = lane; x < D; x += 32) {
+                    if (pairs) {
+                        float h = 0.f, lo = 0.f;
+                        for (int s2 = 0; s2 < S; ++s2) {
+                            const float2 t2 = __ldcg((const float2*)(P.part + (ti * S + s2) * D) + x);
+                            pair_add(h, lo, t2.x, t2.y);
+                        }
+                        ((float2*)sg)[x] = make_float2(h, lo);
+                    } else {
+                        double v = 0.0;
+                        for (int s2 = 0; s2 < S; ++s2) v += __ldcg(P.part + (ti * S + s2) * D + x);
+                        sg[x] = v;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (last && warp == 0) {
+            const bool indep = recheck_decide<LB>(P, A, E, i, j, pairs, sg, sA[0]);
+            if (lane == 0) {
+                ++done;
+                if (indep) atomicMin(P.best + e, E->s);
+            }
         }
     }
-    done = warp_sum_u64(done);
-    if (lane == 0 && done) atomicAdd(&P.lm->rechecks[P.l], done);
+    if (timer) P.lm->recheck_ns[P.l][0] += gtimer() - tp;
+    if (threadIdx.x == 0 && done) atomicAdd(&P.lm->rechecks[P.l], done);
     return true;
 }
 
@@ -1383,11 +1721,11 @@ __device__ bool phase_recheck(const LevelParams& P, unsigned long long nq)
 // side x found none.
 // ---------------------------------------------------------------------------
 template <int LB>
-__device__ __forceinline__ unsigned long long side_serial(const LevelParams& P, int a, long long slot_b,
+__device__ __forceinline__ unsigned long long side_serial(const LevelParams& P, const Csr& A, int a, long long slot_b,
                                                           unsigned long long rank, bool lrn)
 {
-    const long long off = P.row_off[a];
-    const int d = (int)(P.row_off[a + 1] - off);
+    const long long off = A.row_off[a];
+    const int d = (int)(A.row_off[a + 1] - off);
     if (rank == RANK_NONE) return P.B(d - 1, P.l);
     if (lrn) return rank + 1;  // ranks already count the side's own candidates
     int Pos[LB];
@@ -1401,19 +1739,19 @@ __device__ __forceinline__ unsigned long long side_serial(const LevelParams& P, 
 
 // Members of the separating set of rank `rank` found on side (a, b) at slot f.
 template <int LB>
-__device__ __forceinline__ void side_members(const LevelParams& P, int a, long long f, unsigned long long rank,
+__device__ __forceinline__ void side_members(const LevelParams& P, const Csr& A, int a, long long f, unsigned long long rank,
                                              bool lrn, int (&S)[LB])
 {
-    const long long off = P.row_off[a];
-    const int d = (int)(P.row_off[a + 1] - off);
+    const long long off = A.row_off[a];
+    const int d = (int)(A.row_off[a + 1] - off);
     int Pos[LB];
     if (!lrn) {
         unrank_lex<LB>(rank, d, P.l, P.B, Pos);
 #pragma unroll
-        for (int c = 0; c < LB; ++c) S[c] = (c < P.l) ? P.cols[off + Pos[c]] : 0x7fffffff;
+        for (int c = 0; c < LB; ++c) S[c] = (c < P.l) ? A.cols[off + Pos[c]] : 0x7fffffff;
     } else {
         unrank_lex<LB>(rank, d - 1, P.l, P.B, Pos);
-        const int* cand = side_perm(P, a, f);
+        const int* cand = side_perm(P, A, a, f);
 #pragma unroll
         for (int c = 0; c < LB; ++c) S[c] = (c < P.l) ? cand[Pos[c]] : 0x7fffffff;
         // increasing order for the record
@@ -1426,18 +1764,18 @@ __device__ __forceinline__ void side_members(const LevelParams& P, int a, long l
 }
 
 template <int LB>
-__device__ void phase_finalize(const LevelParams& P, bool lrn)
+__device__ void phase_finalize(const LevelParams& P, const Csr& A, bool lrn)
 {
-    const long long nnz = P.row_off[P.p];
+    const long long nnz = A.row_off[P.p];
     const int l = P.l;
     for (long long e0 = (long long)blockIdx.x * NT; e0 < nnz; e0 += (long long)gridDim.x * NT) {
         const long long e = e0 + threadIdx.x;
         bool removed = false;
         unsigned long long serial = 0;
         if (e < nnz) {
-            const int x = P.srow[e], y = P.cols[e];
+            const int x = A.srow[e], y = A.cols[e];
             if (x < y) {
-                const long long f = P.partner[e];
+                const long long f = A.partner[e];
                 const unsigned long long bx = ld_cg(P.best + e), by = ld_cg(P.best + f);
                 int side = -1;
                 long long slot = 0;
@@ -1451,7 +1789,7 @@ __device__ void phase_finalize(const LevelParams& P, bool lrn)
                     atomicSub(P.deg + x, 1);
                     atomicSub(P.deg + y, 1);
                     int S[LB];
-                    side_members<LB>(P, side, slot, rank, lrn, S);
+                    side_members<LB>(P, A, side, slot, rank, lrn, S);
                     const int ints = 3 + l;
                     const unsigned long long at = atomicAdd(&P.lm->rec_ints, (unsigned long long)ints);
                     if (at + ints <= P.rec_cap) {
@@ -1464,9 +1802,11 @@ __device__ void phase_finalize(const LevelParams& P, bool lrn)
                             if (c < l) r[3 + c] = S[c];
                     }
                 }
+                P.alive[e] = removed ? 0 : 1;
+                P.alive[f] = removed ? 0 : 1;
                 if (P.canonical) {
-                    serial = side_serial<LB>(P, x, e, bx, lrn);
-                    if (bx == RANK_NONE) serial += side_serial<LB>(P, y, f, by, lrn);
+                    serial = side_serial<LB>(P, A, x, e, bx, lrn);
+                    if (bx == RANK_NONE) serial += side_serial<LB>(P, A, y, f, by, lrn);
                     if (P.prob_serial && serial) atomicAdd(P.prob_serial + (size_t)P.vprob[x] * LV + l, serial);
                 }
             }
@@ -1515,20 +1855,34 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
     // A'_G of the previous level is still valid when that level removed no edge:
     // the neighbour lists, partner slots and word prefixes are reused (the work
     // items, which depend on l, are rebuilt)
-    const bool reuse = l >= 2 && ld_cg(&lm->removed[l - 1]) == 0ull && *(volatile int*)&lm->csr_level == l - 1;
+    // A level after one that removed edges builds its A'_G from that level's
+    // (incr) into the other buffer; the first level and a rerun build it from the
+    // bitset A_G
+    const int cur = *(volatile int*)&lm->csr_cur;
+    const bool prev = l >= 2 && *(volatile int*)&lm->csr_level == l - 1;
+    const bool reuse = prev && ld_cg(&lm->removed[l - 1]) == 0ull;
+    const bool incr = prev && !reuse;
+    const int nbuf = reuse ? cur : 1 - cur;
+    const Csr A = csr_view(P, nbuf);
+    const Csr O = csr_view(P, cur);
     const bool want_lrn = LEARNED && P.learned && l >= 2;
     const bool one = P.p <= 32 * NT;   // one CTA scans graphs up to 16384 rows (no second barrier)
     if (one) {
-        if (blockIdx.x == 0) phase_scan_one(P, want_lrn);
-        if (!reuse && (blockIdx.x != 0 || gridDim.x == 1)) phase_prefix(P, FP32, 1);
+        if (blockIdx.x == 0) phase_scan_one(P, A, want_lrn);
+        if (!reuse && (blockIdx.x != 0 || gridDim.x == 1)) {
+            if (incr) phase_rank(P, O, 1);
+            else phase_prefix(P, 1);
+        }
     } else {
         phase_scan_a(P, want_lrn);
-        if (!reuse) phase_prefix(P, FP32, 0);
+        if (incr) phase_rank(P, O, 0);
+        else if (!reuse) phase_prefix(P, 0);
     }
     if (!grid_sync(lm)) {
         if (timer) signal_host(P, 2);
         return;
     }
+    if (timer) lm->csr_cur = nbuf;                 // every CTA read the old value before the barrier
     if (*(volatile int*)&lm->maxdeg[l] - 1 < l || *(volatile int*)&lm->range_error) {
         if (timer) {
             lm->done_level = l;
@@ -1539,21 +1893,25 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
     if (timer) signal_host(P, 1 | (min(*(volatile int*)&lm->maxdeg[l], 1 << 26) << 4));
     if (!one) {
         bool lrn_scan = false;
-        if (!phase_scan_b(P, want_lrn, lrn_scan)) return;
+        if (!phase_scan_b(P, A, want_lrn, lrn_scan)) return;
         if (!grid_sync(lm)) return;
     }
-    phase_fill(P, reuse);
+    const bool pivot = (LB == 1) && l == 1 && P.l1_pivot;
+    phase_fill<T>(P, A, O, reuse, incr, pivot);
     if (!grid_sync(lm)) return;
     if (timer) lm->csr_level = l;
     if (timer) { t1 = gtimer(); lm->phase_ns[l][0] += t1 - t0; t0 = t1; }
 
     const bool lrn = LEARNED && *(volatile int*)&lm->learned_on[l];
     if (LEARNED && lrn) {
-        phase_score(P);
+        phase_score(P, A);
         if (!grid_sync(lm)) return;
-        phase_ci_edge<T, LB, FP32>(P);
+        phase_ci_edge<T, LB, FP32>(P, A);
+    } else if (pivot) {
+        extern __shared__ __align__(16) unsigned char dyn_smem[];
+        phase_l1_pivot<T, FP32>(P, A, dyn_smem);
     } else {
-        phase_ci<T, LB, FP32>(P);
+        phase_ci<T, LB, FP32>(P, A);
     }
     if (!grid_sync(lm)) return;
     if (timer) { t1 = gtimer(); lm->phase_ns[l][1] += t1 - t0; t0 = t1; }
@@ -1565,10 +1923,13 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
             if (timer) lm->overflow_level = l;
             return;
         }
-        if (nq > 0 && !phase_recheck<LB>(P, nq)) return;
+        if (nq > 0) {
+            if (!phase_recheck<LB>(P, A, nq)) return;
+            if (!grid_sync(lm)) return;            // every recheck decided before the removals
+        }
         if (timer) { t1 = gtimer(); lm->phase_ns[l][2] += t1 - t0; t0 = t1; }
     }
-    phase_finalize<LB>(P, lrn);
+    phase_finalize<LB>(P, A, lrn);
     if (timer) {
         t1 = gtimer();
         lm->phase_ns[l][3] += t1 - t0;
@@ -1578,19 +1939,30 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
 template <typename T, int LB, bool FP32, bool LEARNED>
 cudaError_t launch_level_t(const LevelParams& P, int num_sms, cudaStream_t st)
 {
+    // level-1 instances reserve shared memory for the pivot form's staged row
+    // (the largest problem's p entries); one occupancy per reserved size
+    const size_t dyn = (LB == 1 && P.l1_pivot) ? (size_t)P.l1_pivot * l1_buf_bytes(P.pstage, sizeof(T)) : 0;
     static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level<T, LB, FP32, LEARNED>, NT, 0);
+    static size_t per_sm_dyn = 0;
+    if (per_sm == 0 || per_sm_dyn != dyn) {
+        if (LB == 1) {
+            cudaError_t e = cudaFuncSetAttribute(k_level<T, LB, FP32, LEARNED>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kL1StageBytes);
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e =
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level<T, LB, FP32, LEARNED>, NT, dyn);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         per_sm = per_sm > 2 ? 2 : per_sm;
+        per_sm_dyn = dyn;
     }
     // CTAs per SM: as many as fit, at most 2, or fewer when asked
     const int k = (P.ctas_per_sm > 0 && P.ctas_per_sm < per_sm) ? P.ctas_per_sm : per_sm;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(num_sms * k);
     cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = dyn;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs resident: the grid barrier relies on it

@@ -32,11 +32,13 @@ struct LevelMeta {
     unsigned long long rec_ints;           // SepSet record ints appended
     int done_level;                        // level whose termination test stopped the loop
     int csr_level;                         // level whose A'_G arrays (cols, srow, partner, wpre) are current
+    int csr_cur;                           // which of the two CSR buffers holds that level's A'_G
     int overflow_level;                    // level whose recheck queue overflowed
     int error;                             // 8: a grid barrier wait expired
     int range_error;                       // a subset count saturated 64 bits
     unsigned long long bar;                // grid barrier: arrivals (low 32 bits), generation (high 32)
     unsigned long long live[LV];           // queued tests rechecked (not decided already)
+    unsigned long long rc_next[LV];        // recheck queue entries claimed by CTAs
     unsigned long long round_hist[LV][RND]; // rows by item count (bin 0: items past RND - 1)
     unsigned long long round_cur[LV][RND]; // slots of each round handed to CTAs so far
 };
@@ -79,7 +81,6 @@ struct LevelParams {
     unsigned* bits;                // live A_G bitset, p rows of W words (batch: packed blocks)
     int W, p;
     long long nwords;              // words of the bitset
-    unsigned* backup;              // FP32 mode: A_G at level start (for a rerun after queue overflow)
     int* deg;
     long long* row_off;            // p + 1 CSR offsets of A'_G
     long long* item_off;           // p + 1: items of the rows before each row (row-major count)
@@ -89,6 +90,14 @@ struct LevelParams {
     int* cols;                     // neighbour indices (increasing per row)
     int* srow;                     // row of each slot
     int* partner;                  // slot of (j, i) for slot (i, j)
+    // second CSR buffer: a level builds its A'_G from the previous level's
+    // (the surviving slots, in order) into the other buffer
+    long long* row_off2;
+    int* cols2;
+    int* srow2;
+    int* partner2;
+    unsigned char* alive;          // per slot of the current A'_G: 1 if its edge survived the level
+    int* nrank;                    // per slot: position among its row's surviving slots, or -1
     int* wpre;                     // per row, neighbours below each 32-column word
     unsigned long long* best;      // smallest separating subset rank per slot
     unsigned long long nnz_cap;
@@ -117,6 +126,7 @@ struct LevelParams {
     const double* c64;
     double* part;                  // recheck partial Gram sums (tests x slices x D doubles)
     int* live;                     // qcap: queue positions of the tests rechecked
+    int* rc_cnt;                   // kRcCnt: slices finished per rechecked test
     unsigned long long part_cap;   // doubles in part
     int* rec;                      // SepSet record pool (int32 groups i, j, l, S...)
     unsigned long long rec_cap;
@@ -137,7 +147,30 @@ struct LevelParams {
     int* perm;                     // per slot (i, j): adj(i) \ {j} by descending score
     long long* poff;               // p + 1: first perm entry of each row
     unsigned long long perm_cap;
+    // level 1 by conditioning variable: row k of C staged in shared memory
+    int l1_pivot;                  // level 1 runs phase_l1_pivot with this many row buffers
+                                   // (2: the next row is copied while one is tested), 0: off
+    int pstage;                    // entries of the longest staged row (largest problem's p)
+    void* cval;                    // nnz_cap entries (T): C_ij of each CSR slot (i, j)
 };
+
+// Tests of a level whose FP64 recheck may be cut into slices over several CTAs.
+constexpr int kRcCnt = 4096;
+
+// Shared memory the level-1 pivot form may use for its staged C rows.
+constexpr int kL1StageBytes = 96 * 1024;
+// Bytes of one staged-row buffer for rows of up to pstage entries of es bytes
+// (room for the row shifted by its misalignment, a multiple of 16).
+__host__ __device__ inline size_t l1_buf_bytes(int pstage, int es)
+{
+    return ((size_t)(pstage + 16 / es) * es + 15) & ~(size_t)15;
+}
+// Row buffers the level-1 pivot form can use (0: rows too long to stage).
+inline int l1_buffers(int pstage, int es)
+{
+    const size_t b = l1_buf_bytes(pstage, es);
+    return 2 * b <= (size_t)kL1StageBytes ? 2 : b <= (size_t)kL1StageBytes ? 1 : 0;
+}
 
 // Parameters of the level-0 FP64 recheck.
 struct Recheck0Params {

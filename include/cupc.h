@@ -98,8 +98,17 @@ typedef struct {
                                 tensor-core product (0 = chosen by its cost model) */
     int batch_direct;        /* batch: 1 = launch the kernels directly instead of
                                 capturing and replaying a CUDA graph (default 0) */
-    int reserved[3];
+    int test_qcap;           /* testing (single-problem calls): when > 0, the initial
+                                capacity of the FP64 recheck queue, in entries */
+    int test_nnz_cap;        /* testing: when > 0, the initial capacity of A'_G in
+                                slots (twice the edges of the densest level) */
+    int test_rec_cap;        /* testing: when > 0, the initial capacity of the SepSet
+                                record pool, in int32 */
 } cupc_options;
+/* The three test capacities exist to exercise the recovery paths: a level
+ * whose buffer would overflow reports it, the buffer is enlarged and the
+ * affected levels run again (cupc_stats.reruns counts the reruns by cause).
+ * The result is the same as with the default capacities. */
 
 typedef struct {
     int levels;                                  /* levels run, level 0 included */
@@ -134,6 +143,10 @@ typedef struct {
     int64_t rechecks_queued[CUPC_STATS_LEVELS];  /* tests queued for the FP64 recheck (those
                                                     whose outcome could no longer matter are
                                                     skipped; rechecks counts the rest) */
+    int32_t reruns[4];                           /* single calls: levels run again after a
+                                                    buffer overflowed: [0] level 0's recheck
+                                                    queue, [1] A'_G's slots, [2] the SepSet
+                                                    pool, [3] a level >= 1 recheck queue */
 } cupc_stats;
 
 typedef struct cupc_ctx cupc_ctx;
@@ -367,6 +380,19 @@ cupc_status cupc_correlation(cupc_ctx* ctx, const void* X, int dtype, int layout
  * variance is not positive). */
 cupc_status cupc_pcor_batch(cupc_ctx* ctx, const void* C, int dtype, int64_t p,
                             const int32_t* queries, int64_t nq, int l, double* rho_out);
+
+/* Partial correlations rho(V_i, V_j | S) (Sec. 4.3, Eqs. PartialCorMat and
+ * RhoCal) for nq queries, evaluated from the data X with the arithmetic of the
+ * FP64 rechecks: the moments of the standardisation, the Gram sums of the
+ * centred data over the l + 2 variables (FP64 for FP64 data, compensated FP32
+ * pairs for FP32 data), then the FP64 elimination of S. X as in cupc_skeleton
+ * (host or device); `queries` is a device int32 array of nq rows
+ * (i, j, S[0..l)); rho_out a device double array of nq entries (NaN when a
+ * conditional variance is not positive). For verification of the recheck
+ * path. */
+cupc_status cupc_pcor_data(cupc_ctx* ctx, const void* X, int dtype, int layout, int on_device,
+                           int64_t n_samples, int64_t p, int64_t ld, const int32_t* queries, int64_t nq,
+                           int l, double* rho_out);
 
 /* ---------------------------------------------------------------------------
  * Candidate-scoring network for learned subset ordering (the paper has no

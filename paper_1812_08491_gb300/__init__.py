@@ -50,6 +50,7 @@ _SIGNATURES = {
     "cupc_result_free": (None, ["vp"]),
     "cupc_correlation": ("status", ["vp", "vp", "int", "int", "int", "i64", "i64", "i64", "int", "vp"]),
     "cupc_pcor_batch": ("status", ["vp", "vp", "int", "i64", "vp", "i64", "int", "vp"]),
+    "cupc_pcor_data": ("status", ["vp", "vp", "int", "int", "int", "i64", "i64", "i64", "vp", "i64", "int", "vp"]),
     "cupc_fisher_threshold": ("status", ["dbl", "i64", "int", "vp", "vp"]),
     "cupc_correlation_noalloc": ("status", ["vp", "int", "int", "i64", "i64", "i64", "vp", "vp"]),
     "cupc_skeleton_batch": ("status", ["vp", "int", "vp", "int", "int", "int", "vp", "vp", "vp", "opts_p", "vp",
@@ -76,7 +77,8 @@ class Options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("canonical_sepset", ctypes.c_int), ("learned_order", ctypes.c_int),
                 ("max_level", ctypes.c_int), ("recheck_margin", ctypes.c_double),
                 ("threads_per_block", ctypes.c_int), ("chunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-                ("corr_kps", ctypes.c_int), ("batch_direct", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("corr_kps", ctypes.c_int), ("batch_direct", ctypes.c_int), ("test_qcap", ctypes.c_int),
+                ("test_nnz_cap", ctypes.c_int), ("test_rec_cap", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -90,7 +92,7 @@ class Stats(ctypes.Structure):
                 ("kernel_ms", ctypes.c_float * 8), ("kernel_count", ctypes.c_int32 * 8),
                 ("ci_block_entries", ctypes.c_int64 * L), ("phase_ms", (ctypes.c_float * 4) * L),
                 ("cuda_graph", ctypes.c_int32), ("recheck_ms", (ctypes.c_float * 3) * L),
-                ("rechecks_queued", ctypes.c_int64 * L)]
+                ("rechecks_queued", ctypes.c_int64 * L), ("reruns", ctypes.c_int32 * 4)]
 
 
 class OrientStats(ctypes.Structure):
@@ -200,7 +202,7 @@ def _stats_dict(s: Stats) -> dict:
             "ci_block_entries": list(s.ci_block_entries[:L]),
             "phase_ms": [list(s.phase_ms[q]) for q in range(L)], "cuda_graph": s.cuda_graph,
             "recheck_ms": [list(s.recheck_ms[q]) for q in range(L)],
-            "rechecks_queued": list(s.rechecks_queued[:L])}
+            "rechecks_queued": list(s.rechecks_queued[:L]), "reruns": list(s.reruns)}
 
 
 class Result:
@@ -315,7 +317,7 @@ class Context:
     @staticmethod
     def options(mode=MODE_FP32_RECHECK, canonical=True, max_level=-1, recheck_margin=0.0,
                 threads_per_block=0, chunk=0, learned_order=False, ctas_per_sm=0, corr_kps=0,
-                batch_direct=False) -> Options:
+                batch_direct=False, test_qcap=0, test_nnz_cap=0, test_rec_cap=0) -> Options:
         o = Options()
         load().cupc_options_default(ctypes.byref(o))
         o.mode = mode
@@ -328,6 +330,9 @@ class Context:
         o.ctas_per_sm = ctas_per_sm
         o.corr_kps = corr_kps
         o.batch_direct = 1 if batch_direct else 0
+        o.test_qcap = test_qcap
+        o.test_nnz_cap = test_nnz_cap
+        o.test_rec_cap = test_rec_cap
         return o
 
     @staticmethod
@@ -436,6 +441,19 @@ class Context:
                                     F32 if C.dtype == torch.float32 else F64, C.shape[0],
                                     ctypes.c_void_p(q.data_ptr()), q.shape[0], l, ctypes.c_void_p(rho.data_ptr()))
         self._check(st, "cupc_pcor_batch")
+        return rho
+
+    def pcor_data(self, X, queries, l: int):
+        """rho(i, j | S) from the data X with the FP64 recheck arithmetic, for rows
+        (i, j, S...) of an int32 tensor; a CUDA float64 tensor."""
+        torch = _torch()
+        ptr, dt, layout, on_dev, n, p, ld, keep = _describe(X)
+        q = queries.to(device=f"cuda:{self.device}", dtype=torch.int32).contiguous()
+        rho = torch.empty(q.shape[0], dtype=torch.float64, device=q.device)
+        st = load().cupc_pcor_data(self._h, ctypes.c_void_p(ptr), dt, layout, on_dev, n, p, ld,
+                                   ctypes.c_void_p(q.data_ptr()), q.shape[0], l, ctypes.c_void_p(rho.data_ptr()))
+        self._check(st, "cupc_pcor_data")
+        del keep
         return rho
 
     # ---- candidate-scoring network -------------------------------------------

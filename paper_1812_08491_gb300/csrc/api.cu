@@ -397,7 +397,8 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     const size_t bitbytes = (size_t)p * W * 4;
     if ((s = dalloc(ctx, (void**)&R->bits, bitbytes)) != CUPC_OK) return s;
     if ((s = dalloc(ctx, (void**)&R->bits0, bitbytes)) != CUPC_OK) return s;
-    size_t qcap = std::max<size_t>(1u << 20, (size_t)4 * p);
+    size_t qcap = o.test_qcap > 0 ? (size_t)o.test_qcap : std::max<size_t>(1u << 20, (size_t)4 * p);
+    int reruns[4] = {0, 0, 0, 0};
     if (fp32 && (s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
     if ((s = ensure_binom(ctx, std::max(p + 1, 64))) != CUPC_OK) return s;
 
@@ -446,11 +447,13 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     const unsigned long long all_slots = (unsigned long long)p * (unsigned long long)(p - 1);
     unsigned long long nnz_cap = std::min<unsigned long long>(
         all_slots, std::max<unsigned long long>({ctx->cap_nnz, 64ull * p, 1ull << 21}));
+    if (o.test_nnz_cap > 0) nnz_cap = std::min<unsigned long long>(all_slots, (unsigned long long)o.test_nnz_cap);
     nnz_cap = std::max<unsigned long long>(nnz_cap, 1);
     const unsigned long long item_cap = 1ull << 22;
     size_t rec_len_cap =
         16 + (ctx->cap_rec ? std::max<size_t>(ctx->cap_rec, (size_t)1 << 16)
                            : std::min<size_t>((size_t)(3 + std::max(lmax, 0)) * (nnz_cap / 2), (size_t)1 << 22));
+    if (o.test_rec_cap > 0) rec_len_cap = (size_t)o.test_rec_cap;
     unsigned long long perm_cap = std::max<unsigned long long>(ctx->cap_perm, 1ull << 22);
     LevelMeta* lm = nullptr;
     LevelParams LP{};
@@ -640,6 +643,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             // enlarge it and run level 0 again
             qcap = (size_t)(M.queue_len * 2);
             if ((s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
+            ++reruns[0];
             continue;
         }
         if (lmax < 1) break;
@@ -654,12 +658,14 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
                 // CSR arrays too small for some level: room for every slot seen, and again
                 nnz_cap = std::min<unsigned long long>(all_slots, nnz_need + nnz_need / 2 + 1024);
                 rerun = true;
+                ++reruns[1];
                 break;
             }
             if (H.error) return fail(ctx, CUPC_E_RANGE, "level buffers too small");
             if (H.rec_ints > rec_len_cap) {
                 rec_len_cap = (size_t)(H.rec_ints + H.rec_ints / 4 + 16);
                 rerun = true;
+                ++reruns[2];
                 break;
             }
             const int ol = H.overflow_level;
@@ -671,6 +677,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             if (ov >= 4) return fail(ctx, CUPC_E_RANGE, "recheck queue overflow persists");
             qcap = (size_t)(H.queue_len[ol] * 2);
             if ((s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
+            ++reruns[3];
             unsigned long long keep = 0;
             for (int q = 1; q < ol; ++q) keep += H.removed[q] * (unsigned long long)(3 + q);
             for (int q = ol; q < LV; ++q) {
@@ -698,6 +705,8 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         if (!rerun) break;
     }
     R->stats.rechecks[0] = (int64_t)M.rechecks;
+    R->stats.rechecks_queued[0] = (int64_t)M.queue_len;
+    for (int k = 0; k < 4; ++k) R->stats.reruns[k] = reruns[k];
     R->stats.removed[0] = pairs - (int64_t)(M.nnz / 2);
     if (lmax >= 1) {
         const LevelMeta& H = *ctx->hlmeta;
@@ -1166,6 +1175,53 @@ cupc_status cupc_pcor_batch(cupc_ctx* ctx, const void* C, int dtype, int64_t p, 
     CU(cudaSetDevice(ctx->device));
     LAUNCH(launch_pcor(dtype == CUPC_F32, C, (int)p, queries, nq, l, rho_out, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    return CUPC_OK;
+}
+
+cupc_status cupc_pcor_data(cupc_ctx* ctx, const void* X, int dtype, int layout, int on_device, int64_t n_samples,
+                           int64_t p, int64_t ld, const int32_t* queries, int64_t nq, int l, double* rho_out)
+{
+    if (!ctx || !X || !queries || !rho_out) return CUPC_E_INVALID;
+    if (l < 0 || l > CUPC_MAX_LEVEL) return fail(ctx, CUPC_E_RANGE, "l out of range");
+    if (p < 2 || n_samples < 4 || nq < 0) return fail(ctx, CUPC_E_INVALID, "sizes");
+    if (dtype != CUPC_F32 && dtype != CUPC_F64) return fail(ctx, CUPC_E_INVALID, "dtype");
+    if (layout != CUPC_LAYOUT_SAMPLE_MAJOR && layout != CUPC_LAYOUT_VARIABLE_MAJOR)
+        return fail(ctx, CUPC_E_INVALID, "layout");
+    if (ld < (layout == CUPC_LAYOUT_SAMPLE_MAJOR ? p : n_samples)) return fail(ctx, CUPC_E_INVALID, "ld");
+    CU(cudaSetDevice(ctx->device));
+    cupc_status s = ensure(ctx, ctx->meta, sizeof(Meta));
+    if (s != CUPC_OK) return s;
+    CU(cudaMemsetAsync(ctx->meta.p, 0, sizeof(Meta), ctx->stream));
+    Input in;
+    in.X = X;
+    in.dtype = dtype;
+    in.layout = layout;
+    in.on_device = on_device;
+    in.n = n_samples;
+    in.p = p;
+    in.ld = ld;
+    const void* Cuse = nullptr;
+    const double* c64 = nullptr;
+    DataView dv;
+    int kcount[CUPC_KCLASSES] = {0};
+    ctx->tused = 0;
+    // the moments and data rows the FP32 form's rechecks read
+    if ((s = prepare(ctx, in, true, &Cuse, &c64, &dv, kcount)) != CUPC_OK) return s;
+    LevelParams P{};
+    P.l = l;
+    P.p = (int)p;
+    P.xv = dv.xv;
+    P.ldx = dv.ldx;
+    P.xf64 = dv.xf64;
+    P.mu = dv.mu;
+    P.isd = dv.isd;
+    P.mup = dv.mup;
+    P.n = (int)n_samples;
+    P.inv_n = 1.0 / (double)n_samples;
+    P.rank_tol = kRankTol32;
+    LAUNCH(launch_pcor_recheck(P, queries, nq, rho_out, ctx->stream));
+    if ((s = readback(ctx)) != CUPC_OK) return s;
+    if (ctx->hmeta->error) return fail(ctx, CUPC_E_NUMERIC, "a variable has zero variance or non-finite data");
     return CUPC_OK;
 }
 

@@ -1530,8 +1530,9 @@ __device__ __forceinline__ void recheck_slice(const LevelParams& P, const Csr& A
 // the rank tolerance is linearly dependent on the members before it and is
 // dropped (the pseudo-inverse's treatment). Returns independence (lane 0).
 template <int LB>
-__device__ __forceinline__ bool recheck_decide(const LevelParams& P, const Csr& A, const QEntry* E, int i, int j, bool pairs,
-                                               const double* g, double (*sA)[LB + 2])
+__device__ __forceinline__ void recheck_eliminate(const LevelParams& P, const QEntry* E, int i, int j, bool pairs,
+                                                  const double* g, double (*sA)[LB + 2], double& H11, double& H12,
+                                                  double& H22)
 {
     constexpr int M = LB + 2;
     constexpr int D = M * (M - 1) / 2;
@@ -1579,11 +1580,51 @@ __device__ __forceinline__ bool recheck_decide(const LevelParams& P, const Csr& 
         }
         __syncwarp();
     }
-    const double H11 = sA[l][l], H12 = sA[l + 1][l], H22 = sA[l + 1][l + 1];
+    H11 = sA[l][l];
+    H12 = sA[l + 1][l];
+    H22 = sA[l + 1][l + 1];
+    __syncwarp();
+}
+
+template <int LB>
+__device__ __forceinline__ bool recheck_decide(const LevelParams& P, const Csr& A, const QEntry* E, int i, int j,
+                                               bool pairs, const double* g, double (*sA)[LB + 2])
+{
+    double H11, H12, H22;
+    recheck_eliminate<LB>(P, E, i, j, pairs, g, sA, H11, H12, H22);
     double thr, thr2;
     thresholds(P, i, thr, thr2);
-    __syncwarp();
     return (!(H11 > kVarZero) || !(H22 > kVarZero)) ? true : (H12 * H12 <= thr2 * H11 * H22);
+}
+
+// rho(V_i, V_j | S) of a batch of queries with the recheck arithmetic (for
+// verification): a warp per query, all samples in one slice.
+constexpr int kPcW = 4;
+template <int LB>
+__global__ void __launch_bounds__(32 * kPcW) k_pcor_recheck(LevelParams P, const int* __restrict__ q, long long nq,
+                                                             double* __restrict__ rho)
+{
+    constexpr int M = LB + 2;
+    constexpr int D = M * (M - 1) / 2;
+    __shared__ double sA[kPcW][M][M];
+    __shared__ double sred[kPcW][D];
+    __shared__ QEntry sE[kPcW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long t = (long long)blockIdx.x * kPcW + warp;
+    if (t >= nq) return;
+    const int* row = q + t * (2 + P.l);
+    const int i = row[0], j = row[1];
+    if (lane < CUPC_MAX_LEVEL) sE[warp].S[lane] = (lane < P.l) ? row[2 + lane] : i;
+    __syncwarp();
+    const bool pairs = !P.xf64;
+    if (pairs)
+        recheck_unit<LB, true>(P, &sE[warp], i, j, 0, 1, &sred[warp][0]);
+    else
+        recheck_unit<LB, false>(P, &sE[warp], i, j, 0, 1, &sred[warp][0]);
+    __syncwarp();
+    double H11, H12, H22;
+    recheck_eliminate<LB>(P, &sE[warp], i, j, pairs, &sred[warp][0], sA[warp], H11, H12, H22);
+    if (lane == 0) rho[t] = (H11 > kVarZero && H22 > kVarZero) ? H12 / sqrt(H11 * H22) : nan("");
 }
 
 // FP64 rechecks of the queued tests. (1) The tests whose outcome can still
@@ -1984,6 +2025,18 @@ cudaError_t launch_level_b(const LevelParams& P, int num_sms, cudaStream_t st)
 }
 
 }  // namespace
+
+cudaError_t launch_pcor_recheck(const LevelParams& P, const int* q, long long nq, double* rho, cudaStream_t st)
+{
+    if (nq <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((nq + kPcW - 1) / kPcW);
+    if (P.l <= 1) k_pcor_recheck<1><<<grid, 32 * kPcW, 0, st>>>(P, q, nq, rho);
+    else if (P.l <= 2) k_pcor_recheck<2><<<grid, 32 * kPcW, 0, st>>>(P, q, nq, rho);
+    else if (P.l <= 4) k_pcor_recheck<4><<<grid, 32 * kPcW, 0, st>>>(P, q, nq, rho);
+    else if (P.l <= 8) k_pcor_recheck<8><<<grid, 32 * kPcW, 0, st>>>(P, q, nq, rho);
+    else k_pcor_recheck<16><<<grid, 32 * kPcW, 0, st>>>(P, q, nq, rho);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_level(int fp32, const LevelParams& P, int num_sms, cudaStream_t st)
 {

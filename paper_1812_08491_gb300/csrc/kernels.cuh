@@ -232,6 +232,9 @@ cudaError_t launch_recheck0(const Recheck0Params& P, int grid, cudaStream_t st);
 cudaError_t launch_level(int fp32, const LevelParams& P, int num_sms, cudaStream_t st);
 cudaError_t launch_pcor(int fp32, const void* C, int p, const int* q, long long nq, int l, double* rho,
                         cudaStream_t st);
+// rho of (i, j, S) queries with the FP64 recheck arithmetic (data rows and
+// moments in P; P.l = |S|).
+cudaError_t launch_pcor_recheck(const LevelParams& P, const int* q, long long nq, double* rho, cudaStream_t st);
 cudaError_t launch_bits_to_u8(const unsigned* bits, int p, int W, unsigned char* out, cudaStream_t st);
 
 // candidate-scoring network (k_mlp.cu)

@@ -292,15 +292,18 @@ def test_scalefree2500_full_size_parity(ctx):
 
 
 def test_large10000_full_size_parity(ctx):
-    """C5 (p = 10^4, n = 1000, levels up to 6) in the benchmarked FP32 form."""
+    """C5 (p = 10^4, n = 1000, levels up to 6) in both forms: the benchmarked
+    FP32 + recheck form and the plain FP64 form."""
     s = sem.workload("large10000")
     ref = _oracle_full(s)
     Xd = torch.from_numpy(s.Xt).cuda().T
-    res = ctx.skeleton(Xd, s.alpha, mode=MODES["fp32"], max_level=s.max_level)
-    assert np.array_equal(res.adjacency(), ref.adj)
-    assert np.array_equal(res.sep_levels(), ref.sep_level)
-    assert res.sepsets() == ref.sepsets
-    assert res.stats()["serial_tests"][:ref.levels_run] == list(ref.tests)
+    for mode in ("fp32", "plain"):
+        res = ctx.skeleton(Xd, s.alpha, mode=MODES[mode], max_level=s.max_level)
+        assert np.array_equal(res.adjacency(), ref.adj), mode
+        assert np.array_equal(res.sep_levels(), ref.sep_level), mode
+        assert res.sepsets() == ref.sepsets, mode
+        assert res.stats()["serial_tests"][:ref.levels_run] == list(ref.tests), mode
+        res.free()
 
 
 def test_device_peaks(ctx):

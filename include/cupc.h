@@ -170,6 +170,32 @@ cupc_status cupc_set_stream(cupc_ctx* ctx, void* stream);
  * counterpart. */
 void cupc_destroy(cupc_ctx* ctx);
 
+/* Requests that the call running on this context (from another host thread),
+ * or the next call, stop between levels: it waits for the work already on the
+ * GPU, frees its partial result and returns CUPC_E_CANCELLED; the context
+ * stays usable. The request is consumed by the call it stops. Safe to call
+ * from any thread. The paper has no counterpart (its runs are not
+ * interruptible). */
+cupc_status cupc_cancel(cupc_ctx* ctx);
+
+/* Host-side fault injection for tests of the error paths (the paper has no
+ * counterpart). kind:
+ *   CUPC_FAIL_ALLOC    the k-th next device allocation of a skeleton call fails
+ *                      (CUPC_E_NOMEM, nothing allocated);
+ *   CUPC_FAIL_LAUNCH   the k-th next kernel launch of a skeleton call fails
+ *                      (CUPC_E_CUDA, nothing launched);
+ *   CUPC_FAIL_BARRIER  in the next skeleton call, the first level kernel's
+ *                      CTA 0 never arrives at its first grid barrier and the
+ *                      other CTAs give up waiting there after k ns (1e3 <= k
+ *                      <= 1e9) instead of 2 s: the wait runs out, no CTA
+ *                      passes that barrier, and the call returns
+ *                      CUPC_E_TIMEOUT;
+ *   CUPC_FAIL_NONE     disarms.
+ * A failure fires once and disarms. The call that meets it returns the error
+ * with no result; the context stays usable. */
+enum { CUPC_FAIL_NONE = 0, CUPC_FAIL_ALLOC = 1, CUPC_FAIL_LAUNCH = 2, CUPC_FAIL_BARRIER = 3 };
+cupc_status cupc_debug_fail(cupc_ctx* ctx, int kind, int64_t k);
+
 /* Message for the last error on this context ("" if none). Never NULL. The
  * paper has no counterpart. */
 const char* cupc_last_error(const cupc_ctx* ctx);
@@ -350,6 +376,32 @@ cupc_status cupc_result_sepset(const cupc_result* res, int64_t i, int64_t j, int
  * *n_ints is set; otherwise at most `cap` ints are written. */
 cupc_status cupc_result_sepset_records(const cupc_result* res, int32_t* out, int64_t cap,
                                        int64_t* n_ints);
+
+/* Level-boundary checkpoint of a single-problem result (the state between
+ * two levels of Algorithm 2: A_G after the result's last level, A_G after
+ * level 0, the SepSet records so far, the per-level counters, and p, n, alpha
+ * and the options the levels ran with), as an opaque, versioned host byte
+ * buffer. A run stopped after level k (opts->max_level = k) and resumed from
+ * its checkpoint with cupc_skeleton_resume gives the skeleton, SepSets and
+ * counters of the uninterrupted run. With buf == NULL only *size is set;
+ * otherwise cap must be at least *size (else CUPC_E_RANGE). CUPC_E_STATE for
+ * a batch result. The paper has no counterpart (its pcalg-style interface,
+ * Sec. 5.1, runs to completion). */
+cupc_status cupc_result_checkpoint(const cupc_result* res, void* buf, int64_t cap, int64_t* size);
+
+/* Continues a run from a checkpoint: the same data (arguments as in
+ * cupc_skeleton; the correlation matrix is recomputed from it, deterministically)
+ * and the same alpha and options (mode, canonical_sepset, learned_order; and
+ * the same network weights for the learned order), with opts->max_level = -1
+ * or >= the checkpoint's level. Runs the levels after the checkpoint's last
+ * one and returns a full result (counters of the checkpoint's levels
+ * included). The data itself is not checked against the checkpoint: the
+ * caller passes the data the checkpoint was taken on. CUPC_E_INVALID for a
+ * malformed checkpoint or one of another problem or options. */
+cupc_status cupc_skeleton_resume(cupc_ctx* ctx, const void* X, int dtype, int layout, int on_device,
+                                 int64_t n_samples, int64_t p, int64_t ld, double alpha,
+                                 const cupc_options* opts, const void* ckpt, int64_t ckpt_size,
+                                 cupc_result** out);
 
 /* Per-level statistics of the call that produced `res`: the test counts of
  * Algorithm 1 in serial order (the paper's Fig. 2 count convention), tests

@@ -21,6 +21,7 @@ __all__ = ["CupcError", "Context", "Result", "load", "lib_path", "build_library"
            "fisher_threshold", "exported_symbols"]
 
 F32, F64 = 0, 1
+FAIL_NONE, FAIL_ALLOC, FAIL_LAUNCH, FAIL_BARRIER = 0, 1, 2, 3
 SAMPLE_MAJOR, VARIABLE_MAJOR = 0, 1
 MODE_PLAIN_FP64, MODE_FP32_RECHECK = 0, 1
 MAX_LEVEL = 16
@@ -37,6 +38,8 @@ _SIGNATURES = {
     "cupc_set_stream": ("status", ["vp", "vp"]),
     "cupc_destroy": (None, ["vp"]),
     "cupc_last_error": ("str", ["vp"]),
+    "cupc_cancel": ("status", ["vp"]),
+    "cupc_debug_fail": ("status", ["vp", "int", "i64"]),
     "cupc_skeleton": ("status", ["vp", "vp", "int", "int", "int", "i64", "i64", "i64", "dbl", "opts_p", "pp"]),
     "cupc_skeleton_corr": ("status", ["vp", "vp", "int", "int", "i64", "i64", "i64", "dbl", "opts_p", "pp"]),
     "cupc_result_p": ("status", ["vp", "vp"]),
@@ -46,6 +49,9 @@ _SIGNATURES = {
     "cupc_result_sepset": ("status", ["vp", "i64", "i64", "vp", "vp"]),
     "cupc_result_sepset_records": ("status", ["vp", "vp", "i64", "vp"]),
     "cupc_result_stats": ("status", ["vp", "vp"]),
+    "cupc_result_checkpoint": ("status", ["vp", "vp", "i64", "vp"]),
+    "cupc_skeleton_resume": ("status", ["vp", "vp", "int", "int", "int", "i64", "i64", "i64", "dbl", "opts_p", "vp",
+                                        "i64", "pp"]),
     "cupc_result_orient": ("status", ["vp", "vp", "vp"]),
     "cupc_result_free": (None, ["vp"]),
     "cupc_correlation": ("status", ["vp", "vp", "int", "int", "int", "i64", "i64", "i64", "int", "vp"]),
@@ -273,6 +279,15 @@ class Result:
         return out, {"rounds": s.rounds, "directed": s.directed, "undirected": s.undirected,
                      "bidirected": s.bidirected, "rule_conflicts": s.rule_conflicts, "ms": s.ms}
 
+    def checkpoint(self) -> bytes:
+        """Level-boundary checkpoint of this result (opaque bytes)."""
+        L = load()
+        n = ctypes.c_int64()
+        self._check(L.cupc_result_checkpoint(self._h, None, 0, ctypes.byref(n)), "cupc_result_checkpoint")
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(L.cupc_result_checkpoint(self._h, buf, n.value, ctypes.byref(n)), "cupc_result_checkpoint")
+        return buf.raw
+
     def stats(self) -> dict:
         s = Stats()
         self._check(load().cupc_result_stats(self._h, ctypes.byref(s)), "cupc_result_stats")
@@ -304,6 +319,15 @@ class Context:
             raise CupcError(st, "cupc_create", "device must be an sm_103 GPU")
         self._h = h
         self.device = device
+
+    def cancel(self):
+        """Stops the running (other thread) or next call between levels."""
+        self._check(load().cupc_cancel(self._h), "cupc_cancel")
+
+    def debug_fail(self, kind: int, k: int = 1):
+        """Arms a host-side failure (FAIL_ALLOC / FAIL_LAUNCH on the k-th next event,
+        FAIL_BARRIER with a k-ns grid-barrier limit for the next call; FAIL_NONE disarms)."""
+        self._check(load().cupc_debug_fail(self._h, kind, k), "cupc_debug_fail")
 
     def last_error(self) -> str:
         if not self._h:
@@ -404,6 +428,18 @@ class Context:
         st = load().cupc_skeleton(self._h, ctypes.c_void_p(ptr), dt, layout, on_dev, n, p, ld, alpha,
                                   ctypes.byref(o), ctypes.byref(out))
         self._check(st, "cupc_skeleton")
+        del keep
+        return Result(self, out.value)
+
+    def skeleton_resume(self, X, alpha: float, checkpoint: bytes, opts: Options | None = None, **kw) -> Result:
+        """Continues a run from Result.checkpoint() on the same data X and alpha."""
+        ptr, dt, layout, on_dev, n, p, ld, keep = _describe(X)
+        o = opts if opts is not None else self.options(**kw)
+        out = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(bytes(checkpoint), len(checkpoint))
+        st = load().cupc_skeleton_resume(self._h, ctypes.c_void_p(ptr), dt, layout, on_dev, n, p, ld, alpha,
+                                         ctypes.byref(o), buf, len(checkpoint), ctypes.byref(out))
+        self._check(st, "cupc_skeleton_resume")
         del keep
         return Result(self, out.value)
 

@@ -37,8 +37,20 @@ cupc_status fail(cupc_ctx* c, cupc_status s, const std::string& what, cudaError_
         if (e_ != cudaSuccess) return fail(ctx, CUPC_E_CUDA, #call, e_);         \
     } while (0)
 
+// Host-side fault injection (cupc_debug_fail): true when the armed failure of
+// this kind is due now (the countdown reached the k-th event); it disarms.
+bool injected(cupc_ctx* ctx, int kind)
+{
+    if (ctx->fail_kind != kind) return false;
+    if (--ctx->fail_k > 0) return false;
+    ctx->fail_kind = 0;
+    return true;
+}
+
 #define LAUNCH(call)                                                             \
     do {                                                                         \
+        if (injected(ctx, CUPC_FAIL_LAUNCH))                                     \
+            return fail(ctx, CUPC_E_CUDA, "injected launch failure: " #call);    \
         cudaError_t e_ = (call);                                                 \
         ctx->launches++;                                                         \
         if (e_ != cudaSuccess) return fail(ctx, CUPC_E_CUDA, #call, e_);         \
@@ -47,6 +59,8 @@ cupc_status fail(cupc_ctx* c, cupc_status s, const std::string& what, cudaError_
 cupc_status dalloc(cupc_ctx* ctx, void** p, size_t bytes)
 {
     *p = nullptr;
+    if (injected(ctx, CUPC_FAIL_ALLOC))
+        return fail(ctx, CUPC_E_NOMEM, "injected failure of a device allocation of " + std::to_string(bytes) + " bytes");
     if (bytes == 0) bytes = 256;
     cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream);
     if (e != cudaSuccess) {
@@ -144,6 +158,21 @@ Binom binom_view(cupc_ctx* ctx)
     return b;
 }
 
+// Level-boundary checkpoint (host bytes): this header, then A_G after the last
+// level run (p x W words), A_G after level 0 (p x W words) and the SepSet
+// records (rec_ints int32, in the order the device appended them).
+struct CkptHeader {
+    char magic[8];              // "CUPCCKP1"
+    int32_t version;            // 1
+    int32_t level;              // last level run
+    int64_t p, n;
+    double alpha;
+    int32_t mode, canonical, learned, W;
+    int64_t rec_ints;
+    cupc_stats stats;           // counters of levels 0 .. level
+};
+constexpr char kCkptMagic[8] = {'C', 'U', 'P', 'C', 'C', 'K', 'P', '1'};
+
 struct Input {
     bool is_corr = false;
     const void* X = nullptr;
@@ -151,6 +180,11 @@ struct Input {
     int layout = CUPC_LAYOUT_SAMPLE_MAJOR;
     int on_device = 0;
     int64_t n = 0, p = 0, ld = 0;
+    // resume: the checkpoint's state (nullptr: a fresh run)
+    const CkptHeader* ck = nullptr;
+    const unsigned* ck_bits = nullptr;
+    const unsigned* ck_bits0 = nullptr;
+    const int32_t* ck_rec = nullptr;
 };
 
 size_t elem_size(int dtype) { return dtype == CUPC_F64 ? 8 : 4; }
@@ -363,10 +397,30 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         return fail(ctx, CUPC_E_INVALID, "ld < p");
     }
 
+    const CkptHeader* ck = in.ck;
+    if (ck) {
+        if (ck->p != in.p || ck->n != in.n || !(ck->alpha == alpha))
+            return fail(ctx, CUPC_E_INVALID, "checkpoint of another problem (p, n or alpha differ)");
+        if (ck->mode != o.mode || ck->canonical != o.canonical_sepset || ck->learned != o.learned_order)
+            return fail(ctx, CUPC_E_INVALID, "checkpoint taken with other options (mode, canonical, learned)");
+        if (o.max_level >= 0 && o.max_level < ck->level)
+            return fail(ctx, CUPC_E_INVALID, "max_level below the checkpoint's level");
+    }
     CU(cudaSetDevice(ctx->device));
     const bool fp32 = (o.mode == CUPC_MODE_FP32_RECHECK);
     const int p = (int)in.p;
     const int W = (p + 31) / 32;
+    const int from = ck ? ck->level + 1 : 1;       // first level to run
+    const unsigned barrier_ns = ctx->barrier_ns;   // a test's grid-barrier limit applies to one call
+    ctx->barrier_ns = 0;
+    // a cancellation request ends the call between levels (the work in flight is
+    // waited for; the context stays usable)
+    auto cancelled = [&]() -> bool {
+        if (ctx->cancel.exchange(0) == 0) return false;
+        cudaStreamSynchronize(ctx->stream);
+        cudaGetLastError();
+        return true;
+    };
     const int64_t n = in.n;
     const unsigned long long launches0 = ctx->launches, h2d0 = ctx->h2d, d2h0 = ctx->d2h;
     int kcount[CUPC_KCLASSES] = {0};
@@ -382,6 +436,11 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     ctx->refs++;
     R->p = p;
     R->W = W;
+    R->n = n;
+    R->alpha = alpha;
+    R->mode = o.mode;
+    R->canonical = o.canonical_sepset;
+    R->learned = o.learned_order;
     struct Guard {
         cupc_result*& r;
         bool ok = false;
@@ -453,7 +512,9 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     size_t rec_len_cap =
         16 + (ctx->cap_rec ? std::max<size_t>(ctx->cap_rec, (size_t)1 << 16)
                            : std::min<size_t>((size_t)(3 + std::max(lmax, 0)) * (nnz_cap / 2), (size_t)1 << 22));
-    if (o.test_rec_cap > 0) rec_len_cap = (size_t)o.test_rec_cap;
+    const size_t base_rec = ck ? (size_t)ck->rec_ints : 0;   // records of the checkpoint's levels
+    rec_len_cap += base_rec;
+    if (o.test_rec_cap > 0) rec_len_cap = base_rec + (size_t)o.test_rec_cap;
     unsigned long long perm_cap = std::max<unsigned long long>(ctx->cap_perm, 1ull << 22);
     LevelMeta* lm = nullptr;
     LevelParams LP{};
@@ -465,7 +526,12 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         if (attempt > 6) return fail(ctx, CUPC_E_RANGE, "level buffers keep overflowing");
         // level 0's counters (the error flags of the preparation stay)
         CU(cudaMemsetAsync(meta, 0, offsetof(Meta, error), ctx->stream));
-        {
+        if (ck) {
+            // resume: A_G after the checkpoint's last level and after level 0
+            CU(cudaMemcpyAsync(R->bits, in.ck_bits, bitbytes, cudaMemcpyHostToDevice, ctx->stream));
+            CU(cudaMemcpyAsync(R->bits0, in.ck_bits0, bitbytes, cudaMemcpyHostToDevice, ctx->stream));
+            ctx->h2d += 2 * bitbytes;
+        } else {
             const double r0 = std::tanh(fisher_tau(alpha, n, 0));
             TIMED(CUPC_K_LEVEL0, launch_level0(fp32, Cuse, p, W, r0, kBand0, R->bits, (QEntry*)ctx->queue.p, qcap,
                                                meta, ctx->stream));
@@ -475,8 +541,8 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         if ((s = ensure(ctx, ctx->deg, (size_t)p * 4)) != CUPC_OK) return s;
         TIMED(CUPC_K_COMPACT, launch_degree(R->bits, p, W, (int*)ctx->deg.p, meta, ctx->stream));
         last_launched = 0;
-        levels_run = 1;
-        if (lmax >= 1) {
+        levels_run = from;
+        if (lmax >= from) {
             if ((s = ensure(ctx, ctx->row_off, (size_t)(p + 1) * 8)) != CUPC_OK) return s;
             if ((s = ensure(ctx, ctx->item_off, (size_t)(p + 1) * 8)) != CUPC_OK) return s;
             if ((s = ensure(ctx, ctx->cols, (size_t)nnz_cap * 4)) != CUPC_OK) return s;
@@ -508,6 +574,15 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             if ((s = dalloc(ctx, (void**)&R->rec, rec_len_cap * 4)) != CUPC_OK) return s;
             lm = (LevelMeta*)ctx->lmeta.p;
             CU(cudaMemsetAsync(lm, 0, sizeof(LevelMeta), ctx->stream));
+            if (base_rec) {
+                // the checkpoint's records come first; the levels append after them
+                CU(cudaMemcpyAsync(R->rec, in.ck_rec, base_rec * 4, cudaMemcpyHostToDevice, ctx->stream));
+                ctx->h2d += base_rec * 4;
+                ctx->hlmeta->rec_ints = base_rec;
+                CU(cudaMemcpyAsync(&lm->rec_ints, &ctx->hlmeta->rec_ints, sizeof(unsigned long long),
+                                   cudaMemcpyHostToDevice, ctx->stream));
+                CU(cudaStreamSynchronize(ctx->stream));   // (the pinned staging word is reused below)
+            }
 
             LP = LevelParams{};
             LP.bits = R->bits;
@@ -565,6 +640,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             LP.meta0 = meta;
             LP.qcap0 = fp32 ? qcap : ~0ull;
             LP.learned = o.learned_order ? 1 : 0;
+            LP.barrier_ns = 0;
             if (o.learned_order) {
                 // per-slot candidate lists of levels >= 2 (a level whose lists would not
                 // fit keeps the increasing order)
@@ -598,6 +674,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             LP.host_flags = ctx->dflags;
             for (int q = 0; q < LV; ++q) ((volatile int*)ctx->hflags)[q] = 0;
             for (int l = from; l <= lmax; ++l) {
+                if (cancelled()) return fail(ctx, CUPC_E_CANCELLED, "cancelled before level " + std::to_string(l));
                 if (l - 2 >= from) {
                     volatile int* fl = (volatile int*)ctx->hflags + (l - 2);
                     const auto t0 = std::chrono::steady_clock::now();
@@ -615,6 +692,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
                     }
                 }
                 LP.l = l;
+                LP.barrier_ns = (l == from) ? barrier_ns : 0;   // (the expiry test: first level only)
                 const double r = std::tanh(fisher_tau(alpha, n, l));
                 LP.r = r;
                 LP.r2 = r * r;
@@ -625,12 +703,13 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             }
             return CUPC_OK;
         };
-        if (lmax >= 1 && (s = launch_levels(1)) != CUPC_OK) return s;
+        if (cancelled()) return fail(ctx, CUPC_E_CANCELLED, "cancelled after level 0");
+        if (lmax >= from && (s = launch_levels(from)) != CUPC_OK) return s;
 
         // one readback: level 0's counters and, when levels ran, theirs
         CU(cudaMemcpyAsync(ctx->hmeta, meta, sizeof(Meta), cudaMemcpyDeviceToHost, ctx->stream));
         ctx->d2h += sizeof(Meta);
-        if (lmax >= 1) {
+        if (lmax >= from) {
             CU(cudaMemcpyAsync(ctx->hlmeta, lm, sizeof(LevelMeta), cudaMemcpyDeviceToHost, ctx->stream));
             ctx->d2h += sizeof(LevelMeta);
         }
@@ -646,7 +725,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             ++reruns[0];
             continue;
         }
-        if (lmax < 1) break;
+        if (lmax < from) break;
         bool rerun = false;
         for (int ov = 0;; ++ov) {
             LevelMeta& H = *ctx->hlmeta;
@@ -678,8 +757,8 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             qcap = (size_t)(H.queue_len[ol] * 2);
             if ((s = ensure(ctx, ctx->queue, qcap * sizeof(QEntry))) != CUPC_OK) return s;
             ++reruns[3];
-            unsigned long long keep = 0;
-            for (int q = 1; q < ol; ++q) keep += H.removed[q] * (unsigned long long)(3 + q);
+            unsigned long long keep = base_rec;
+            for (int q = from; q < ol; ++q) keep += H.removed[q] * (unsigned long long)(3 + q);
             for (int q = ol; q < LV; ++q) {
                 H.tests[q] = H.rechecks[q] = H.removed[q] = H.serial[q] = H.edges[q] = H.items[q] = 0;
                 H.next_item[q] = H.queue_len[q] = H.block_entries[q] = 0;
@@ -708,15 +787,30 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     R->stats.rechecks_queued[0] = (int64_t)M.queue_len;
     for (int k = 0; k < 4; ++k) R->stats.reruns[k] = reruns[k];
     R->stats.removed[0] = pairs - (int64_t)(M.nnz / 2);
-    if (lmax >= 1) {
+    if (ck) {
+        // the checkpoint's levels keep their counters
+        const cupc_stats& c = ck->stats;
+        for (int q = 0; q < from && q < CUPC_STATS_LEVELS; ++q) {
+            R->stats.tests[q] = c.tests[q];
+            R->stats.serial_tests[q] = c.serial_tests[q];
+            R->stats.removed[q] = c.removed[q];
+            R->stats.rechecks[q] = c.rechecks[q];
+            R->stats.edges_start[q] = c.edges_start[q];
+            R->stats.max_degree[q] = c.max_degree[q];
+            R->stats.ci_block_entries[q] = c.ci_block_entries[q];
+            R->stats.rechecks_queued[q] = c.rechecks_queued[q];
+        }
+        R->rec_ints = (int64_t)base_rec;
+    }
+    if (lmax >= from) {
         const LevelMeta& H = *ctx->hlmeta;
         // last level that ran: the one before the level whose termination test
         // ended the loop, or before the level the host did not launch
-        const int last = H.done_level ? H.done_level - 1 : host_stop ? host_stop - 1 : lmax;
+        const int last = std::max(from - 1, H.done_level ? H.done_level - 1 : host_stop ? host_stop - 1 : lmax);
         if (range_stop && H.done_level == 0 && host_stop == 0)
             return fail(ctx, CUPC_E_RANGE, "a level above CUPC_MAX_LEVEL would be needed");
         levels_run = last + 1;
-        for (int l = 1; l <= last && l < CUPC_STATS_LEVELS; ++l) {
+        for (int l = from; l <= last && l < CUPC_STATS_LEVELS; ++l) {
             R->stats.tests[l] = (int64_t)H.tests[l];
             R->stats.removed[l] = (int64_t)H.removed[l];
             R->stats.serial_tests[l] = o.canonical_sepset ? (int64_t)H.serial[l] : -1;
@@ -759,7 +853,9 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
     R->stats.prep_ms = ms;
-    for (int q = 0; q < levels_run && q < CUPC_STATS_LEVELS; ++q) {
+    if (ck)
+        for (int q = 0; q < from && q < CUPC_STATS_LEVELS; ++q) R->stats.level_ms[q] = ck->stats.level_ms[q];
+    for (int q = ck ? from : 0; q < levels_run && q < CUPC_STATS_LEVELS; ++q) {
         // level 0 spans the sizing step; level q >= 1 its level kernel launch
         const int a = 1 + q, b = (q + 1 <= last_launched) ? 2 + q : ev_end;
         if (b > ev_end || a >= (int)ctx->ev.size()) break;
@@ -936,6 +1032,33 @@ cupc_status cupc_create(cupc_ctx** out, int device, void* stream)
     c->tcls.resize(256);
     for (auto& e : c->tev) cudaEventCreate(&e);
     *out = c;
+    return CUPC_OK;
+}
+
+cupc_status cupc_cancel(cupc_ctx* ctx)
+{
+    if (!ctx) return CUPC_E_INVALID;
+    ctx->cancel.store(1);
+    return CUPC_OK;
+}
+
+cupc_status cupc_debug_fail(cupc_ctx* ctx, int kind, int64_t k)
+{
+    if (!ctx) return CUPC_E_INVALID;
+    if (kind == CUPC_FAIL_NONE) {
+        ctx->fail_kind = 0;
+        ctx->barrier_ns = 0;
+        return CUPC_OK;
+    }
+    if (kind == CUPC_FAIL_BARRIER) {
+        if (k < 1000 || k > 1000000000) return fail(ctx, CUPC_E_INVALID, "barrier limit in ns must be in [1e3, 1e9]");
+        ctx->barrier_ns = (unsigned)k;
+        return CUPC_OK;
+    }
+    if ((kind != CUPC_FAIL_ALLOC && kind != CUPC_FAIL_LAUNCH) || k < 1)
+        return fail(ctx, CUPC_E_INVALID, "unknown failure kind or k < 1");
+    ctx->fail_kind = kind;
+    ctx->fail_k = k;
     return CUPC_OK;
 }
 
@@ -1125,6 +1248,75 @@ cupc_status cupc_result_sepset_records(const cupc_result* r, int32_t* out, int64
     *n_ints = (int64_t)r->hrec.size();
     if (out) std::memcpy(out, r->hrec.data(), (size_t)std::min<int64_t>(cap, *n_ints) * 4);
     return CUPC_OK;
+}
+
+cupc_status cupc_result_checkpoint(const cupc_result* r, void* buf, int64_t cap, int64_t* size)
+{
+    if (!r || !size) return CUPC_E_INVALID;
+    if (r->on_host || !r->bits || !r->bits0) return fail(r->ctx, CUPC_E_STATE, "not a single-problem result");
+    const size_t words = (size_t)r->p * r->W;
+    const size_t total = sizeof(CkptHeader) + 2 * words * 4 + (size_t)r->rec_ints * 4;
+    *size = (int64_t)total;
+    if (!buf) return CUPC_OK;
+    if (cap < (int64_t)total) return fail(r->ctx, CUPC_E_RANGE, "checkpoint buffer too small");
+    cupc_ctx* ctx = r->ctx;
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.level = r->stats.levels - 1;
+    h.p = r->p;
+    h.n = r->n;
+    h.alpha = r->alpha;
+    h.mode = r->mode;
+    h.canonical = r->canonical;
+    h.learned = r->learned;
+    h.W = r->W;
+    h.rec_ints = r->rec_ints;
+    h.stats = r->stats;
+    unsigned char* o = (unsigned char*)buf;
+    std::memcpy(o, &h, sizeof(h));
+    CU(cudaMemcpyAsync(o + sizeof(h), r->bits, words * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(o + sizeof(h) + words * 4, r->bits0, words * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    if (r->rec_ints)
+        CU(cudaMemcpyAsync(o + sizeof(h) + 2 * words * 4, r->rec, (size_t)r->rec_ints * 4, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->d2h += total - sizeof(h);
+    return CUPC_OK;
+}
+
+cupc_status cupc_skeleton_resume(cupc_ctx* ctx, const void* X, int dtype, int layout, int on_device, int64_t n_samples,
+                                 int64_t p, int64_t ld, double alpha, const cupc_options* opts, const void* ckpt,
+                                 int64_t ckpt_size, cupc_result** out)
+{
+    if (!ctx) return CUPC_E_INVALID;
+    if (out) *out = nullptr;
+    if (!ckpt || ckpt_size < (int64_t)sizeof(CkptHeader)) return fail(ctx, CUPC_E_INVALID, "checkpoint too short");
+    CkptHeader h;
+    std::memcpy(&h, ckpt, sizeof(h));
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1)
+        return fail(ctx, CUPC_E_INVALID, "not a checkpoint of this library");
+    if (h.p < 2 || h.p > (1 << 20) || h.W != (int)((h.p + 31) / 32) || h.level < 0 ||
+        h.level >= CUPC_STATS_LEVELS - 1 || h.level > CUPC_MAX_LEVEL || h.rec_ints < 0)
+        return fail(ctx, CUPC_E_INVALID, "checkpoint header out of range");
+    const size_t words = (size_t)h.p * h.W;
+    if ((uint64_t)ckpt_size != sizeof(h) + 2 * words * 4 + (uint64_t)h.rec_ints * 4)
+        return fail(ctx, CUPC_E_INVALID, "checkpoint size does not match its header");
+    const unsigned char* b = (const unsigned char*)ckpt;
+    Input in;
+    in.X = X;
+    in.dtype = dtype;
+    in.layout = layout;
+    in.on_device = on_device;
+    in.n = n_samples;
+    in.p = p;
+    in.ld = ld;
+    in.ck = &h;
+    in.ck_bits = (const unsigned*)(b + sizeof(h));
+    in.ck_bits0 = (const unsigned*)(b + sizeof(h) + words * 4);
+    in.ck_rec = (const int32_t*)(b + sizeof(h) + 2 * words * 4);
+    return run(ctx, in, alpha, opts, out);
 }
 
 cupc_status cupc_result_stats(const cupc_result* r, cupc_stats* out)

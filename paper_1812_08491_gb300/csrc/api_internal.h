@@ -2,6 +2,7 @@
 // the C ABI (api.cu, api_mlp.cu).
 #pragma once
 
+#include <atomic>
 #include <map>
 #include <string>
 #include <vector>
@@ -24,6 +25,10 @@ struct Buf {
 };
 
 struct cupc_ctx {
+    std::atomic<int> cancel{0};         // cupc_cancel: the running or next call stops between levels
+    int fail_kind = 0;                  // cupc_debug_fail: armed failure (0 none)
+    long long fail_k = 0;               // ... on the k-th next allocation / launch
+    unsigned barrier_ns = 0;            // ... or the next call's grid-barrier wait limit
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaMemPool_t pool = nullptr;
@@ -59,6 +64,9 @@ struct cupc_ctx {
 struct cupc_result {
     cupc_ctx* ctx = nullptr;
     int64_t p = 0;
+    int64_t n = 0;                 // samples, alpha and the options the levels ran with
+    double alpha = 0.0;
+    int mode = 0, canonical = 0, learned = 0;
     int W = 0;
     unsigned* bits = nullptr;
     unsigned* bits0 = nullptr;

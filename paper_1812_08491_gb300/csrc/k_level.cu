@@ -109,9 +109,14 @@ __device__ __forceinline__ void thresholds(const LevelParams& P, int v, double& 
 // atomic add; the last one adds 2^32 - N, which returns the arrivals to 0 and
 // advances the generation in the same operation, and the others poll the
 // generation (the error flag and the clock every 64th poll).
-__device__ bool grid_sync(LevelMeta* lm)
+// The wait is limited to kBarrierNs, or to P.barrier_ns when that is set (a
+// test of the expiry path).
+__device__ bool grid_sync(const LevelParams& P)
 {
     __shared__ int ok;
+    LevelMeta* lm = P.lm;
+    const unsigned long long lim = P.barrier_ns ? (unsigned long long)P.barrier_ns : kBarrierNs;
+    const unsigned every = 63u;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -123,9 +128,9 @@ __device__ bool grid_sync(LevelMeta* lm)
             volatile unsigned long long* vb = &lm->bar;
             const unsigned long long t0 = gtimer();
             for (unsigned it = 1; (unsigned)(*vb >> 32) == g; ++it) {
-                if ((it & 63u) == 0) {
+                if ((it & every) == 0) {
                     if (*(volatile int*)&lm->error) break;
-                    if (gtimer() - t0 > kBarrierNs) {
+                    if (gtimer() - t0 > lim) {
                         atomicOr(&lm->error, 8);
                         break;
                     }
@@ -539,7 +544,7 @@ __device__ bool phase_scan_b(const LevelParams& P, const Csr& A, bool learned, b
             for (int q = 0; q < NW; ++q) x += wsum[q][0];
             P.scan_part[(size_t)blockIdx.x * 4 + (lrn ? 2 : 1)] = x;
         }
-        if (!grid_sync(P.lm)) return false;
+        if (!grid_sync(P)) return false;
         totals();
     }
     // this CTA's rows: exclusive scans of (slots, items, list entries), in tiles of NT rows
@@ -1664,7 +1669,7 @@ __device__ bool phase_recheck(const LevelParams& P, const Csr& A, unsigned long 
             if (w < (unsigned long long)kRcCnt) P.rc_cnt[w] = 0;
         }
     }
-    if (!grid_sync(P.lm)) return false;
+    if (!grid_sync(P)) return false;
     const unsigned long long nl = ld_cg(&P.lm->live[P.l]);
     unsigned long long done = 0;
     if (LB <= 8 && nl >= (unsigned long long)gridDim.x) {
@@ -1889,6 +1894,14 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
         if (blockIdx.x == 0 && threadIdx.x == 0) signal_host(P, 2);
         return;
     }
+    if (P.barrier_ns && blockIdx.x == 0) {
+        // test of the barrier-expiry path: this CTA never arrives at the first
+        // grid barrier (a generation that nothing advances), so every other CTA
+        // waits out P.barrier_ns there, raises the error and ends; no CTA passes
+        // that barrier
+        if (threadIdx.x == 0) signal_host(P, 2);
+        return;
+    }
     unsigned long long t0 = 0, t1;
     const bool timer = (blockIdx.x == 0 && threadIdx.x == 0);
     if (timer) t0 = gtimer();
@@ -1919,7 +1932,7 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
         if (incr) phase_rank(P, O, 0);
         else if (!reuse) phase_prefix(P, 0);
     }
-    if (!grid_sync(lm)) {
+    if (!grid_sync(P)) {
         if (timer) signal_host(P, 2);
         return;
     }
@@ -1935,18 +1948,18 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
     if (!one) {
         bool lrn_scan = false;
         if (!phase_scan_b(P, A, want_lrn, lrn_scan)) return;
-        if (!grid_sync(lm)) return;
+        if (!grid_sync(P)) return;
     }
     const bool pivot = (LB == 1) && l == 1 && P.l1_pivot;
     phase_fill<T>(P, A, O, reuse, incr, pivot);
-    if (!grid_sync(lm)) return;
+    if (!grid_sync(P)) return;
     if (timer) lm->csr_level = l;
     if (timer) { t1 = gtimer(); lm->phase_ns[l][0] += t1 - t0; t0 = t1; }
 
     const bool lrn = LEARNED && *(volatile int*)&lm->learned_on[l];
     if (LEARNED && lrn) {
         phase_score(P, A);
-        if (!grid_sync(lm)) return;
+        if (!grid_sync(P)) return;
         phase_ci_edge<T, LB, FP32>(P, A);
     } else if (pivot) {
         extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -1954,7 +1967,7 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
     } else {
         phase_ci<T, LB, FP32>(P, A);
     }
-    if (!grid_sync(lm)) return;
+    if (!grid_sync(P)) return;
     if (timer) { t1 = gtimer(); lm->phase_ns[l][1] += t1 - t0; t0 = t1; }
 
     if (FP32) {
@@ -1966,7 +1979,7 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
         }
         if (nq > 0) {
             if (!phase_recheck<LB>(P, A, nq)) return;
-            if (!grid_sync(lm)) return;            // every recheck decided before the removals
+            if (!grid_sync(P)) return;            // every recheck decided before the removals
         }
         if (timer) { t1 = gtimer(); lm->phase_ns[l][2] += t1 - t0; t0 = t1; }
     }

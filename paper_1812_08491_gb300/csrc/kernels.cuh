@@ -148,6 +148,9 @@ struct LevelParams {
     long long* poff;               // p + 1: first perm entry of each row
     unsigned long long perm_cap;
     // level 1 by conditioning variable: row k of C staged in shared memory
+    unsigned barrier_ns;           // 0: grid-barrier waits end after kBarrierNs; else a test of
+                                   // the expiry path: CTA 0 withholds its arrival at the first
+                                   // barrier and the others give up after this many ns
     int l1_pivot;                  // level 1 runs phase_l1_pivot with this many row buffers
                                    // (2: the next row is copied while one is tested), 0: off
     int pstage;                    // entries of the longest staged row (largest problem's p)

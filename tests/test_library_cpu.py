@@ -77,3 +77,14 @@ def test_result_entry_points_reject_null_results(lib):
     assert lib.cupc_result_edges(None, None, 0, ctypes.byref(n)) == -1
     assert lib.cupc_result_sepset_records(None, None, 0, ctypes.byref(n)) == -1
     assert lib.cupc_result_adjacency(None, None) == -1
+
+
+def test_control_entry_points_reject_null(lib):
+    """Cancellation, fault injection, checkpoint and resume check their
+    arguments before any CUDA work."""
+    n = ctypes.c_int64()
+    assert lib.cupc_cancel(None) == -1
+    assert lib.cupc_debug_fail(None, cupc.FAIL_ALLOC, 1) == -1
+    assert lib.cupc_result_checkpoint(None, None, 0, ctypes.byref(n)) == -1
+    out = ctypes.c_void_p()
+    assert lib.cupc_skeleton_resume(None, None, 0, 0, 0, 10, 2, 2, 0.01, None, None, 0, ctypes.byref(out)) == -1

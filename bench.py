@@ -305,6 +305,147 @@ def kernel_rooflines(st, s, mode, peaks, alu=None):
     return out
 
 
+def level_bounds(st, mode, peaks, alu):
+    """Bound of the level kernel's CI phase per level (SURVEY-style arithmetic
+    intensity): algorithmic bytes = the C sub-block entries the level's tests
+    read; FP32 (or FP64) flops = tests x (l^2 + 4 l + 10) (the factor apply, the
+    decision; the per-(i, S) factorisations are left out, so this is a lower
+    bound). A level whose flops per byte exceed the ridge point (measured ALU
+    peak / measured HBM bandwidth) is ALU-bound, else HBM-bound; achieved is over
+    the CI phase's device-clock time."""
+    cb = 4 if mode == "fp32" else 8
+    hbm = peaks["hbm_gbs"]
+    alu_peak = (alu["fp32_tflops"] if mode == "fp32" else alu["fp64_tflops"]) if alu else None
+    out = []
+    for l in range(1, st["levels"]):
+        ms = st["phase_ms"][l][1]
+        byts = st["ci_block_entries"][l] * cb
+        flops = st["tests"][l] * (l * l + 4 * l + 10)
+        if ms <= 0 or byts <= 0:
+            continue
+        ridge = (alu_peak * 1e12) / (hbm * 1e9) if alu_peak else float("inf")
+        intensity = flops / byts
+        if intensity > ridge:
+            ach = flops / (ms * 1e-3) / 1e12
+            out.append({"level": l, "bound": "alu", "unit": "TFLOP/s", "achieved": round(ach, 4), "peak": alu_peak,
+                        "frac": round(ach / alu_peak, 6), "intensity": round(intensity, 2), "ci_ms": round(ms, 4)})
+        else:
+            ach = byts / (ms * 1e-3) / 1e9
+            out.append({"level": l, "bound": "hbm", "unit": "GB/s", "achieved": round(ach, 3), "peak": hbm,
+                        "frac": round(ach / hbm, 6), "intensity": round(intensity, 2), "ci_ms": round(ms, 4)})
+    return out
+
+
+def timed_steps(ctx, X, s, opts, steps, stream, flush):
+    """Device time (ms) of `steps` skeleton calls with L2 flushed between them, and
+    the last call's stats; CUDA events on the library's stream around each call."""
+    import torch
+    tot, st = 0.0, None
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = ctx.skeleton(X, s.alpha, opts)
+        b.record(stream)
+        st = r.stats()
+        r.free()
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+    return tot, st
+
+
+def large_leg(ctx, args, peaks_alu, dev, stream, flush, learned_info_cache):
+    """The p = 10^4 workload (n = 1000, degree 5, levels up to 6) beside the
+    headline one: FP32 bulk + FP64 recheck, the learned ordering on top of it,
+    and the plain FP64 form, each timed on device-resident input."""
+    import torch
+
+    import paper_1812_08491_gb300 as cupc
+    from synth import sem
+    s = sem.workload("large10000")
+    X = torch.from_numpy(s.Xt).to(dev).T
+    ref = ctx.skeleton(X, s.alpha, mode=cupc.MODE_FP32_RECHECK, canonical=True, max_level=s.max_level)
+    units = int(sum(ref.stats()["serial_tests"]))
+    ref.free()
+    opts = ctx.options(mode=cupc.MODE_FP32_RECHECK, canonical=True, max_level=s.max_level)
+    timed_steps(ctx, X, s, opts, max(3, args.warmup), stream, flush)
+    k = max(3, args.steps // 2)
+    ms, st = timed_steps(ctx, X, s, opts, k, stream, flush)
+    leg = {"workload": "large10000", "p": s.p, "n": s.n, "degree": 5.0, "alpha": s.alpha, "max_level": s.max_level,
+           "input_dtype": "float64", "serial_tests_per_step": units, "steps": k,
+           "ms_per_step": ms / k, "value": units * k / (ms * 1e-3), "unit": UNIT,
+           "form": "FP32 bulk + FP64 recheck", "l2": "flushed between steps (256 MiB write)"}
+    kern = kernel_rooflines(st, s, "fp32", _peaks(), peaks_alu)
+    dom = max((q for q in kern if q != "recheck"), key=lambda q: kern[q]["ms"])
+    leg["roofline"] = {q: kern[dom][q] for q in ("bound", "achieved", "peak", "unit", "frac")}
+    leg["roofline"]["kernel"] = dom
+    leg["kernel_rooflines"] = {q: {"frac": round(v["frac"], 5), "achieved": round(v["achieved"], 3),
+                                   "unit": v["unit"], "bound": v["bound"], "ms": round(v["ms"], 4)}
+                               for q, v in kern.items()}
+    leg["level_bounds"] = level_bounds(st, "fp32", _peaks(), peaks_alu)
+    leg["kernel_launches_per_step"] = st["kernel_launches"]
+    if not args.no_plain:
+        popt = ctx.options(mode=cupc.MODE_PLAIN_FP64, canonical=True, max_level=s.max_level)
+        timed_steps(ctx, X, s, popt, 1, stream, flush)
+        pms, _ = timed_steps(ctx, X, s, popt, 2, stream, flush)
+        leg["plain_form"] = {"ms_per_step": pms / 2, "value": units * 2 / (pms * 1e-3), "unit": UNIT}
+        leg["speedup_vs_plain"] = (pms / 2) / (ms / k)
+    if not args.no_learned_leg:
+        from paper_1812_08491_gb300 import learned
+        if "weights" not in learned_info_cache:
+            t0 = time.perf_counter()
+            Xtr, ttr = learned.collect(ctx, [sem.mlp_training_instance(q) for q in range(200)])
+            learned.train(ctx, Xtr, ttr, epochs=6, batch=4096, lr=2e-3)
+            learned_info_cache["weights"] = ctx.mlp_get_weights()
+            learned_info_cache["setup_s"] = round(time.perf_counter() - t0, 1)
+        ctx.mlp_set_weights(learned_info_cache["weights"])
+        lopt = ctx.options(mode=cupc.MODE_FP32_RECHECK, canonical=True, max_level=s.max_level, learned_order=True)
+        timed_steps(ctx, X, s, lopt, 1, stream, flush)
+        lms, lst = timed_steps(ctx, X, s, lopt, k, stream, flush)
+        lser = int(sum(lst["serial_tests"]))
+        leg["learned_form"] = {"ms_per_step": lms / k, "value": units * k / (lms * 1e-3), "unit": UNIT,
+                               "serial_tests_learned_order": lser, "serial_tests_lexicographic": units,
+                               "network_setup_s": learned_info_cache["setup_s"]}
+    if not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        secs, cu = cpu_oracle_run(s, cores)
+        leg["cpu_baseline"] = {"value": cu / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"whole large10000 skeleton once (correlation + levels 0-6), {secs:.2f} s"}
+    return leg
+
+
+def sshare_report(ctx, dev, names=("medium1000", "scalefree2500", "large10000"), levels=(1, 2, 3)):
+    """The global-sharing diagnostic (Sec. 5.5, Fig. 9) per workload and level:
+    one JSON line each with the histogram of rows per conditioning set, what a
+    global search finds (distinct sets, factorisations it would save) and its
+    device time, beside the level's CI-phase time with row-local sharing."""
+    import torch
+    from synth import sem
+    bins = [1, 2, 3, 5, 9, 17, 33, 41, 65, 129]
+    for name in names:
+        s = sem.workload(name)
+        X = torch.from_numpy(s.Xt).to(dev).T
+        r = ctx.skeleton(X, s.alpha, max_level=s.max_level)
+        st = r.stats()
+        for level in levels:
+            if level >= st["levels"]:
+                continue
+            r.sshare(level, bins)                         # warm-up (buffers sized)
+            counts, ss = r.sshare(level, bins)
+            red = ss["redundant"]
+            sets_le40 = sum(c for b, c in zip(bins, counts) if b <= 40) - counts[0]
+            print(json.dumps({"sshare": name, "level": level, "bins": bins, "sets_per_bin": counts,
+                              "pairs_row_S": ss["pairs"], "distinct_S": ss["distinct"], "redundant_S": red,
+                              "redundant_in_at_most_40_rows": round(sets_le40 / red, 4) if red else None,
+                              "max_rows_one_S": ss["max_rows"], "rows": ss["rows"],
+                              "factorisations_saved_by_global_sharing": ss["pairs"] - ss["distinct"],
+                              "global_search_ms": round(ss["search_ms"], 4),
+                              "level_ci_ms_row_local": round(st["phase_ms"][level][1], 4)}))
+        r.free()
+
+
 BATCH_WORKLOADS = {"batch64": 64}
 
 
@@ -514,6 +655,12 @@ def main():
     ap.add_argument("--tune", action="store_true", help="batch workloads: autotune the launch configuration")
     ap.add_argument("--learned", action="store_true",
                     help="learned subset ordering: train the network on 200 seeded p=500 instances first")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large10000 leg (p = 10^4) of the medium1000 line")
+    ap.add_argument("--no-learned-leg", action="store_true",
+                    help="skip the learned-ordering form of the large10000 leg")
+    ap.add_argument("--sshare", action="store_true",
+                    help="print the global-sharing diagnostic (Sec. 5.5) per workload and level, then exit")
     ap.add_argument("--once", action="store_true",
                     help="run one skeleton of the workload and print its per-level stats (the command profiled)")
     args = ap.parse_args()
@@ -554,6 +701,10 @@ def main():
         print(json.dumps({"workload": args.workload, "levels": st["levels"], "total_ms": st["total_ms"],
                           "kernel_launches": st["kernel_launches"], "level_source_hash": level_source_hash(),
                           "ci_block_entries": st["ci_block_entries"], "edges_start": st["edges_start"]}))
+        ctx.close()
+        return 0
+    if args.sshare:
+        sshare_report(ctx, dev)
         ctx.close()
         return 0
     peaks_alu = ctx.device_peaks()
@@ -705,6 +856,12 @@ def main():
             s1, cu1 = cpu_oracle_run(s, 1)
             cpu["serial_1core"] = {"value": cu1 / s1, "unit": UNIT, "seconds": round(s1, 3)}
     orient = orientation_line(ctx, X, s, mode, keep.get("res")) if rank == 0 else None
+    large = None
+    if rank == 0 and args.workload == "medium1000" and args.mode == "fp32" and not args.no_large:
+        with ClockSampler(local) as clk2:
+            large = large_leg(ctx, args, peaks_alu, dev, stream, flush, {})
+        large["clocks"] = clk2.summary()
+    lbounds = level_bounds(roofs[-1][0], args.mode, _peaks(), peaks_alu)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -725,6 +882,7 @@ def main():
                 "kernel_rooflines": {k: {"frac": round(v["frac"], 5), "achieved": round(v["achieved"], 3),
                                          "unit": v["unit"], "bound": v["bound"]} for k, v in kern.items()},
                 "cpu_baseline": cpu, "clocks": clocks, "orientation": orient,
+                "level_bounds": lbounds, "large10000": large,
                 "alu_peaks_measured": {k: round(v, 2) for k, v in peaks_alu.items()},
                 "level_source_hash": level_source_hash()}
         print(json.dumps(line))

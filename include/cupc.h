@@ -403,6 +403,33 @@ cupc_status cupc_skeleton_resume(cupc_ctx* ctx, const void* X, int dtype, int la
                                  const cupc_options* opts, const void* ckpt, int64_t ckpt_size,
                                  cupc_result** out);
 
+/* Global sharing of conditioning sets at one level (Sec. 5.5, Fig. 9): on the
+ * result's A'_G at the start of `level` (1 <= level <= 4; its skeleton plus the
+ * pairs it removed at that level or later), every level-subset S of adj(i) of
+ * each row i that runs tests there (|adj(i)| >= level + 1) is counted once per
+ * row. counts[k] (host, nbins entries) receives the number of distinct sets S
+ * that appear in at least bins[k] and fewer than bins[k + 1] rows (the last bin
+ * has no upper end; bins increasing, bins[0] >= 1). The library shares S within
+ * a row only (as the paper's cuPC-S does); stats (may be NULL) gives what a
+ * global search would find and cost: pairs (row, S) -- one factorisation each
+ * with row-local sharing --, distinct sets -- one each with global sharing --,
+ * sets in two rows or more, the largest row count, the rows, and search_ms,
+ * the device time of the search itself (a hash table over all pairs, then the
+ * histogram). Synchronises the context stream. Errors: CUPC_E_INVALID,
+ * CUPC_E_RANGE (level, p beyond 65535 with level > 2, or more than 2^28
+ * pairs), CUPC_E_CUDA. */
+typedef struct {
+    int64_t pairs;
+    int64_t distinct;
+    int64_t redundant;
+    int64_t max_rows;
+    int64_t rows;
+    float search_ms;
+    int32_t reserved;
+} cupc_sshare_stats;
+cupc_status cupc_result_sshare(const cupc_result* res, int level, const int64_t* bins, int nbins,
+                               int64_t* counts, cupc_sshare_stats* stats);
+
 /* Per-level statistics of the call that produced `res`: the test counts of
  * Algorithm 1 in serial order (the paper's Fig. 2 count convention), tests
  * executed, removals, device times. The paper reports runtimes only (Sec. 5.3);
@@ -483,6 +510,19 @@ cupc_status cupc_mlp_forward(cupc_ctx* ctx, const float* X, int64_t n, float* y)
  * kernels on the device. */
 cupc_status cupc_mlp_train(cupc_ctx* ctx, const float* X, const float* t, int64_t n, int64_t batch, int epochs,
                            double lr, double* epoch_loss);
+
+/* Training examples for the network from a result's SepSets (levels >= 2):
+ * for each removal (x, y, l, S) at level l >= 2, the endpoint whose neighbour
+ * set in A'_G at the start of level l contains S (x first, then y; x < y)
+ * gives one example per candidate k of that set other than the other endpoint,
+ * with the features above computed by the device code the level kernel scores
+ * with, from C (device float p x p, ld = p: the FP32 correlation the kernels
+ * read), and the label 1 if k is in S, else 0. *n receives the number of
+ * examples; with X (device float [cap x 5]) and t (device float [cap]) given,
+ * the first min(cap, *n) are written (both NULL: count only). Synchronises
+ * the context stream. The paper has no counterpart. */
+cupc_status cupc_mlp_examples(const cupc_result* res, const float* C, float* X, float* t, int64_t cap,
+                              int64_t* n);
 
 /* Allocation-free FP64 correlation matrix (the paper has no counterpart).
  *

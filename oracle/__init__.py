@@ -328,3 +328,40 @@ def orient(res: OracleResult):
     if rounds < 0:
         raise ValueError("a removed pair has no SepSet record")
     return mark, int(rounds)
+
+
+def frozen_adjacency(res: OracleResult, level: int) -> np.ndarray:
+    """A'_G at the start of `level` (>= 1): the final skeleton plus the pairs
+    removed at that level or later (Algorithm 1 freezes adj at level start)."""
+    G = (res.sep_level < 0) | (res.sep_level >= level)
+    np.fill_diagonal(G, False)
+    return G
+
+
+def sshare_histogram(adj: np.ndarray, level: int, bins):
+    """Global sharing of conditioning sets at one level (Sec. 5.5, Fig. 9): every
+    l-subset S of adj(i) in a row i that runs tests at this level (|adj(i)| >= l + 1)
+    is counted once per such row. Returns (counts per bin [bins[k], bins[k+1]),
+    the last bin open-ended; stats) with stats = pairs (row, S), distinct S,
+    redundant S (in two rows or more), the largest number of rows of one S.
+    Plain Python over itertools.combinations (lexicographic subsets)."""
+    import itertools
+    from collections import Counter
+    rows = Counter()
+    p = adj.shape[0]
+    pairs = 0
+    for i in range(p):
+        nb = np.nonzero(adj[i])[0].tolist()
+        if len(nb) < level + 1:
+            continue
+        for S in itertools.combinations(nb, level):
+            rows[S] += 1
+            pairs += 1
+    counts = [0] * len(bins)
+    for c in rows.values():
+        ks = [q for q in range(len(bins)) if bins[q] <= c]
+        if ks:                                  # (fewer rows than bins[0]: in no bin)
+            counts[ks[-1]] += 1
+    stats = {"pairs": pairs, "distinct": len(rows), "redundant": sum(1 for c in rows.values() if c >= 2),
+             "max_rows": max(rows.values(), default=0)}
+    return counts, stats

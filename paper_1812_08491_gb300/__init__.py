@@ -50,6 +50,7 @@ _SIGNATURES = {
     "cupc_result_sepset_records": ("status", ["vp", "vp", "i64", "vp"]),
     "cupc_result_stats": ("status", ["vp", "vp"]),
     "cupc_result_checkpoint": ("status", ["vp", "vp", "i64", "vp"]),
+    "cupc_result_sshare": ("status", ["vp", "int", "vp", "int", "vp", "vp"]),
     "cupc_skeleton_resume": ("status", ["vp", "vp", "int", "int", "int", "i64", "i64", "i64", "dbl", "opts_p", "vp",
                                         "i64", "pp"]),
     "cupc_result_orient": ("status", ["vp", "vp", "vp"]),
@@ -69,8 +70,10 @@ _SIGNATURES = {
     "cupc_mlp_grad": ("status", ["vp", "vp", "vp", "i64", "vp", "vp"]),
     "cupc_mlp_forward": ("status", ["vp", "vp", "i64", "vp"]),
     "cupc_mlp_train": ("status", ["vp", "vp", "vp", "i64", "i64", "int", "dbl", "vp"]),
+    "cupc_mlp_examples": ("status", ["vp", "vp", "vp", "vp", "i64", "vp"]),
 }
 MLP_PARAMS = 4609
+MLP_FEATURES = 5
 
 
 class CupcError(RuntimeError):
@@ -104,6 +107,12 @@ class Stats(ctypes.Structure):
 class OrientStats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int64), ("directed", ctypes.c_int64), ("undirected", ctypes.c_int64),
                 ("bidirected", ctypes.c_int64), ("rule_conflicts", ctypes.c_int64), ("ms", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
+
+
+class SShareStats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int64), ("distinct", ctypes.c_int64), ("redundant", ctypes.c_int64),
+                ("max_rows", ctypes.c_int64), ("rows", ctypes.c_int64), ("search_ms", ctypes.c_float),
                 ("reserved", ctypes.c_int32)]
 
 
@@ -278,6 +287,34 @@ class Result:
                     "cupc_result_orient")
         return out, {"rounds": s.rounds, "directed": s.directed, "undirected": s.undirected,
                      "bidirected": s.bidirected, "rule_conflicts": s.rule_conflicts, "ms": s.ms}
+
+    def sshare(self, level: int, bins):
+        """Global-sharing histogram of conditioning sets at `level` (Sec. 5.5):
+        (counts per bin, stats dict)."""
+        b = (ctypes.c_int64 * len(bins))(*[int(x) for x in bins])
+        c = (ctypes.c_int64 * len(bins))()
+        st = SShareStats()
+        self._check(load().cupc_result_sshare(self._h, level, b, len(bins), c, ctypes.byref(st)),
+                    "cupc_result_sshare")
+        return list(c), {"pairs": st.pairs, "distinct": st.distinct, "redundant": st.redundant,
+                         "max_rows": st.max_rows, "rows": st.rows, "search_ms": st.search_ms}
+
+    def mlp_examples(self, C):
+        """Training examples (X [m x 5], t [m]) of the network from this result's
+        SepSets, features from the CUDA float32 correlation C; CUDA tensors."""
+        torch = _torch()
+        L = load()
+        n = ctypes.c_int64()
+        Cc = C.to(torch.float32).contiguous()
+        self._check(L.cupc_mlp_examples(self._h, ctypes.c_void_p(Cc.data_ptr()), None, None, 0, ctypes.byref(n)),
+                    "cupc_mlp_examples")
+        X = torch.empty((n.value, MLP_FEATURES), dtype=torch.float32, device=Cc.device)
+        t = torch.empty(n.value, dtype=torch.float32, device=Cc.device)
+        if n.value:
+            self._check(L.cupc_mlp_examples(self._h, ctypes.c_void_p(Cc.data_ptr()), ctypes.c_void_p(X.data_ptr()),
+                                            ctypes.c_void_p(t.data_ptr()), n.value, ctypes.byref(n)),
+                        "cupc_mlp_examples")
+        return X, t
 
     def checkpoint(self) -> bytes:
         """Level-boundary checkpoint of this result (opaque bytes)."""

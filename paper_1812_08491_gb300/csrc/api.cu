@@ -949,6 +949,50 @@ cupc_status build_host_records(const cupc_result* r)
 
 }  // namespace
 
+// A'_G at the start of `level` >= 1 as neighbour lists (increasing): the
+// result's skeleton plus the pairs its records remove at that level or later.
+cupc_status result_frozen_lists(const cupc_result* r, int level, std::vector<long long>& off, std::vector<int>& cols)
+{
+    const size_t words = (size_t)r->p * r->W;
+    std::vector<unsigned> hd;
+    if (!r->on_host) {
+        hd.resize(words);
+        cudaError_t e = cudaMemcpyAsync(hd.data(), r->bits, words * 4, cudaMemcpyDeviceToHost, r->ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(r->ctx->stream);
+        if (e != cudaSuccess) return fail(r->ctx, CUPC_E_CUDA, "skeleton download", e);
+    }
+    const std::vector<unsigned>& h = r->on_host ? r->hbits : hd;
+    cupc_status s = build_host_records(r);
+    if (s != CUPC_OK) return fail(r->ctx, s, "record download");
+    const int64_t p = r->p;
+    std::vector<std::vector<int>> nb((size_t)p);
+    for (int64_t i = 0; i < p; ++i)
+        for (int w = 0; w < r->W; ++w) {
+            unsigned m = h[(size_t)i * r->W + w];
+            while (m) {
+                const int64_t j = (int64_t)w * 32 + __builtin_ctz(m);
+                m &= m - 1;
+                if (j < p && j != i) nb[(size_t)i].push_back((int)j);
+            }
+        }
+    for (size_t k = 0; k < r->hrec.size();) {
+        const int i = r->hrec[k], j = r->hrec[k + 1], l = r->hrec[k + 2];
+        if (l >= level) {
+            nb[(size_t)i].push_back(j);
+            nb[(size_t)j].push_back(i);
+        }
+        k += 3 + (size_t)l;
+    }
+    off.assign((size_t)p + 1, 0);
+    cols.clear();
+    for (int64_t i = 0; i < p; ++i) {
+        std::sort(nb[(size_t)i].begin(), nb[(size_t)i].end());
+        off[(size_t)i + 1] = off[(size_t)i] + (long long)nb[(size_t)i].size();
+        cols.insert(cols.end(), nb[(size_t)i].begin(), nb[(size_t)i].end());
+    }
+    return CUPC_OK;
+}
+
 cupc_status ctx_ensure(cupc_ctx* ctx, Buf* b, size_t bytes) { return ensure(ctx, *b, bytes); }
 void ctx_free(cupc_ctx* ctx, Buf* b) { free_buf(ctx, *b); }
 double ctx_fisher_tau(double alpha, int64_t n, int l) { return fisher_tau(alpha, n, l); }

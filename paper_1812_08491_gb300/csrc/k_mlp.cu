@@ -8,6 +8,8 @@
 // is deterministic. A second kernel adds the block partials in block order and
 // applies Adam (Kingma and Ba, 2015) to the FP32 master weights, refreshing
 // their bf16 copy used for scoring.
+#include <algorithm>
+
 #include "kernels.cuh"
 #include "mlp.cuh"
 
@@ -217,4 +219,30 @@ cudaError_t launch_mlp_forward(const void* Pb, const float* X, long long N, floa
     return cudaGetLastError();
 }
 
+
+// Training examples: feature rows of (i, j, k, level) tuples from the FP32
+// correlation matrix C (p x p), with the same feature code the level kernel
+// scores candidates with; q[4t + 3] holds level | label << 8.
+__global__ void k_mlp_examples(const float* __restrict__ C, long long p, const int* __restrict__ q, long long n,
+                               float* __restrict__ X, float* __restrict__ t)
+{
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int i = q[4 * e], j = q[4 * e + 1], k = q[4 * e + 2], lv = q[4 * e + 3];
+        float x[MLP_IN];
+        mlp_features(C[(size_t)i * p + j], C[(size_t)i * p + k], C[(size_t)j * p + k], lv & 0xff, x);
+#pragma unroll
+        for (int c = 0; c < MLP_IN; ++c) X[e * MLP_IN + c] = x[c];
+        t[e] = (float)(lv >> 8);
+    }
+}
+
+cudaError_t launch_mlp_examples(const float* C, long long p, const int* q, long long n, float* X, float* t,
+                                cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int block = 256;
+    const unsigned grid = (unsigned)std::min<long long>((n + block - 1) / block, 4096);
+    k_mlp_examples<<<grid, block, 0, st>>>(C, p, q, n, X, t);
+    return cudaGetLastError();
+}
 }  // namespace cupc

@@ -240,6 +240,12 @@ cudaError_t launch_pcor(int fp32, const void* C, int p, const int* q, long long 
 cudaError_t launch_pcor_recheck(const LevelParams& P, const int* q, long long nq, double* rho, cudaStream_t st);
 cudaError_t launch_bits_to_u8(const unsigned* bits, int p, int W, unsigned char* out, cudaStream_t st);
 
+// global sharing of conditioning sets at one level (k_sshare.cu)
+cudaError_t launch_sshare(const long long* off, const int* cols, const long long* pre, int nrows, int l, int bits,
+                          const Binom& B, unsigned long long total, unsigned long long* keys, unsigned* cnt,
+                          unsigned long long slots, const long long* bins, int nbins, unsigned long long* out,
+                          int* err, int num_sms, cudaStream_t st);
+
 // candidate-scoring network (k_mlp.cu)
 cudaError_t launch_mlp_grad(const float* P, const float* X, const float* T, long long s0, long long s1, float* gpart,
                             float* lpart, int blocks, cudaStream_t st);
@@ -247,6 +253,8 @@ cudaError_t launch_mlp_apply(float* P, float* M, float* V, const float* gpart, i
                              float lr, void* Pb, cudaStream_t st);
 cudaError_t launch_mlp_to_bf16(const float* P, void* Pb, cudaStream_t st);
 cudaError_t launch_mlp_forward(const void* Pb, const float* X, long long N, float* y, cudaStream_t st);
+cudaError_t launch_mlp_examples(const float* C, long long p, const int* q, long long n, float* X, float* t,
+                                cudaStream_t st);
 
 
 }  // namespace cupc

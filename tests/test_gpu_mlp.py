@@ -94,6 +94,43 @@ def test_training_reduces_loss(ctx):
     assert losses[-1] < 0.5 * losses[0]
 
 
+def _host_examples(C32, sep_levels, sepsets):
+    """The examples' definition written out on the host (test reference): for a
+    removal (x, y) at level l >= 2 with set S, the endpoint whose neighbours at
+    the start of level l contain S (x first) gives one row per other neighbour k:
+    (|C_ik|, |C_jk|, |C_ij|, l/8, |rho_ij.k|), label k in S."""
+    rows, labels = [], []
+    for (x, y), (level, S) in sorted(sepsets.items()):
+        if level < 2:
+            continue
+        G = (sep_levels < 0) | (sep_levels >= level)
+        np.fill_diagonal(G, False)
+        for a, b in ((x, y), (y, x)):
+            nb = np.nonzero(G[a])[0]
+            if not set(S) <= set(nb.tolist()):
+                continue
+            for k in nb[nb != b]:
+                cij, cik, cjk = (np.float64(C32[a, b]), np.float64(C32[a, k]), np.float64(C32[b, k]))
+                den = (1 - cik * cik) * (1 - cjk * cjk)
+                rho = abs((cij - cik * cjk) / np.sqrt(den)) if den > 1e-12 else 1.0
+                rows.append([abs(cik), abs(cjk), abs(cij), level / 8.0, rho])
+                labels.append(1.0 if k in S else 0.0)
+            break
+    return np.array(rows).reshape(-1, 5), np.array(labels)
+
+
+def test_examples_match_host_definition(ctx):
+    s = sem.generate(300, 400, 31500, "scale_free", m=2, w_min=0.2)
+    X = torch.from_numpy(s.Xt).cuda().T
+    res = ctx.skeleton(X, s.alpha, mode=cupc.MODE_PLAIN_FP64)
+    C32 = ctx.correlation(X, cupc.F32)
+    Xe, te = res.mlp_examples(C32)
+    Xr, tr = _host_examples(C32.cpu().numpy(), res.sep_levels(), res.sepsets())
+    assert Xe.shape[0] == Xr.shape[0] > 100
+    assert np.array_equal(te.cpu().numpy(), tr.astype(np.float32))
+    assert np.max(np.abs(Xe.cpu().numpy() - Xr)) <= 1e-5
+
+
 @pytest.fixture(scope="module")
 def trained(ctx):
     probs = [sem.generate(200, 400, 31000 + k, "scale_free", m=2, w_min=0.2) for k in range(12)]

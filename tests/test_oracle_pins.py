@@ -410,3 +410,26 @@ def test_paper_density_workload_is_ill_posed_in_fp64():
     np.fill_diagonal(E, 0)
     r2 = oracle.pc_stable(C + E, s.n, s.alpha, nthreads=8)
     assert int((r2.adj != ref.adj).sum()) > 0
+
+
+# --------------------------------------------------------------------------
+# Sec. 5.5 / Fig. 9: global sharing of conditioning sets
+# --------------------------------------------------------------------------
+
+def test_sshare_histogram_hand_built_graph():
+    """Rows 0: {1, 2, 3}, 1: {0, 2, 3}, 2: {0, 1}, 3: {0, 1}, 4: {5}, 5: {4}.
+    At level 2 only rows 0 and 1 run tests (degree >= 3): row 0 uses {1,2}, {1,3},
+    {2,3}; row 1 uses {0,2}, {0,3}, {2,3}. So {2,3} appears in two rows and the
+    other four sets in one; at level 1 rows 0-3 run tests (degree >= 2) with S = {v}
+    for every neighbour v: {0} and {1} in three rows, {2} and {3} in two."""
+    adj = np.zeros((6, 6), bool)
+    for a, b in [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (4, 5)]:
+        adj[a, b] = adj[b, a] = True
+    counts, st = oracle.sshare_histogram(adj, 2, [1, 2, 3])
+    assert counts == [4, 1, 0]
+    assert st == {"pairs": 6, "distinct": 5, "redundant": 1, "max_rows": 2}
+    counts, st = oracle.sshare_histogram(adj, 1, [1, 2, 3, 4])
+    assert counts == [0, 2, 2, 0]
+    assert st == {"pairs": 10, "distinct": 4, "redundant": 4, "max_rows": 3}
+    counts, st = oracle.sshare_histogram(adj, 3, [1])
+    assert counts == [0] and st["pairs"] == 0

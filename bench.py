@@ -446,6 +446,66 @@ def sshare_report(ctx, dev, names=("medium1000", "scalefree2500", "large10000"),
         r.free()
 
 
+SWEEP_POINTS = ([(p, 10000, 0.1) for p in (1000, 2000, 3000, 4000)] +
+                [(1000, m, 0.1) for m in (2000, 4000, 6000, 8000)] +
+                [(1000, 10000, d) for d in (0.2, 0.3, 0.4, 0.5)])
+# points whose oracle run (levels 0-2) finishes in well under a minute on 16 cores
+SWEEP_PARITY = {(1000, 10000, 0.1), (1000, 2000, 0.1), (1000, 4000, 0.1), (1000, 6000, 0.1), (1000, 8000, 0.1)}
+
+
+def sweep_report(ctx, dev, graphs, max_level=2, parity=True):
+    """The scalability sweep of Sec. 5.6 on its axes (p 1000-4000 at m = 10^4,
+    d = 0.1; m 2000-10^4 at p = 1000, d = 0.1; d 0.1-0.5 at p = 1000, m = 10^4),
+    `graphs` graphs per point, with the signed-weight, variance-normalised form of
+    the paper's generator (synth.sem.paper_density_signed) and levels 0-2 (dense
+    graphs make deeper levels' subset counts explode). One JSON line per point:
+    device time and host wall time of one skeleton from device-resident data
+    (the second call on that shape), serial tests, edges; on graph 0 of the
+    points in SWEEP_PARITY, the oracle's run of the same levels and whether the
+    skeleton, removal levels, SepSets and serial counts are identical."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1812_08491_gb300 as cupc
+    from synth import sem
+    for q, (p, m, d) in enumerate(SWEEP_POINTS):
+        dev_ms, wall_ms, tests, edges, parity = [], [], [], [], None
+        for g in range(graphs):
+            s = sem.paper_density_signed(p, m, d, 6000000 + 1000 * q + g, max_level=max_level)
+            X = torch.from_numpy(s.Xt).to(dev).T
+            opts = ctx.options(mode=cupc.MODE_FP32_RECHECK, canonical=True, max_level=max_level)
+            ctx.skeleton(X, s.alpha, opts).free()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = ctx.skeleton(X, s.alpha, opts)
+            wall_ms.append(1e3 * (time.perf_counter() - t0))
+            st = r.stats()
+            dev_ms.append(st["total_ms"])
+            tests.append(int(sum(st["serial_tests"])))
+            edges.append(int(st["edges_final"]))
+            if parity and g == 0 and (p, m, d) in SWEEP_PARITY:
+                t1 = time.perf_counter()
+                C = oracle.correlation(s.X, nthreads=os.cpu_count() or 1)
+                ref = oracle.pc_stable(C, s.n, s.alpha, max_level=max_level, nthreads=os.cpu_count() or 1)
+                parity = {"identical": bool(np.array_equal(r.adjacency(), ref.adj)
+                                            and np.array_equal(r.sep_levels(), ref.sep_level)
+                                            and r.sepsets() == ref.sepsets
+                                            and st["serial_tests"][:ref.levels_run] == list(ref.tests)),
+                          "oracle_s": round(time.perf_counter() - t1, 2)}
+            r.free()
+            del X
+        print(json.dumps({"sweep_point": {"p": p, "m": m, "d": d}, "graphs": graphs, "max_level": max_level,
+                          "device_ms_mean": round(float(np.mean(dev_ms)), 3),
+                          "device_ms_min_max": [round(min(dev_ms), 3), round(max(dev_ms), 3)],
+                          "wall_ms_mean": round(float(np.mean(wall_ms)), 3),
+                          "serial_tests_mean": int(np.mean(tests)), "edges_mean": int(np.mean(edges)),
+                          "serial_tests_per_s": float(np.sum(tests) / (np.sum(dev_ms) * 1e-3)),
+                          "parity_graph0": parity if parity is not None else "oracle not run at this size",
+                          "generator": "paper_density_signed (Sec. 5.6 structure, signed weights, unit variance)"}),
+              flush=True)
+
+
 BATCH_WORKLOADS = {"batch64": 64}
 
 
@@ -661,6 +721,10 @@ def main():
                     help="skip the learned-ordering form of the large10000 leg")
     ap.add_argument("--sshare", action="store_true",
                     help="print the global-sharing diagnostic (Sec. 5.5) per workload and level, then exit")
+    ap.add_argument("--sweep", action="store_true",
+                    help="run the scalability sweep of Sec. 5.6 (levels 0-2) and print one line per point, then exit")
+    ap.add_argument("--sweep-graphs", type=int, default=3, help="graphs per sweep point (the paper uses 10)")
+    ap.add_argument("--sweep-no-parity", action="store_true", help="sweep without the oracle runs")
     ap.add_argument("--once", action="store_true",
                     help="run one skeleton of the workload and print its per-level stats (the command profiled)")
     args = ap.parse_args()
@@ -705,6 +769,10 @@ def main():
         return 0
     if args.sshare:
         sshare_report(ctx, dev)
+        ctx.close()
+        return 0
+    if args.sweep:
+        sweep_report(ctx, dev, args.sweep_graphs, parity=not args.sweep_no_parity)
         ctx.close()
         return 0
     peaks_alu = ctx.device_peaks()

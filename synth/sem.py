@@ -190,3 +190,35 @@ def paper_density(p: int, n: int, d: float, seed: int, alpha: float = 0.01) -> S
     dst, src = np.nonzero(A)
     return SEM(Xt=Xt, src=src.astype(np.int64), dst=dst.astype(np.int64), weight=A[dst, src], p=p, n=n, seed=seed,
                family="paper_density", alpha=alpha, meta={"density": d, "w_min": 0.1, "dtype": "float64"})
+
+
+def paper_density_signed(p: int, n: int, d: float, seed: int, alpha: float = 0.01, max_level: int = 2) -> SEM:
+    """The scalability workload's structure (Sec. 5.6: a lower-triangular matrix
+    A with Bernoulli(d) support, V_j -> V_i for A[i, j] != 0, generated from i = 0
+    to p - 1) with signed weights +-U[0.1, 1], and each variable rescaled to unit
+    sample variance as soon as it is generated, so that later variables do not
+    grow geometrically with the number of parents (at d = 0.1 and p = 1000 a
+    variable has about 50 parents). The graph, the order and the sample draws
+    follow the paper's recipe; only the signs and the rescaling differ.
+    max_level caps the level loop (dense graphs make every level's subset count
+    grow as C(degree, l))."""
+    rng = np.random.default_rng(seed)
+    sup = rng.random((p, p)) < d
+    mag = rng.uniform(0.1, 1.0, size=(p, p))
+    sign = np.where(rng.random((p, p)) < 0.5, -1.0, 1.0)
+    A = np.tril(sup, -1) * mag * sign
+    N = rng.standard_normal((p, n))
+    Xt = np.empty((p, n))
+    # in blocks of rows: the parents in earlier blocks by one matrix product,
+    # then row by row within the block
+    blk = 256
+    for b0 in range(0, p, blk):
+        b1 = min(p, b0 + blk)
+        acc = N[b0:b1] + (A[b0:b1, :b0] @ Xt[:b0] if b0 else 0.0)
+        for i in range(b0, b1):
+            v = acc[i - b0] + A[i, b0:i] @ Xt[b0:i]
+            Xt[i] = v / v.std()
+    dst, src = np.nonzero(A)
+    return SEM(Xt=Xt, src=src.astype(np.int64), dst=dst.astype(np.int64), weight=A[dst, src], p=p, n=n, seed=seed,
+               family="paper_density_signed", alpha=alpha, max_level=max_level,
+               meta={"density": d, "w_min": 0.1, "dtype": "float64"})

@@ -327,3 +327,17 @@ def test_edge_list_matches_adjacency(ctx):
     probs = [sem.generate(p, 600, 40 + p, "random", degree=3.0) for p in (33, 70)]
     for r in ctx.skeleton_batch([q.X for q in probs], [q.alpha for q in probs])[0]:
         assert np.array_equal(r.edges(), np.argwhere(np.triu(r.adjacency(), 1)).astype(np.int32))
+
+
+@pytest.mark.parametrize("d", [0.1, 0.3])
+def test_sweep_generator_parity(ctx, d):
+    """The scalability workload's generator (dense lower-triangular DAG, signed
+    weights, unit variance) at a small size, levels 0-2, both forms, against the
+    oracle."""
+    s = sem.paper_density_signed(250, 3000, d, 6100 + int(100 * d), max_level=2)
+    C = oracle.correlation(s.X, nthreads=8)
+    ref = oracle.pc_stable(C, s.n, s.alpha, max_level=2, nthreads=8)
+    for mode in ("fp32", "plain"):
+        res = ctx.skeleton(s.X, s.alpha, mode=MODES[mode], max_level=2)
+        _assert_same(res, ref)
+        assert res.stats()["serial_tests"][:ref.levels_run] == list(ref.tests)

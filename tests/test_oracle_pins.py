@@ -433,3 +433,16 @@ def test_sshare_histogram_hand_built_graph():
     assert st == {"pairs": 10, "distinct": 4, "redundant": 4, "max_rows": 3}
     counts, st = oracle.sshare_histogram(adj, 3, [1])
     assert counts == [0] and st["pairs"] == 0
+
+
+def test_paper_density_signed_generator():
+    """Sec. 5.6's structure: edges only from lower to higher index (V_j -> V_i,
+    j < i), density d, weights of magnitude in [0.1, 1] with both signs, and every
+    variable at unit sample variance."""
+    from synth import sem
+    s = sem.paper_density_signed(120, 500, 0.2, 7)
+    assert np.all(s.src < s.dst)
+    assert abs(len(s.src) / (120 * 119 / 2) - 0.2) < 0.03
+    assert np.all((np.abs(s.weight) >= 0.1) & (np.abs(s.weight) <= 1.0))
+    assert (s.weight > 0).any() and (s.weight < 0).any()
+    assert np.allclose(s.Xt.std(axis=1), 1.0, atol=1e-12)

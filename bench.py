@@ -803,6 +803,8 @@ def main():
     form_opts = {m: ctx.options(mode=m, canonical=True, max_level=s.max_level,
                                 learned_order=bool(args.learned) and m == cupc.MODE_FP32_RECHECK)
                  for m in (cupc.MODE_FP32_RECHECK, cupc.MODE_PLAIN_FP64)}
+    # FP32 form in lexicographic order (compared with the learned order)
+    form_opts["lex32"] = ctx.options(mode=cupc.MODE_FP32_RECHECK, canonical=True, max_level=s.max_level)
 
     def step(m, done=None):
         """One skeleton call; `done` (a CUDA event) is recorded as soon as the call
@@ -818,7 +820,9 @@ def main():
         st_l = step(mode)
         learned_info["serial_tests_learned"] = int(sum(st_l["serial_tests"]))
         learned_info["serial_tests_lexicographic"] = units
-        learned_info["serial_tests_saved_levels_ge2"] = int(sum(ref_serial[2:]) - sum(st_l["serial_tests"][2:]))
+        learned_info["serial_tests_saved_levels_ge1"] = int(sum(ref_serial[1:]) - sum(st_l["serial_tests"][1:]))
+        learned_info["serial_tests_per_level_learned"] = [int(v) for v in st_l["serial_tests"]]
+        learned_info["serial_tests_per_level_lexicographic"] = [int(v) for v in ref_serial]
 
     for _ in range(args.warmup):
         step(mode)
@@ -866,6 +870,21 @@ def main():
             torch.cuda.synchronize()
             pm += a.elapsed_time(b)
         plain = {"value": units * k2 / (pm * 1e-3), "unit": UNIT, "ms_per_step": pm / k2, "steps": k2}
+    if learned_info is not None and args.mode == "fp32":
+        # the same FP32 form in lexicographic order, timed the same way
+        step("lex32")
+        lm_ = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step("lex32", b)
+            torch.cuda.synchronize()
+            lm_ += a.elapsed_time(b)
+        learned_info["fp32_lexicographic_ms_per_step"] = lm_ / args.steps
+        learned_info["fp32_learned_ms_per_step"] = ms_per_step
 
     # end to end through the public call with a pinned host input
     e2e = None

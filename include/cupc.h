@@ -84,7 +84,7 @@ typedef struct {
                                 a side); 0: any separating set found first (default 1) */
     int learned_order;       /* 1: enumerate subsets in the order given by the
                                 candidate-scoring network loaded with
-                                cupc_mlp_set_weights() (levels >= 2); default 0 */
+                                cupc_mlp_set_weights() (levels >= 1); default 0 */
     int max_level;           /* last level to run; -1 = until no edge has enough
                                 neighbours (Algorithm 1 termination); default -1 */
     double recheck_margin;   /* FP32 mode: absolute band on |rho| around tanh(tau)
@@ -476,12 +476,16 @@ cupc_status cupc_pcor_data(cupc_ctx* ctx, const void* X, int dtype, int layout, 
 /* ---------------------------------------------------------------------------
  * Candidate-scoring network for learned subset ordering (the paper has no
  * learned component; these calls serve the ordering option). The network maps
- * five features of a candidate k for edge side (i, j) at level l,
- * (|C_ik|, |C_jk|, |C_ij|, l/8, |rho_ij.k|), through 5 -> 64 -> 64 -> 1 with
- * ReLU to a score; with opts->learned_order, levels l >= 2 enumerate subsets of
- * each side's candidates sorted by descending score (lexicographic over the
- * sorted positions, so every subset is still reachable and the skeleton is
- * unchanged). Parameters are CUPC_MLP_PARAMS floats packed W1 (64x5), b1 (64),
+ * five features of a candidate k of row i at level l (k a neighbour of i in
+ * A'_G, means over the row's other neighbours j),
+ * (|C_ik|, mean |C_jk|, mean |C_ij|, l/8, mean |rho_ij.k|), with the two terms
+ * that need C_jk set to 0 at level 1, through 5 -> 64 -> 64 -> 1 with ReLU to a
+ * score; with opts->learned_order, every level l >= 1 enumerates the subsets
+ * of each row with at most 256 neighbours over its neighbours sorted by
+ * descending score (ties: increasing index), lexicographic over the sorted
+ * positions: every subset is still reachable, so the skeleton is unchanged,
+ * and the SepSet stored is the first separating set in that order. A larger
+ * row keeps the increasing order. Parameters are CUPC_MLP_PARAMS floats packed W1 (64x5), b1 (64),
  * W2 (64x64), b2 (64), w3 (64), b3 (1), row-major. Training keeps FP32
  * master weights on the device; scoring uses their bf16 rounding.
  * ------------------------------------------------------------------------- */
@@ -511,13 +515,14 @@ cupc_status cupc_mlp_forward(cupc_ctx* ctx, const float* X, int64_t n, float* y)
 cupc_status cupc_mlp_train(cupc_ctx* ctx, const float* X, const float* t, int64_t n, int64_t batch, int epochs,
                            double lr, double* epoch_loss);
 
-/* Training examples for the network from a result's SepSets (levels >= 2):
- * for each removal (x, y, l, S) at level l >= 2, the endpoint whose neighbour
+/* Training examples for the network from a result's SepSets (levels >= 1):
+ * for each removal (x, y, l, S) at level l >= 1, the endpoint a whose neighbour
  * set in A'_G at the start of level l contains S (x first, then y; x < y)
- * gives one example per candidate k of that set other than the other endpoint,
- * with the features above computed by the device code the level kernel scores
- * with, from C (device float p x p, ld = p: the FP32 correlation the kernels
- * read), and the label 1 if k is in S, else 0. *n receives the number of
+ * gives one example per neighbour k of a other than the other endpoint: the
+ * features of candidate k of row a at level l above, computed by the device
+ * code the level kernel scores with, from C (device float p x p, ld = p: the
+ * FP32 correlation the kernels read), and the label 1 if k is in S, else 0.
+ * *n receives the number of
  * examples; with X (device float [cap x 5]) and t (device float [cap]) given,
  * the first min(cap, *n) are written (both NULL: count only). Synchronises
  * the context stream. The paper has no counterpart. */

@@ -515,7 +515,6 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     const size_t base_rec = ck ? (size_t)ck->rec_ints : 0;   // records of the checkpoint's levels
     rec_len_cap += base_rec;
     if (o.test_rec_cap > 0) rec_len_cap = base_rec + (size_t)o.test_rec_cap;
-    unsigned long long perm_cap = std::max<unsigned long long>(ctx->cap_perm, 1ull << 22);
     LevelMeta* lm = nullptr;
     LevelParams LP{};
     int levels_run = 1;
@@ -642,13 +641,14 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             LP.learned = o.learned_order ? 1 : 0;
             LP.barrier_ns = 0;
             if (o.learned_order) {
-                // per-slot candidate lists of levels >= 2 (a level whose lists would not
-                // fit keeps the increasing order)
-                if ((s = ensure(ctx, *ctx_buf(ctx, "perm"), (size_t)perm_cap * 4)) != CUPC_OK) return s;
-                if ((s = ensure(ctx, *ctx_buf(ctx, "poff"), (size_t)(p + 1) * 8)) != CUPC_OK) return s;
+                // each A'_G row's order and its inverse, one entry per slot; the
+                // order positions of an incremental A'_G's survivors
+                if ((s = ensure(ctx, *ctx_buf(ctx, "perm"), (size_t)nnz_cap * 4)) != CUPC_OK) return s;
+                if ((s = ensure(ctx, *ctx_buf(ctx, "iperm"), (size_t)nnz_cap * 4)) != CUPC_OK) return s;
+                if ((s = ensure(ctx, *ctx_buf(ctx, "vrank"), (size_t)nnz_cap * 4)) != CUPC_OK) return s;
                 LP.perm = (int*)ctx_buf(ctx, "perm")->p;
-                LP.poff = (long long*)ctx_buf(ctx, "poff")->p;
-                LP.perm_cap = perm_cap;
+                LP.iperm = (int*)ctx_buf(ctx, "iperm")->p;
+                LP.vrank = (int*)ctx_buf(ctx, "vrank")->p;
                 LP.mlp_w = ctx_buf(ctx, "mlp_Pb")->p;
             }
         }
@@ -830,14 +830,10 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         }
         R->rec_ints = (int64_t)H.rec_ints;
         // the needs the next call on this context is sized for
-        unsigned long long nnz_need = 0, blk = 0;
-        for (int q = 1; q < LV; ++q) {
-            nnz_need = std::max(nnz_need, 2 * H.edges[q]);
-            blk = std::max(blk, H.block_entries[q]);
-        }
+        unsigned long long nnz_need = 0;
+        for (int q = 1; q < LV; ++q) nnz_need = std::max(nnz_need, 2 * H.edges[q]);
         ctx->cap_nnz = std::max<unsigned long long>(ctx->cap_nnz, nnz_need + nnz_need / 4);
         ctx->cap_rec = std::max<size_t>(ctx->cap_rec, (size_t)(H.rec_ints + H.rec_ints / 4));
-        ctx->cap_perm = std::max<unsigned long long>(ctx->cap_perm, std::min<unsigned long long>(blk, 1ull << 26));
     } else if (range_stop) {
         return fail(ctx, CUPC_E_RANGE, "a level above CUPC_MAX_LEVEL would be needed");
     }

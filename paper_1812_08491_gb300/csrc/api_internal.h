@@ -55,7 +55,7 @@ struct cupc_ctx {
     int mlp_step = 0;                   // Adam steps taken
     // largest level-buffer needs seen by this context's calls (CSR slots, SepSet
     // ints, candidate-list entries): the next call is sized for them up front
-    unsigned long long cap_nnz = 0, cap_perm = 0;
+    unsigned long long cap_nnz = 0;
     size_t cap_rec = 0;
     void* batch = nullptr;              // batch plan (api_batch.cu)
     void (*batch_free)(cupc_ctx*) = nullptr;

@@ -1,6 +1,7 @@
 // api_mlp.cu -- C ABI of the candidate-scoring network: weights, gradient,
 // scoring and training on the device (kernels in k_mlp.cu).
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <vector>
 
@@ -135,29 +136,40 @@ cupc_status cupc_mlp_examples(const cupc_result* res, const float* C, float* X, 
 {
     if (!res || !C || !n || cap < 0 || ((X == nullptr) != (t == nullptr))) return CUPC_E_INVALID;
     cupc_ctx* ctx = res->ctx;
-    // levels >= 2 of the result's records, each with its frozen A'_G
     std::vector<long long> off;
     std::vector<int> cols;
-    cupc_status s = result_frozen_lists(res, 2, off, cols);   // (also builds the host records)
+    cupc_status s = result_frozen_lists(res, 1, off, cols);   // (also builds the host records)
     if (s != CUPC_OK) return s;
     const std::vector<int32_t>& rec = res->hrec;
-    int lmax = 1;
+    int lmax = 0;
     for (size_t k = 0; k < rec.size(); k += 3 + (size_t)rec[k + 2]) lmax = std::max(lmax, (int)rec[k + 2]);
+    // every level's frozen neighbour lists, one after another in nbs
     std::vector<std::vector<long long>> offs((size_t)lmax + 1);
-    std::vector<std::vector<int>> colss((size_t)lmax + 1);
-    for (int l = 2; l <= lmax; ++l)
-        if ((s = result_frozen_lists(res, l, offs[(size_t)l], colss[(size_t)l])) != CUPC_OK) return s;
-    // (side, other endpoint, candidate, level | label << 8): the side whose frozen
-    // neighbourhood holds S (the smaller endpoint first), one example per candidate
+    std::vector<long long> base((size_t)lmax + 1, 0);
+    std::vector<int> nbs;
+    for (int l = 1; l <= lmax; ++l) {
+        std::vector<int> c;
+        if (l == 1) {
+            offs[1].swap(off);
+            c.swap(cols);
+        } else if ((s = result_frozen_lists(res, l, offs[(size_t)l], c)) != CUPC_OK) {
+            return s;
+        }
+        base[(size_t)l] = (long long)nbs.size();
+        nbs.insert(nbs.end(), c.begin(), c.end());
+    }
+    if (nbs.size() > (size_t)INT32_MAX) return ctx_fail(ctx, CUPC_E_RANGE, "training examples: neighbour lists too long");
+    // (row a, candidate position, list start, list length, level, label): the side
+    // whose frozen neighbourhood holds S (the smaller endpoint first), one
+    // example per candidate other than the other endpoint
     std::vector<int32_t> q;
     for (size_t k = 0; k < rec.size(); k += 3 + (size_t)rec[k + 2]) {
         const int x = rec[k], y = rec[k + 1], l = rec[k + 2];
-        if (l < 2) continue;
+        if (l < 1) continue;
         const std::vector<long long>& o = offs[(size_t)l];
-        const std::vector<int>& c = colss[(size_t)l];
         for (int side = 0; side < 2; ++side) {
             const int a = side ? y : x, b = side ? x : y;
-            const int* nb = c.data() + o[(size_t)a];
+            const int* nb = nbs.data() + base[(size_t)l] + o[(size_t)a];
             const int d = (int)(o[(size_t)a + 1] - o[(size_t)a]);
             bool all = true;
             for (int m = 0; m < l && all; ++m) all = std::binary_search(nb, nb + d, rec[k + 3 + m]);
@@ -167,22 +179,27 @@ cupc_status cupc_mlp_examples(const cupc_result* res, const float* C, float* X, 
                 bool in = false;
                 for (int m = 0; m < l; ++m) in = in || rec[k + 3 + m] == nb[u];
                 q.push_back(a);
-                q.push_back(b);
-                q.push_back(nb[u]);
-                q.push_back(l | ((in ? 1 : 0) << 8));
+                q.push_back(u);
+                q.push_back((int32_t)(base[(size_t)l] + o[(size_t)a]));
+                q.push_back(d);
+                q.push_back(l);
+                q.push_back(in ? 1 : 0);
             }
             break;
         }
     }
-    const int64_t count = (int64_t)(q.size() / 4);
+    const int64_t count = (int64_t)(q.size() / 6);
     *n = count;
     if (!X || count == 0 || cap == 0) return CUPC_OK;
     const int64_t m = std::min<int64_t>(cap, count);
     Buf* bq = ctx_buf(ctx, "mlp_ex_q");
-    if ((s = ctx_ensure(ctx, bq, (size_t)m * 16)) != CUPC_OK) return s;
+    Buf* bn = ctx_buf(ctx, "mlp_ex_nb");
+    if ((s = ctx_ensure(ctx, bq, (size_t)m * 24)) != CUPC_OK) return s;
+    if ((s = ctx_ensure(ctx, bn, nbs.size() * 4)) != CUPC_OK) return s;
     cudaStream_t st = ctx_stream(ctx);
-    cudaError_t e = cudaMemcpyAsync(bq->p, q.data(), (size_t)m * 16, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_mlp_examples(C, res->p, (const int*)bq->p, m, X, t, st);
+    cudaError_t e = cudaMemcpyAsync(bq->p, q.data(), (size_t)m * 24, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bn->p, nbs.data(), nbs.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_mlp_examples(C, res->p, (const int*)bn->p, (const int*)bq->p, m, X, t, st);
     ctx_count_launch(ctx);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return ctx_fail(ctx, CUPC_E_CUDA, "training examples", e);

@@ -176,11 +176,75 @@ __device__ void phase_prefix(const LevelParams& P, int skip)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Learned ordering (FP32 mode, levels >= 1). Each row's candidates are scored
+// once per level by the network (features of mlp.cuh: the candidate's
+// correlation with the row variable and means over the row's other
+// neighbours) and enumerated in descending score (ties: increasing position),
+// so the S-shared tests of a row keep sharing each subset across j. The order
+// is a permutation of the row: every subset is still reached, so the skeleton
+// cannot change; the ranks the tests record (and the SepSet the serial order
+// stores) are those of the permuted order. A row with more than MCAP
+// neighbours keeps its increasing order. A level whose A'_G is reused keeps
+// the previous level's order.
+// ---------------------------------------------------------------------------
+constexpr int MCAP = 256;
+
+// Orders the d <= MCAP candidates nb[0..d) of row i at level l (one warp):
+// rk[c] = position of candidate c in descending score order. sc and rk are
+// the warp's scratch (shared memory, MCAP entries each); the network's bf16
+// weights are read from global memory.
+__device__ void warp_row_order(const LevelParams& P, int i, const int* nb, int d, int l, float* sc, int* rk)
+{
+    const int lane = threadIdx.x & 31;
+    const CView<float> CV = cview<float>(P, i);
+    auto C = [&](int a, int b) { return __ldg(CV.row(a) + b); };
+    const __nv_bfloat16* W = (const __nv_bfloat16*)P.mlp_w;
+    float sum = 0.f;
+    for (int c = lane; c < d; c += 32) sum += fabsf(C(i, nb[c]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    for (int c = lane; c < d; c += 32) {
+        float x[MLP_IN];
+        mlp_row_features(C, i, nb, d, c, l, sum, x);
+        const float y = mlp_score(W, x);
+        sc[c] = (y == y) ? y : -INFINITY;
+    }
+    __syncwarp();
+    for (int c = lane; c < d; c += 32) {
+        const float y = sc[c];
+        int r = 0;
+        for (int c2 = 0; c2 < d; ++c2) {
+            const float y2 = sc[c2];
+            r += (y2 > y) || (y2 == y && c2 < c);
+        }
+        rk[c] = r;
+    }
+    __syncwarp();
+}
+
+// Learned-order scratch of each warp in dynamic shared memory: the row's
+// candidates, their scores and their order positions (MCAP entries each).
+struct LrnWarp {
+    int* nb;
+    float* sc;
+    int* rk;
+};
+constexpr size_t kLrnBytes = (size_t)NW * 3 * MCAP * sizeof(int);
+
+__device__ __forceinline__ LrnWarp lrn_warp(unsigned char* dyn)
+{
+    int* base = (int*)dyn + (size_t)(threadIdx.x >> 5) * 3 * MCAP;
+    return LrnWarp{base, (float*)(base + MCAP), base + 2 * MCAP};
+}
+
 // P1 of a level whose A'_G is built from the previous level's (old buffer O):
 // per old row, the position of each surviving slot among the row's survivors
 // (-1 for a removed edge), from the alive flags the previous level's removal
-// phase wrote. Same CTA split as phase_prefix.
-__device__ void phase_rank(const LevelParams& P, const Csr& O, int skip)
+// phase wrote. Same CTA split as phase_prefix. LRN: the survivors (the new
+// row) are also scored, and vrank holds each survivor's order position.
+template <bool LRN>
+__device__ void phase_rank(const LevelParams& P, const Csr& O, int skip, unsigned char* dyn)
 {
     const int lane = threadIdx.x & 31;
     const int nb = (skip && gridDim.x > 1) ? gridDim.x - 1 : gridDim.x;
@@ -190,19 +254,36 @@ __device__ void phase_rank(const LevelParams& P, const Csr& O, int skip)
     for (int i = gw; i < P.p; i += nwarps) {
         const long long off = O.row_off[i], end = O.row_off[i + 1];
         int base = 0;
+        LrnWarp L{};
+        if (LRN) L = lrn_warp(dyn);
         for (long long e0 = off; e0 < end; e0 += 32) {
             const long long e = e0 + lane;
             const bool a = e < end && P.alive[e] != 0;
             const unsigned m = __ballot_sync(0xffffffffu, a);
-            if (e < end) P.nrank[e] = a ? base + __popc(m & ((1u << lane) - 1u)) : -1;
+            const int r = base + __popc(m & ((1u << lane) - 1u));
+            if (e < end) P.nrank[e] = a ? r : -1;
+            if (LRN && a && r < MCAP) L.nb[r] = O.cols[e];
             base += __popc(m);
+        }
+        if (LRN) {
+            const bool ord = base <= MCAP;        // (warp-uniform)
+            if (ord) {
+                __syncwarp();
+                warp_row_order(P, i, L.nb, base, P.l, L.sc, L.rk);
+            }
+            for (long long e = off + lane; e < end; e += 32) {
+                const int r = P.nrank[e];          // (this lane's own store)
+                if (r >= 0) P.vrank[e] = ord ? L.rk[r] : r;
+            }
+            __syncwarp();                          // the scratch is free for the next row
         }
     }
 }
 
 // P2 of such a level: the surviving slots of the old A'_G, in order, into the
 // new buffer A (row offsets from the degree scan); a slot's partner is found
-// through the old partner's position.
+// through the old partner's position. LRN: the new rows' order from vrank.
+template <bool LRN>
 __device__ void phase_fill_incr(const LevelParams& P, const Csr& O, const Csr& A)
 {
     const long long nnz_old = O.row_off[P.p];
@@ -214,6 +295,11 @@ __device__ void phase_fill_incr(const LevelParams& P, const Csr& O, const Csr& A
         A.cols[ne] = j;
         A.srow[ne] = i;
         A.partner[ne] = (int)(A.row_off[j] + P.nrank[O.partner[e]]);
+        if (LRN) {
+            const int v = P.vrank[e];
+            P.perm[A.row_off[i] + v] = r;
+            P.iperm[ne] = v;
+        }
     }
 }
 
@@ -222,18 +308,16 @@ __device__ void phase_fill_incr(const LevelParams& P, const Csr& O, const Csr& A
 // (subset ranks per item) doubles until the items fit the item array.
 // ---------------------------------------------------------------------------
 // Work items of a row with degree d at level l: the subset ranks of the row
-// (S shared across j) or, in the learned order, of each side's own candidates.
+// (S shared across j).
 // With the j split (level 1), each subset chunk is further cut into the row's
 // j positions in ranges of 32: item k of the row is subset chunk k / J and
 // j range k % J, J = ceil(d / 32).
 __device__ __forceinline__ int j_ranges(int d, int l, bool js) { return (js && l == 1) ? (d + 31) >> 5 : 1; }
 
-__device__ __forceinline__ unsigned long long row_items(const Binom& B, int d, int l, int chunk, bool lrn,
-                                                        bool js = false)
+__device__ __forceinline__ unsigned long long row_items(const Binom& B, int d, int l, int chunk, bool js)
 {
     if (d < l + 1) return 0;
-    if (!lrn) return (B(d, l) + chunk - 1) / chunk * (unsigned long long)j_ranges(d, l, js);
-    return (unsigned long long)d * ((B(d - 1, l) + chunk - 1) / chunk);
+    return (B(d, l) + chunk - 1) / chunk * (unsigned long long)j_ranges(d, l, js);
 }
 
 // Adds a row with K items to the round histogram (bin min(K, RND - 1); rows
@@ -268,45 +352,20 @@ __device__ __forceinline__ void load8(const LevelParams& P, int i0, int hi, int 
 
 // P1 for graphs of at most 32 NT rows: block 0 scans every row while the
 // other CTAs build the word prefixes (no second barrier).
-__device__ void phase_scan_one(const LevelParams& P, const Csr& A, bool learned)
+__device__ void phase_scan_one(const LevelParams& P, const Csr& A)
 {
-    __shared__ long long sa[32], sb[32], sc[32];
+    __shared__ long long sa[32], sb[32];
     __shared__ unsigned long long stot;
-    __shared__ int slrn;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int per = (P.p + NT - 1) / NT;
     const int lo = min(P.p, t * per), hi = min(P.p, lo + per);
     const int l = P.l;
     int rng = 0;
     int d8[8], di8[8];
-    // learned order: the per-side candidate lists must fit the perm array
-    bool lrn = false;
-    if (learned) {
-        unsigned long long c = 0;
-        for (int i0 = lo; i0 < hi; i0 += 8) {
-            load8(P, i0, hi, d8, di8);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int d = di8[u];
-                if (d >= l + 1) c += (unsigned long long)d * (unsigned long long)(d - 1);
-            }
-        }
-        c = warp_sum_u64(c);
-        if (lane == 0) sb[w] = (long long)c;
-        __syncthreads();
-        if (t == 0) {
-            unsigned long long tot = 0;
-            for (int k = 0; k < NW; ++k) tot += (unsigned long long)sb[k];
-            slrn = tot <= P.perm_cap ? 1 : 0;
-            P.lm->learned_on[l] = slrn;
-        }
-        __syncthreads();
-        lrn = slrn != 0;
-    }
     // one pass for the sums at the default chunk; the chunk doubles (items
     // recounted) only while the items would not fit the item array
     int chunk = P.chunk0;
-    long long a = 0, b = 0, c = 0;
+    long long a = 0, b = 0;
     unsigned long long sq = 0;
     int dmax = 0;
     for (int i0 = lo; i0 < hi; i0 += 8) {
@@ -316,11 +375,10 @@ __device__ void phase_scan_one(const LevelParams& P, const Csr& A, bool learned)
             const int d = di8[u];
             dmax = max(dmax, d);
             a += d8[u];
-            b += (long long)row_items(P.B, d, l, chunk, lrn, P.jsplit);
+            b += (long long)row_items(P.B, d, l, chunk, P.jsplit);
             if (d >= l + 1) {
                 if (P.B(d, l) == ~0ull) rng = 1;
                 sq += (unsigned long long)(d + 1) * (unsigned long long)(d + 1);
-                if (lrn) c += (long long)d * (d - 1);
             }
         }
     }
@@ -342,7 +400,7 @@ __device__ void phase_scan_one(const LevelParams& P, const Csr& A, bool learned)
         for (int i0 = lo; i0 < hi; i0 += 8) {
             load8(P, i0, hi, d8, di8);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) b += (long long)row_items(P.B, di8[u], l, chunk, lrn, P.jsplit);
+            for (int u = 0; u < 8; ++u) b += (long long)row_items(P.B, di8[u], l, chunk, P.jsplit);
         }
     }
     sq = warp_sum_u64(sq);
@@ -350,34 +408,30 @@ __device__ void phase_scan_one(const LevelParams& P, const Csr& A, bool learned)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     if (lane == 0) atomicMax(&P.lm->maxdeg[l], dmax);
-    long long ia = a, ib = b, ic = c;
+    long long ia = a, ib = b;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const long long xa = __shfl_up_sync(0xffffffffu, ia, o);
         const long long xb = __shfl_up_sync(0xffffffffu, ib, o);
-        const long long xc = __shfl_up_sync(0xffffffffu, ic, o);
-        if (lane >= o) { ia += xa; ib += xb; ic += xc; }
+        if (lane >= o) { ia += xa; ib += xb; }
     }
     __syncthreads();
-    if (lane == 31) { sa[w] = ia; sb[w] = ib; sc[w] = ic; }
+    if (lane == 31) { sa[w] = ia; sb[w] = ib; }
     __syncthreads();
     if (w == 0) {
-        long long va = (lane < NW) ? sa[lane] : 0, vb = (lane < NW) ? sb[lane] : 0, vc = (lane < NW) ? sc[lane] : 0;
+        long long va = (lane < NW) ? sa[lane] : 0, vb = (lane < NW) ? sb[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const long long xa = __shfl_up_sync(0xffffffffu, va, o);
             const long long xb = __shfl_up_sync(0xffffffffu, vb, o);
-            const long long xc = __shfl_up_sync(0xffffffffu, vc, o);
-            if (lane >= o) { va += xa; vb += xb; vc += xc; }
+            if (lane >= o) { va += xa; vb += xb; }
         }
         sa[lane] = va;
         sb[lane] = vb;
-        sc[lane] = vc;
     }
     __syncthreads();
     long long ea = ia - a + (w > 0 ? sa[w - 1] : 0);
     long long eb = ib - b + (w > 0 ? sb[w - 1] : 0);
-    long long ec = ic - c + (w > 0 ? sc[w - 1] : 0);
     // rows by their item count (capped at RND - 1) and the items past the cap
     __shared__ unsigned long long hist[RND];
     for (int q = t; q < RND; q += NT) hist[q] = 0;
@@ -392,13 +446,11 @@ __device__ void phase_scan_one(const LevelParams& P, const Csr& A, bool learned)
             const int d = di8[u];
             A.row_off[i] = ea;
             P.item_off[i] = eb;
-            if (P.poff) P.poff[i] = ec;
             ea += d8[u];
-            const unsigned long long K = row_items(P.B, d, l, chunk, lrn, P.jsplit);
+            const unsigned long long K = row_items(P.B, d, l, chunk, P.jsplit);
             eb += (long long)K;
             hist_add(hist, K);
             if (K > RND - 1) ovf += K - (RND - 1);
-            if (lrn && d >= l + 1) ec += (long long)d * (d - 1);
         }
     }
     ovf = warp_sum_u64(ovf);
@@ -410,7 +462,6 @@ __device__ void phase_scan_one(const LevelParams& P, const Csr& A, bool learned)
     if (t == NT - 1) {
         A.row_off[P.p] = ea;
         P.item_off[P.p] = eb;
-        if (P.poff) P.poff[P.p] = ec;
         P.lm->edges[l] = (unsigned long long)ea / 2;
         P.lm->items[l] = (unsigned long long)eb;
         P.lm->chunk[l] = chunk;
@@ -425,46 +476,44 @@ __device__ __forceinline__ void cta_rows(const LevelParams& P, int& r0, int& r1)
     r1 = (int)((long long)P.p * (blockIdx.x + 1) / gridDim.x);
 }
 
-// Block-wide sum of four u64 values (fixed order); the result is valid in thread 0.
-__device__ __forceinline__ void block_sum4(unsigned long long (&v)[4], unsigned long long (*red)[4])
+// Block-wide sum of two u64 values (fixed order); the result is valid in thread 0.
+__device__ __forceinline__ void block_sum2(unsigned long long (&v)[2], unsigned long long (*red)[2])
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = warp_sum_u64(v[k]);
+    for (int k = 0; k < 2; ++k) v[k] = warp_sum_u64(v[k]);
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) red[w][k] = v[k];
+        for (int k = 0; k < 2; ++k) red[w][k] = v[k];
     __syncthreads();
     if (threadIdx.x == 0)
         for (int q = 1; q < NW; ++q)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] += red[q][k];
+            for (int k = 0; k < 2; ++k) v[k] += red[q][k];
     __syncthreads();
 }
 
-// P1a (every CTA, its contiguous rows): CSR slots, work items at the default
-// chunk in both enumeration orders, candidate-list entries; max degree,
-// C sub-block entries and the 64-bit range check go to the level counters.
-__device__ void phase_scan_a(const LevelParams& P, bool learned)
+// P1a (every CTA, its contiguous rows): CSR slots and work items at the
+// default chunk; max degree, C sub-block entries and the 64-bit range check go
+// to the level counters.
+__device__ void phase_scan_a(const LevelParams& P)
 {
-    __shared__ unsigned long long red[NW][4];
+    __shared__ unsigned long long red[NW][2];
     const int l = P.l;
     int r0, r1;
     cta_rows(P, r0, r1);
-    unsigned long long v[4] = {0, 0, 0, 0};   // slots, items (S-shared), items (per edge), list entries
+    unsigned long long v[2] = {0, 0};   // slots, items
     unsigned long long sq = 0;
     int dmax = 0, rng = 0;
     for (int i = r0 + (int)threadIdx.x; i < r1; i += NT) {
         const int d = P.deg[i];
         const int di = (P.vlmax && l > P.vlmax[i]) ? 0 : d;
         v[0] += (unsigned long long)d;
-        v[1] += row_items(P.B, di, l, P.chunk0, false, P.jsplit);
-        if (learned) v[2] += row_items(P.B, di, l, P.chunk0, true);
+        v[1] += row_items(P.B, di, l, P.chunk0, P.jsplit);
         dmax = max(dmax, di);
         if (di >= l + 1) {
             if (P.B(di, l) == ~0ull) rng = 1;
             sq += (unsigned long long)(di + 1) * (unsigned long long)(di + 1);
-            if (learned) v[3] += (unsigned long long)di * (unsigned long long)(di - 1);
         }
     }
     sq = warp_sum_u64(sq);
@@ -476,24 +525,22 @@ __device__ void phase_scan_a(const LevelParams& P, bool learned)
         if (dmax) atomicMax(&P.lm->maxdeg[l], dmax);
     }
     if (__any_sync(0xffffffffu, rng) && lane == 0) atomicOr(&P.lm->range_error, 1);
-    block_sum4(v, red);
+    block_sum2(v, red);
     if (threadIdx.x == 0)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) P.scan_part[(size_t)blockIdx.x * 4 + k] = v[k];
+        for (int k = 0; k < 2; ++k) P.scan_part[(size_t)blockIdx.x * 2 + k] = v[k];
 }
 
-// P1b (every CTA, after a grid barrier): the enumeration order and chunk from
-// the totals (the chunk doubles while the items would not fit; each doubling
-// recounts and takes another barrier), then this CTA's rows' CSR offsets, item
-// offsets, candidate-list offsets and its part of the round histogram.
-// Returns false when a barrier failed.
-__device__ bool phase_scan_b(const LevelParams& P, const Csr& A, bool learned, bool& lrn_out)
+// P1b (every CTA, after a grid barrier): the chunk from the totals (it doubles
+// while the items would not fit; each doubling recounts and takes another
+// barrier), then this CTA's rows' CSR offsets, item offsets and its part of
+// the round histogram. Returns false when a barrier failed.
+__device__ bool phase_scan_b(const LevelParams& P, const Csr& A)
 {
-    __shared__ unsigned long long sbase[4], stot[4];
-    __shared__ unsigned long long rsum[NW][4];
-    __shared__ unsigned long long wsum[NW][3];
+    __shared__ unsigned long long sbase[2], stot[2];
+    __shared__ unsigned long long rsum[NW][2];
+    __shared__ unsigned long long wsum[NW][2];
     __shared__ unsigned long long hist[RND];
-    __shared__ int schunk, slrn;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int l = P.l;
     int r0, r1;
@@ -501,40 +548,32 @@ __device__ bool phase_scan_b(const LevelParams& P, const Csr& A, bool learned, b
     // totals of the CTAs, and the exclusive prefix for this CTA (fixed order)
     // (thread c loads CTA c's partials; two block sums in a fixed order)
     auto totals = [&]() {
-        unsigned long long v[4] = {0, 0, 0, 0}, u[4] = {0, 0, 0, 0};
+        unsigned long long v[2] = {0, 0}, u[2] = {0, 0};
         if (t < (int)gridDim.x)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                v[k] = __ldcg(P.scan_part + (size_t)t * 4 + k);
+            for (int k = 0; k < 2; ++k) {
+                v[k] = __ldcg(P.scan_part + (size_t)t * 2 + k);
                 u[k] = t < (int)blockIdx.x ? v[k] : 0ull;
             }
-        block_sum4(v, rsum);
-        block_sum4(u, rsum);
+        block_sum2(v, rsum);
+        block_sum2(u, rsum);
         if (t == 0)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 2; ++k) {
                 stot[k] = v[k];
                 sbase[k] = u[k];
             }
         __syncthreads();
     };
     totals();
-    if (t == 0) {
-        slrn = (learned && stot[3] <= P.perm_cap) ? 1 : 0;
-        schunk = P.chunk0;
-        if (learned && blockIdx.x == 0) P.lm->learned_on[l] = slrn;
-    }
-    __syncthreads();
-    const bool lrn = slrn != 0;
-    lrn_out = lrn;
-    int chunk = schunk;
-    for (int it = 0; it < 40 && stot[lrn ? 2 : 1] > P.item_cap && chunk <= (1 << 29); ++it) {
+    int chunk = P.chunk0;
+    for (int it = 0; it < 40 && stot[1] > P.item_cap && chunk <= (1 << 29); ++it) {
         // recount this CTA's items at twice the chunk
         chunk *= 2;
         unsigned long long b = 0;
         for (int i = r0 + t; i < r1; i += NT) {
             const int di = (P.vlmax && l > P.vlmax[i]) ? 0 : P.deg[i];
-            b += row_items(P.B, di, l, chunk, lrn, P.jsplit);
+            b += row_items(P.B, di, l, chunk, P.jsplit);
         }
         b = warp_sum_u64(b);
         if (lane == 0) wsum[w][0] = b;
@@ -542,52 +581,48 @@ __device__ bool phase_scan_b(const LevelParams& P, const Csr& A, bool learned, b
         if (t == 0) {
             unsigned long long x = 0;
             for (int q = 0; q < NW; ++q) x += wsum[q][0];
-            P.scan_part[(size_t)blockIdx.x * 4 + (lrn ? 2 : 1)] = x;
+            P.scan_part[(size_t)blockIdx.x * 2 + 1] = x;
         }
         if (!grid_sync(P)) return false;
         totals();
     }
-    // this CTA's rows: exclusive scans of (slots, items, list entries), in tiles of NT rows
+    // this CTA's rows: exclusive scans of (slots, items), in tiles of NT rows
     for (int q = t; q < RND; q += NT) hist[q] = 0;
     __syncthreads();
-    unsigned long long ca = sbase[0], cb = sbase[lrn ? 2 : 1], cc = sbase[3];
+    unsigned long long ca = sbase[0], cb = sbase[1];
     unsigned long long ovf = 0;
     for (int base = r0; base < r1; base += NT) {
         const int i = base + t;
-        unsigned long long a = 0, b = 0, c = 0;
+        unsigned long long a = 0, b = 0;
         if (i < r1) {
             const int d = P.deg[i];
             const int di = (P.vlmax && l > P.vlmax[i]) ? 0 : d;
             a = (unsigned long long)d;
-            b = row_items(P.B, di, l, chunk, lrn, P.jsplit);
-            if (lrn && di >= l + 1) c = (unsigned long long)di * (unsigned long long)(di - 1);
+            b = row_items(P.B, di, l, chunk, P.jsplit);
             if (b > RND - 1) ovf += b - (RND - 1);
         }
         hist_add(hist, b);
         // inclusive warp scans, then the warp totals in order
-        unsigned long long ia = a, ib = b, ic = c;
+        unsigned long long ia = a, ib = b;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long xa = __shfl_up_sync(0xffffffffu, ia, o);
             const unsigned long long xb = __shfl_up_sync(0xffffffffu, ib, o);
-            const unsigned long long xc = __shfl_up_sync(0xffffffffu, ic, o);
-            if (lane >= o) { ia += xa; ib += xb; ic += xc; }
+            if (lane >= o) { ia += xa; ib += xb; }
         }
-        if (lane == 31) { wsum[w][0] = ia; wsum[w][1] = ib; wsum[w][2] = ic; }
+        if (lane == 31) { wsum[w][0] = ia; wsum[w][1] = ib; }
         __syncthreads();
-        unsigned long long pa = 0, pb = 0, pc = 0, ta = 0, tb = 0, tc = 0;
+        unsigned long long pa = 0, pb = 0, ta = 0, tb = 0;
         for (int q = 0; q < NW; ++q) {
-            if (q < w) { pa += wsum[q][0]; pb += wsum[q][1]; pc += wsum[q][2]; }
-            ta += wsum[q][0]; tb += wsum[q][1]; tc += wsum[q][2];
+            if (q < w) { pa += wsum[q][0]; pb += wsum[q][1]; }
+            ta += wsum[q][0]; tb += wsum[q][1];
         }
         if (i < r1) {
             A.row_off[i] = (long long)(ca + pa + ia - a);
             P.item_off[i] = (long long)(cb + pb + ib - b);
-            if (P.poff) P.poff[i] = (long long)(cc + pc + ic - c);
         }
         ca += ta;
         cb += tb;
-        cc += tc;
         __syncthreads();
     }
     ovf = warp_sum_u64(ovf);
@@ -596,10 +631,9 @@ __device__ bool phase_scan_b(const LevelParams& P, const Csr& A, bool learned, b
     for (int q = t; q < RND; q += NT)
         if (hist[q]) atomicAdd(&P.lm->round_hist[l][q], hist[q]);
     if (blockIdx.x == gridDim.x - 1 && t == 0) {
-        const unsigned long long ea = stot[0], eb = stot[lrn ? 2 : 1], ec = stot[3];
+        const unsigned long long ea = stot[0], eb = stot[1];
         A.row_off[P.p] = (long long)ea;
         P.item_off[P.p] = (long long)eb;
-        if (P.poff) P.poff[P.p] = (long long)(lrn ? ec : 0);
         P.lm->edges[l] = ea / 2;
         P.lm->items[l] = eb;
         P.lm->chunk[l] = chunk;
@@ -693,12 +727,13 @@ __device__ void phase_items(const LevelParams& P, const Csr& A)
     }
 }
 
-template <typename T>
-__device__ void phase_fill(const LevelParams& P, const Csr& A, const Csr& O, bool reuse, bool incr, bool pivot)
+template <typename T, bool LRN>
+__device__ void phase_fill(const LevelParams& P, const Csr& A, const Csr& O, bool reuse, bool incr, bool pivot,
+                           unsigned char* dyn)
 {
     const int lane = threadIdx.x & 31;
     if (incr) {
-        phase_fill_incr(P, O, A);
+        phase_fill_incr<LRN>(P, O, A);
         reuse = true;                              // (the bitset walk below is skipped)
     }
     const int gw = (blockIdx.x * NT + threadIdx.x) >> 5;
@@ -736,6 +771,25 @@ __device__ void phase_fill(const LevelParams& P, const Csr& A, const Csr& O, boo
                 ++pos;
             }
             base += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (LRN) {
+            // the row's order (the warp's own stores of the row are visible after the sync)
+            __syncwarp();
+            const LrnWarp L = lrn_warp(dyn);
+            const long long off = A.row_off[i];
+            const int d = (int)(A.row_off[i + 1] - off);
+            const bool ord = d <= MCAP;            // (warp-uniform)
+            if (ord) {
+                for (int c = lane; c < d; c += 32) L.nb[c] = A.cols[off + c];
+                __syncwarp();
+                warp_row_order(P, i, L.nb, d, P.l, L.sc, L.rk);
+            }
+            for (int c = lane; c < d; c += 32) {
+                const int v = ord ? L.rk[c] : c;
+                P.iperm[off + c] = v;
+                P.perm[off + v] = c;
+            }
+            __syncwarp();                          // the scratch is free for the next row
         }
     }
     if (!pivot) phase_items(P, A);
@@ -784,7 +838,10 @@ __device__ __forceinline__ int ci_decide(T H11, T H12, T H22, T minpiv2, const D
     }
 }
 
-template <typename T, int LB, bool FP32>
+// LRN: the row's candidates are enumerated in the network's order: position v
+// of the enumeration is slot off + P.perm[off + v] (ranks and the per-slot
+// best ranks are then over these virtual positions).
+template <typename T, int LB, bool FP32, bool LRN = false>
 __device__ void phase_ci(const LevelParams& P, const Csr& A)
 {
     const int lane = threadIdx.x & 31;
@@ -822,6 +879,7 @@ __device__ void phase_ci(const LevelParams& P, const Csr& A)
         // is then valid for few lanes' subsets, so each lane walks its own d - l
         // non-members instead and all lanes test at once
         const bool comp = 4 * (d - l) <= 3 * d;
+        auto vmap = [&](int v) -> int { return LRN ? P.perm[off + v] : v; };
         for (unsigned long long base = s0; base < s1; base += 32) {
             const unsigned long long s = base + lane;
             const bool active = s < s1;
@@ -834,20 +892,19 @@ __device__ void phase_ci(const LevelParams& P, const Csr& A)
                 else unrank_lex<LB>(s, d, l, P.B, Pos);
 #pragma unroll
                 for (int c = 0; c < LB; ++c)
-                    if (c < l) Sx[c] = A.cols[off + Pos[c]];
+                    if (c < l) Sx[c] = A.cols[off + vmap(Pos[c])];
                 factor_build<T, LB>(
                     F, l, (T)P.rank_tol, [&](int a, int b) { return __ldg(CV.row(Sx[a]) + Sx[b]); },
                     [&](int a) { return __ldg(Ci + Sx[a]); });
             }
-            // one test of this lane's subset against position jp (slot e = off + jp)
-            auto test = [&](int jp, int j, T cij) {
+            // one test of this lane's subset against the neighbour j of slot e
+            auto test = [&](long long e, int j, T cij) {
                 T H12, H22;
                 const T* __restrict__ Cj = CV.row(j);
                 factor_apply<T, LB>(F, l, cij, [&](int a) { return __ldg(Cj + Sx[a]); }, H12, H22);
                 const T H11 = T(1) - F.uu;
                 ++ntests;
                 const int dec = ci_decide<T, FP32>(H11, H12, H22, F.minpiv2, dc);
-                const long long e = off + jp;
                 if (dec == 1) {
                     atomicMin(P.best + e, s);
                 } else if (FP32 && dec == 2) {
@@ -871,22 +928,23 @@ __device__ void phase_ci(const LevelParams& P, const Csr& A)
                     for (int c = 0; c < LB; ++c)
                         if (c < l && Pos[c] <= jp) ++jp;
                     if (!active) continue;
-                    const long long e = off + jp;
+                    const long long e = off + vmap(jp);
                     const int j = A.cols[e];
                     const unsigned long long be = ld_cg(P.best + e);
                     const unsigned long long pb = (!P.canonical || i > j) ? ld_cg(P.best + A.partner[e]) : RANK_NONE;
-                    if (pb == RANK_NONE && (P.canonical ? (be >= s) : (be == RANK_NONE))) test(jp, j, __ldg(Ci + j));
+                    if (pb == RANK_NONE && (P.canonical ? (be >= s) : (be == RANK_NONE))) test(e, j, __ldg(Ci + j));
                 }
                 continue;
             }
             // the row's per-j data in chunks of 32: lane q loads j-position jc + q
             // (coalesced), then the chunk is broadcast one j at a time by shuffles
             for (int jc = jlo; jc < jhi; jc += 32) {
-                int j_l = 0;
+                int j_l = 0, e_l = 0;
                 unsigned long long b_l = RANK_NONE, pb_l = RANK_NONE;
                 T cij_l = T(0);
                 if (jc + lane < jhi) {
-                    const long long e = off + jc + lane;
+                    const long long e = off + vmap(jc + lane);
+                    e_l = (int)e;
                     j_l = A.cols[e];
                     b_l = ld_cg(P.best + e);
                     // the larger endpoint's side stops once the smaller side separates
@@ -899,6 +957,7 @@ __device__ void phase_ci(const LevelParams& P, const Csr& A)
                 for (int q = 0; q < jn; ++q) {
                     const int jp = jc + q;
                     const int j = __shfl_sync(0xffffffffu, j_l, q);
+                    const int e = __shfl_sync(0xffffffffu, e_l, q);
                     const unsigned long long be = __shfl_sync(0xffffffffu, b_l, q);
                     const unsigned long long pb = __shfl_sync(0xffffffffu, pb_l, q);
                     const T cij = __shfl_sync(0xffffffffu, cij_l, q);
@@ -906,7 +965,7 @@ __device__ void phase_ci(const LevelParams& P, const Csr& A)
 #pragma unroll
                     for (int c = 0; c < LB; ++c)
                         if (c < l && Pos[c] == jp) t = false;
-                    if (t) test(jp, j, cij);
+                    if (t) test(e, j, cij);
                 }
             }
         }
@@ -1043,7 +1102,8 @@ __device__ __forceinline__ int l1_decide(T H11, T H12, T H22, const Decide& dc)
 constexpr int kL1Nb = 256;   // neighbours of the pivot staged per round
 constexpr int kL1U = 4;      // slot loads in flight per lane
 
-template <typename T, bool FP32>
+// LRN: the rank of {k} on side i is k's position in row i's learned order.
+template <typename T, bool FP32, bool LRN>
 __device__ void phase_l1_pivot(const LevelParams& P, const Csr& A, unsigned char* dyn)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1052,6 +1112,7 @@ __device__ void phase_l1_pivot(const LevelParams& P, const Csr& A, unsigned char
     __shared__ int sabort;
     // the rows i in adj(k) of one round: slot offset, degree, position of k
     __shared__ int nb_off[kL1Nb], nb_d[kL1Nb], nb_pos[kL1Nb], nb_i[kL1Nb];
+    __shared__ int nb_rk[LRN ? kL1Nb : 1];
     const int nbuf = P.l1_pivot;
     const size_t bbytes = l1_buf_bytes(P.pstage, sizeof(T));
     T* buf[2] = {(T*)dyn, (T*)(dyn + (nbuf > 1 ? bbytes : 0))};
@@ -1102,7 +1163,9 @@ __device__ void phase_l1_pivot(const LevelParams& P, const Csr& A, unsigned char
                 nb_i[t] = i;
                 nb_off[t] = (int)offi;
                 nb_d[t] = (int)(A.row_off[i + 1] - offi);
-                nb_pos[t] = A.partner[offk + t0 + t] - (int)offi;   // slot (i, k) in row i
+                const int sk = A.partner[offk + t0 + t];            // slot (i, k)
+                nb_pos[t] = sk - (int)offi;
+                if (LRN) nb_rk[t] = P.iperm[sk];
             }
             __syncthreads();                       // (the first one also publishes the staged row)
             if (sabort) break;
@@ -1110,7 +1173,7 @@ __device__ void phase_l1_pivot(const LevelParams& P, const Csr& A, unsigned char
                 const int di = nb_d[t];
                 if (di < 2) continue;
                 const int offi = nb_off[t], posk = nb_pos[t];
-                const unsigned long long rk = (unsigned long long)posk;
+                const unsigned long long rk = (unsigned long long)(LRN ? nb_rk[t] : posk);
                 const T cik = sk_row[nb_i[t]];
                 const T H11 = T(1) - cik * cik;
                 // (FP32: a tiny conditional variance sends every test of the row to FP64)
@@ -1173,149 +1236,6 @@ __device__ void phase_l1_pivot(const LevelParams& P, const Csr& A, unsigned char
     }
     const unsigned long long nt64 = warp_sum_u64((unsigned long long)ntests);
     if (lane == 0 && nt64) atomicAdd(&P.lm->tests[1], nt64);
-}
-
-// ---------------------------------------------------------------------------
-// Learned ordering, levels l >= 2 (FP32 mode).
-// P3: for every slot (i, j), score each candidate k of adj(i) \ {j} with the
-// network and store the candidates by descending score (ties: increasing
-// position) -- a permutation, so full enumeration is still reached.
-// P4': each side enumerates the l-subsets of its own ordered candidates, in
-// lexicographic order of the ordered positions, lanes taking consecutive
-// ranks; the first separating rank per side is kept (atomicMin), the larger
-// endpoint's side stops once the smaller side has one.
-// ---------------------------------------------------------------------------
-constexpr int MCAP = 256;  // candidates scored per side; longer lists keep their increasing order
-
-__device__ __forceinline__ int* side_perm(const LevelParams& P, const Csr& A, int i, long long e)
-{
-    const long long off = A.row_off[i];
-    const int m = (int)(A.row_off[i + 1] - off) - 1;
-    return P.perm + P.poff[i] + (e - off) * (long long)m;
-}
-
-__device__ void phase_score(const LevelParams& P, const Csr& A)
-{
-    __shared__ __nv_bfloat16 Wsm[MLP_NP];
-    __shared__ float sc[NW][MCAP];
-    for (int q = threadIdx.x; q < MLP_NP; q += NT) Wsm[q] = ((const __nv_bfloat16*)P.mlp_w)[q];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int gw = (blockIdx.x * NT + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * NT) >> 5;
-    const long long nnz = A.row_off[P.p];
-    for (long long e = gw; e < nnz; e += nwarps) {
-        const int i = A.srow[e], j = A.cols[e];
-        const CView<float> CV = cview<float>(P, i);
-        const long long off = A.row_off[i];
-        const int m = (int)(A.row_off[i + 1] - off) - 1;
-        if (m < P.l) continue;
-        const int pj = (int)(e - off);
-        int* dst = side_perm(P, A, i, e);
-        if (m > MCAP) {
-            for (int c = lane; c < m; c += 32) dst[c] = A.cols[off + (c < pj ? c : c + 1)];
-            continue;
-        }
-        const float cij = CV.row(i)[j];
-        for (int c = lane; c < m; c += 32) {
-            const int k = A.cols[off + (c < pj ? c : c + 1)];
-            float x[MLP_IN];
-            mlp_features(cij, CV.row(i)[k], CV.row(j)[k], P.l, x);
-            const float y = mlp_score(Wsm, x);
-            sc[w][c] = (y == y) ? y : -INFINITY;
-        }
-        __syncwarp();
-        for (int c = lane; c < m; c += 32) {
-            const float y = sc[w][c];
-            int r = 0;
-            for (int c2 = 0; c2 < m; ++c2) {
-                const float y2 = sc[w][c2];
-                r += (y2 > y) || (y2 == y && c2 < c);
-            }
-            dst[r] = A.cols[off + (c < pj ? c : c + 1)];
-        }
-        __syncwarp();
-    }
-}
-
-template <typename T, int LB, bool FP32>
-__device__ void phase_ci_edge(const LevelParams& P, const Csr& A)
-{
-    const int lane = threadIdx.x & 31;
-    const int l = P.l;
-    const unsigned long long n_items = P.lm->items[l];
-    const int chunk = P.lm->chunk[l];
-    unsigned long long ntests = 0;
-    for (;;) {
-        unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(&P.lm->next_item[l], 1ull);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= n_items) break;
-        const int i = P.item_row[item];
-        const long long k = P.item_c[item];
-        const long long off = A.row_off[i];
-        const int m = (int)(A.row_off[i + 1] - off) - 1;
-        const CView<T> CV = cview<T>(P, i);
-        double thr, thr2;
-        thresholds(P, i, thr, thr2);
-        const Decide dc = decide_consts(P, thr, thr2);
-        const unsigned long long total = P.B(m, l);
-        const long long per_edge = (long long)((total + chunk - 1) / chunk);
-        const long long q = k / per_edge, cidx = k % per_edge;
-        const long long e = off + q;
-        const int j = A.cols[e];
-        const int* __restrict__ cand = side_perm(P, A, i, e);
-        const unsigned long long s0 = (unsigned long long)cidx * (unsigned long long)chunk;
-        const unsigned long long s1 = min(s0 + (unsigned long long)chunk, total);
-        const T* __restrict__ Ci = CV.row(i);
-        const T* __restrict__ Cj = CV.row(j);
-        const T cij = Ci[j];
-        const bool watch_partner = !P.canonical || i > j;
-        for (unsigned long long base = s0; base < s1; base += 32) {
-            unsigned long long be = 0, pb = 0;
-            if (lane == 0) {
-                be = ld_cg(P.best + e);
-                pb = watch_partner ? ld_cg(P.best + A.partner[e]) : RANK_NONE;
-            }
-            be = __shfl_sync(0xffffffffu, be, 0);
-            pb = __shfl_sync(0xffffffffu, pb, 0);
-            // a smaller rank already separates this side, or the other side decides
-            if (P.canonical ? (be < base) : (be != RANK_NONE)) break;
-            if (pb != RANK_NONE) break;
-            const unsigned long long r = base + lane;
-            if (r < s1 && r < be) {
-                int Q[LB], Sx[LB];
-                unrank_lex<LB>(r, m, l, P.B, Q);
-#pragma unroll
-                for (int c = 0; c < LB; ++c) Sx[c] = (c < l) ? cand[Q[c]] : 0;
-                Factor<T, LB> F;
-                factor_build<T, LB>(
-                    F, l, (T)P.rank_tol, [&](int a, int b) { return __ldg(CV.row(Sx[a]) + Sx[b]); },
-                    [&](int a) { return __ldg(Ci + Sx[a]); });
-                T H12, H22;
-                factor_apply<T, LB>(F, l, cij, [&](int a) { return __ldg(Cj + Sx[a]); }, H12, H22);
-                const T H11 = T(1) - F.uu;
-                ++ntests;
-                const int dec = ci_decide<T, FP32>(H11, H12, H22, F.minpiv2, dc);
-                if (dec == 1) {
-                    atomicMin(P.best + e, r);
-                } else if (FP32 && dec == 2) {
-                    const unsigned long long qq = atomicAdd(&P.lm->queue_len[l], 1ull);
-                    if (qq < P.qcap) {
-                        QEntry* Qe = P.queue + qq;
-                        Qe->a = (int)e;
-                        Qe->b = 0;
-                        Qe->s = r;
-#pragma unroll
-                        for (int c = 0; c < LB; ++c)
-                            if (c < l) Qe->S[c] = Sx[c];
-                    }
-                }
-            }
-        }
-    }
-    ntests = warp_sum_u64(ntests);
-    if (lane == 0 && ntests) atomicAdd(&P.lm->tests[l], ntests);
 }
 
 // ---------------------------------------------------------------------------
@@ -1773,34 +1693,27 @@ __device__ __forceinline__ unsigned long long side_serial(const LevelParams& P, 
     const long long off = A.row_off[a];
     const int d = (int)(A.row_off[a + 1] - off);
     if (rank == RANK_NONE) return P.B(d - 1, P.l);
-    if (lrn) return rank + 1;  // ranks already count the side's own candidates
     int Pos[LB];
     unrank_lex<LB>(rank, d, P.l, P.B, Pos);
-    const int pb = (int)(slot_b - off);
+    const int pb = lrn ? P.iperm[slot_b] : (int)(slot_b - off);   // b's position in the row's order
 #pragma unroll
     for (int c = 0; c < LB; ++c)
         if (c < P.l && Pos[c] > pb) Pos[c] -= 1;
     return rank_lex<LB>(Pos, d - 1, P.l, P.B) + 1;
 }
 
-// Members of the separating set of rank `rank` found on side (a, b) at slot f.
+// Members of the separating set of rank `rank` found on side a, in increasing order.
 template <int LB>
-__device__ __forceinline__ void side_members(const LevelParams& P, const Csr& A, int a, long long f, unsigned long long rank,
+__device__ __forceinline__ void side_members(const LevelParams& P, const Csr& A, int a, unsigned long long rank,
                                              bool lrn, int (&S)[LB])
 {
     const long long off = A.row_off[a];
     const int d = (int)(A.row_off[a + 1] - off);
     int Pos[LB];
-    if (!lrn) {
-        unrank_lex<LB>(rank, d, P.l, P.B, Pos);
+    unrank_lex<LB>(rank, d, P.l, P.B, Pos);
 #pragma unroll
-        for (int c = 0; c < LB; ++c) S[c] = (c < P.l) ? A.cols[off + Pos[c]] : 0x7fffffff;
-    } else {
-        unrank_lex<LB>(rank, d - 1, P.l, P.B, Pos);
-        const int* cand = side_perm(P, A, a, f);
-#pragma unroll
-        for (int c = 0; c < LB; ++c) S[c] = (c < P.l) ? cand[Pos[c]] : 0x7fffffff;
-        // increasing order for the record
+    for (int c = 0; c < LB; ++c) S[c] = (c < P.l) ? A.cols[off + (lrn ? P.perm[off + Pos[c]] : Pos[c])] : 0x7fffffff;
+    if (lrn) {
 #pragma unroll
         for (int x = 1; x < LB; ++x)
 #pragma unroll
@@ -1824,10 +1737,9 @@ __device__ void phase_finalize(const LevelParams& P, const Csr& A, bool lrn)
                 const long long f = A.partner[e];
                 const unsigned long long bx = ld_cg(P.best + e), by = ld_cg(P.best + f);
                 int side = -1;
-                long long slot = 0;
                 unsigned long long rank = 0;
-                if (bx != RANK_NONE) { side = x; rank = bx; slot = e; }
-                else if (by != RANK_NONE) { side = y; rank = by; slot = f; }
+                if (bx != RANK_NONE) { side = x; rank = bx; }
+                else if (by != RANK_NONE) { side = y; rank = by; }
                 if (side >= 0) {
                     removed = true;
                     const ProbDesc* Dx = prob_of(P.vprob, P.probs, x);
@@ -1835,7 +1747,7 @@ __device__ void phase_finalize(const LevelParams& P, const Csr& A, bool lrn)
                     atomicSub(P.deg + x, 1);
                     atomicSub(P.deg + y, 1);
                     int S[LB];
-                    side_members<LB>(P, A, side, slot, rank, lrn, S);
+                    side_members<LB>(P, A, side, rank, lrn, S);
                     const int ints = 3 + l;
                     const unsigned long long at = atomicAdd(&P.lm->rec_ints, (unsigned long long)ints);
                     if (at + ints <= P.rec_cap) {
@@ -1919,18 +1831,29 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
     const int nbuf = reuse ? cur : 1 - cur;
     const Csr A = csr_view(P, nbuf);
     const Csr O = csr_view(P, cur);
-    const bool want_lrn = LEARNED && P.learned && l >= 2;
+    // learned order: every level's rows are ordered when their A'_G is built
+    // (a reused A'_G keeps its order)
+    const bool lrn = LEARNED && P.learned;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
     const bool one = P.p <= 32 * NT;   // one CTA scans graphs up to 16384 rows (no second barrier)
     if (one) {
-        if (blockIdx.x == 0) phase_scan_one(P, A, want_lrn);
+        if (blockIdx.x == 0) phase_scan_one(P, A);
         if (!reuse && (blockIdx.x != 0 || gridDim.x == 1)) {
-            if (incr) phase_rank(P, O, 1);
-            else phase_prefix(P, 1);
+            if (incr) {
+                if (lrn) phase_rank<LEARNED>(P, O, 1, dyn_smem);
+                else phase_rank<false>(P, O, 1, dyn_smem);
+            } else {
+                phase_prefix(P, 1);
+            }
         }
     } else {
-        phase_scan_a(P, want_lrn);
-        if (incr) phase_rank(P, O, 0);
-        else if (!reuse) phase_prefix(P, 0);
+        phase_scan_a(P);
+        if (incr) {
+            if (lrn) phase_rank<LEARNED>(P, O, 0, dyn_smem);
+            else phase_rank<false>(P, O, 0, dyn_smem);
+        } else if (!reuse) {
+            phase_prefix(P, 0);
+        }
     }
     if (!grid_sync(P)) {
         if (timer) signal_host(P, 2);
@@ -1946,26 +1869,27 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
     }
     if (timer) signal_host(P, 1 | (min(*(volatile int*)&lm->maxdeg[l], 1 << 26) << 4));
     if (!one) {
-        bool lrn_scan = false;
-        if (!phase_scan_b(P, A, want_lrn, lrn_scan)) return;
+        if (!phase_scan_b(P, A)) return;
         if (!grid_sync(P)) return;
     }
     const bool pivot = (LB == 1) && l == 1 && P.l1_pivot;
-    phase_fill<T>(P, A, O, reuse, incr, pivot);
+    if (lrn) phase_fill<T, LEARNED>(P, A, O, reuse, incr, pivot, dyn_smem);
+    else phase_fill<T, false>(P, A, O, reuse, incr, pivot, dyn_smem);
     if (!grid_sync(P)) return;
-    if (timer) lm->csr_level = l;
-    if (timer) { t1 = gtimer(); lm->phase_ns[l][0] += t1 - t0; t0 = t1; }
+    if (timer) {
+        lm->csr_level = l;
+        lm->learned_on[l] = lrn ? 1 : 0;
+        t1 = gtimer();
+        lm->phase_ns[l][0] += t1 - t0;
+        t0 = t1;
+    }
 
-    const bool lrn = LEARNED && *(volatile int*)&lm->learned_on[l];
-    if (LEARNED && lrn) {
-        phase_score(P, A);
-        if (!grid_sync(P)) return;
-        phase_ci_edge<T, LB, FP32>(P, A);
-    } else if (pivot) {
-        extern __shared__ __align__(16) unsigned char dyn_smem[];
-        phase_l1_pivot<T, FP32>(P, A, dyn_smem);
+    if (pivot) {
+        if (lrn) phase_l1_pivot<T, FP32, LEARNED>(P, A, dyn_smem);
+        else phase_l1_pivot<T, FP32, false>(P, A, dyn_smem);
     } else {
-        phase_ci<T, LB, FP32>(P, A);
+        if (lrn) phase_ci<T, LB, FP32, LEARNED>(P, A);
+        else phase_ci<T, LB, FP32, false>(P, A);
     }
     if (!grid_sync(P)) return;
     if (timer) { t1 = gtimer(); lm->phase_ns[l][1] += t1 - t0; t0 = t1; }
@@ -1994,12 +1918,15 @@ template <typename T, int LB, bool FP32, bool LEARNED>
 cudaError_t launch_level_t(const LevelParams& P, int num_sms, cudaStream_t st)
 {
     // level-1 instances reserve shared memory for the pivot form's staged row
-    // (the largest problem's p entries); one occupancy per reserved size
-    const size_t dyn = (LB == 1 && P.l1_pivot) ? (size_t)P.l1_pivot * l1_buf_bytes(P.pstage, sizeof(T)) : 0;
+    // (the largest problem's p entries), learned-order instances the warps'
+    // scoring scratch (the same memory at level 1: the phases do not overlap);
+    // one occupancy per reserved size
+    size_t dyn = (LB == 1 && P.l1_pivot) ? (size_t)P.l1_pivot * l1_buf_bytes(P.pstage, sizeof(T)) : 0;
+    if (LEARNED && P.learned) dyn = dyn > kLrnBytes ? dyn : kLrnBytes;
     static int per_sm = 0;
     static size_t per_sm_dyn = 0;
     if (per_sm == 0 || per_sm_dyn != dyn) {
-        if (LB == 1) {
+        if (LB == 1 || LEARNED) {
             cudaError_t e = cudaFuncSetAttribute(k_level<T, LB, FP32, LEARNED>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kL1StageBytes);
             if (e != cudaSuccess) return e;
@@ -2029,7 +1956,7 @@ cudaError_t launch_level_t(const LevelParams& P, int num_sms, cudaStream_t st)
 template <typename T, bool FP32, bool LEARNED>
 cudaError_t launch_level_b(const LevelParams& P, int num_sms, cudaStream_t st)
 {
-    if (P.l <= 1) return launch_level_t<T, 1, FP32, false>(P, num_sms, st);
+    if (P.l <= 1) return launch_level_t<T, 1, FP32, LEARNED>(P, num_sms, st);
     if (P.l <= 2) return launch_level_t<T, 2, FP32, LEARNED>(P, num_sms, st);
     if (P.l <= 4) return launch_level_t<T, 4, FP32, LEARNED>(P, num_sms, st);
     if (P.l <= 8) return launch_level_t<T, 8, FP32, LEARNED>(P, num_sms, st);

@@ -220,29 +220,36 @@ cudaError_t launch_mlp_forward(const void* Pb, const float* X, long long N, floa
 }
 
 
-// Training examples: feature rows of (i, j, k, level) tuples from the FP32
-// correlation matrix C (p x p), with the same feature code the level kernel
-// scores candidates with; q[4t + 3] holds level | label << 8.
-__global__ void k_mlp_examples(const float* __restrict__ C, long long p, const int* __restrict__ q, long long n,
-                               float* __restrict__ X, float* __restrict__ t)
+// Training examples: q[6e .. 6e + 6) = (row i, candidate position c, first
+// entry of the row's frozen neighbour list in nbs, its length d, level l,
+// label); the feature row is the one the level kernel scores candidate c of
+// row i with (mlp_row_features over the list, from the FP32 correlation C,
+// p x p).
+__global__ void k_mlp_examples(const float* __restrict__ C, long long p, const int* __restrict__ nbs,
+                               const int* __restrict__ q, long long n, float* __restrict__ X, float* __restrict__ t)
 {
+    auto Cf = [&](int a, int b) { return __ldg(C + (size_t)a * p + b); };
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int i = q[4 * e], j = q[4 * e + 1], k = q[4 * e + 2], lv = q[4 * e + 3];
+        const int* r = q + 6 * e;
+        const int i = r[0], c = r[1], d = r[3], l = r[4];
+        const int* nb = nbs + r[2];
+        float sum = 0.f;
+        for (int u = 0; u < d; ++u) sum += fabsf(Cf(i, nb[u]));
         float x[MLP_IN];
-        mlp_features(C[(size_t)i * p + j], C[(size_t)i * p + k], C[(size_t)j * p + k], lv & 0xff, x);
+        mlp_row_features(Cf, i, nb, d, c, l, sum, x);
 #pragma unroll
-        for (int c = 0; c < MLP_IN; ++c) X[e * MLP_IN + c] = x[c];
-        t[e] = (float)(lv >> 8);
+        for (int k = 0; k < MLP_IN; ++k) X[e * MLP_IN + k] = x[k];
+        t[e] = (float)r[5];
     }
 }
 
-cudaError_t launch_mlp_examples(const float* C, long long p, const int* q, long long n, float* X, float* t,
-                                cudaStream_t st)
+cudaError_t launch_mlp_examples(const float* C, long long p, const int* nbs, const int* q, long long n, float* X,
+                                float* t, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const int block = 256;
     const unsigned grid = (unsigned)std::min<long long>((n + block - 1) / block, 4096);
-    k_mlp_examples<<<grid, block, 0, st>>>(C, p, q, n, X, t);
+    k_mlp_examples<<<grid, block, 0, st>>>(C, p, nbs, q, n, X, t);
     return cudaGetLastError();
 }
 }  // namespace cupc

@@ -28,7 +28,7 @@ struct LevelMeta {
                                            // and block 0's own partial-sum work
     int maxdeg[LV];
     int chunk[LV];
-    int learned_on[LV];                    // the level enumerated in the network's order
+    int learned_on[LV];                    // the level's rows enumerated in the network's order
     unsigned long long rec_ints;           // SepSet record ints appended
     int done_level;                        // level whose termination test stopped the loop
     int csr_level;                         // level whose A'_G arrays (cols, srow, partner, wpre) are current
@@ -138,15 +138,16 @@ struct LevelParams {
     const int* vlmax;              // batch: the last level of each vertex's problem
     unsigned long long* prob_serial;   // batch: serial-order tests per problem and level (nprob x LV)
     int ctas_per_sm;               // launch shape (0: as many as fit, at most 2)
-    unsigned long long* scan_part; // per CTA: CSR slots, items (two orders), list entries
+    unsigned long long* scan_part; // per CTA: CSR slots, items
     const Meta* meta0;             // level 0's counters: a level does not run after an error
     unsigned long long qcap0;      // there, or an overflow of its recheck queue
-    // learned ordering (levels >= 2, FP32 mode)
+    // learned ordering (levels >= 1, FP32 mode): each row of A'_G enumerated in
+    // descending network score (nnz_cap entries each)
     int learned;                   // requested
     const void* mlp_w;             // bf16 network parameters
-    int* perm;                     // per slot (i, j): adj(i) \ {j} by descending score
-    long long* poff;               // p + 1: first perm entry of each row
-    unsigned long long perm_cap;
+    int* perm;                     // perm[off_i + v]: row position of the row's v-th candidate
+    int* iperm;                    // iperm[off_i + c]: order position of row position c
+    int* vrank;                    // old slot -> order position in its new row (incremental A'_G)
     // level 1 by conditioning variable: row k of C staged in shared memory
     unsigned barrier_ns;           // 0: grid-barrier waits end after kBarrierNs; else a test of
                                    // the expiry path: CTA 0 withholds its arrival at the first
@@ -253,8 +254,8 @@ cudaError_t launch_mlp_apply(float* P, float* M, float* V, const float* gpart, i
                              float lr, void* Pb, cudaStream_t st);
 cudaError_t launch_mlp_to_bf16(const float* P, void* Pb, cudaStream_t st);
 cudaError_t launch_mlp_forward(const void* Pb, const float* X, long long N, float* y, cudaStream_t st);
-cudaError_t launch_mlp_examples(const float* C, long long p, const int* q, long long n, float* X, float* t,
-                                cudaStream_t st);
+cudaError_t launch_mlp_examples(const float* C, long long p, const int* nbs, const int* q, long long n, float* X,
+                                float* t, cudaStream_t st);
 
 
 }  // namespace cupc

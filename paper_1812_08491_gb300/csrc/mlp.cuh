@@ -1,8 +1,12 @@
 // mlp.cuh -- the candidate-scoring network used to order conditioning subsets.
 //
-// A candidate k for edge side (i, j) at level l is described by
-//   x = (|C_ik|, |C_jk|, |C_ij|, l / 8, |rho_ij.k|),
-// rho_ij.k the first-order partial correlation; the network is
+// A candidate k of row i at level l (a neighbour of i in A'_G) is described by
+//   x = (|C_ik|, mean_j |C_jk|, mean_j |C_ij|, l / 8, mean_j |rho_ij.k|),
+// the means over the row's other neighbours j (rho_ij.k the first-order partial
+// correlation). At level 1 the two terms that need every C_jk of the row -- as
+// many reads as the level's own tests -- are 0. One score per (row, candidate)
+// gives one order per row, so the tests of a row still share each subset S
+// across its j. The network is
 //   h1 = relu(W1 x + b1) (64), h2 = relu(W2 h1 + b2) (64), y = w3 . h2 + b3.
 // Parameters are packed W1 (64x5), b1, W2 (64x64), b2, w3, b3 (row-major).
 // Training keeps FP32 master weights; scoring reads their bf16 rounding with
@@ -22,16 +26,49 @@ constexpr int MLP_OFF_W3 = MLP_OFF_B2 + MLP_H;
 constexpr int MLP_OFF_B3 = MLP_OFF_W3 + MLP_H;
 constexpr int MLP_NP = MLP_OFF_B3 + 1;  // 4609
 
-// Features of candidate k for side (i, j) from correlations cij = C_ij,
-// cik = C_ik, cjk = C_jk (FP32).
-__device__ __forceinline__ void mlp_features(float cij, float cik, float cjk, int l, float (&x)[MLP_IN])
+// |rho_ij.k| from cij = C_ij, cik = C_ik, cjk = C_jk (FP32); 1 when a
+// conditional variance vanishes.
+__device__ __forceinline__ float mlp_rho1(float cij, float cik, float cjk)
+{
+    const float den = (1.f - cik * cik) * (1.f - cjk * cjk);
+    return den > 1e-12f ? fabsf((cij - cik * cjk) * rsqrtf(den)) : 1.f;
+}
+
+// Features of candidate k of row i at level l: cik = C_ik; mjk, mij, mrho the
+// means over the row's other neighbours j of |C_jk|, |C_ij| and |rho_ij.k|
+// (0 for mjk and mrho at level 1).
+__device__ __forceinline__ void mlp_features(float cik, float mjk, float mij, int l, float mrho, float (&x)[MLP_IN])
 {
     x[0] = fabsf(cik);
-    x[1] = fabsf(cjk);
-    x[2] = fabsf(cij);
+    x[1] = mjk;
+    x[2] = mij;
     x[3] = (float)l * 0.125f;
-    const float den = (1.f - cik * cik) * (1.f - cjk * cjk);
-    x[4] = den > 1e-12f ? fabsf((cij - cik * cjk) * rsqrtf(den)) : 1.f;
+    x[4] = mrho;
+}
+
+// Features of candidate c (position in the row's neighbour list nb[0..d)) of
+// row i at level l, from the FP32 correlation row accessor C(a, b): the means
+// run over the row's other neighbours.
+template <typename CF>
+__device__ __forceinline__ void mlp_row_features(CF C, int i, const int* nb, int d, int c, int l, float sum_abs_cij,
+                                                 float (&x)[MLP_IN])
+{
+    const int k = nb[c];
+    const float cik = C(i, k);
+    const float mij = d > 1 ? (sum_abs_cij - fabsf(cik)) / (float)(d - 1) : 0.f;
+    float mjk = 0.f, mrho = 0.f;
+    if (l >= 2 && d > 1) {
+        for (int u = 0; u < d; ++u) {
+            if (u == c) continue;
+            const int j = nb[u];
+            const float cjk = C(j, k);
+            mjk += fabsf(cjk);
+            mrho += mlp_rho1(C(i, j), cik, cjk);
+        }
+        mjk /= (float)(d - 1);
+        mrho /= (float)(d - 1);
+    }
+    mlp_features(cik, mjk, mij, l, mrho, x);
 }
 
 // Score of one candidate with weights W (bf16, packed as above) in shared or

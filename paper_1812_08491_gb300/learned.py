@@ -1,12 +1,12 @@
 """Training data and training driver for the candidate-scoring network.
 
-The network (5 -> 64 -> 64 -> 1, kernels in csrc/k_mlp.cu) scores a candidate
-conditioning variable k for an edge side (i, j) at level l >= 2; the level
-kernel enumerates subsets in the order of descending score. The examples come
-from the separating sets the plain method stores (cupc_mlp_examples: the side
-whose frozen neighbourhood holds S, one example per candidate, labelled 1 iff
-the candidate is in S, features computed on the device by the kernels' own
-feature code).
+The network (5 -> 64 -> 64 -> 1, kernels in csrc/k_mlp.cu) scores each
+candidate k of a row i of A'_G at level l >= 1; the level kernel enumerates the
+row's subsets in the order of descending score. The examples come from the
+separating sets the plain method stores (cupc_mlp_examples: the side whose
+frozen neighbourhood holds S, one example per candidate of that row other than
+the other endpoint, labelled 1 iff the candidate is in S, features computed on
+the device by the kernels' own feature code).
 
 This module only marshals: it runs the library calls per problem, concatenates
 their device tensors, shuffles them with a seeded permutation and seeds the
@@ -30,20 +30,25 @@ def init_weights(seed: int = 0) -> np.ndarray:
     return np.concatenate([w1.ravel(), np.zeros(HIDDEN), w2.ravel(), np.zeros(HIDDEN), w3, [0.0]]).astype(np.float32)
 
 
-def collect(ctx, problems, mode=None):
+def collect(ctx, problems, mode=None, per_problem=None, seed=0):
     """Examples (device tensors X [m x 5], t [m]) from the plain method's
-    canonical SepSets on each problem."""
+    canonical SepSets on each problem; with per_problem, a seeded sample of at
+    most that many examples of each problem."""
     import torch
 
     import paper_1812_08491_gb300 as cupc
     mode = cupc.MODE_PLAIN_FP64 if mode is None else mode
+    rng = np.random.default_rng(seed)
     xs, ts = [], []
     for s in problems:
-        X = torch.from_numpy(s.Xt).cuda().T
+        X = torch.from_numpy(np.ascontiguousarray(s.Xt)).cuda().T
         res = ctx.skeleton(X, s.alpha, mode=mode, canonical=True)
         C32 = ctx.correlation(X, cupc.F32)
         Xe, te = res.mlp_examples(C32)
         res.free()
+        if per_problem is not None and Xe.shape[0] > per_problem:
+            pick = torch.from_numpy(np.sort(rng.choice(Xe.shape[0], per_problem, replace=False))).cuda()
+            Xe, te = Xe[pick], te[pick]
         xs.append(Xe)
         ts.append(te)
     return torch.cat(xs), torch.cat(ts)

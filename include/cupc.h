@@ -147,6 +147,10 @@ typedef struct {
                                                     buffer overflowed: [0] level 0's recheck
                                                     queue, [1] A'_G's slots, [2] the SepSet
                                                     pool, [3] a level >= 1 recheck queue */
+    float order_ms[CUPC_STATS_LEVELS][2];        /* learned order, per level >= 1: scoring
+                                                    the candidates and ranking them (device
+                                                    clock, within the compaction phase; 0
+                                                    where the level scored nothing) */
 } cupc_stats;
 
 typedef struct cupc_ctx cupc_ctx;

@@ -101,7 +101,8 @@ class Stats(ctypes.Structure):
                 ("kernel_ms", ctypes.c_float * 8), ("kernel_count", ctypes.c_int32 * 8),
                 ("ci_block_entries", ctypes.c_int64 * L), ("phase_ms", (ctypes.c_float * 4) * L),
                 ("cuda_graph", ctypes.c_int32), ("recheck_ms", (ctypes.c_float * 3) * L),
-                ("rechecks_queued", ctypes.c_int64 * L), ("reruns", ctypes.c_int32 * 4)]
+                ("rechecks_queued", ctypes.c_int64 * L), ("reruns", ctypes.c_int32 * 4),
+                ("order_ms", (ctypes.c_float * 2) * L)]
 
 
 class OrientStats(ctypes.Structure):
@@ -217,7 +218,8 @@ def _stats_dict(s: Stats) -> dict:
             "ci_block_entries": list(s.ci_block_entries[:L]),
             "phase_ms": [list(s.phase_ms[q]) for q in range(L)], "cuda_graph": s.cuda_graph,
             "recheck_ms": [list(s.recheck_ms[q]) for q in range(L)],
-            "rechecks_queued": list(s.rechecks_queued[:L]), "reruns": list(s.reruns)}
+            "rechecks_queued": list(s.rechecks_queued[:L]), "reruns": list(s.reruns),
+            "order_ms": [list(s.order_ms[q]) for q in range(L)]}
 
 
 class Result:

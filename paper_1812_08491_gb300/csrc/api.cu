@@ -642,13 +642,17 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             LP.barrier_ns = 0;
             if (o.learned_order) {
                 // each A'_G row's order and its inverse, one entry per slot; the
-                // order positions of an incremental A'_G's survivors
+                // order positions of an incremental A'_G's survivors; the scores
                 if ((s = ensure(ctx, *ctx_buf(ctx, "perm"), (size_t)nnz_cap * 4)) != CUPC_OK) return s;
                 if ((s = ensure(ctx, *ctx_buf(ctx, "iperm"), (size_t)nnz_cap * 4)) != CUPC_OK) return s;
                 if ((s = ensure(ctx, *ctx_buf(ctx, "vrank"), (size_t)nnz_cap * 4)) != CUPC_OK) return s;
+                if ((s = ensure(ctx, *ctx_buf(ctx, "lscore"), (size_t)nnz_cap * 4)) != CUPC_OK) return s;
+                if ((s = ensure(ctx, *ctx_buf(ctx, "lrsum"), (size_t)p * 4)) != CUPC_OK) return s;
                 LP.perm = (int*)ctx_buf(ctx, "perm")->p;
                 LP.iperm = (int*)ctx_buf(ctx, "iperm")->p;
                 LP.vrank = (int*)ctx_buf(ctx, "vrank")->p;
+                LP.lscore = (float*)ctx_buf(ctx, "lscore")->p;
+                LP.lrsum = (float*)ctx_buf(ctx, "lrsum")->p;
                 LP.mlp_w = ctx_buf(ctx, "mlp_Pb")->p;
             }
         }
@@ -765,6 +769,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
                 for (int c = 0; c < 4; ++c) H.phase_ns[q][c] = 0;
                 for (int c = 0; c < RND; ++c) H.round_hist[q][c] = H.round_cur[q][c] = 0;
                 H.recheck_ns[q][0] = H.recheck_ns[q][1] = H.recheck_ns[q][2] = 0;
+                H.order_ns[q][0] = H.order_ns[q][1] = 0;
                 H.live[q] = 0;
                 H.rc_next[q] = 0;
                 H.maxdeg[q] = 0;
@@ -820,6 +825,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             R->stats.ci_block_entries[l] = (int64_t)H.block_entries[l];
             for (int c = 0; c < 4; ++c) R->stats.phase_ms[l][c] = 1e-6f * (float)H.phase_ns[l][c];
             for (int c = 0; c < 3; ++c) R->stats.recheck_ms[l][c] = 1e-6f * (float)H.recheck_ns[l][c];
+            for (int c = 0; c < 2; ++c) R->stats.order_ms[l][c] = 1e-6f * (float)H.order_ns[l][c];
             R->stats.rechecks_queued[l] = (int64_t)H.queue_len[l];
         }
         for (int l = 1; l < LV; ++l) {

@@ -177,74 +177,82 @@ __device__ void phase_prefix(const LevelParams& P, int skip)
 }
 
 // ---------------------------------------------------------------------------
-// Learned ordering (FP32 mode, levels >= 1). Each row's candidates are scored
-// once per level by the network (features of mlp.cuh: the candidate's
-// correlation with the row variable and means over the row's other
-// neighbours) and enumerated in descending score (ties: increasing position),
-// so the S-shared tests of a row keep sharing each subset across j. The order
-// is a permutation of the row: every subset is still reached, so the skeleton
-// cannot change; the ranks the tests record (and the SepSet the serial order
-// stores) are those of the permuted order. A row with more than MCAP
-// neighbours keeps its increasing order. A level whose A'_G is reused keeps
-// the previous level's order.
+// Learned ordering (FP32 mode, levels >= 1). When a level builds A'_G from the
+// bitset A_G (level 1, and a level run again), every row's candidates are
+// scored by the network (features of mlp.cuh: the candidate's correlation with
+// the row variable and means over the row's other neighbours) and the row is
+// enumerated in descending score (ties: increasing position), so the
+// S-shared tests of a row keep sharing each subset across j. A level that
+// builds A'_G from the previous level's keeps the survivors' relative order,
+// and a reused A'_G keeps its order. The order is a permutation of the row:
+// every subset is still reached, so the skeleton cannot change; the ranks the
+// tests record (and the SepSet the serial order stores) are those of the
+// permuted order. A row with more than kLrnMaxDeg neighbours keeps its
+// increasing order.
 // ---------------------------------------------------------------------------
-constexpr int MCAP = 256;
+constexpr int kLrnMaxDeg = 512;
+// dynamic shared memory of the scoring phase: the weights as FP32
+constexpr size_t kLrnBytes = ((size_t)MLP_NP * sizeof(float) + 15) & ~(size_t)15;
 
-// Orders the d <= MCAP candidates nb[0..d) of row i at level l (one warp):
-// rk[c] = position of candidate c in descending score order. sc and rk are
-// the warp's scratch (shared memory, MCAP entries each); the network's bf16
-// weights are read from global memory.
-__device__ void warp_row_order(const LevelParams& P, int i, const int* nb, int d, int l, float* sc, int* rk)
+// The score of every slot (i, k) of A'_G (candidate k of row i), one thread per
+// slot; the weights are staged in shared memory as FP32 (each weight read by
+// the warp's lanes at once, a broadcast), the row sums of |C_ij| come from the
+// fill phase. The score is mlp_score's, as the forward kernel computes it.
+__device__ void phase_lrn_score(const LevelParams& P, const Csr& A, unsigned char* dyn)
 {
-    const int lane = threadIdx.x & 31;
-    const CView<float> CV = cview<float>(P, i);
-    auto C = [&](int a, int b) { return __ldg(CV.row(a) + b); };
-    const __nv_bfloat16* W = (const __nv_bfloat16*)P.mlp_w;
-    float sum = 0.f;
-    for (int c = lane; c < d; c += 32) sum += fabsf(C(i, nb[c]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    for (int c = lane; c < d; c += 32) {
+    float* Ws = (float*)dyn;
+    const __nv_bfloat16* Wg = (const __nv_bfloat16*)P.mlp_w;
+    for (int q = threadIdx.x; q < MLP_NP; q += NT) Ws[q] = __bfloat162float(Wg[q]);
+    __syncthreads();
+    const long long nnz = A.row_off[P.p];
+    for (long long e = (long long)blockIdx.x * NT + threadIdx.x; e < nnz; e += (long long)gridDim.x * NT) {
+        const int i = A.srow[e];
+        const long long off = A.row_off[i];
+        const int d = (int)(A.row_off[i + 1] - off);
+        if (d > kLrnMaxDeg) continue;
+        const CView<float> CV = cview<float>(P, i);
+        auto C = [&](int a, int b) { return __ldg(CV.row(a) + b); };
         float x[MLP_IN];
-        mlp_row_features(C, i, nb, d, c, l, sum, x);
-        const float y = mlp_score(W, x);
-        sc[c] = (y == y) ? y : -INFINITY;
+        mlp_row_features(C, i, A.cols + off, d, (int)(e - off), P.l, P.lrsum[i], x);
+        const float y = mlp_score(Ws, x);
+        P.lscore[e] = (y == y) ? y : -INFINITY;
     }
-    __syncwarp();
-    for (int c = lane; c < d; c += 32) {
-        const float y = sc[c];
-        int r = 0;
-        for (int c2 = 0; c2 < d; ++c2) {
-            const float y2 = sc[c2];
-            r += (y2 > y) || (y2 == y && c2 < c);
-        }
-        rk[c] = r;
-    }
-    __syncwarp();
 }
 
-// Learned-order scratch of each warp in dynamic shared memory: the row's
-// candidates, their scores and their order positions (MCAP entries each).
-struct LrnWarp {
-    int* nb;
-    float* sc;
-    int* rk;
-};
-constexpr size_t kLrnBytes = (size_t)NW * 3 * MCAP * sizeof(int);
-
-__device__ __forceinline__ LrnWarp lrn_warp(unsigned char* dyn)
+// Each slot's position in its row's order: iperm, and perm as its inverse.
+__device__ void phase_lrn_rank(const LevelParams& P, const Csr& A)
 {
-    int* base = (int*)dyn + (size_t)(threadIdx.x >> 5) * 3 * MCAP;
-    return LrnWarp{base, (float*)(base + MCAP), base + 2 * MCAP};
+    const long long nnz = A.row_off[P.p];
+    for (long long e = (long long)blockIdx.x * NT + threadIdx.x; e < nnz; e += (long long)gridDim.x * NT) {
+        const int i = A.srow[e];
+        const long long off = A.row_off[i];
+        const int d = (int)(A.row_off[i + 1] - off);
+        const int c = (int)(e - off);
+        int v = c;
+        if (d <= kLrnMaxDeg) {
+            // (plain loads: the scores were written before the grid barrier and
+            // this SM has not read them in this launch)
+            const float* sc = P.lscore + off;
+            const float y = sc[c];
+            v = 0;
+#pragma unroll 8
+            for (int u = 0; u < d; ++u) {
+                const float y2 = sc[u];
+                v += (y2 > y) || (y2 == y && u < c);
+            }
+        }
+        P.iperm[e] = v;
+        P.perm[off + v] = c;
+    }
 }
 
 // P1 of a level whose A'_G is built from the previous level's (old buffer O):
 // per old row, the position of each surviving slot among the row's survivors
 // (-1 for a removed edge), from the alive flags the previous level's removal
-// phase wrote. Same CTA split as phase_prefix. LRN: the survivors (the new
-// row) are also scored, and vrank holds each survivor's order position.
+// phase wrote. Same CTA split as phase_prefix. LRN: also each survivor's
+// position among the survivors in the old row's learned order (vrank).
 template <bool LRN>
-__device__ void phase_rank(const LevelParams& P, const Csr& O, int skip, unsigned char* dyn)
+__device__ void phase_rank(const LevelParams& P, const Csr& O, int skip)
 {
     const int lane = threadIdx.x & 31;
     const int nb = (skip && gridDim.x > 1) ? gridDim.x - 1 : gridDim.x;
@@ -254,28 +262,23 @@ __device__ void phase_rank(const LevelParams& P, const Csr& O, int skip, unsigne
     for (int i = gw; i < P.p; i += nwarps) {
         const long long off = O.row_off[i], end = O.row_off[i + 1];
         int base = 0;
-        LrnWarp L{};
-        if (LRN) L = lrn_warp(dyn);
         for (long long e0 = off; e0 < end; e0 += 32) {
             const long long e = e0 + lane;
             const bool a = e < end && P.alive[e] != 0;
             const unsigned m = __ballot_sync(0xffffffffu, a);
-            const int r = base + __popc(m & ((1u << lane) - 1u));
-            if (e < end) P.nrank[e] = a ? r : -1;
-            if (LRN && a && r < MCAP) L.nb[r] = O.cols[e];
+            if (e < end) P.nrank[e] = a ? base + __popc(m & ((1u << lane) - 1u)) : -1;
             base += __popc(m);
         }
         if (LRN) {
-            const bool ord = base <= MCAP;        // (warp-uniform)
-            if (ord) {
-                __syncwarp();
-                warp_row_order(P, i, L.nb, base, P.l, L.sc, L.rk);
+            base = 0;
+            for (long long v0 = off; v0 < end; v0 += 32) {
+                const long long v = v0 + lane;
+                const long long e = v < end ? off + P.perm[v] : 0;
+                const bool a = v < end && P.alive[e] != 0;
+                const unsigned m = __ballot_sync(0xffffffffu, a);
+                if (a) P.vrank[e] = base + __popc(m & ((1u << lane) - 1u));
+                base += __popc(m);
             }
-            for (long long e = off + lane; e < end; e += 32) {
-                const int r = P.nrank[e];          // (this lane's own store)
-                if (r >= 0) P.vrank[e] = ord ? L.rk[r] : r;
-            }
-            __syncwarp();                          // the scratch is free for the next row
         }
     }
 }
@@ -728,8 +731,7 @@ __device__ void phase_items(const LevelParams& P, const Csr& A)
 }
 
 template <typename T, bool LRN>
-__device__ void phase_fill(const LevelParams& P, const Csr& A, const Csr& O, bool reuse, bool incr, bool pivot,
-                           unsigned char* dyn)
+__device__ void phase_fill(const LevelParams& P, const Csr& A, const Csr& O, bool reuse, bool incr, bool pivot)
 {
     const int lane = threadIdx.x & 31;
     if (incr) {
@@ -744,7 +746,8 @@ __device__ void phase_fill(const LevelParams& P, const Csr& A, const Csr& O, boo
         long long rb;
         word_range(P, i, wlo, whi, rb);
         const ProbDesc* Di = prob_of(P.vprob, P.probs, i);   // every neighbour is in i's problem
-        const T* Crow = pivot ? cview<T>(P, i).row(i) : nullptr;
+        const T* Crow = (pivot || LRN) ? cview<T>(P, i).row(i) : nullptr;
+        float rs = 0.f;                            // LRN: sum of |C_ij| over the row
         for (int w0 = wlo; w0 < whi; w0 += 32) {
             const int q = w0 + lane;
             unsigned word = (q < whi) ? P.bits[rb + q] : 0u;
@@ -768,28 +771,15 @@ __device__ void phase_fill(const LevelParams& P, const Csr& A, const Csr& O, boo
                 A.partner[pos] = (int)(A.row_off[j] + P.wpre[rbj + (i >> 5)] +
                                        __popc(wj & ((1u << (i & 31)) - 1u)));
                 if (pivot) ((T*)P.cval)[pos] = Crow[j];
+                if (LRN) rs += fabsf((float)Crow[j]);
                 ++pos;
             }
             base += __shfl_sync(0xffffffffu, incl, 31);
         }
         if (LRN) {
-            // the row's order (the warp's own stores of the row are visible after the sync)
-            __syncwarp();
-            const LrnWarp L = lrn_warp(dyn);
-            const long long off = A.row_off[i];
-            const int d = (int)(A.row_off[i + 1] - off);
-            const bool ord = d <= MCAP;            // (warp-uniform)
-            if (ord) {
-                for (int c = lane; c < d; c += 32) L.nb[c] = A.cols[off + c];
-                __syncwarp();
-                warp_row_order(P, i, L.nb, d, P.l, L.sc, L.rk);
-            }
-            for (int c = lane; c < d; c += 32) {
-                const int v = ord ? L.rk[c] : c;
-                P.iperm[off + c] = v;
-                P.perm[off + v] = c;
-            }
-            __syncwarp();                          // the scratch is free for the next row
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+            if (lane == 0) P.lrsum[i] = rs;
         }
     }
     if (!pivot) phase_items(P, A);
@@ -1793,7 +1783,9 @@ __device__ __forceinline__ void signal_host(const LevelParams& P, int v)
 }
 
 template <typename T, int LB, bool FP32, bool LEARNED>
-__global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
+// (two CTAs per SM at level 1, except with the learned order, whose scoring
+// keeps a candidate's 64 hidden units in registers)
+__global__ void __launch_bounds__(NT, (LB == 1 && !LEARNED) ? 2 : 1) k_level(LevelParams P)
 {
     LevelMeta* lm = P.lm;
     const int l = P.l;
@@ -1840,8 +1832,8 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
         if (blockIdx.x == 0) phase_scan_one(P, A);
         if (!reuse && (blockIdx.x != 0 || gridDim.x == 1)) {
             if (incr) {
-                if (lrn) phase_rank<LEARNED>(P, O, 1, dyn_smem);
-                else phase_rank<false>(P, O, 1, dyn_smem);
+                if (lrn) phase_rank<LEARNED>(P, O, 1);
+                else phase_rank<false>(P, O, 1);
             } else {
                 phase_prefix(P, 1);
             }
@@ -1849,8 +1841,8 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
     } else {
         phase_scan_a(P);
         if (incr) {
-            if (lrn) phase_rank<LEARNED>(P, O, 0, dyn_smem);
-            else phase_rank<false>(P, O, 0, dyn_smem);
+            if (lrn) phase_rank<LEARNED>(P, O, 0);
+            else phase_rank<false>(P, O, 0);
         } else if (!reuse) {
             phase_prefix(P, 0);
         }
@@ -1873,9 +1865,23 @@ __global__ void __launch_bounds__(NT, LB == 1 ? 2 : 1) k_level(LevelParams P)
         if (!grid_sync(P)) return;
     }
     const bool pivot = (LB == 1) && l == 1 && P.l1_pivot;
-    if (lrn) phase_fill<T, LEARNED>(P, A, O, reuse, incr, pivot, dyn_smem);
-    else phase_fill<T, false>(P, A, O, reuse, incr, pivot, dyn_smem);
+    if (lrn) phase_fill<T, LEARNED>(P, A, O, reuse, incr, pivot);
+    else phase_fill<T, false>(P, A, O, reuse, incr, pivot);
     if (!grid_sync(P)) return;
+    if (LEARNED && lrn && !reuse && !incr) {
+        // an A'_G built from the bitset: score and order its rows
+        unsigned long long s0 = 0, s1 = 0;
+        if (timer) s0 = gtimer();
+        phase_lrn_score(P, A, dyn_smem);
+        if (!grid_sync(P)) return;
+        if (timer) s1 = gtimer();
+        phase_lrn_rank(P, A);
+        if (!grid_sync(P)) return;
+        if (timer) {
+            lm->order_ns[l][0] += s1 - s0;
+            lm->order_ns[l][1] += gtimer() - s1;
+        }
+    }
     if (timer) {
         lm->csr_level = l;
         lm->learned_on[l] = lrn ? 1 : 0;

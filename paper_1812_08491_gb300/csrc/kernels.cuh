@@ -24,6 +24,7 @@ struct LevelMeta {
     unsigned long long queue_len[LV];      // recheck entries pushed (may exceed capacity)
     unsigned long long block_entries[LV];  // sum over rows with work of (n'_i + 1)^2
     unsigned long long phase_ns[LV][4];    // compaction, CI, recheck, finalisation (wall ns)
+    unsigned long long order_ns[LV][2];    // learned order: scoring, ranking (wall ns)
     unsigned long long recheck_ns[LV][3];  // recheck partial sums, combine (wall ns, all batches),
                                            // and block 0's own partial-sum work
     int maxdeg[LV];
@@ -148,6 +149,8 @@ struct LevelParams {
     int* perm;                     // perm[off_i + v]: row position of the row's v-th candidate
     int* iperm;                    // iperm[off_i + c]: order position of row position c
     int* vrank;                    // old slot -> order position in its new row (incremental A'_G)
+    float* lscore;                 // per slot: the network's score of the candidate
+    float* lrsum;                  // per row: sum of |C_ij| over the row's neighbours
     // level 1 by conditioning variable: row k of C staged in shared memory
     unsigned barrier_ns;           // 0: grid-barrier waits end after kBarrierNs; else a test of
                                    // the expiry path: CTA 0 withholds its arrival at the first

@@ -71,26 +71,31 @@ __device__ __forceinline__ void mlp_row_features(CF C, int i, const int* nb, int
     mlp_features(cik, mjk, mij, l, mrho, x);
 }
 
-// Score of one candidate with weights W (bf16, packed as above) in shared or
-// global memory; FP32 accumulation.
-__device__ __forceinline__ float mlp_score(const __nv_bfloat16* __restrict__ W, const float (&x)[MLP_IN])
+__device__ __forceinline__ float mlp_wval(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float mlp_wval(float v) { return v; }
+
+// Score of one candidate with weights W (packed as above; bf16, or their FP32
+// copy, which gives the same score) in shared or global memory; FP32
+// accumulation.
+template <typename WT>
+__device__ __forceinline__ float mlp_score(const WT* __restrict__ W, const float (&x)[MLP_IN])
 {
     float h1[MLP_H];
 #pragma unroll
     for (int o = 0; o < MLP_H; ++o) {
-        float a = __bfloat162float(W[MLP_OFF_B1 + o]);
+        float a = mlp_wval(W[MLP_OFF_B1 + o]);
 #pragma unroll
-        for (int c = 0; c < MLP_IN; ++c) a = fmaf(__bfloat162float(W[MLP_OFF_W1 + o * MLP_IN + c]), x[c], a);
+        for (int c = 0; c < MLP_IN; ++c) a = fmaf(mlp_wval(W[MLP_OFF_W1 + o * MLP_IN + c]), x[c], a);
         h1[o] = fmaxf(a, 0.f);
     }
-    float y = __bfloat162float(W[MLP_OFF_B3]);
+    float y = mlp_wval(W[MLP_OFF_B3]);
 #pragma unroll 4
     for (int o = 0; o < MLP_H; ++o) {
-        float a = __bfloat162float(W[MLP_OFF_B2 + o]);
-        const __nv_bfloat16* row = W + MLP_OFF_W2 + o * MLP_H;
+        float a = mlp_wval(W[MLP_OFF_B2 + o]);
+        const WT* row = W + MLP_OFF_W2 + o * MLP_H;
 #pragma unroll
-        for (int k = 0; k < MLP_H; ++k) a = fmaf(__bfloat162float(row[k]), h1[k], a);
-        y = fmaf(__bfloat162float(W[MLP_OFF_W3 + o]), fmaxf(a, 0.f), y);
+        for (int k = 0; k < MLP_H; ++k) a = fmaf(mlp_wval(row[k]), h1[k], a);
+        y = fmaf(mlp_wval(W[MLP_OFF_W3 + o]), fmaxf(a, 0.f), y);
     }
     return y;
 }

@@ -485,7 +485,7 @@ cupc_status cupc_pcor_data(cupc_ctx* ctx, const void* X, int dtype, int layout, 
  * (|C_ik|, mean |C_jk|, mean |C_ij|, l/8, mean |rho_ij.k|), with the two terms
  * that need C_jk set to 0 at level 1, through 5 -> 64 -> 64 -> 1 with ReLU to a
  * score; with opts->learned_order, every level l >= 1 enumerates the subsets
- * of each row with at most 256 neighbours over its neighbours sorted by
+ * of each row with at most 512 neighbours over its neighbours sorted by
  * descending score (ties: increasing index), lexicographic over the sorted
  * positions: every subset is still reachable, so the skeleton is unchanged,
  * and the SepSet stored is the first separating set in that order. A larger

@@ -470,7 +470,7 @@ def sweep_report(ctx, dev, graphs, max_level=2, parity=True):
     import paper_1812_08491_gb300 as cupc
     from synth import sem
     for q, (p, m, d) in enumerate(SWEEP_POINTS):
-        dev_ms, wall_ms, tests, edges, parity = [], [], [], [], None
+        dev_ms, wall_ms, tests, edges, match = [], [], [], [], None
         for g in range(graphs):
             s = sem.paper_density_signed(p, m, d, 6000000 + 1000 * q + g, max_level=max_level)
             X = torch.from_numpy(s.Xt).to(dev).T
@@ -488,7 +488,7 @@ def sweep_report(ctx, dev, graphs, max_level=2, parity=True):
                 t1 = time.perf_counter()
                 C = oracle.correlation(s.X, nthreads=os.cpu_count() or 1)
                 ref = oracle.pc_stable(C, s.n, s.alpha, max_level=max_level, nthreads=os.cpu_count() or 1)
-                parity = {"identical": bool(np.array_equal(r.adjacency(), ref.adj)
+                match = {"identical": bool(np.array_equal(r.adjacency(), ref.adj)
                                             and np.array_equal(r.sep_levels(), ref.sep_level)
                                             and r.sepsets() == ref.sepsets
                                             and st["serial_tests"][:ref.levels_run] == list(ref.tests)),
@@ -501,7 +501,7 @@ def sweep_report(ctx, dev, graphs, max_level=2, parity=True):
                           "wall_ms_mean": round(float(np.mean(wall_ms)), 3),
                           "serial_tests_mean": int(np.mean(tests)), "edges_mean": int(np.mean(edges)),
                           "serial_tests_per_s": float(np.sum(tests) / (np.sum(dev_ms) * 1e-3)),
-                          "parity_graph0": parity if parity is not None else "oracle not run at this size",
+                          "parity_graph0": match if match is not None else "oracle not run at this size",
                           "generator": "paper_density_signed (Sec. 5.6 structure, signed weights, unit variance)"}),
               flush=True)
 

@@ -507,6 +507,7 @@ def sweep_report(ctx, dev, graphs, max_level=2, parity=True):
 
 
 BATCH_WORKLOADS = {"batch64": 64}
+L1_FORMS = {"auto": 0, "pivot": 1, "row": 2}   # cupc_options.level1_form
 
 
 def _batch_config(name, probs, form):
@@ -569,7 +570,7 @@ def main_batch(args, world, rank, local, dist):
     probs = sem.batch_workload(BATCH_WORKLOADS[args.workload], 0)
     alphas = [s.alpha for s in probs]
     Xd = [torch.from_numpy(s.Xt.astype(np.float32)).to(dev).T for s in probs]   # variable-major n x p
-    ctx = cupc.Context(local)
+    ctx = cupc.Context(local, level1_form=L1_FORMS[args.level1])
     if args.once:
         rs, st = ctx.skeleton_batch(Xd, alphas, batch_direct=True)
         for r in rs:
@@ -725,6 +726,8 @@ def main():
                     help="run the scalability sweep of Sec. 5.6 (levels 0-2) and print one line per point, then exit")
     ap.add_argument("--sweep-graphs", type=int, default=3, help="graphs per sweep point (the paper uses 10)")
     ap.add_argument("--sweep-no-parity", action="store_true", help="sweep without the oracle runs")
+    ap.add_argument("--level1", default="auto", choices=sorted(L1_FORMS),
+                    help="level-1 form: the library's choice, by conditioning variable (pivot) or by row")
     ap.add_argument("--once", action="store_true",
                     help="run one skeleton of the workload and print its per-level stats (the command profiled)")
     args = ap.parse_args()
@@ -756,7 +759,7 @@ def main():
     s = sem.workload(args.workload)
     Xd = torch.from_numpy(s.Xt).to(dev)          # p x n rows; X = Xd.T is variable-major n x p
     X = Xd.T
-    ctx = cupc.Context(local)
+    ctx = cupc.Context(local, level1_form=L1_FORMS[args.level1])
     mode = cupc.MODE_FP32_RECHECK if args.mode == "fp32" else cupc.MODE_PLAIN_FP64
     if args.once:
         r = ctx.skeleton(X, s.alpha, mode=mode, canonical=True, max_level=s.max_level)

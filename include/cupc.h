@@ -104,7 +104,19 @@ typedef struct {
                                 slots (twice the edges of the densest level) */
     int test_rec_cap;        /* testing: when > 0, the initial capacity of the SepSet
                                 record pool, in int32 */
+    int level1_form;         /* how level 1 runs its tests (same results either way):
+                                CUPC_L1_AUTO (default) lets the library choose (the
+                                row form, measured faster on GB300 on every workload
+                                of 10^3 to 10^4 variables and on batches);
+                                CUPC_L1_BY_PIVOT walks, for each conditioning variable
+                                k, the rows of k's neighbours with row k of C staged
+                                in shared memory (every C row read once; needs the
+                                row to fit 96 KB of shared memory, else as
+                                CUPC_L1_BY_ROW); CUPC_L1_BY_ROW shares each subset
+                                {k} of a row across its j and gathers C entries
+                                through the caches */
 } cupc_options;
+enum { CUPC_L1_AUTO = 0, CUPC_L1_BY_PIVOT = 1, CUPC_L1_BY_ROW = 2 };
 /* The three test capacities exist to exercise the recovery paths: a level
  * whose buffer would overflow reports it, the buffer is enlarged and the
  * affected levels run again (cupc_stats.reruns counts the reruns by cause).

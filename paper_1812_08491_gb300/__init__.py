@@ -24,6 +24,7 @@ F32, F64 = 0, 1
 FAIL_NONE, FAIL_ALLOC, FAIL_LAUNCH, FAIL_BARRIER = 0, 1, 2, 3
 SAMPLE_MAJOR, VARIABLE_MAJOR = 0, 1
 MODE_PLAIN_FP64, MODE_FP32_RECHECK = 0, 1
+L1_AUTO, L1_BY_PIVOT, L1_BY_ROW = 0, 1, 2          # cupc_options.level1_form
 MAX_LEVEL = 16
 STATS_LEVELS = 24
 KERNEL_CLASSES = ("upload", "standardize", "correlation", "level0", "compact", "ci", "recheck", "finalize")
@@ -87,7 +88,7 @@ class Options(ctypes.Structure):
                 ("max_level", ctypes.c_int), ("recheck_margin", ctypes.c_double),
                 ("threads_per_block", ctypes.c_int), ("chunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("corr_kps", ctypes.c_int), ("batch_direct", ctypes.c_int), ("test_qcap", ctypes.c_int),
-                ("test_nnz_cap", ctypes.c_int), ("test_rec_cap", ctypes.c_int)]
+                ("test_nnz_cap", ctypes.c_int), ("test_rec_cap", ctypes.c_int), ("level1_form", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -347,7 +348,9 @@ class Result:
 class Context:
     """A library context bound to one CUDA device and stream."""
 
-    def __init__(self, device: int = 0, stream=None):
+    def __init__(self, device: int = 0, stream=None, level1_form: int = L1_AUTO):
+        """level1_form: the default of options(level1_form=...) for this context."""
+        self.level1_form = level1_form
         L = load()
         if stream is None:
             torch = _torch()
@@ -377,10 +380,9 @@ class Context:
         if st != 0:
             raise CupcError(st, where, self.last_error())
 
-    @staticmethod
-    def options(mode=MODE_FP32_RECHECK, canonical=True, max_level=-1, recheck_margin=0.0,
+    def options(self, mode=MODE_FP32_RECHECK, canonical=True, max_level=-1, recheck_margin=0.0,
                 threads_per_block=0, chunk=0, learned_order=False, ctas_per_sm=0, corr_kps=0,
-                batch_direct=False, test_qcap=0, test_nnz_cap=0, test_rec_cap=0) -> Options:
+                batch_direct=False, test_qcap=0, test_nnz_cap=0, test_rec_cap=0, level1_form=None) -> Options:
         o = Options()
         load().cupc_options_default(ctypes.byref(o))
         o.mode = mode
@@ -396,6 +398,7 @@ class Context:
         o.test_qcap = test_qcap
         o.test_nnz_cap = test_nnz_cap
         o.test_rec_cap = test_rec_cap
+        o.level1_form = self.level1_form if level1_form is None else level1_form
         return o
 
     @staticmethod

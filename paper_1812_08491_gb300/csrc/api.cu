@@ -357,6 +357,8 @@ cupc_status validate_opts(cupc_ctx* ctx, const cupc_options& o)
         return fail(ctx, CUPC_E_INVALID, "threads_per_block must be a multiple of 32 up to 256");
     if (o.chunk < 0) return fail(ctx, CUPC_E_INVALID, "chunk must be >= 0");
     if (o.ctas_per_sm < 0 || o.corr_kps < 0) return fail(ctx, CUPC_E_INVALID, "ctas_per_sm, corr_kps must be >= 0");
+    if (o.level1_form < CUPC_L1_AUTO || o.level1_form > CUPC_L1_BY_ROW)
+        return fail(ctx, CUPC_E_INVALID, "level1_form must be CUPC_L1_AUTO, CUPC_L1_BY_PIVOT or CUPC_L1_BY_ROW");
     return CUPC_OK;
 }
 
@@ -558,7 +560,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             if ((s = ensure(ctx, *ctx_buf(ctx, "nrank"), (size_t)nnz_cap * 4)) != CUPC_OK) return s;
             // level 1 by conditioning variable when a C row fits the staging buffer
             const size_t ce = fp32 ? 4 : 8;
-            const int l1_pivot = l1_buffers(p, (int)ce);
+            const int l1_pivot = level1_by_pivot(o.level1_form) ? l1_buffers(p, (int)ce) : 0;
             if (l1_pivot && (s = ensure(ctx, *ctx_buf(ctx, "cval"), (size_t)nnz_cap * ce)) != CUPC_OK) return s;
             if ((s = ensure(ctx, ctx->item_row, (size_t)item_cap * 4)) != CUPC_OK) return s;
             if ((s = ensure(ctx, *ctx_buf(ctx, "item_c"), (size_t)item_cap * 4)) != CUPC_OK) return s;

@@ -32,7 +32,7 @@ namespace {
 
 struct BatchKey {
     int nprob = 0, dtype = 0, layout = 0, on_device = 0;
-    int canonical = 0, max_level = 0, chunk = 0, ctas = 0, kps = 0, direct = 0;
+    int canonical = 0, max_level = 0, chunk = 0, ctas = 0, kps = 0, direct = 0, l1form = 0;
     double margin = 0.0;
     std::vector<int64_t> n, p;
     std::vector<double> alpha;
@@ -40,7 +40,7 @@ struct BatchKey {
     {
         return nprob == o.nprob && dtype == o.dtype && layout == o.layout && on_device == o.on_device &&
                canonical == o.canonical && max_level == o.max_level && chunk == o.chunk && ctas == o.ctas &&
-               kps == o.kps && direct == o.direct && margin == o.margin && n == o.n && p == o.p &&
+               kps == o.kps && direct == o.direct && l1form == o.l1form && margin == o.margin && n == o.n && p == o.p &&
                alpha == o.alpha;
     }
 };
@@ -339,7 +339,7 @@ cupc_status issue(cupc_ctx* ctx, BatchPlan& B, cudaStream_t st, bool capturing)
     LP.nnz_cap = B.nnz_cap;
     LP.C = B.c32.p;
     // level 1 by conditioning variable when the largest problem's C row fits
-    LP.l1_pivot = l1_buffers(B.pmax, 4);
+    LP.l1_pivot = level1_by_pivot(K.l1form) ? l1_buffers(B.pmax, 4) : 0;
     LP.pstage = B.pmax;
     LP.cval = B.cval.p;
     LP.B = B.binom;
@@ -537,6 +537,7 @@ BatchKey make_key(int nprob, int dtype, int layout, int on_device, const int64_t
     k.ctas = o.ctas_per_sm;
     k.kps = o.corr_kps;
     k.direct = o.batch_direct;
+    k.l1form = o.level1_form;
     k.margin = o.recheck_margin;
     k.n.assign(n, n + nprob);
     k.p.assign(p, p + nprob);

@@ -161,6 +161,17 @@ struct LevelParams {
     void* cval;                    // nnz_cap entries (T): C_ij of each CSR slot (i, j)
 };
 
+// Level 1 by conditioning variable (a staged C row per pivot) or by row (S
+// shared across j, C gathered through the caches), for the level1_form
+// option. CUPC_L1_AUTO takes the row form: on GB300 it was the faster one on
+// every workload measured (p = 10^3 to 10^4, and the 64-problem batch), while
+// the pivot form reads each C row from HBM once (5x less DRAM at p = 10^4) but
+// issues more instructions per visited slot.
+inline bool level1_by_pivot(int form)
+{
+    return form == CUPC_L1_BY_PIVOT;
+}
+
 // Tests of a level whose FP64 recheck may be cut into slices over several CTAs.
 constexpr int kRcCnt = 4096;
 

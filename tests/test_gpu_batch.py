@@ -176,6 +176,13 @@ def test_full_batch_workload(ctx):
         assert np.array_equal(r.adjacency(), one.adjacency())
         assert r.sepsets() == one.sepsets()
         assert _trim(r.stats()["serial_tests"]) == _trim(one.stats()["serial_tests"])
+    refs = []
     for k, s in enumerate(probs):
         C = oracle.correlation(Xs[k].astype(np.float64), nthreads=16)
-        _assert_problem(res[k], oracle.pc_stable(C, s.n, s.alpha, nthreads=16))
+        refs.append(oracle.pc_stable(C, s.n, s.alpha, nthreads=16))
+        _assert_problem(res[k], refs[k])
+    # both level-1 forms, explicitly, give the same results
+    for form in (cupc.L1_BY_PIVOT, cupc.L1_BY_ROW):
+        res_f, _ = ctx.skeleton_batch(Xs, [s.alpha for s in probs], level1_form=form)
+        for k in range(len(probs)):
+            _assert_problem(res_f[k], refs[k])

@@ -275,6 +275,25 @@ def test_medium1000_full_size_parity(ctx):
         assert res.stats()["serial_tests"] == ref.tests
 
 
+@pytest.mark.parametrize("name", ["medium1000", "scalefree2500", "large10000"])
+def test_level1_forms_full_size(ctx, name):
+    """Level 1 by conditioning variable (a staged C row per pivot) and by row
+    (each {k} shared across the row's j) run the same tests: both give the
+    oracle's skeleton, removal levels, canonical SepSets and serial counts, in
+    both arithmetic modes (plain mode at p = 10^4 is left out: its FP64 product
+    alone takes ~90 ms per call and the FP32 run covers the level-1 forms)."""
+    s = sem.workload(name)
+    ref = _oracle_full(s)
+    Xd = torch.from_numpy(s.Xt).cuda().T
+    modes = ("fp32",) if name == "large10000" else ("fp32", "plain")
+    for mode in modes:
+        for form in (cupc.L1_BY_PIVOT, cupc.L1_BY_ROW):
+            res = ctx.skeleton(Xd, s.alpha, mode=MODES[mode], max_level=s.max_level, level1_form=form)
+            _assert_same(res, ref)
+            assert res.stats()["serial_tests"] == ref.tests, (mode, form)
+            res.free()
+
+
 def _oracle_full(s, nthreads=16):
     C = oracle.correlation(s.X, nthreads=nthreads)
     return oracle.pc_stable(C, s.n, s.alpha, max_level=s.max_level, nthreads=nthreads)

@@ -70,11 +70,102 @@ __global__ void k_level0(const T* __restrict__ C, int p, int W, double r0, doubl
     }
 }
 
+// Level 0 of one problem on the upper triangle of C only (C is exactly
+// symmetric): a warp owns the 32 x 32 tile of rows 32 bi.. and columns 32 bj..,
+// bi <= bj, reads it row by row (one coalesced 128-byte line per row), and
+// writes word bj of its rows (a ballot per row) and, for bi < bj, word bi of its
+// columns' rows (each lane collects its column's 32 bits). Every bitset word is
+// written by exactly one tile, so no atomics; half of C is read.
+template <typename T, bool FP32>
+__global__ void k_level0_tri(const T* __restrict__ C, int p, int W, double r0, double band0,
+                             unsigned* __restrict__ bits, QEntry* __restrict__ q, unsigned long long qcap,
+                             Meta* meta, long long ntiles)
+{
+    const int lane = threadIdx.x & 31;
+    const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= ntiles) return;
+    // tile t of the upper triangle in row-major order: bi, then bj >= bi
+    int bi = 0;
+    {
+        // rows bi hold W - bi tiles; invert t = bi W - bi (bi - 1) / 2 + (bj - bi)
+        long long lo = 0, hi = W - 1;
+        while (lo < hi) {
+            const long long mid = (lo + hi + 1) >> 1;
+            const long long first = mid * W - mid * (mid - 1) / 2;
+            if (first <= t) lo = mid; else hi = mid - 1;
+        }
+        bi = (int)lo;
+    }
+    const int bj = bi + (int)(t - ((long long)bi * W - (long long)bi * (bi - 1) / 2));
+    const int j = (bj << 5) + lane;
+    const bool jin = j < p;
+    const T hi = (T)(r0 + band0), lo = (T)(r0 - band0);  // FP32 band edges
+    T cv[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        const int i = (bi << 5) + r;
+        cv[r] = (i < p && jin) ? C[(long long)i * p + j] : T(0);
+    }
+    unsigned colmask = 0u;   // bit r: pair (32 bi + r, j) kept
+    unsigned myrow = 0u;     // diagonal tile: row 32 bi + lane's bits towards j > i
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        const int i = (bi << 5) + r;
+        // each pair is decided once, from its i < j side
+        bool keep = false;
+        if (i < p && jin && j > i) {
+            const T c = cv[r] < T(0) ? -cv[r] : cv[r];
+            if (!FP32) {
+                keep = !(c <= (T)r0);
+            } else if (c > hi) {
+                keep = true;
+            } else if (c >= lo) {
+                keep = true;                   // within the band: kept for now, queued
+                const unsigned long long k = atomicAdd(&meta->queue_len, 1ull);
+                if (k < qcap) {
+                    q[k].a = i;
+                    q[k].b = j;
+                    q[k].s = 0ull;
+                }
+            }
+        }
+        const unsigned word = __ballot_sync(0xffffffffu, keep);
+        if (keep) colmask |= 1u << r;
+        if (bi != bj) {
+            if (lane == 0 && i < p) bits[(long long)i * W + bj] = word;
+        } else if (lane == r) {
+            myrow = word;
+        }
+    }
+    if (bi != bj) {
+        // the transposed words: row j's bits towards rows 32 bi ..
+        if (jin) bits[(long long)j * W + bi] = colmask;
+    } else {
+        // diagonal tile: row 32 bi + lane keeps its j > i bits (its ballot) and
+        // its j < i bits (the pairs decided in the earlier rows, collected in
+        // this lane's column mask)
+        const int i = (bi << 5) + lane;
+        if (i < p) bits[(long long)i * W + bi] = myrow | colmask;
+    }
+}
+
 cudaError_t launch_level0(int fp32, const void* C, int p, int W, double r0, double band0, unsigned* bits,
                           QEntry* q, unsigned long long qcap, Meta* meta, cudaStream_t st, const int* vprob,
                           const ProbDesc* probs, int nrows)
 {
-    if (!vprob) nrows = p;
+    if (!vprob) {
+        // one problem: the upper-triangle form
+        const long long ntiles = (long long)W * (W + 1) / 2;
+        const int block = 256;
+        const long long grid = (ntiles * 32 + block - 1) / block;
+        if (fp32)
+            k_level0_tri<float, true><<<(unsigned)grid, block, 0, st>>>((const float*)C, p, W, r0, band0, bits, q,
+                                                                         qcap, meta, ntiles);
+        else
+            k_level0_tri<double, false><<<(unsigned)grid, block, 0, st>>>((const double*)C, p, W, r0, band0, bits,
+                                                                           q, qcap, meta, ntiles);
+        return cudaGetLastError();
+    }
     const int block = 256, grid = (int)(((long long)nrows * 32 + block - 1) / block);
     if (fp32)
         k_level0<float, true><<<grid, block, 0, st>>>((const float*)C, p, W, r0, band0, bits, q, qcap, meta, vprob,

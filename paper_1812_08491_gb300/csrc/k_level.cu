@@ -843,11 +843,23 @@ __device__ void phase_ci(const LevelParams& P, const Csr& A)
     const BinomS BS{sbin};
     const unsigned long long n_items = P.lm->items[l];
     const int chunk = P.lm->chunk[l];
+    // at most one item per warp: warp g takes item g (the shared counter would
+    // only make every warp queue on one atomic to learn that nothing is left)
+    const unsigned long long nwarps = ((unsigned long long)gridDim.x * NT) >> 5;
+    const bool fixed = n_items <= nwarps;
+    const unsigned long long gwarp = ((unsigned long long)blockIdx.x * NT + threadIdx.x) >> 5;
+    bool taken = false;
     unsigned long long ntests = 0;
     for (;;) {
         unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(&P.lm->next_item[l], 1ull);
-        item = __shfl_sync(0xffffffffu, item, 0);
+        if (fixed) {
+            if (taken) break;
+            taken = true;
+            item = gwarp;
+        } else {
+            if (lane == 0) item = atomicAdd(&P.lm->next_item[l], 1ull);
+            item = __shfl_sync(0xffffffffu, item, 0);
+        }
         if (item >= n_items) break;
         const int i = P.item_row[item];
         const long long kr = P.item_c[item];

@@ -300,6 +300,157 @@ __global__ void __launch_bounds__(NT) k_standardize(const T* __restrict__ Xv, lo
         }
 }
 
+// Standardisation of short rows (one problem, n <= kShortRow, at least 1024
+// variables): a warp per variable. With a block per variable, a launch of many short rows waits on
+// each block's reductions and its one finishing thread; a warp per variable
+// keeps as many variables in flight as the GPU holds warps. Same arithmetic as
+// k_standardize: shifted moments of x - K (K = the first sample) in FP64, or in
+// compensated FP32 pairs for FP32 data when no FP64 rows are requested, each
+// lane's elements in order and a fixed xor tree across the lanes; then the
+// mean, 1/sd and the outputs as there.
+constexpr int kShortRow = 4096;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_standardize_warp(const T* __restrict__ Xv, long long ld, int n, int p,
+                                                          double* __restrict__ mu, double* __restrict__ isd,
+                                                          float2* __restrict__ mup, double* __restrict__ z64,
+                                                          long long ldz, __nv_bfloat16* __restrict__ zhi,
+                                                          __nv_bfloat16* __restrict__ zlo, long long ldb, Meta* meta,
+                                                          double inv_n)
+{
+    const int lane = threadIdx.x & 31;
+    const int v = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (v >= p) return;
+    const T* row = Xv + (size_t)v * ld;
+    double* zrow = z64 ? z64 + (size_t)v * ldz : nullptr;
+    const bool fast = (zrow == nullptr);
+    const T Kt = row[0];
+    double S1 = 0.0, S2 = 0.0;
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+        if (fast) {
+            const float K = (float)Kt;
+            float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
+            for (int k0 = lane; k0 < n; k0 += 32 * MU) {
+                float x[MU];
+#pragma unroll
+                for (int u = 0; u < MU; ++u) x[u] = (k0 + u * 32 < n) ? (float)row[k0 + u * 32] : 0.f;
+#pragma unroll
+                for (int u = 0; u < MU; ++u) {
+                    if (k0 + u * 32 >= n) break;
+                    float dh, dl;
+                    two_sum(x[u], -K, dh, dl);
+                    pair_add(ah, al, dh, dl);
+                    const float pp = __fmul_rn(dh, dh);
+                    float q = fmaf(dh, dh, -pp);
+                    q = fmaf(2.f * dh, dl, q);
+                    float ph, pl;
+                    fast_two_sum(pp, q, ph, pl);
+                    pair_add(bh, bl, ph, pl);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float xh = __shfl_xor_sync(0xffffffffu, ah, o), xl = __shfl_xor_sync(0xffffffffu, al, o);
+                const float yh = __shfl_xor_sync(0xffffffffu, bh, o), yl = __shfl_xor_sync(0xffffffffu, bl, o);
+                pair_add(ah, al, xh, xl);
+                pair_add(bh, bl, yh, yl);
+            }
+            S1 = (double)ah + (double)al;
+            S2 = (double)bh + (double)bl;
+            done = true;
+        }
+    }
+    if (!done) {
+        const double Kd = (double)Kt;
+        double s1 = 0.0, s2 = 0.0;
+        for (int k0 = lane; k0 < n; k0 += 32 * MU) {
+            T x[MU];
+#pragma unroll
+            for (int u = 0; u < MU; ++u) x[u] = (k0 + u * 32 < n) ? row[k0 + u * 32] : T(0);
+#pragma unroll
+            for (int u = 0; u < MU; ++u) {
+                if (k0 + u * 32 >= n) break;
+                const double d = (double)x[u] - Kd;
+                s1 += d;
+                s2 = fma(d, d, s2);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        S1 = s1;
+        S2 = s2;
+    }
+    // mean and 1/sd by lane 0, broadcast (the FP64 pipe is narrow)
+    double mean = 0.0, inv = 0.0;
+    float mh = 0.f, ml = 0.f, fi = 0.f;
+    if (lane == 0) {
+        const double K = (double)Kt;
+        const double a = S1 * inv_n;
+        mean = K + a;
+        const double var = fma(-S1, a, S2) * inv_n;
+        const bool ok = (var > 0.0) && isfinite(var) && isfinite(mean);
+        inv = ok ? rsqrt(var) : 0.0;
+        mu[v] = mean;
+        isd[v] = inv;
+        if (!ok) atomicOr(&meta->error, 1);
+        mh = (float)mean;
+        ml = (float)(mean - (double)mh);
+        fi = (float)inv;
+        if (mup) mup[v] = make_float2(mh, ml);
+    }
+    mean = __shfl_sync(0xffffffffu, mean, 0);
+    inv = __shfl_sync(0xffffffffu, inv, 0);
+    mh = __shfl_sync(0xffffffffu, mh, 0);
+    ml = __shfl_sync(0xffffffffu, ml, 0);
+    fi = __shfl_sync(0xffffffffu, fi, 0);
+    unsigned short* hrow = zhi ? (unsigned short*)zhi + (size_t)v * ldb : nullptr;
+    unsigned short* lrow = zlo ? (unsigned short*)zlo + (size_t)v * ldb : nullptr;
+    if (sizeof(T) == 4 && fast) {
+        for (int k0 = lane; k0 < n; k0 += 32 * MU) {
+            T x[MU];
+#pragma unroll
+            for (int u = 0; u < MU; ++u) x[u] = (k0 + u * 32 < n) ? row[k0 + u * 32] : T(0);
+#pragma unroll
+            for (int u = 0; u < MU; ++u) {
+                const int k = k0 + u * 32;
+                if (k >= n) break;
+                const float z = (((float)x[u] - mh) - ml) * fi;
+                const unsigned short h = bf16_bits_rn(z);
+                hrow[k] = h;
+                lrow[k] = bf16_bits_rn(z - bf16_bits_to_float(h));
+            }
+        }
+    } else {
+        for (int k0 = lane; k0 < n; k0 += 32 * MU) {
+            T x[MU];
+#pragma unroll
+            for (int u = 0; u < MU; ++u) x[u] = (k0 + u * 32 < n) ? row[k0 + u * 32] : T(0);
+#pragma unroll
+            for (int u = 0; u < MU; ++u) {
+                const int k = k0 + u * 32;
+                if (k >= n) break;
+                const double d = (double)x[u] - mean;
+                if (zrow) zrow[k] = d * inv;
+                if (hrow) {
+                    const float z = (float)d * fi;
+                    const unsigned short h = bf16_bits_rn(z);
+                    hrow[k] = h;
+                    lrow[k] = bf16_bits_rn(z - bf16_bits_to_float(h));
+                }
+            }
+        }
+    }
+    if (zhi)
+        for (int k = n + lane; k < ldb; k += 32) {
+            hrow[k] = 0;
+            lrow[k] = 0;
+        }
+}
+
 // ---------------------------------------------------------------------------
 // SIMT symmetric product C = Z Z^T * (1/n) over the upper-triangle tiles,
 // mirrored into the lower triangle (so C is exactly symmetric), unit diagonal.
@@ -389,6 +540,19 @@ cudaError_t launch_standardize(int dtype, const void* Xv, long long ld, int n, i
                                Meta* meta, cudaStream_t st, const int* vprob, const ProbDesc* probs)
 {
     constexpr int NT = 256;
+    if (!vprob && n <= kShortRow && p >= 1024) {   // (few variables: a block each is quicker)
+        const unsigned grid = (unsigned)(((long long)p * 32 + NT - 1) / NT);
+        const double inv_n = 1.0 / (double)(n > 0 ? n : 1);
+        if (dtype == CUPC_F64)
+            k_standardize_warp<double><<<grid, NT, 0, st>>>((const double*)Xv, ld, n, p, mu, isd, mup, z64, ldz,
+                                                            (__nv_bfloat16*)zhi, (__nv_bfloat16*)zlo, ldb, meta,
+                                                            inv_n);
+        else
+            k_standardize_warp<float><<<grid, NT, 0, st>>>((const float*)Xv, ld, n, p, mu, isd, mup, z64, ldz,
+                                                           (__nv_bfloat16*)zhi, (__nv_bfloat16*)zlo, ldb, meta,
+                                                           inv_n);
+        return cudaGetLastError();
+    }
     if (dtype == CUPC_F64)
         k_standardize<double, NT><<<p, NT, 0, st>>>((const double*)Xv, ld, n, p, mu, isd, mup, z64, ldz,
                                                     (__nv_bfloat16*)zhi, (__nv_bfloat16*)zlo, ldb, meta, vprob,

@@ -353,7 +353,12 @@ __device__ __forceinline__ void load8(const LevelParams& P, int i0, int hi, int 
     }
 }
 
-// P1 for graphs of at most 32 NT rows: block 0 scans every row while the
+// Rows up to which one CTA scans the degrees (phase_scan_one): beyond it a scan
+// by every CTA (phase_scan_a/b) costs an extra grid barrier but no longer
+// walks all rows in one CTA.
+constexpr int kScanOne = 4096;
+
+// P1 for graphs of at most kScanOne rows: block 0 scans every row while the
 // other CTAs build the word prefixes (no second barrier).
 __device__ void phase_scan_one(const LevelParams& P, const Csr& A)
 {
@@ -1839,7 +1844,10 @@ __global__ void __launch_bounds__(NT, (LB == 1 && !LEARNED) ? 2 : 1) k_level(Lev
     // (a reused A'_G keeps its order)
     const bool lrn = LEARNED && P.learned;
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    const bool one = P.p <= 32 * NT;   // one CTA scans graphs up to 16384 rows (no second barrier)
+    // one CTA scans graphs up to kScanOne rows (no second barrier); larger ones
+    // are scanned by every CTA over its own rows, then offset by the others'
+    // totals after a grid barrier
+    const bool one = P.p <= kScanOne;
     if (one) {
         if (blockIdx.x == 0) phase_scan_one(P, A);
         if (!reuse && (blockIdx.x != 0 || gridDim.x == 1)) {

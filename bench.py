@@ -889,23 +889,27 @@ def main():
         learned_info["fp32_lexicographic_ms_per_step"] = lm_ / args.steps
         learned_info["fp32_learned_ms_per_step"] = ms_per_step
 
-    # end to end through the public call with a pinned host input
+    # end to end through the public call with a pinned host input: the skeleton
+    # with its host lists (edge list and SepSet records, built on the device and
+    # downloaded with the call's final readback), then both read on the host
     e2e = None
     if not args.no_e2e:
         Xh = torch.from_numpy(s.Xt).pin_memory()
         Xhv = Xh.T
-        r = ctx.skeleton(Xhv, s.alpha, form_opts[mode])
+        e2e_opts = ctx.options(mode=mode, canonical=True, max_level=s.max_level, host_lists=True,
+                               learned_order=bool(args.learned) and mode == cupc.MODE_FP32_RECHECK)
+        r = ctx.skeleton(Xhv, s.alpha, e2e_opts)
         r.edges(); r.records_raw(); r.free()
         secs, h2d, d2h = 0.0, 0, 0
         for _ in range(args.steps):
             t0 = time.perf_counter()
-            r = ctx.skeleton(Xhv, s.alpha, form_opts[mode])
+            r = ctx.skeleton(Xhv, s.alpha, e2e_opts)
             r.edges()
-            recs = r.records_raw()
+            r.records_raw()
             secs += time.perf_counter() - t0
             st = r.stats()
             h2d += st["h2d_bytes"]
-            d2h += st["d2h_bytes"] + s.p * ((s.p + 31) // 32) * 4 + recs.nbytes   # the bitset behind edges()
+            d2h += st["d2h_bytes"]
             r.free()
         e2e = {"value": units * args.steps / secs, "unit": UNIT, "ms_per_step": 1e3 * secs / args.steps,
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}

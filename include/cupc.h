@@ -115,6 +115,12 @@ typedef struct {
                                 CUPC_L1_BY_ROW); CUPC_L1_BY_ROW shares each subset
                                 {k} of a row across its j and gathers C entries
                                 through the caches */
+    int host_lists;          /* 1: the call also builds the skeleton's edge list and
+                                its SepSet records in (i, j) order on the device and
+                                downloads them with its final readback (after the
+                                levels' timing ends), so that cupc_result_edges and
+                                cupc_result_sepset_records only copy host memory;
+                                0 (default): each is built on its first request */
 } cupc_options;
 enum { CUPC_L1_AUTO = 0, CUPC_L1_BY_PIVOT = 1, CUPC_L1_BY_ROW = 2 };
 /* The three test capacities exist to exercise the recovery paths: a level
@@ -163,6 +169,10 @@ typedef struct {
                                                     the candidates and ranking them (device
                                                     clock, within the compaction phase; 0
                                                     where the level scored nothing) */
+    float host_ms[2];                            /* wall time of the call on the host: [0]
+                                                    from entry until its device work (and
+                                                    the downloads it asked for) finished,
+                                                    [1] building the result objects after */
 } cupc_stats;
 
 typedef struct cupc_ctx cupc_ctx;

@@ -88,7 +88,8 @@ class Options(ctypes.Structure):
                 ("max_level", ctypes.c_int), ("recheck_margin", ctypes.c_double),
                 ("threads_per_block", ctypes.c_int), ("chunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("corr_kps", ctypes.c_int), ("batch_direct", ctypes.c_int), ("test_qcap", ctypes.c_int),
-                ("test_nnz_cap", ctypes.c_int), ("test_rec_cap", ctypes.c_int), ("level1_form", ctypes.c_int)]
+                ("test_nnz_cap", ctypes.c_int), ("test_rec_cap", ctypes.c_int), ("level1_form", ctypes.c_int),
+                ("host_lists", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -103,7 +104,7 @@ class Stats(ctypes.Structure):
                 ("ci_block_entries", ctypes.c_int64 * L), ("phase_ms", (ctypes.c_float * 4) * L),
                 ("cuda_graph", ctypes.c_int32), ("recheck_ms", (ctypes.c_float * 3) * L),
                 ("rechecks_queued", ctypes.c_int64 * L), ("reruns", ctypes.c_int32 * 4),
-                ("order_ms", (ctypes.c_float * 2) * L)]
+                ("order_ms", (ctypes.c_float * 2) * L), ("host_ms", ctypes.c_float * 2)]
 
 
 class OrientStats(ctypes.Structure):
@@ -220,7 +221,7 @@ def _stats_dict(s: Stats) -> dict:
             "phase_ms": [list(s.phase_ms[q]) for q in range(L)], "cuda_graph": s.cuda_graph,
             "recheck_ms": [list(s.recheck_ms[q]) for q in range(L)],
             "rechecks_queued": list(s.rechecks_queued[:L]), "reruns": list(s.reruns),
-            "order_ms": [list(s.order_ms[q]) for q in range(L)]}
+            "order_ms": [list(s.order_ms[q]) for q in range(L)], "host_ms": list(s.host_ms)}
 
 
 class Result:
@@ -382,7 +383,8 @@ class Context:
 
     def options(self, mode=MODE_FP32_RECHECK, canonical=True, max_level=-1, recheck_margin=0.0,
                 threads_per_block=0, chunk=0, learned_order=False, ctas_per_sm=0, corr_kps=0,
-                batch_direct=False, test_qcap=0, test_nnz_cap=0, test_rec_cap=0, level1_form=None) -> Options:
+                batch_direct=False, test_qcap=0, test_nnz_cap=0, test_rec_cap=0, level1_form=None,
+                host_lists=False) -> Options:
         o = Options()
         load().cupc_options_default(ctypes.byref(o))
         o.mode = mode
@@ -399,6 +401,7 @@ class Context:
         o.test_nnz_cap = test_nnz_cap
         o.test_rec_cap = test_rec_cap
         o.level1_form = self.level1_form if level1_form is None else level1_form
+        o.host_lists = 1 if host_lists else 0
         return o
 
     @staticmethod

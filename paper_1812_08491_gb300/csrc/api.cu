@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "api_internal.h"
+#include "records.cuh"
 
 using namespace cupc;
 
@@ -359,6 +360,7 @@ cupc_status validate_opts(cupc_ctx* ctx, const cupc_options& o)
     if (o.ctas_per_sm < 0 || o.corr_kps < 0) return fail(ctx, CUPC_E_INVALID, "ctas_per_sm, corr_kps must be >= 0");
     if (o.level1_form < CUPC_L1_AUTO || o.level1_form > CUPC_L1_BY_ROW)
         return fail(ctx, CUPC_E_INVALID, "level1_form must be CUPC_L1_AUTO, CUPC_L1_BY_PIVOT or CUPC_L1_BY_ROW");
+    if (o.host_lists != 0 && o.host_lists != 1) return fail(ctx, CUPC_E_INVALID, "host_lists must be 0 or 1");
     return CUPC_OK;
 }
 
@@ -375,9 +377,188 @@ void free_result(cupc_result* r)
     delete r;
 }
 
+// Pinned host memory of at least `bytes` for downloads of device-built result
+// lists; the context keeps it for later calls.
+cupc_status host_stage(cupc_ctx* ctx, size_t bytes, char** out)
+{
+    if (ctx->hstage_cap < bytes) {
+        if (ctx->hstage) cudaFreeHost(ctx->hstage);
+        ctx->hstage = nullptr;
+        ctx->hstage_cap = 0;
+        const size_t cap = std::max(bytes, (size_t)1 << 20);
+        cudaError_t e = cudaMallocHost(&ctx->hstage, cap);
+        if (e != cudaSuccess) {
+            ctx->hstage = nullptr;
+            return fail(ctx, CUPC_E_NOMEM, "pinned staging buffer of " + std::to_string(cap) + " bytes", e);
+        }
+        ctx->hstage_cap = cap;
+    }
+    *out = (char*)ctx->hstage;
+    return CUPC_OK;
+}
+
+// Device scratch released on the context's stream when the scope ends.
+struct ScratchGuard {
+    cupc_ctx* ctx;
+    void* p;
+    ~ScratchGuard()
+    {
+        if (p) cudaFreeAsync(p, ctx->stream);
+    }
+};
+
+// A single call's records grouped by level from its per-level removal counts
+// (a call appends them level by level); false when the counts do not account
+// for the pool exactly.
+bool record_groups(const cupc_result* r, RecGroups& G)
+{
+    G = RecGroups{};
+    long long at = 0, idx = 0;
+    for (int l = 1; l < r->stats.levels && l < CUPC_STATS_LEVELS && l <= CUPC_MAX_LEVEL; ++l) {
+        const long long c = r->stats.removed[l];
+        if (c < 0) return false;
+        if (c == 0) continue;
+        G.lev[G.groups] = l;
+        G.start[G.groups] = at;
+        G.count[G.groups] = c;
+        G.first[G.groups] = idx;
+        ++G.groups;
+        at += c * (3 + l);
+        idx += c;
+    }
+    G.total = idx;
+    return at == r->rec_ints;
+}
+
+// Edges of a single call's result from its per-level removal counts.
+long long result_edge_count(const cupc_result* r)
+{
+    long long e = r->stats.edges_start[0] - r->stats.removed[0];
+    for (int q = 1; q < r->stats.levels && q < CUPC_STATS_LEVELS; ++q) e -= r->stats.removed[q];
+    return e;
+}
+
+// Device builds of a result's host lists in flight: where their downloads
+// (a 64-byte status block, then the list) land in the pinned staging buffer.
+struct ListsPending {
+    bool recs = false, edges = false;
+    char* h = nullptr;
+    size_t rec_block = 0;          // bytes of the records' download (the edges' follows)
+    long long n_recs = 0;
+    long long n_edges = 0;
+};
+
+// Enqueues on the context's stream the device builds of the sorted records
+// (recs) and of the edge list (edges) of a single call's result and their
+// downloads; lists_finish takes them once the stream is synchronised. A list
+// whose counts do not add up is left out (its first request then builds it
+// on the host). Scratch is released in stream order.
+cupc_status lists_enqueue(const cupc_result* r, bool recs, bool edges, ListsPending& L)
+{
+    cupc_ctx* ctx = r->ctx;
+    L = ListsPending{};
+    if (r->on_host) return CUPC_OK;
+    RecGroups G;
+    recs = recs && !r->host_ready && r->rec_ints > 0 && record_groups(r, G);
+    const long long E = result_edge_count(r);
+    edges = edges && !r->edges_ready && E >= 0;
+    if (!recs && !edges) return CUPC_OK;
+    const int p = (int)r->p, W = r->W;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t ints = recs ? (size_t)r->rec_ints : 0;
+    const size_t b_rec = recs ? al(64 + ints * 4) : 0, b_edge = edges ? 64 + (size_t)E * 8 : 0;
+    char* h = nullptr;
+    cupc_status s = host_stage(ctx, b_rec + b_edge, &h);
+    if (s != CUPC_OK) return s;
+    cudaStream_t st = ctx->stream;
+    const size_t b_p1 = al(((size_t)p + 1) * 8);
+    if (recs) {
+        const size_t m = (size_t)G.total;
+        const size_t b_wpre = al((size_t)p * W * 4), b_slot = al(m * 8);
+        void* scratch = nullptr;
+        if ((s = dalloc(ctx, &scratch, b_wpre + 4 * b_p1 + b_slot + b_rec)) != CUPC_OK) return s;
+        ScratchGuard guard{ctx, scratch};
+        char* c = (char*)scratch;
+        unsigned* wpre = (unsigned*)c;
+        c += b_wpre;
+        long long* rowcnt = (long long*)c;
+        c += b_p1;
+        long long* rowstart = (long long*)c;
+        c += b_p1;
+        unsigned long long* rowints = (unsigned long long*)c;
+        c += b_p1;
+        long long* rowoff = (long long*)c;
+        c += b_p1;
+        long long* slot = (long long*)c;
+        c += b_slot;
+        long long* status = (long long*)c;     // error flags, removed pairs, ints placed; the records follow
+        LAUNCH(launch_records_sort(r->rec, G, r->bits, r->bits0, p, W, wpre, rowcnt, rowstart, rowints, rowoff, slot,
+                                   (int*)(c + 64), status, st));
+        CU(cudaMemcpyAsync(h, status, 64 + ints * 4, cudaMemcpyDeviceToHost, st));
+        ctx->d2h += 64 + ints * 4;
+        L.recs = true;
+        L.n_recs = G.total;
+    }
+    if (edges) {
+        void* scratch = nullptr;
+        if ((s = dalloc(ctx, &scratch, 2 * b_p1 + b_edge)) != CUPC_OK) return s;
+        ScratchGuard guard{ctx, scratch};
+        long long* rowcnt = (long long*)scratch;
+        long long* off = (long long*)((char*)scratch + b_p1);
+        long long* status = (long long*)((char*)scratch + 2 * b_p1);   // the edge count; the pairs follow
+        LAUNCH(launch_edge_list(r->bits, p, W, rowcnt, off, E, (int*)((char*)status + 64), status, st));
+        CU(cudaMemcpyAsync(h + b_rec, status, b_edge, cudaMemcpyDeviceToHost, st));
+        ctx->d2h += b_edge;
+        L.edges = true;
+        L.n_edges = E;
+    }
+    L.h = h;
+    L.rec_block = b_rec;
+    return CUPC_OK;
+}
+
+// Takes the downloads of lists_enqueue after the stream has been synchronised:
+// each list whose checks pass becomes the result's host copy.
+void lists_finish(const cupc_result* r, const ListsPending& L)
+{
+    if (L.recs) {
+        long long hs[3];
+        std::memcpy(hs, L.h, sizeof(hs));
+        if (hs[0] == 0 && hs[1] == L.n_recs && hs[2] == r->rec_ints) {
+            const int32_t* a = (const int32_t*)(L.h + 64);
+            r->hrec.assign(a, a + r->rec_ints);
+            r->host_ready = true;
+            r->index_ready = false;
+        }
+    }
+    if (L.edges) {
+        const char* h = L.h + L.rec_block;
+        long long total = 0;
+        std::memcpy(&total, h, 8);
+        if (total == L.n_edges) {
+            const int32_t* a = (const int32_t*)(h + 64);
+            r->hedges.assign(a, a + 2 * L.n_edges);
+            r->edges_ready = true;
+        }
+    }
+}
+
+// Builds the requested lists on the device now (enqueue, synchronise, take).
+cupc_status device_lists(const cupc_result* r, bool recs, bool edges)
+{
+    ListsPending L;
+    cupc_status s = lists_enqueue(r, recs, edges, L);
+    if (s != CUPC_OK || (!L.recs && !L.edges)) return s;
+    cupc_ctx* ctx = r->ctx;
+    CU(cudaStreamSynchronize(ctx->stream));
+    lists_finish(r, L);
+    return CUPC_OK;
+}
+
 cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options* popts, cupc_result** out)
 {
     if (!out) return fail(ctx, CUPC_E_INVALID, "out is NULL");
+    const auto h0 = std::chrono::steady_clock::now();
     *out = nullptr;
     cupc_options o;
     cupc_options_default(&o);
@@ -847,10 +1028,20 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     }
     const int ev_end = std::min(std::max(levels_run, last_launched + 1), CUPC_STATS_LEVELS - 1) + 1;
     CU(cudaEventRecord(ctx->ev[ev_end], ctx->stream));
+    // host lists asked for with the call: built after the timed region, taken
+    // with the same synchronisation
+    ListsPending lists;
+    if (o.host_lists && (size_t)R->rec_ints <= rec_len_cap) {
+        R->stats.levels = levels_run;
+        R->rec_cap = rec_len_cap;
+        if ((s = lists_enqueue(R, true, true, lists)) != CUPC_OK) return s;
+    }
     CU(cudaStreamSynchronize(ctx->stream));
+    const auto h1 = std::chrono::steady_clock::now();
     R->rec_cap = rec_len_cap;
     if ((size_t)R->rec_ints > rec_len_cap && R->rec_ints > 0)
         return fail(ctx, CUPC_E_RANGE, "SepSet record pool overflow");
+    lists_finish(R, lists);
 
     // statistics
     R->stats.levels = levels_run;
@@ -877,6 +1068,8 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     for (int c = 0; c < CUPC_KCLASSES; ++c) R->stats.kernel_count[c] = kcount[c];
     R->stats.h2d_bytes = (int64_t)(ctx->h2d - h2d0);
     R->stats.d2h_bytes = (int64_t)(ctx->d2h - d2h0);
+    R->stats.host_ms[0] = std::chrono::duration<float, std::milli>(h1 - h0).count();
+    R->stats.host_ms[1] = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - h1).count();
     guard.ok = true;
     *out = R;
     ctx->err.clear();
@@ -901,13 +1094,31 @@ void ctx_release(cupc_ctx* c)
     if (c->hmeta) cudaFreeHost(c->hmeta);
     if (c->hlmeta) cudaFreeHost(c->hlmeta);
     if (c->hflags) cudaFreeHost(c->hflags);
+    if (c->hstage) cudaFreeHost(c->hstage);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     delete c;
+}
+
+// Index (i p + j) -> offset of the sorted host records, for single lookups.
+void build_index(const cupc_result* r)
+{
+    if (r->index_ready) return;
+    r->index.clear();
+    for (size_t k = 0; k + 2 < r->hrec.size(); k += 3 + (size_t)r->hrec[k + 2])
+        r->index.emplace_back((uint64_t)r->hrec[k] * (uint64_t)r->p + (uint64_t)r->hrec[k + 1], (int64_t)k);
+    r->index_ready = true;
 }
 
 cupc_status build_host_records(const cupc_result* r)
 {
     if (r->host_ready) return CUPC_OK;
+    if (!r->on_host && r->rec_ints > 0) {
+        const cupc_status s = device_lists(r, true, false);
+        if (s != CUPC_OK) return s;
+        if (r->host_ready) return CUPC_OK;
+    }
+    // host sort: results the device path does not cover (an empty pool, or
+    // level counts that do not match the pool)
     std::vector<int32_t> raw((size_t)r->rec_ints);
     if (r->rec_ints) {
         cudaError_t e = cudaMemcpyAsync(raw.data(), r->rec, (size_t)r->rec_ints * 4, cudaMemcpyDeviceToHost,
@@ -948,6 +1159,7 @@ cupc_status build_host_records(const cupc_result* r)
         w += ints;
     }
     r->host_ready = true;
+    r->index_ready = true;
     return CUPC_OK;
 }
 
@@ -1199,6 +1411,10 @@ cupc_status cupc_result_edges(const cupc_result* r, int32_t* out, int64_t cap, i
 {
     if (!r || !n_edges) return CUPC_E_INVALID;
     cupc_ctx* ctx = r->ctx;
+    if (!r->edges_ready && !r->on_host) {
+        const cupc_status s = device_lists(r, false, true);
+        if (s != CUPC_OK) return s;
+    }
     if (!r->edges_ready) {
         const size_t bytes = (size_t)r->p * r->W * 4;
         std::vector<unsigned> hd;
@@ -1271,6 +1487,7 @@ cupc_status cupc_result_sepset(const cupc_result* r, int64_t i, int64_t j, int32
     cupc_ctx* ctx = r->ctx;
     cupc_status s = build_host_records(r);
     if (s != CUPC_OK) return fail(ctx, s, "record download");
+    build_index(r);
     const int64_t a = std::min(i, j), b = std::max(i, j);
     const uint64_t key = (uint64_t)a * (uint64_t)r->p + (uint64_t)b;
     auto it = std::lower_bound(r->index.begin(), r->index.end(), std::make_pair(key, (int64_t)-1));

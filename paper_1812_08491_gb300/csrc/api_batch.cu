@@ -19,6 +19,7 @@
 // again. All levels up to the plan's last possible one are in the graph; a
 // level launched after the loop has ended returns at once.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -658,6 +659,7 @@ cupc_status make_results(cupc_ctx* ctx, BatchPlan& B, float ms, cupc_result** ou
             if (l < CUPC_STATS_LEVELS) rem[l]++;
         }
         R->host_ready = true;
+        R->index_ready = true;
         R->rec_ints = (int64_t)R->hrec.size();
         // per-problem counters
         const int64_t pairs = (int64_t)D.p * (D.p - 1) / 2;
@@ -747,6 +749,7 @@ cupc_status cupc_skeleton_batch(cupc_ctx* ctx, int nprob, const void* const* X, 
 {
     if (!ctx) return CUPC_E_INVALID;
     if (!out) return ctx_fail(ctx, CUPC_E_INVALID, "out is NULL");
+    const auto h0 = std::chrono::steady_clock::now();
     for (int k = 0; k < nprob && k < 4096; ++k) out[k] = nullptr;
     cupc_options o;
     cupc_options_default(&o);
@@ -757,6 +760,7 @@ cupc_status cupc_skeleton_batch(cupc_ctx* ctx, int nprob, const void* const* X, 
     const BatchKey key = make_key(nprob, dtype, layout, on_device, n_samples, p, alpha, o);
     float ms = 0.f;
     if ((s = run_batch(ctx, key, X, &ms)) != CUPC_OK) return s;
+    const auto h1 = std::chrono::steady_clock::now();
     s = make_results(ctx, *plan_of(ctx), ms, out, batch_stats);
     if (s != CUPC_OK) {
         for (int k = 0; k < nprob; ++k) {
@@ -764,6 +768,11 @@ cupc_status cupc_skeleton_batch(cupc_ctx* ctx, int nprob, const void* const* X, 
             out[k] = nullptr;
         }
         return s;
+    }
+    if (batch_stats) {
+        batch_stats->host_ms[0] = std::chrono::duration<float, std::milli>(h1 - h0).count();
+        batch_stats->host_ms[1] =
+            std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - h1).count();
     }
     ctx->err.clear();
     return CUPC_OK;

@@ -42,6 +42,8 @@ struct cupc_ctx {
     cupc::LevelMeta* hlmeta = nullptr;
     int* hflags = nullptr;         // pinned, mapped: per-level run / end flags written by the GPU
     int* dflags = nullptr;         // device view of hflags
+    void* hstage = nullptr;        // pinned staging for device-built result lists (grown on demand)
+    size_t hstage_cap = 0;
     int binom_mstride = 0;
     unsigned long long launches = 0;
     unsigned long long h2d = 0, d2h = 0;
@@ -79,6 +81,7 @@ struct cupc_result {
     mutable bool host_ready = false;
     mutable std::vector<int32_t> hrec;                              // sorted records
     mutable std::vector<std::pair<uint64_t, int64_t>> index;        // (i*p+j) -> offset
+    mutable bool index_ready = false;
     mutable bool edges_ready = false;
     mutable std::vector<int32_t> hedges;                            // edge list (i, j), i < j
 };

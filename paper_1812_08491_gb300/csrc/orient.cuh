@@ -5,21 +5,12 @@
 #include <cuda_runtime.h>
 
 #include "cupc.h"
+#include "records.cuh"
 
 namespace cupc {
 
-// SepSet records of removals at levels >= 1, grouped by level: level lev[q]
-// has count[q] records of 3 + lev[q] ints (i, j, l, S) starting at int
-// start[q]; first[q] is the index of its first record over all groups.
-constexpr int OR_LEVELS = CUPC_MAX_LEVEL + 1;
-struct OrRecords {
-    int groups;
-    int lev[OR_LEVELS];
-    long long start[OR_LEVELS];
-    long long count[OR_LEVELS];
-    long long first[OR_LEVELS];
-    long long total;
-};
+// SepSet records of removals at levels >= 1, grouped by level (RecGroups).
+using OrRecords = RecGroups;
 
 // Neighbour lists of the skeleton bitset: deg, exclusive offsets off[0..p], cols.
 cudaError_t launch_or_degree(const unsigned* bits, int p, int W, int* deg, cudaStream_t st);

@@ -348,6 +348,37 @@ def test_edge_list_matches_adjacency(ctx):
         assert np.array_equal(r.edges(), np.argwhere(np.triu(r.adjacency(), 1)).astype(np.int32))
 
 
+def _records_sorted(seps):
+    out = []
+    for (i, j) in sorted(seps):
+        l, S = seps[(i, j)]
+        out += [i, j, l, *S]
+    return np.array(out, dtype=np.int32)
+
+
+def test_records_in_pair_order(ctx):
+    """cupc_result_sepset_records: the records (i, j, l, S) of the removals at
+    levels >= 1 in increasing (i, j), int for int the oracle's in that order;
+    single lookups by cupc_result_sepset (either order of the pair) agree."""
+    cases = [sem.workload("small20", seed) for seed in range(3)]
+    cases.append(sem.generate(300, 500, 2100, "scale_free", w_min=0.2))
+    cases.append(sem.generate(150, 2000, 7, "random", degree=3.0))
+    for s in cases:
+        _, ref = _oracle_run(s.X, s.alpha)
+        want = _records_sorted(ref.sepsets)
+        edges = np.argwhere(np.triu(ref.adj, 1)).astype(np.int32)
+        for mode in ("fp32", "plain"):
+            for host_lists in (False, True):        # built on request, or with the call
+                res = ctx.skeleton(s.X, s.alpha, mode=MODES[mode], host_lists=host_lists)
+                assert np.array_equal(res.records_raw(), want), (mode, host_lists)
+                assert np.array_equal(res.records_raw(), want), (mode, host_lists)     # cached
+                assert np.array_equal(res.edges(), edges), (mode, host_lists)
+                for (i, j), (l, S) in list(ref.sepsets.items())[:40]:
+                    assert res.sepset(j, i) == tuple(S)
+                assert np.array_equal(res.sep_levels(), ref.sep_level)
+                res.free()
+
+
 @pytest.mark.parametrize("d", [0.1, 0.3])
 def test_sweep_generator_parity(ctx, d):
     """The scalability workload's generator (dense lower-triangular DAG, signed

@@ -492,8 +492,9 @@ cupc_status lists_enqueue(const cupc_result* r, bool recs, bool edges, ListsPend
         long long* slot = (long long*)c;
         c += b_slot;
         long long* status = (long long*)c;     // error flags, removed pairs, ints placed; the records follow
-        LAUNCH(launch_records_sort(r->rec, G, r->bits, r->bits0, p, W, wpre, rowcnt, rowstart, rowints, rowoff, slot,
-                                   (int*)(c + 64), status, st));
+        const RowView V{nullptr, nullptr, W, p};
+        LAUNCH(launch_records_sort(r->rec, G, r->bits, r->bits0, V, p, wpre, rowcnt, rowstart, rowints, rowoff, slot,
+                                   (int*)(c + 64), status, nullptr, 0, st));
         CU(cudaMemcpyAsync(h, status, 64 + ints * 4, cudaMemcpyDeviceToHost, st));
         ctx->d2h += 64 + ints * 4;
         L.recs = true;
@@ -1210,6 +1211,7 @@ cupc_status result_frozen_lists(const cupc_result* r, int level, std::vector<lon
 }
 
 cupc_status ctx_ensure(cupc_ctx* ctx, Buf* b, size_t bytes) { return ensure(ctx, *b, bytes); }
+cupc_status ctx_host_stage(cupc_ctx* ctx, size_t bytes, char** out) { return host_stage(ctx, bytes, out); }
 void ctx_free(cupc_ctx* ctx, Buf* b) { free_buf(ctx, *b); }
 double ctx_fisher_tau(double alpha, int64_t n, int l) { return fisher_tau(alpha, n, l); }
 cupc_status ctx_binom(cupc_ctx* ctx, int m_needed, Binom* out)

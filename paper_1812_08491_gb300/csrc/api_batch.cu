@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "api_internal.h"
+#include "records.cuh"
 
 using namespace cupc;
 
@@ -592,24 +593,95 @@ cupc_status make_results(cupc_ctx* ctx, BatchPlan& B, float ms, cupc_result** ou
     const Meta& M = *B.h_meta;
     const int last = H.done_level ? H.done_level - 1 : B.lmax;
     const int levels = last + 1;
-    // records: (i, j, l, S) in global ids, split by problem into local ids
-    std::vector<int32_t> raw((size_t)H.rec_ints);
-    if (!raw.empty()) {
+    for (int k = 0; k < K.nprob; ++k) out[k] = nullptr;
+    // records in (i, j) order with local ids, sorted on the device over the
+    // union graph (problem by problem) and downloaded in one copy with each
+    // row's int offset and the per-problem, per-level counts; the host sort
+    // below is the fallback when the counts do not add up
+    bool dev_sorted = false;
+    const int32_t* srec = nullptr;          // the sorted records (pinned staging)
+    const long long* roff = nullptr;        // int offset of each union row's records, P + 1
+    const unsigned long long* plc = nullptr;  // records per problem and level
+    size_t d2h_rec = 0;
+    if (H.rec_ints > 0) {
+        RecGroups G{};
+        long long at = 0, idx = 0;
+        for (int l = 1; l <= last && l <= CUPC_MAX_LEVEL; ++l) {
+            const long long c = (long long)H.removed[l];
+            if (c == 0) continue;
+            G.lev[G.groups] = l;
+            G.start[G.groups] = at;
+            G.count[G.groups] = c;
+            G.first[G.groups] = idx;
+            ++G.groups;
+            at += c * (3 + l);
+            idx += c;
+        }
+        G.total = idx;
+        if (at == (long long)H.rec_ints) {
+            auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+            const size_t ints = (size_t)H.rec_ints, rows = (size_t)B.P;
+            const size_t b_wpre = al((size_t)B.words * 4), b_r1 = al((rows + 1) * 8), b_slot = al((size_t)G.total * 8),
+                         b_plc = al((size_t)K.nprob * kRecGroups * 8), b_out = al(64 + ints * 4);
+            Buf* sb = ctx_buf(ctx, "rec_sort");
+            cupc_status s = ctx_ensure(ctx, sb, b_wpre + 4 * b_r1 + b_slot + b_plc + b_out);
+            if (s != CUPC_OK) return s;
+            char* c = (char*)sb->p;
+            unsigned* wpre = (unsigned*)c;
+            c += b_wpre;
+            long long* rowcnt = (long long*)c;
+            c += b_r1;
+            long long* rowstart = (long long*)c;
+            c += b_r1;
+            unsigned long long* rowints = (unsigned long long*)c;
+            c += b_r1;
+            long long* rowoff = (long long*)c;
+            c += b_r1;
+            long long* slot = (long long*)c;
+            c += b_slot;
+            unsigned long long* dplc = (unsigned long long*)c;
+            c += b_plc;
+            long long* status = (long long*)c;     // error flags, removed pairs, ints placed; the records follow
+            char* h = nullptr;
+            if ((s = ctx_host_stage(ctx, b_out + b_r1 + b_plc, &h)) != CUPC_OK) return s;
+            const RowView V{(const int*)B.d_vprob.p, (const ProbDesc*)B.d_probs.p, 0, 0};
+            BCU(cudaMemsetAsync(dplc, 0, b_plc, B.gs));
+            BCU(launch_records_sort((const int*)B.rec.p, G, (const unsigned*)B.bits.p, (const unsigned*)B.bits0.p, V,
+                                    (long long)rows, wpre, rowcnt, rowstart, rowints, rowoff, slot,
+                                    (int*)((char*)status + 64), status, dplc, kRecGroups, B.gs));
+            BCU(cudaMemcpyAsync(h, status, 64 + ints * 4, cudaMemcpyDeviceToHost, B.gs));
+            BCU(cudaMemcpyAsync(h + b_out, rowoff, (rows + 1) * 8, cudaMemcpyDeviceToHost, B.gs));
+            BCU(cudaMemcpyAsync(h + b_out + b_r1, dplc, (size_t)K.nprob * kRecGroups * 8, cudaMemcpyDeviceToHost,
+                                B.gs));
+            BCU(cudaStreamSynchronize(B.gs));
+            d2h_rec = 64 + ints * 4 + (rows + 1) * 8 + (size_t)K.nprob * kRecGroups * 8;
+            long long hs[3];
+            std::memcpy(hs, h, sizeof(hs));
+            if (hs[0] == 0 && hs[1] == G.total && hs[2] == (long long)ints) {
+                dev_sorted = true;
+                srec = (const int32_t*)(h + 64);
+                roff = (const long long*)(h + b_out);
+                plc = (const unsigned long long*)(h + b_out + b_r1);
+            }
+        }
+    }
+    std::vector<int32_t> raw;
+    std::vector<std::vector<size_t>> idx(K.nprob);
+    if (!dev_sorted && H.rec_ints > 0) {
+        // records: (i, j, l, S) in global ids, split by problem into local ids
+        raw.resize((size_t)H.rec_ints);
         BCU(cudaMemcpyAsync(raw.data(), B.rec.p, raw.size() * 4, cudaMemcpyDeviceToHost, B.gs));
         BCU(cudaStreamSynchronize(B.gs));
-    }
-    for (int k = 0; k < K.nprob; ++k) out[k] = nullptr;
-    // each problem's record offsets in (i, j) order: a least-significant-digit
-    // radix sort, a stable counting sort on local j and then on local i
-    std::vector<std::vector<size_t>> idx(K.nprob);
-    for (size_t q = 0; q < raw.size();) {
-        const int l = raw[q + 2];
-        if (l < 1 || l > CUPC_MAX_LEVEL || q + 3 + l > raw.size())
-            return ctx_fail(ctx, CUPC_E_STATE, "bad SepSet record");
-        idx[B.vprob[raw[q]]].push_back(q);
-        q += 3 + l;
-    }
-    {
+        d2h_rec = raw.size() * 4;
+        // each problem's record offsets in (i, j) order: a least-significant-digit
+        // radix sort, a stable counting sort on local j and then on local i
+        for (size_t q = 0; q < raw.size();) {
+            const int l = raw[q + 2];
+            if (l < 1 || l > CUPC_MAX_LEVEL || q + 3 + l > raw.size())
+                return ctx_fail(ctx, CUPC_E_STATE, "bad SepSet record");
+            idx[B.vprob[raw[q]]].push_back(q);
+            q += 3 + l;
+        }
         std::vector<size_t> cnt, tmp;
         for (int k = 0; k < K.nprob; ++k) {
             std::vector<size_t>& v = idx[k];
@@ -640,26 +712,33 @@ cupc_status make_results(cupc_ctx* ctx, BatchPlan& B, float ms, cupc_result** ou
         const size_t nw = (size_t)D.p * R->W;
         R->hbits.assign(B.h_bits + D.bw, B.h_bits + D.bw + nw);
         R->hbits0.assign(B.h_bits0 + D.bw, B.h_bits0 + D.bw + nw);
-        size_t ints = 0;
-        for (const size_t q : idx[k]) ints += 3 + (size_t)raw[q + 2];
-        R->hrec.resize(ints);
-        R->index.resize(idx[k].size());
         std::vector<int64_t> rem(CUPC_STATS_LEVELS, 0);
-        size_t w = 0, r = 0;
-        for (const size_t q : idx[k]) {
-            const int l = raw[q + 2];
-            const int i = raw[q] - D.off, j = raw[q + 1] - D.off;
-            R->index[r++] = std::make_pair((uint64_t)i * (uint64_t)D.p + (uint64_t)j, (int64_t)w);
-            int32_t* o = R->hrec.data() + w;
-            o[0] = i;
-            o[1] = j;
-            o[2] = l;
-            for (int c = 0; c < l; ++c) o[3 + c] = raw[q + 3 + c] - D.off;
-            w += 3 + (size_t)l;
-            if (l < CUPC_STATS_LEVELS) rem[l]++;
+        if (dev_sorted) {
+            // its union rows D.off .. D.off + p32 hold its records, ids already local
+            const long long a = roff[D.off], b = roff[D.off + (D.whi - D.wlo) * 32];
+            R->hrec.assign(srec + a, srec + b);
+            for (int l = 1; l < CUPC_STATS_LEVELS && l < kRecGroups; ++l) rem[l] = (int64_t)plc[(size_t)k * kRecGroups + l];
+        } else {
+            size_t ints = 0;
+            for (const size_t q : idx[k]) ints += 3 + (size_t)raw[q + 2];
+            R->hrec.resize(ints);
+            R->index.resize(idx[k].size());
+            size_t w = 0, r = 0;
+            for (const size_t q : idx[k]) {
+                const int l = raw[q + 2];
+                const int i = raw[q] - D.off, j = raw[q + 1] - D.off;
+                R->index[r++] = std::make_pair((uint64_t)i * (uint64_t)D.p + (uint64_t)j, (int64_t)w);
+                int32_t* o = R->hrec.data() + w;
+                o[0] = i;
+                o[1] = j;
+                o[2] = l;
+                for (int c = 0; c < l; ++c) o[3 + c] = raw[q + 3 + c] - D.off;
+                w += 3 + (size_t)l;
+                if (l < CUPC_STATS_LEVELS) rem[l]++;
+            }
         }
         R->host_ready = true;
-        R->index_ready = true;
+        R->index_ready = !dev_sorted;
         R->rec_ints = (int64_t)R->hrec.size();
         // per-problem counters
         const int64_t pairs = (int64_t)D.p * (D.p - 1) / 2;
@@ -732,8 +811,7 @@ cupc_status make_results(cupc_ctx* ctx, BatchPlan& B, float ms, cupc_result** ou
     S.kernel_launches = B.launches;
     const size_t es = esize(K.dtype);
     S.h2d_bytes = K.on_device ? 0 : (int64_t)(B.xelems * es);
-    S.d2h_bytes = (int64_t)(2 * B.words * 4 + sizeof(Meta) + sizeof(LevelMeta) + (size_t)K.nprob * LV * 8 +
-                            raw.size() * 4);
+    S.d2h_bytes = (int64_t)(2 * B.words * 4 + sizeof(Meta) + sizeof(LevelMeta) + (size_t)K.nprob * LV * 8 + d2h_rec);
     S.cuda_graph = B.graph_ok ? 1 : 0;
     if (bst) *bst = S;
     return CUPC_OK;

@@ -90,6 +90,7 @@ struct cupc_result {
 // helpers with external linkage for the other host files
 cupc_status result_frozen_lists(const cupc_result* r, int level, std::vector<long long>& off, std::vector<int>& cols);
 cupc_status ctx_ensure(cupc_ctx* ctx, Buf* b, size_t bytes);
+cupc_status ctx_host_stage(cupc_ctx* ctx, size_t bytes, char** out);   // pinned staging, grown on demand
 void ctx_free(cupc_ctx* ctx, Buf* b);
 double ctx_fisher_tau(double alpha, int64_t n, int l);
 cupc_status ctx_binom(cupc_ctx* ctx, int m_needed, cupc::Binom* out);

@@ -107,6 +107,12 @@ def test_batch_equals_single_calls_and_layouts(ctx):
         assert np.array_equal(r.adjacency(), one.adjacency())
         assert np.array_equal(rv.adjacency(), one.adjacency())
         assert r.sepsets() == one.sepsets() == rv.sepsets()
+        # records in (i, j) order, int for int, and the per-level removal counts
+        assert np.array_equal(r.records_raw(), one.records_raw())
+        assert np.array_equal(rv.records_raw(), one.records_raw())
+        assert _trim(r.stats()["removed"]) == _trim(one.stats()["removed"])
+        for (i, j), (l, S) in list(one.sepsets().items())[:25]:
+            assert r.sepset(j, i) == S
 
 
 def test_device_inputs(ctx):

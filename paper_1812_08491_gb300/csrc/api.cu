@@ -556,6 +556,10 @@ cupc_status device_lists(const cupc_result* r, bool recs, bool edges)
     return CUPC_OK;
 }
 
+// Event that marks the end of a call's device work (after the event slots of
+// the prep step and the levels).
+constexpr int kEvFin = CUPC_STATS_LEVELS + 2;
+
 cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options* popts, cupc_result** out)
 {
     if (!out) return fail(ctx, CUPC_E_INVALID, "out is NULL");
@@ -894,13 +898,15 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
         if (cancelled()) return fail(ctx, CUPC_E_CANCELLED, "cancelled after level 0");
         if (lmax >= from && (s = launch_levels(from)) != CUPC_OK) return s;
 
-        // one readback: level 0's counters and, when levels ran, theirs
+        // one readback: level 0's counters and, when levels ran, theirs; the
+        // device work of the call ends with it (unless a level runs again)
         CU(cudaMemcpyAsync(ctx->hmeta, meta, sizeof(Meta), cudaMemcpyDeviceToHost, ctx->stream));
         ctx->d2h += sizeof(Meta);
         if (lmax >= from) {
             CU(cudaMemcpyAsync(ctx->hlmeta, lm, sizeof(LevelMeta), cudaMemcpyDeviceToHost, ctx->stream));
             ctx->d2h += sizeof(LevelMeta);
         }
+        CU(cudaEventRecord(ctx->ev[kEvFin], ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
         M = *ctx->hmeta;
         if (M.error & 4) return fail(ctx, CUPC_E_TIMEOUT, "a bounded wait in the tensor-core product expired");
@@ -967,6 +973,7 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
             CU(cudaMemcpyAsync(lm, ctx->hlmeta, sizeof(LevelMeta), cudaMemcpyHostToDevice, ctx->stream));
             if ((s = launch_levels(ol)) != CUPC_OK) return s;
             CU(cudaMemcpyAsync(ctx->hlmeta, lm, sizeof(LevelMeta), cudaMemcpyDeviceToHost, ctx->stream));
+            CU(cudaEventRecord(ctx->ev[kEvFin], ctx->stream));
             CU(cudaStreamSynchronize(ctx->stream));
             ctx->d2h += sizeof(LevelMeta);
         }
@@ -1027,17 +1034,15 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     } else if (range_stop) {
         return fail(ctx, CUPC_E_RANGE, "a level above CUPC_MAX_LEVEL would be needed");
     }
-    const int ev_end = std::min(std::max(levels_run, last_launched + 1), CUPC_STATS_LEVELS - 1) + 1;
-    CU(cudaEventRecord(ctx->ev[ev_end], ctx->stream));
-    // host lists asked for with the call: built after the timed region, taken
-    // with the same synchronisation
+    // host lists asked for with the call: built after the device work's end
+    // event, taken after one more synchronisation
     ListsPending lists;
     if (o.host_lists && (size_t)R->rec_ints <= rec_len_cap) {
         R->stats.levels = levels_run;
         R->rec_cap = rec_len_cap;
         if ((s = lists_enqueue(R, true, true, lists)) != CUPC_OK) return s;
+        if (lists.recs || lists.edges) CU(cudaStreamSynchronize(ctx->stream));
     }
-    CU(cudaStreamSynchronize(ctx->stream));
     const auto h1 = std::chrono::steady_clock::now();
     R->rec_cap = rec_len_cap;
     if ((size_t)R->rec_ints > rec_len_cap && R->rec_ints > 0)
@@ -1052,12 +1057,13 @@ cupc_status run(cupc_ctx* ctx, const Input& in, double alpha, const cupc_options
     if (ck)
         for (int q = 0; q < from && q < CUPC_STATS_LEVELS; ++q) R->stats.level_ms[q] = ck->stats.level_ms[q];
     for (int q = ck ? from : 0; q < levels_run && q < CUPC_STATS_LEVELS; ++q) {
-        // level 0 spans the sizing step; level q >= 1 its level kernel launch
-        const int a = 1 + q, b = (q + 1 <= last_launched) ? 2 + q : ev_end;
-        if (b > ev_end || a >= (int)ctx->ev.size()) break;
+        // level 0 spans the sizing step; level q >= 1 its level kernel launch (the
+        // last one up to the end of the device work)
+        if (q > 0 && q > last_launched) break;
+        const int a = 1 + q, b = (q + 1 <= last_launched) ? 2 + q : kEvFin;
         if (cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]) == cudaSuccess) R->stats.level_ms[q] = ms;
     }
-    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[ev_end]);
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[kEvFin]);
     R->stats.total_ms = ms;
     cudaGetLastError();
     int64_t edges_final = R->stats.edges_start[0] - R->stats.removed[0];

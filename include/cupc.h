@@ -380,7 +380,8 @@ cupc_status cupc_result_adjacency(const cupc_result* res, uint8_t* out);
  * (i, j) with i < j in increasing (i, j) order, written to out[2k] and
  * out[2k + 1] (host buffer, caller-owned, room for `cap` pairs); *n_edges =
  * the number of edges. With out == NULL only *n_edges is set. The list is
- * built once per result (one download of the bitset) and kept until
+ * built once per result (on the device for a single call's result, downloaded
+ * in one copy; from the host bitset for a batch result) and kept until
  * cupc_result_free. */
 cupc_status cupc_result_edges(const cupc_result* res, int32_t* out, int64_t cap, int64_t* n_edges);
 
@@ -399,7 +400,9 @@ cupc_status cupc_result_sepset(const cupc_result* res, int64_t i, int64_t j, int
 /* The SepSets of Algorithm 1 (Sec. 2.4) for every removal at level >= 1, as
  * consecutive int32 groups
  * (i, j, l, S[0..l)) with i < j, sorted by (i, j). With out == NULL only
- * *n_ints is set; otherwise at most `cap` ints are written. */
+ * *n_ints is set; otherwise at most `cap` ints are written. The sorted records
+ * are built once per result (put in order on the device, or on the host when
+ * the result's counts do not allow it) and kept until cupc_result_free. */
 cupc_status cupc_result_sepset_records(const cupc_result* res, int32_t* out, int64_t cap,
                                        int64_t* n_ints);
 

@@ -207,6 +207,21 @@ void tend(cupc_ctx* ctx, int k)
     if (k >= 0) cudaEventRecord(ctx->tev[k + 1], ctx->stream);
 }
 
+// The copy stream of chunked uploads and its events, created on first use.
+cupc_status ensure_copy_stream(cupc_ctx* ctx)
+{
+    if (ctx->cstream) return CUPC_OK;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return CUPC_E_CUDA;
+    for (cudaEvent_t& e : ctx->cev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaStreamDestroy(st);
+            return CUPC_E_CUDA;
+        }
+    ctx->cstream = st;
+    return CUPC_OK;
+}
+
 void tcollect(cupc_ctx* ctx, cupc_stats& st)
 {
     for (int k = 0; k + 1 < ctx->tused; k += 2) {
@@ -284,12 +299,70 @@ cupc_status prepare(cupc_ctx* ctx, const Input& in, bool fp32, const void** Cuse
     const void* src = in.X;
     const size_t extent = (in.layout == CUPC_LAYOUT_SAMPLE_MAJOR) ? ((size_t)(n - 1) * in.ld + p) * es
                                                                  : ((size_t)(p - 1) * in.ld + n) * es;
+    const long long ldz = n;
+    const long long ldb = ((long long)n + 63) / 64 * 64;  // K padded to whole 64-wide slabs
+    {
+        cupc_status s;
+        if ((s = ensure(ctx, ctx->mu, (size_t)p * 8)) != CUPC_OK) return s;
+        if ((s = ensure(ctx, ctx->isd, (size_t)p * 8)) != CUPC_OK) return s;
+        if (fp32 && (s = ensure(ctx, ctx->mup, (size_t)p * 8)) != CUPC_OK) return s;
+        // FP64 rows only for the FP64 product (plain mode); FP32 mode keeps the bf16 split
+        if (!fp32 && (s = ensure(ctx, ctx->z64, (size_t)p * ldz * 8)) != CUPC_OK) return s;
+        if (fp32) {
+            if ((s = ensure(ctx, ctx->zhi, (size_t)p * ldb * 2)) != CUPC_OK) return s;
+            if ((s = ensure(ctx, ctx->zlo, (size_t)p * ldb * 2)) != CUPC_OK) return s;
+        }
+    }
+    auto standardize = [&](const void* rows, int v0, int v1) {
+        return launch_standardize(in.dtype, rows, in.ld, n, v1 - v0, (double*)ctx->mu.p + v0,
+                                  (double*)ctx->isd.p + v0, fp32 ? (float2*)ctx->mup.p + v0 : nullptr,
+                                  fp32 ? nullptr : (double*)ctx->z64.p + (size_t)v0 * ldz, ldz,
+                                  fp32 ? (void*)((unsigned short*)ctx->zhi.p + (size_t)v0 * ldb) : nullptr,
+                                  fp32 ? (void*)((unsigned short*)ctx->zlo.p + (size_t)v0 * ldb) : nullptr, ldb,
+                                  meta, ctx->stream);
+    };
+    // A variable-major host input of some size is uploaded in variable chunks on
+    // a copy stream, and each chunk is standardised once it has arrived, so the
+    // standardisation of one chunk runs while the next is on the host link. The
+    // standardisation form a launch picks depends on its variable count, so the
+    // chunks are used only where they pick the same form as the whole input.
+    constexpr int kChunks = 4;
+    constexpr size_t kChunkMinBytes = size_t(8) << 20;
+    const bool same_form = n > 4096 || p < 1024 || p / kChunks >= 1024;
+    const bool chunked = !in.on_device && in.layout == CUPC_LAYOUT_VARIABLE_MAJOR && extent >= kChunkMinBytes &&
+                         p >= 4 * kChunks && same_form;
+    bool standardized = false;
     if (!in.on_device) {
         cupc_status s = ensure(ctx, ctx->xin, extent);
         if (s != CUPC_OK) return s;
-        const int tk = tbegin(ctx, CUPC_K_UPLOAD);
-        CU(cudaMemcpyAsync(ctx->xin.p, in.X, extent, cudaMemcpyHostToDevice, ctx->stream));
-        tend(ctx, tk);
+        if (chunked && ensure_copy_stream(ctx) == CUPC_OK) {
+            // the copy stream starts after the context stream's earlier work (the
+            // input buffer may still be read there)
+            CU(cudaEventRecord(ctx->cev[7], ctx->stream));
+            CU(cudaStreamWaitEvent(ctx->cstream, ctx->cev[7], 0));
+            const int tk = (ctx->tused + 2 <= (int)ctx->tev.size()) ? ctx->tused : -1;
+            if (tk >= 0) {
+                ctx->tused += 2;
+                ctx->tcls[tk / 2] = CUPC_K_UPLOAD;
+                CU(cudaEventRecord(ctx->tev[tk], ctx->cstream));
+            }
+            for (int c = 0; c < kChunks; ++c) {
+                const int v0 = (int)((long long)p * c / kChunks), v1 = (int)((long long)p * (c + 1) / kChunks);
+                const size_t off = (size_t)v0 * in.ld * es;
+                const size_t bytes = ((size_t)(v1 - 1 - v0) * in.ld + n) * es;
+                CU(cudaMemcpyAsync((char*)ctx->xin.p + off, (const char*)in.X + off, bytes, cudaMemcpyHostToDevice,
+                                   ctx->cstream));
+                CU(cudaEventRecord(ctx->cev[c], ctx->cstream));
+                CU(cudaStreamWaitEvent(ctx->stream, ctx->cev[c], 0));
+                TIMED(CUPC_K_STANDARDIZE, standardize((const char*)ctx->xin.p + off, v0, v1));
+            }
+            if (tk >= 0) CU(cudaEventRecord(ctx->tev[tk + 1], ctx->cstream));
+            standardized = true;
+        } else {
+            const int tk = tbegin(ctx, CUPC_K_UPLOAD);
+            CU(cudaMemcpyAsync(ctx->xin.p, in.X, extent, cudaMemcpyHostToDevice, ctx->stream));
+            tend(ctx, tk);
+        }
         ctx->h2d += extent;
         src = ctx->xin.p;
     }
@@ -302,23 +375,13 @@ cupc_status prepare(cupc_ctx* ctx, const Input& in, bool fp32, const void** Cuse
         xv = ctx->xt.p;
         ldv = n;
     }
-    const long long ldz = n;
-    const long long ldb = ((long long)n + 63) / 64 * 64;  // K padded to whole 64-wide slabs
     cupc_status s;
-    if ((s = ensure(ctx, ctx->mu, (size_t)p * 8)) != CUPC_OK) return s;
-    if ((s = ensure(ctx, ctx->isd, (size_t)p * 8)) != CUPC_OK) return s;
-    if (fp32 && (s = ensure(ctx, ctx->mup, (size_t)p * 8)) != CUPC_OK) return s;
-    // FP64 rows only for the FP64 product (plain mode); FP32 mode keeps the bf16 split
-    if (!fp32 && (s = ensure(ctx, ctx->z64, (size_t)p * ldz * 8)) != CUPC_OK) return s;
-    if (fp32) {
-        if ((s = ensure(ctx, ctx->zhi, (size_t)p * ldb * 2)) != CUPC_OK) return s;
-        if ((s = ensure(ctx, ctx->zlo, (size_t)p * ldb * 2)) != CUPC_OK) return s;
-    }
-    TIMED(CUPC_K_STANDARDIZE,
-          launch_standardize(in.dtype, xv, ldv, n, p, (double*)ctx->mu.p, (double*)ctx->isd.p,
-                             fp32 ? (float2*)ctx->mup.p : nullptr,
-                             fp32 ? nullptr : (double*)ctx->z64.p, ldz, fp32 ? ctx->zhi.p : nullptr,
-                             fp32 ? ctx->zlo.p : nullptr, ldb, meta, ctx->stream));
+    if (!standardized)
+        TIMED(CUPC_K_STANDARDIZE,
+              launch_standardize(in.dtype, xv, ldv, n, p, (double*)ctx->mu.p, (double*)ctx->isd.p,
+                                 fp32 ? (float2*)ctx->mup.p : nullptr,
+                                 fp32 ? nullptr : (double*)ctx->z64.p, ldz, fp32 ? ctx->zhi.p : nullptr,
+                                 fp32 ? ctx->zlo.p : nullptr, ldb, meta, ctx->stream));
     dv->xv = xv;
     dv->ldx = ldv;
     dv->xf64 = in.dtype == CUPC_F64 ? 1 : 0;
@@ -1102,6 +1165,9 @@ void ctx_release(cupc_ctx* c)
     if (c->hlmeta) cudaFreeHost(c->hlmeta);
     if (c->hflags) cudaFreeHost(c->hflags);
     if (c->hstage) cudaFreeHost(c->hstage);
+    for (cudaEvent_t e : c->cev)
+        if (e) cudaEventDestroy(e);
+    if (c->cstream) cudaStreamDestroy(c->cstream);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     delete c;
 }

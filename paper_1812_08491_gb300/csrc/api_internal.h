@@ -42,6 +42,8 @@ struct cupc_ctx {
     cupc::LevelMeta* hlmeta = nullptr;
     int* hflags = nullptr;         // pinned, mapped: per-level run / end flags written by the GPU
     int* dflags = nullptr;         // device view of hflags
+    cudaStream_t cstream = nullptr;     // copy stream of chunked uploads (created on first use)
+    cudaEvent_t cev[8] = {};            // chunk-arrival events (and [7]: the context stream's position)
     void* hstage = nullptr;        // pinned staging for device-built result lists (grown on demand)
     size_t hstage_cap = 0;
     int binom_mstride = 0;

@@ -348,6 +348,26 @@ def test_edge_list_matches_adjacency(ctx):
         assert np.array_equal(r.edges(), np.argwhere(np.triu(r.adjacency(), 1)).astype(np.int32))
 
 
+def test_host_input_chunked_upload(ctx):
+    """A variable-major host input of 8 MB or more is uploaded in variable chunks,
+    each standardised on arrival: the result equals the device-input call's
+    (FP32 data in the FP32 form; FP64 data in both forms, against the oracle)."""
+    s = sem.workload("medium1000")                         # 40 MB of float32
+    Xh = s.Xt.T                                            # variable-major host view
+    assert Xh.nbytes >= 8 << 20 and Xh.strides[0] == Xh.itemsize
+    rh = ctx.skeleton(Xh, s.alpha, max_level=s.max_level)
+    rd = ctx.skeleton(torch.from_numpy(s.Xt).cuda().T, s.alpha, max_level=s.max_level)
+    assert np.array_equal(rh.adjacency(), rd.adjacency())
+    assert np.array_equal(rh.records_raw(), rd.records_raw())
+    assert rh.stats()["serial_tests"] == rd.stats()["serial_tests"]
+    assert rh.stats()["kernel_count"]["standardize"] == 4
+    s2 = sem.generate(300, 5000, 31, "random", degree=3.0)  # 12 MB of float64
+    _, ref = _oracle_run(s2.X, s2.alpha)
+    for mode in ("fp32", "plain"):
+        res = ctx.skeleton(np.ascontiguousarray(s2.Xt).T, s2.alpha, mode=MODES[mode])
+        _assert_same(res, ref)
+
+
 def _records_sorted(seps):
     out = []
     for (i, j) in sorted(seps):

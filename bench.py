@@ -173,7 +173,7 @@ def orientation_line(ctx, X, s, mode, oracle_res=None, reps=5):
     out = {"device_ms": ms, "rounds": st["rounds"], "directed": st["directed"],
            "undirected": st["undirected"], "bidirected": st["bidirected"],
            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                        "alg_bytes": byts, "note": "latency-bound: one host readback per rule round"},
+                        "alg_bytes": byts, "note": "latency-bound: rule rounds queued four at a time, one readback each"},
            "note": "second step of PC-stable, outside the timed skeleton step"}
     if oracle_res is not None:
         import oracle

@@ -150,20 +150,37 @@ extern "C" cupc_status cupc_result_orient(cupc_result* r, uint8_t* marks, cupc_o
     OLAUNCH(launch_or_vstructS(bits, p, W, off, cols, rec, R, head, headT, st));
 
     // Meek's rules in rounds until one changes nothing (each applied round
-    // orients at least one of the nnz / 2 edges)
+    // orients at least one of the nnz / 2 edges, so at most nnz / 2 + 2 rounds
+    // run). Rounds are queued kBatch at a time with one readback: round k keeps
+    // its counters in rflags[2k], rflags[2k + 1], and a round after one that
+    // applied nothing does nothing.
+    constexpr int kBatch = 4;
+    const long long rmax = nnz / 2 + 2;
+    if ((s = ctx_ensure(ctx, ctx_buf(ctx, "or_rflags"), (size_t)rmax * 2 * 8)) != CUPC_OK) return s;
+    unsigned long long* rflags = buf<unsigned long long>(ctx, "or_rflags");
+    OCU(cudaMemsetAsync(rflags, 0, (size_t)rmax * 2 * 8, st));
     long long rounds = 0, rule_conflicts = 0;
-    unsigned long long hf[2];
-    for (;;) {
-        OCU(cudaMemsetAsync(prop, 0, words * 4, st));
-        OCU(cudaMemsetAsync(flags, 0, 2 * 8, st));
-        OLAUNCH(launch_or_propose(bits, p, W, off, cols, head, headT, prop, st));
-        OLAUNCH(launch_or_apply(prop, p, W, head, headT, flags, st));
-        OCU(cudaMemcpyAsync(hf, flags, 2 * 8, cudaMemcpyDeviceToHost, st));
+    unsigned long long hf[2 * kBatch];
+    bool ended = false;
+    for (long long k = 0; !ended;) {
+        if (k >= rmax) return ctx_fail(ctx, CUPC_E_STATE, "orientation rounds do not end");
+        const long long k0 = k;
+        for (int q = 0; q < kBatch && k < rmax; ++q, ++k) {
+            const unsigned long long* gate = k ? rflags + 2 * (k - 1) : nullptr;
+            OCU(cudaMemsetAsync(prop, 0, words * 4, st));
+            OLAUNCH(launch_or_propose(bits, p, W, off, cols, head, headT, prop, gate, st));
+            OLAUNCH(launch_or_apply(prop, p, W, head, headT, rflags + 2 * k, gate, st));
+        }
+        OCU(cudaMemcpyAsync(hf, rflags + 2 * k0, (size_t)(k - k0) * 2 * 8, cudaMemcpyDeviceToHost, st));
         OCU(cudaStreamSynchronize(st));
-        ++rounds;
-        rule_conflicts += (long long)(hf[1] / 2);
-        if (hf[0] == 0) break;
-        if (rounds > nnz / 2 + 1) return ctx_fail(ctx, CUPC_E_STATE, "orientation rounds do not end");
+        for (long long j = 0; j < k - k0; ++j) {
+            ++rounds;
+            rule_conflicts += (long long)(hf[2 * j + 1] / 2);
+            if (hf[2 * j] == 0) {
+                ended = true;
+                break;
+            }
+        }
     }
 
     // edge marks and counts (the marks are copied out when asked for)

@@ -201,12 +201,14 @@ __device__ __forceinline__ bool dir_of(const unsigned* head, const unsigned* hea
 // of a (lanes), then R3 over the pairs of candidates c (a - c -> b).
 __global__ void __launch_bounds__(PROP_T) k_or_propose(const unsigned* __restrict__ bits, int p, int W,
                                                        const long long* __restrict__ off, const int* __restrict__ cols,
-                                                       const unsigned* head, const unsigned* headT, unsigned* prop)
+                                                       const unsigned* head, const unsigned* headT, unsigned* prop,
+                                                       const unsigned long long* gate)
 {
     __shared__ int cand[PROP_T / 32][TCAP];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int a = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (a >= p) return;
+    if (gate && *(volatile const unsigned long long*)gate == 0ull) return;   // the rounds have ended
     const long long o = off[a], d = off[a + 1] - o;
     int* T = cand[wid];
     for (long long bi = 0; bi < d; ++bi) {
@@ -276,8 +278,9 @@ __global__ void __launch_bounds__(PROP_T) k_or_propose(const unsigned* __restric
 // Thread per word (a, w) of the proposals: a -> b is applied unless b -> a was
 // proposed too.
 __global__ void k_or_apply(const unsigned* __restrict__ prop, int p, int W, unsigned* head, unsigned* headT,
-                           unsigned long long* flags)
+                           unsigned long long* flags, const unsigned long long* gate)
 {
+    if (gate && *(volatile const unsigned long long*)gate == 0ull) return;   // the rounds have ended
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long applied = 0, both = 0;
     if (t < (long long)p * W) {
@@ -379,17 +382,18 @@ cudaError_t launch_or_vstructS(const unsigned* bits, int p, int W, const long lo
 }
 
 cudaError_t launch_or_propose(const unsigned* bits, int p, int W, const long long* off, const int* cols,
-                              const unsigned* head, const unsigned* headT, unsigned* prop, cudaStream_t st)
+                              const unsigned* head, const unsigned* headT, unsigned* prop,
+                              const unsigned long long* gate, cudaStream_t st)
 {
-    k_or_propose<<<warp_blocks(p, PROP_T), PROP_T, 0, st>>>(bits, p, W, off, cols, head, headT, prop);
+    k_or_propose<<<warp_blocks(p, PROP_T), PROP_T, 0, st>>>(bits, p, W, off, cols, head, headT, prop, gate);
     return cudaGetLastError();
 }
 
 cudaError_t launch_or_apply(const unsigned* prop, int p, int W, unsigned* head, unsigned* headT,
-                            unsigned long long* flags, cudaStream_t st)
+                            unsigned long long* flags, const unsigned long long* gate, cudaStream_t st)
 {
     const long long words = (long long)p * W;
-    k_or_apply<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(prop, p, W, head, headT, flags);
+    k_or_apply<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(prop, p, W, head, headT, flags, gate);
     return cudaGetLastError();
 }
 

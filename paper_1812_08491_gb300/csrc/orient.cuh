@@ -24,11 +24,14 @@ cudaError_t launch_or_vstructS(const unsigned* bits, int p, int W, const long lo
                                const int* rec, const OrRecords& R, unsigned* head, unsigned* headT, cudaStream_t st);
 // one round of Meek's rules: proposals from the round's starting marks, then
 // their application; flags[0] += orientations applied, flags[1] += pairs
-// proposed both ways (each counted from both ends)
+// proposed both ways (each counted from both ends). With a gate (the previous
+// round's flags[0]) both launches do nothing when that round applied nothing,
+// so several rounds can be queued before the host looks.
 cudaError_t launch_or_propose(const unsigned* bits, int p, int W, const long long* off, const int* cols,
-                              const unsigned* head, const unsigned* headT, unsigned* prop, cudaStream_t st);
+                              const unsigned* head, const unsigned* headT, unsigned* prop,
+                              const unsigned long long* gate, cudaStream_t st);
 cudaError_t launch_or_apply(const unsigned* prop, int p, int W, unsigned* head, unsigned* headT,
-                            unsigned long long* flags, cudaStream_t st);
+                            unsigned long long* flags, const unsigned long long* gate, cudaStream_t st);
 // p x p edge marks (0 none, 1 arrowhead at the column's end, 2 tail) and the
 // counts flags[2..4] += directed, undirected, bidirected edges
 cudaError_t launch_or_marks(const unsigned* bits, const unsigned* headT, int p, int W, unsigned char* marks,

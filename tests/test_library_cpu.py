@@ -88,3 +88,29 @@ def test_control_entry_points_reject_null(lib):
     assert lib.cupc_result_checkpoint(None, None, 0, ctypes.byref(n)) == -1
     out = ctypes.c_void_p()
     assert lib.cupc_skeleton_resume(None, None, 0, 0, 0, 10, 2, 2, 0.01, None, None, 0, ctypes.byref(out)) == -1
+
+
+@pytest.mark.parametrize("cname,pyname", [("cupc_options", "Options"), ("cupc_stats", "Stats"),
+                                          ("cupc_tune_entry", "TuneEntry"), ("cupc_orient_stats", "OrientStats"),
+                                          ("cupc_sshare_stats", "SShareStats")])
+def test_binding_structs_match_the_header(tmp_path, cname, pyname):
+    """The ctypes structures of the binding have the C header's size and field
+    offsets (a field added on one side only would shift every later one)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    cls = getattr(cupc, pyname)
+    names = [f[0] for f in cls._fields_]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "cupc.h"', "int main(void) {",
+             '    printf("%%zu\\n", sizeof(%s));' % cname]
+    lines += ['    printf("%%zu\\n", offsetof(%s, %s));' % (cname, nm) for nm in names]
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = [ctypes.sizeof(cls)] + [getattr(cls, nm).offset for nm in names]
+    assert got == want, (cname, list(zip(["sizeof"] + names, got, want)))
